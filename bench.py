@@ -1,0 +1,342 @@
+"""Benchmark: poses x evaluations per second of the persistent fused sampler on one B300.
+
+One benchmark step = one full sampling pass over the batched-screening workload
+(1,024 seeded ligands, 10-60 heavy atoms, 0-15 rotatable bonds, 128 poses each,
+50 score+gradient evaluations in 8 Monte-Carlo loops, 1,500-atom pocket) followed by
+the top-9 rank+cluster, with every input resident in HBM.  The plain form (one launch
+per ligand and evaluation, same device code) is timed beside it, the FP64 CPU oracle
+on a bounded sample, and an end-to-end pass that packs host ligand arrays, samples,
+ranks and copies the results back.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {trids,reference}]
+Multi-GPU (torchrun): every rank samples its own 1,024-ligand batch (weak scaling);
+no collective touches the data path; the timed region is bracketed by barriers and
+the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2510_24186_b300 import synth  # noqa: E402
+
+METRIC = "poses×steps/sec (score + DOF gradient) at 1 B300 vs plain per-ligand launch"
+UNIT = "pose-steps/s"
+F_PAIR_VINA = 53            # FP32 FLOPs per in-cutoff pair of the Vina-form terms (FMA = 2)
+MUFU_PAIR_VINA = 3          # rsqrt + 2 exp per in-cutoff pair
+FP32_LANES_PER_SM = 128
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("paper_2510_24186_b300/csrc/trids.cu", "paper_2510_24186_b300/csrc/trids_internal.h"):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def sm_max_mhz():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]), "measured"
+    except Exception:
+        pass
+    try:
+        out = subprocess.check_output(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                                      text=True)
+        return float(out.split()[0]), "nvidia-smi"
+    except Exception:
+        return 2032.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock + throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                mhz.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample_rate(w, budget_s=12.0, max_ligs=64, n_threads=None, first=0):
+    """FP64 oracle sampler on whole ligands of the workload until ~budget_s of wall time."""
+    import oracle
+    n_threads = n_threads or cpu_threads()
+    op = oracle.make_params(0, [float(np.float32(x)) for x in synth.TYPE_RADIUS], synth.TYPE_FLAGS,
+                            [float(np.float32(x)) for x in synth.VINA_WEIGHTS], w.cutoff)
+    lo = w.box_center - w.box_size / 2
+    hi = w.box_center + w.box_size / 2
+    cfg = oracle.sample_cfg(steps=w.steps, mc_loops=w.mc_loops, seed=7, box_lo=lo, box_hi=hi)
+    pxyz = w.pocket.xyz.astype(np.float32).astype(np.float64)
+    ptype = w.pocket.type.astype(np.int32)
+    t0 = time.perf_counter()
+    n, units = 0, 0
+    for l in range(first, min(len(w.ligands), first + max_ligs)):
+        lg = w.ligands[l]
+        st, ol = oracle.pack(lg.xyz.astype(np.float32).astype(np.float64), lg.type, lg.bonds, lg.rotatable)
+        oracle.sample_ligand(cfg, op, pxyz, ptype, ol, l, w.poses, n_threads)
+        n += 1
+        units += w.poses * w.steps
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return units / dt, n_threads, n, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    w = synth.workload(2)
+    rates = []
+    for k in range(args.warmup + args.steps):
+        r, cores, n, dt = oracle_sample_rate(w, budget_s=0.0, max_ligs=1, first=k % len(w.ligands))
+        if k >= args.warmup:
+            rates.append(r)
+    value = statistics.mean(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w.poses * w.steps / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n_lig": len(w.ligands), "poses": w.poses, "steps": w.steps,
+                       "pocket_atoms": len(w.pocket.type)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"one ligand x {w.poses} poses x {w.steps} evaluations per step, FP64 "
+                                       "all-pairs oracle on all host threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="trids", choices=["trids", "reference"])
+    ap.add_argument("--per-ligand-steps", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--warps", type=int, default=0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    from paper_2510_24186_b300 import api
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    w = synth.workload(2)
+    sp = api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, w.cutoff)
+    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
+    arrays = synth.concat_ligands(w.ligands)
+    b = api.Batch(pk, *arrays)
+    P, S, Lm = w.poses, w.steps, w.mc_loops
+    n_lig = b.n_lig
+    units = n_lig * P * S
+    lig_base = rank * n_lig
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
+    dof = torch.zeros(n_lig, P, b.dof_stride, device="cuda")
+    state = torch.zeros(b.state_floats(P), device="cuda")
+    energy = torch.empty(n_lig, P, device="cuda")
+
+    def one_step(seed, **kw):
+        o = api.sample(pk, b, P, S, mc_loops=Lm, seed=seed, lig_base=lig_base, dof=dof, state=state, energy=energy,
+                       warps_per_block=args.warps, stream=stream, **kw)
+        return o
+
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            one_step(100 + k)
+            api.topk(b, energy, dof, w.topk, 1.0, stream=stream)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    seeds = [1000 + k for k in range(args.steps)]
+    energies = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(k & 0xff)                       # evict the previous step from L2 (untimed)
+                ev[k][0].record(stream)
+                one_step(seeds[k])
+                ev[k][1].record(stream)
+                idx, etop = api.topk(b, energy, dof, w.topk, 1.0, stream=stream)
+                ev[k][2].record(stream)
+                energies.append(energy.clone())
+        stream.synchronize()
+    if dist:
+        dist.barrier()
+    t_sample = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    t_step = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    total_ms = sum(t_step)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    rc = api.sync(b, P, state, timeout_ms=60000)
+
+    # in-cutoff pair counts of the same trajectories (untimed counting variant; the
+    # energies must come out bit-identical to the timed runs)
+    pairs = []
+    identical = True
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            o = one_step(seeds[k], count_pairs=True)
+            stream.synchronize()
+            pairs.append(int(o["pair_count"].item()))
+            identical &= bool(torch.equal(energy, energies[k]))
+
+    # plain per-ligand form, same device code
+    pl_ms = None
+    if args.per_ligand_steps > 0:
+        with torch.cuda.stream(stream):
+            one_step(7, mode=1)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(args.per_ligand_steps):
+                one_step(8 + k, mode=1)
+            e1.record(stream)
+            stream.synchronize()
+            pl_ms = e0.elapsed_time(e1) / args.per_ligand_steps
+
+    # end to end through the public API: pack host arrays, sample, rank, copy results back
+    e2e_ms = []
+    h2d = d2h = 0
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bb = api.Batch(pk, *arrays)
+        with torch.cuda.stream(stream):
+            o = api.sample(pk, bb, P, S, mc_loops=Lm, seed=5000 + k, lig_base=lig_base, dof=dof, state=state,
+                           energy=energy, stream=stream, warps_per_block=args.warps)
+            idx, etop = api.topk(bb, energy, dof, w.topk, 1.0, stream=stream)
+            idx_h, e_h = idx.cpu(), etop.cpu()
+        stream.synchronize()
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_ms.append(1000 * (t1 - t0))
+        ntor = int(bb.n_tor.sum())
+        h2d = 32 * n_lig + 20 * int(bb.n_atoms.sum()) + 48 * ntor + 4 * int(bb.n_intra)
+        d2h = idx_h.numel() * 4 + e_h.numel() * 4
+        bb.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    value = world * units / (total_ms / 1000.0 / args.steps)
+    mhz, mhz_src = sm_max_mhz()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    flops = [p * F_PAIR_VINA for p in pairs]
+    achieved = sum(flops) / (sum(t_sample) / 1000.0) / 1e12
+    clocks = clk.summary()
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "sample_persistent_vina5_batched_screening.json")
+    if os.path.exists(prof):
+        pj = json.load(open(prof))
+        if pj.get("source_hash") == kernel_source_hash():
+            traffic = pj.get("dram_bytes_per_launch")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n_lig": n_lig, "poses": P, "steps": S, "mc_loops": Lm,
+                   "pocket_atoms": len(w.pocket.type), "top_k": w.topk, "term_set": "vina5",
+                   "graph": True, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"ligand shards x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "note": f"in-cutoff pairs x {F_PAIR_VINA} FP32 FLOP / persistent-sampler time; peak = "
+                             f"{n_sm} SM x 128 lanes x 2 x {mhz:.0f} MHz ({mhz_src})"},
+        "kernel": {"sample_ms": statistics.mean(t_sample), "topk_ms": statistics.mean(
+            [t_step[k] - t_sample[k] for k in range(args.steps)]), "pairs_per_step": statistics.mean(pairs),
+            "pairs_per_pose_step": statistics.mean(pairs) / units, "count_run_bit_identical": identical,
+            "status": rc},
+        "per_ligand": None if pl_ms is None else {
+            "value": units / (pl_ms / 1000.0), "ms_per_step": pl_ms, "launches_per_step": n_lig * S,
+            "speedup_persistent": (pl_ms / (sum(t_sample) / args.steps))},
+        "e2e": {"value": units / (statistics.mean(e2e_ms) / 1000.0), "unit": UNIT, "ms_per_step":
+                statistics.mean(e2e_ms), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "includes": "host pack + upload, sample, top-k, D2H of top-k"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+    }
+    if clocks["sm_mhz"]:
+        line["roofline"]["frac_at_load_clock"] = achieved / (peak * clocks["sm_mhz"] / mhz)
+    if not args.no_cpu and world == 1:
+        r, cores, n, dt = oracle_sample_rate(w, budget_s=12.0)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"first {n} ligands x {P} poses x {S} evaluations, FP64 all-pairs "
+                                          f"oracle, {dt:.1f} s"}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

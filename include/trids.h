@@ -1,0 +1,275 @@
+/*
+ * trids.h -- C-ABI of libtrids: gradient-guided ligand pose sampling on one GPU
+ * (the sampling hot path of TRIDS, arXiv 2510.24186), written for sm_103a.
+ *
+ * The problem, as the paper states it (Sec. 2 "Conformation sampling",
+ * "Scoring functions", Fig. 2): a pocket of receptor atoms and a translation box;
+ * ligands whose degrees of freedom are a translation in [box_min, box_max], a
+ * rotation and the torsion angles of their rotatable bonds; a score that is a
+ * weighted sum of pairwise-distance terms (E_dock, and E_screen = E_dock /
+ * (1 + w_tor N_tor)); many copies per ligand refined by Adam on the score's
+ * gradient inside Metropolis Monte-Carlo loops; the copies then ranked,
+ * clustered and cut to the top N.
+ *
+ * Conventions
+ *  - Every function returns an int status: TRIDS_OK (0) or a negative code.
+ *    trids_last_error() returns a message for the calling thread's last failure.
+ *  - Handles (trids_pocket, trids_batch) are owned by the library and freed with
+ *    trids_free_pocket / trids_free_batch.  Array arguments are owned by the caller.
+ *  - Host pointers are used only by pocket/batch construction and topology
+ *    queries.  The hot calls (trids_score_grad, trids_sample, trids_topk) take
+ *    DEVICE pointers (contiguous float32/int32, on the device that was current
+ *    when the pocket was made) and a cudaStream_t passed as void* (NULL = the
+ *    legacy default stream).  They are asynchronous on that stream: argument
+ *    errors are reported synchronously; per-pose numerical failures are recorded
+ *    in the per-pose status words and returned by trids_sync as TRIDS_ENONFINITE.
+ *  - A batch and a pocket must not be used from two host threads at once.
+ *  - All device arithmetic is float32; counts and indices are int32.
+ */
+#ifndef TRIDS_H
+#define TRIDS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TRIDS_OK 0
+#define TRIDS_EINVAL (-1)     /* bad argument or invalid molecule */
+#define TRIDS_ENOMEM (-2)     /* host or device allocation failed */
+#define TRIDS_ECUDA (-3)      /* a CUDA runtime call failed */
+#define TRIDS_ETIMEOUT (-4)   /* trids_sync gave up waiting */
+#define TRIDS_ENONFINITE (-5) /* a pose produced a non-finite energy */
+
+#define TRIDS_MAX_TYPES 16
+#define TRIDS_MAX_GMM 4
+#define TRIDS_MAX_ATOMS 70    /* heavy atoms per ligand */
+#define TRIDS_MAX_TOR 20      /* rotatable bonds per ligand */
+
+#define TRIDS_TERMS_VINA5 0
+#define TRIDS_TERMS_TRIDS 1
+
+#define TRIDS_MODE_PERSISTENT 0 /* one persistent fused launch (optionally a CUDA graph) */
+#define TRIDS_MODE_PER_LIGAND 1 /* plain form: one launch per (ligand, step) */
+
+/*
+ * Scoring parameters.  Every term depends only on pair distances (Sec. 2
+ * "Scoring functions": "all of these terms are calculated based on pairwise
+ * distances"), so they are the same for ligand-pocket and intra-ligand pairs
+ * except E_MDN, which is ligand-pocket only.  A pair contributes only if its
+ * centre distance r < cutoff.
+ *
+ * term_set TRIDS_TERMS_VINA5 (the analytic terms the DSDP line samples with; the
+ *   paper's E_long is "the second Gaussian term in VINA"): with surface distance
+ *   d = r - R_a - R_b and weights w[0..4]:
+ *     w0 exp(-(d/0.5)^2) + w1 exp(-((d-3)/2)^2) + w2 [d<0] d^2
+ *     + w3 [both hydrophobic] (1 if d<0.5; 1.5-d if d<1.5; else 0)
+ *     + w4 [donor-acceptor] (1 if d<-0.7; -d/0.7 if d<0; else 0).
+ * term_set TRIDS_TERMS_TRIDS (Sec. 2 Eqs. P(d), E_MDN, E_long, E_clash, E_Hbond,
+ *   E_dock; default w = 1.0, 0.2, 10.0, 0.6):
+ *     w0 E_MDN:  -sum_k pi_k exp(-(r-mu_k)^2/(2 sigma_k^2)), r < 5, ligand-pocket only,
+ *                (pi, mu, sigma) = gmm[type_lig][type_pocket][k] (the paper's network
+ *                predicts them; here they are inputs);
+ *     w1 E_long: -exp(-(r - R_a - R_b - 3)^2 / 4), r < 10;
+ *     w2 E_clash: -ln(max(r,0.5)/d_clash), r < d_clash, d_clash = 2.6 for a donor-acceptor
+ *                pair, else R_a + R_b;
+ *     w3 E_Hbond: -exp(-(r-2.88)^2/(2*0.3^2)), donor-acceptor pairs, r < 3.4.
+ * flags[type]: bit0 hydrophobic, bit1 donor, bit2 acceptor.  A donor-acceptor pair
+ * is donor on one side and acceptor on the other, either way round.
+ */
+typedef struct trids_params {
+    int32_t term_set;
+    int32_t n_types;                 /* 1..TRIDS_MAX_TYPES */
+    float w[5];
+    float radius[TRIDS_MAX_TYPES];   /* van der Waals radius per type (A) */
+    uint8_t flags[TRIDS_MAX_TYPES];
+    float cutoff;                    /* pair cutoff on r (A), > 0 */
+    float w_tor;                     /* E_screen weight (0.01 in the paper) */
+    int32_t gmm_k;                   /* kernels per type pair, 0..TRIDS_MAX_GMM */
+    float gmm[TRIDS_MAX_TYPES][TRIDS_MAX_TYPES][TRIDS_MAX_GMM][3]; /* (pi, mu, sigma) */
+} trids_params;
+
+typedef struct trids_pocket trids_pocket;
+typedef struct trids_batch trids_batch;
+
+typedef struct trids_batch_dims {
+    int32_t n_lig;
+    int32_t max_atoms;    /* L_max over the batch */
+    int32_t max_tor;      /* T_max over the batch */
+    int32_t dof_stride;   /* 7 + max_tor: floats per pose row of a DOF array */
+    int32_t state_fields; /* floats per pose of the sampler state buffer */
+    int64_t n_intra;      /* intra-ligand pairs over the batch */
+} trids_batch_dims;
+
+/* Sampler configuration (Sec. 2 "Conformation sampling", Fig. 2). */
+typedef struct trids_sample_cfg {
+    int32_t poses;           /* copies per ligand (1,024 in the paper) */
+    int32_t steps;           /* S: score+gradient evaluations of the whole schedule */
+    int32_t step_begin;      /* run evaluations [step_begin, step_end) of the schedule; */
+    int32_t step_end;        /*   step_begin > 0 resumes from dof + state */
+    int32_t mc_loops;        /* Monte-Carlo loops (8 in the paper) */
+    float lr, beta1, beta2, eps; /* Adam (lr 0.1 in the paper; torch defaults otherwise) */
+    float beta;              /* Metropolis beta (0.069 in the paper) */
+    uint64_t seed;           /* Philox4x32-10 key */
+    int32_t lig_base;        /* random-stream id of ligand 0 of this batch */
+    int32_t mode;            /* TRIDS_MODE_* */
+    int32_t warps_per_block; /* 0 = library default; each warp owns 32 poses of one ligand */
+    int32_t use_graph;       /* persistent mode: capture the launch in a CUDA graph and replay it */
+    float* trace;            /* nullable device buffer, see trids_sample */
+    const int32_t* trace_slot; /* device [n_lig*poses]: trace slot of each pose or -1 */
+    int32_t n_trace;         /* number of trace slots */
+    unsigned long long* pair_count; /* nullable device counter: adds in-cutoff pairs evaluated */
+} trids_sample_cfg;
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* trids_last_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int trids_version(void);
+
+/*
+ * trids_make_pocket -- build the pocket and translation box (Sec. 2: pocket of
+ * receptor atoms near the reference ligand; translation range [box_min, box_max]
+ * with box_min = center - size/2 and box_max = center + size/2).
+ *   xyz   host [n_atoms][3] float32 coordinates (A), type host [n_atoms] int32 in
+ *         [0, prm->n_types); n_atoms in [1, 65535].
+ *   cell  edge (A) of the candidate grid used to cull ligand-pocket pairs; 0 selects
+ *         1.0 A.  The grid changes no result, only which pairs are tested.
+ *   prm   scoring parameters, copied.
+ * The pocket's device arrays live on the current CUDA device.  Errors: TRIDS_EINVAL
+ * (bad sizes, non-finite values, types out of range), TRIDS_ENOMEM, TRIDS_ECUDA.
+ */
+int trids_make_pocket(const float* xyz, const int32_t* type, int32_t n_atoms,
+                      const float box_center[3], const float box_size[3], float cell,
+                      const trids_params* prm, trids_pocket** out);
+
+/* Replace the scoring parameters (weights, radii, flags, GMM).  The cutoff may not
+ * exceed the one the pocket was built with.  Stream-ordered on `stream`. */
+int trids_set_params(trids_pocket* pk, const trids_params* prm, void* stream);
+
+int trids_free_pocket(trids_pocket* pk);
+
+/*
+ * trids_pack_ligands -- validate ligands, build their torsion trees and upload them.
+ * Inputs are host arrays, concatenated over ligands: n_atoms[n_lig]; xyz[sum L][3]
+ * float32 input geometry (theta = 0); type[sum L]; n_bonds[n_lig];
+ * bonds[sum nb][2] ligand-local atom indices; rotatable[sum nb] (0/1).
+ * Degrees of freedom (Sec. 2): translation t, rotation quaternion q = (w,x,y,z),
+ * one torsion angle per rotatable bond.  World coordinates are
+ * x_i = t + R(q/|q|) z_i, z = input geometry about the root-fragment centroid after
+ * the torsions; torsion k turns the subtree on its child side by theta_k about the
+ * bond from its parent atom toward its child atom (right-hand rule).
+ * Tree rules (the paper is silent): fragments = components after cutting rotatable
+ * bonds; root = fragment of minimum tree height (ties: smallest input atom index);
+ * torsions in BFS order from the root, children by smallest input atom index; atoms
+ * renumbered in DFS pre-order of fragments so each moving subtree is contiguous;
+ * intra-ligand pairs = atoms in different fragments and >= 4 bonds apart.
+ * Errors: TRIDS_EINVAL for L outside [1, 70], more than 20 rotatable bonds, a
+ * disconnected ligand, a rotatable bond inside a ring, duplicate or self bonds,
+ * non-finite coordinates or types out of range (the message names the ligand).
+ */
+int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_atoms,
+                       const float* xyz, const int32_t* type, const int32_t* n_bonds,
+                       const int32_t* bonds, const uint8_t* rotatable, trids_batch** out);
+
+int trids_free_batch(trids_batch* b);
+
+int trids_batch_info(const trids_batch* b, trids_batch_dims* dims);
+
+/*
+ * Per-ligand sizes (host arrays, nullable): n_tor[n_lig], n_atoms[n_lig].  If topo is
+ * non-null, the packed topology of ligand `lig` is written as int32
+ * [L, T, n_pairs, perm[L] (packed -> input index), frag[L] (0 root, k+1 = moving
+ * fragment of torsion k), T x (parent atom, child atom, parent torsion or -1,
+ * subtree begin, subtree end), n_pairs x (i, j)] in packed indices; returns
+ * TRIDS_EINVAL if topo_cap is too small.
+ */
+int trids_batch_query(const trids_batch* b, int32_t* n_tor, int32_t* n_atoms,
+                      int32_t lig, int32_t* topo, int32_t topo_cap);
+
+/* Host-only packing of one ligand (same rules and layout as trids_batch_query);
+ * needs no GPU.  *topo_len receives the number of int32 written. */
+int trids_pack_topology(int32_t n_atoms, const float* xyz, const int32_t* type, int32_t n_types,
+                        int32_t n_bonds, const int32_t* bonds, const uint8_t* rotatable,
+                        int32_t* topo, int32_t topo_cap, int32_t* topo_len);
+
+/*
+ * trids_score_grad -- score and analytic gradient of given poses (Sec. 2: the score
+ * is differentiable in the ligand coordinates; Sec. 4 item 3: manual differentiation
+ * of the Gaussian terms and of the DOF-to-coordinate map).  Kinematics are
+ * recomputed, nothing per atom is stored between calls.
+ *   dof      device [n_lig][poses][dof_stride]: t(3), q(4), theta(T), padding ignored.
+ *   energy   device [n_lig][poses] out: E_total = ligand-pocket + intra-ligand.
+ *   e_inter  nullable device [n_lig][poses] out: the ligand-pocket part.
+ *   g_dof    nullable device, layout of dof, out: dE/dt, dE/dq (gradient of E(q/|q|)),
+ *            dE/dtheta; padding written 0.
+ *   g_xyz    nullable device [n_lig][poses][max_atoms][3] out: dE/dx_i of world
+ *            coordinates in INPUT atom order, rows past L zero.
+ *   e_bar    nullable device [n_lig][poses]: upstream weights; when given, g_dof and
+ *            g_xyz are multiplied by e_bar and g_w, g_radius are sum e_bar dE/d(.)
+ *            (the backward of a sum-reduced autograd node).
+ *   g_w      nullable device [5] out: dE/dw_t summed over all poses.
+ *   g_radius nullable device [n_types] out: dE/dR_a summed over all poses.
+ * Parameter sums are reduced in a fixed order (bit-reproducible run to run).
+ */
+int trids_score_grad(const trids_pocket* pk, const trids_batch* b, int32_t poses,
+                     const float* dof, float* energy, float* e_inter, float* g_dof,
+                     float* g_xyz, const float* e_bar, float* g_w, float* g_radius,
+                     void* stream);
+
+/* Floats of sampler state per batch: n_lig * poses * dims.state_fields. */
+int64_t trids_state_floats(const trids_batch* b, int32_t poses);
+
+/*
+ * trids_sample -- Metropolis Monte Carlo with Adam refinement (Sec. 2, Fig. 2).
+ *   Each pose starts from random DOFs (t uniform in the box, q uniform on SO(3) by
+ *   Shoemake's method, theta uniform in [-pi, pi)).  Loop l (of mc_loops) gets
+ *   floor(S/mc_loops) evaluations, one more for the first S mod mc_loops loops.  At
+ *   the start of every loop after the first, one of the 6+T scalar variables, drawn
+ *   uniformly, is resampled in its range (t_c in the box; a rotation by U[-pi,pi)
+ *   about world axis c; theta_k in [-pi,pi)) and the Adam moments are reset.  Every
+ *   evaluation but the last of a loop is followed by an Adam step (lr, beta1, beta2,
+ *   eps; PyTorch form) on t, the world rotation vector (q <- exp(dw/2) (x) q) and
+ *   theta; t is clamped to the box and theta wrapped to [-pi, pi).  The last
+ *   evaluation of a loop gives its energy; the loop is accepted if
+ *   u < exp(-beta (E_new - E_old)), else the state from before its perturbation is
+ *   restored.  Random numbers: Philox4x32-10, key = seed, counter = (pose, lig_base +
+ *   ligand, loop<<16 | purpose<<8 | block, 0), purpose 0 init, 1 perturbation,
+ *   2 acceptance; uniform = (word >> 8) * 2^-24.
+ *   dof     device [n_lig][poses][dof_stride], out (in as well when step_begin > 0).
+ *   state   device [trids_state_floats] scratch: Adam moments, saved state, loop
+ *           energies, per-pose status.  Keep it between calls to resume.
+ *   energy  device [n_lig][poses] out: energy of the returned state (valid once
+ *           step_end reaches a loop end).
+ *   trace   if non-null, each traced pose writes one record per evaluation at
+ *           trace[((s - step_begin) * n_trace + slot) * (2*max_tor + 14)]:
+ *           state before the evaluation (dof_stride floats), E, dE/dt (3), world
+ *           torque (3), dE/dtheta (max_tor).
+ * A pose whose energy is not finite is frozen and flagged; trids_sync reports it.
+ */
+int trids_sample(const trids_pocket* pk, const trids_batch* b, const trids_sample_cfg* cfg,
+                 float* dof, float* state, float* energy, void* stream);
+
+/*
+ * trids_topk -- rank and cluster (Sec. 2, end of "Conformation sampling"): per ligand,
+ * poses ordered by (energy ascending, pose index ascending); a pose is skipped when
+ * its heavy-atom RMSD (no symmetry) to an already kept pose is below rmsd (0 disables);
+ * the first k kept are written.  Non-finite energies are never kept.
+ *   idx device [n_lig][k] int32 out (pose index or -1), e_out nullable [n_lig][k].
+ */
+int trids_topk(const trids_batch* b, int32_t poses, const float* energy, const float* dof,
+               int32_t k, float rmsd, int32_t* idx, float* e_out, void* stream);
+
+/*
+ * Wait for `stream` (polling, at most timeout_ms; <= 0 waits without limit), then
+ * check the per-pose status words of `state` (nullable): TRIDS_OK, TRIDS_ETIMEOUT,
+ * TRIDS_ECUDA or TRIDS_ENONFINITE.
+ */
+int trids_sync(const trids_batch* b, int32_t poses, const float* state, void* stream,
+               double timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRIDS_H */

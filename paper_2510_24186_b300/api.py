@@ -1,0 +1,264 @@
+"""Python API over libtrids: pockets, ligand batches and the hot calls on torch CUDA tensors.
+
+PyTorch supplies device memory and streams; every step of the path runs in libtrids'
+kernels.  There is no CPU fallback: the calls raise if CUDA or the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+
+def _require_cuda():
+    if not torch.cuda.is_available():
+        raise RuntimeError("libtrids needs a CUDA device; there is no CPU path")
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclasses.dataclass
+class ScoreParams:
+    """Scoring parameters (include/trids.h, trids_params)."""
+    term_set: int = _lib.TERMS_VINA5
+    radius: Sequence[float] = ()
+    flags: Sequence[int] = ()
+    w: Sequence[float] = (-0.0356, -0.00516, 0.840, -0.0351, -0.587)
+    cutoff: float = 8.0
+    w_tor: float = 0.01
+    gmm: Optional[np.ndarray] = None     # [n_types, n_types, K, 3] (pi, mu, sigma)
+
+    def to_c(self) -> _lib.Params:
+        p = _lib.Params()
+        p.term_set = int(self.term_set)
+        p.n_types = len(self.radius)
+        for i, r in enumerate(self.radius):
+            p.radius[i] = float(r)
+        for i, f in enumerate(self.flags):
+            p.flags[i] = int(f)
+        for i, x in enumerate(self.w):
+            p.w[i] = float(x)
+        p.cutoff = float(self.cutoff)
+        p.w_tor = float(self.w_tor)
+        if self.gmm is not None:
+            g = np.asarray(self.gmm, dtype=np.float32)
+            n, K = g.shape[0], g.shape[2]
+            p.gmm_k = K
+            full = np.zeros((_lib.MAX_TYPES, _lib.MAX_TYPES, _lib.MAX_GMM, 3), dtype=np.float32)
+            full[:n, :n, :K] = g
+            C.memmove(p.gmm, full.ctypes.data, full.nbytes)
+        return p
+
+
+class Pocket:
+    """Receptor pocket atoms, translation box and scoring parameters (trids_make_pocket)."""
+
+    def __init__(self, xyz, types, box_center, box_size, params: ScoreParams, cell: float = 0.0):
+        _require_cuda()
+        L = _lib.lib()
+        xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+        types = np.ascontiguousarray(types, dtype=np.int32)
+        self.params = params
+        self.n_atoms = len(types)
+        self.box_center = np.asarray(box_center, dtype=np.float32)
+        self.box_size = np.asarray(box_size, dtype=np.float32)
+        h = C.c_void_p()
+        bc = (C.c_float * 3)(*self.box_center.tolist())
+        bs = (C.c_float * 3)(*self.box_size.tolist())
+        cp = params.to_c()
+        check(L.trids_make_pocket(xyz.ctypes.data, types.ctypes.data, len(types), C.byref(bc), C.byref(bs),
+                                  float(cell), C.byref(cp), C.byref(h)))
+        self.handle = h
+
+    def set_params(self, params: ScoreParams, stream=None):
+        cp = params.to_c()
+        check(_lib.lib().trids_set_params(self.handle, C.byref(cp), _stream(stream)))
+        self.params = params
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.lib().trids_free_pocket(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Packed ligands (trids_pack_ligands).  Arrays as in include/trids.h."""
+
+    def __init__(self, pocket: Pocket, n_atoms, xyz, types, n_bonds, bonds, rotatable):
+        L = _lib.lib()
+        n_atoms = np.ascontiguousarray(n_atoms, dtype=np.int32)
+        xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+        types = np.ascontiguousarray(types, dtype=np.int32)
+        n_bonds = np.ascontiguousarray(n_bonds, dtype=np.int32)
+        bonds = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
+        rotatable = np.ascontiguousarray(rotatable, dtype=np.uint8)
+        h = C.c_void_p()
+        check(L.trids_pack_ligands(pocket.handle, len(n_atoms), n_atoms.ctypes.data, xyz.ctypes.data,
+                                   types.ctypes.data, n_bonds.ctypes.data,
+                                   bonds.ctypes.data if len(bonds) else None,
+                                   rotatable.ctypes.data if len(rotatable) else None, C.byref(h)))
+        self.handle = h
+        self.pocket = pocket
+        d = _lib.BatchDims()
+        check(L.trids_batch_info(h, C.byref(d)))
+        self.n_lig, self.max_atoms, self.max_tor = d.n_lig, d.max_atoms, d.max_tor
+        self.dof_stride, self.state_fields, self.n_intra = d.dof_stride, d.state_fields, d.n_intra
+        self.n_tor = np.zeros(self.n_lig, dtype=np.int32)
+        self.n_atoms = np.zeros(self.n_lig, dtype=np.int32)
+        check(L.trids_batch_query(h, self.n_tor.ctypes.data, self.n_atoms.ctypes.data, 0, None, 0))
+
+    @classmethod
+    def from_ligands(cls, pocket: Pocket, ligands):
+        from .synth import concat_ligands
+        return cls(pocket, *concat_ligands(ligands))
+
+    def topology(self, lig: int) -> np.ndarray:
+        cap = 3 + 2 * _lib.MAX_ATOMS + 5 * _lib.MAX_TOR + _lib.MAX_ATOMS * (_lib.MAX_ATOMS - 1)
+        out = np.zeros(cap, dtype=np.int32)
+        check(_lib.lib().trids_batch_query(self.handle, None, None, lig, out.ctypes.data, cap))
+        L, T, P = out[0], out[1], out[2]
+        return out[:3 + 2 * L + 5 * T + 2 * P].copy()
+
+    def state_floats(self, poses: int) -> int:
+        return int(_lib.lib().trids_state_floats(self.handle, poses))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.lib().trids_free_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_topology(xyz, types, bonds, rotatable, n_types=8) -> np.ndarray:
+    """Host-only packing of one ligand (no GPU): flat topology as in trids_batch_query."""
+    L = _lib.lib()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+    types = np.ascontiguousarray(types, dtype=np.int32)
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
+    rot = np.ascontiguousarray(rotatable, dtype=np.uint8)
+    cap = 3 + 2 * _lib.MAX_ATOMS + 5 * _lib.MAX_TOR + _lib.MAX_ATOMS * (_lib.MAX_ATOMS - 1)
+    out = np.zeros(cap, dtype=np.int32)
+    n = C.c_int32()
+    check(L.trids_pack_topology(len(types), xyz.ctypes.data, types.ctypes.data, n_types, len(bonds),
+                                bonds.ctypes.data if len(bonds) else None,
+                                rot.ctypes.data if len(rot) else None, out.ctypes.data, cap, C.byref(n)))
+    return out[:n.value].copy()
+
+
+def _check_dev(t: torch.Tensor, name: str, dtype=torch.float32):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor")
+
+
+def score_grad(pocket: Pocket, batch: Batch, dof: torch.Tensor, grad: bool = True, xyz_grad: bool = False,
+               e_bar: Optional[torch.Tensor] = None, param_grad: bool = False, stream=None) -> dict:
+    """Energies and analytic gradients of poses dof [n_lig, P, dof_stride] (trids_score_grad)."""
+    _require_cuda()
+    _check_dev(dof, "dof")
+    n_lig, P, D = dof.shape
+    if n_lig != batch.n_lig or D != batch.dof_stride:
+        raise ValueError("dof must have shape [n_lig, poses, dof_stride]")
+    dev = dof.device
+    out = {"energy": torch.empty(n_lig, P, device=dev), "e_inter": torch.empty(n_lig, P, device=dev)}
+    if grad:
+        out["g_dof"] = torch.empty_like(dof)
+    if xyz_grad:
+        out["g_xyz"] = torch.empty(n_lig, P, batch.max_atoms, 3, device=dev)
+    if param_grad:
+        out["g_w"] = torch.empty(5, device=dev)
+        out["g_radius"] = torch.empty(len(pocket.params.radius), device=dev)
+    if e_bar is not None:
+        _check_dev(e_bar, "e_bar")
+    check(_lib.lib().trids_score_grad(pocket.handle, batch.handle, P, _ptr(dof), _ptr(out["energy"]),
+                                      _ptr(out["e_inter"]), _ptr(out.get("g_dof")), _ptr(out.get("g_xyz")),
+                                      _ptr(e_bar), _ptr(out.get("g_w")), _ptr(out.get("g_radius")),
+                                      _stream(stream)))
+    return out
+
+
+def sample(pocket: Pocket, batch: Batch, poses: int, steps: int, mc_loops: int = 8, lr: float = 0.1,
+           beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, beta: float = 0.069, seed: int = 0,
+           lig_base: int = 0, mode: int = _lib.MODE_PERSISTENT, warps_per_block: int = 0, use_graph: bool = True,
+           trace_poses: Optional[Sequence[int]] = None, count_pairs: bool = False,
+           dof: Optional[torch.Tensor] = None, state: Optional[torch.Tensor] = None,
+           energy: Optional[torch.Tensor] = None, step_begin: int = 0, step_end: Optional[int] = None,
+           stream=None) -> dict:
+    """Monte-Carlo + Adam sampling of every ligand's poses (trids_sample)."""
+    _require_cuda()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n_lig, D = batch.n_lig, batch.dof_stride
+    if dof is None:
+        dof = torch.zeros(n_lig, poses, D, device=dev)
+    if state is None:
+        state = torch.zeros(batch.state_floats(poses), device=dev)
+    if energy is None:
+        energy = torch.empty(n_lig, poses, device=dev)
+    for t, n in ((dof, "dof"), (state, "state"), (energy, "energy")):
+        _check_dev(t, n)
+    step_end = steps if step_end is None else step_end
+    cfg = _lib.SampleCfg()
+    cfg.poses, cfg.steps, cfg.step_begin, cfg.step_end, cfg.mc_loops = poses, steps, step_begin, step_end, mc_loops
+    cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, cfg.beta = lr, beta1, beta2, eps, beta
+    cfg.seed, cfg.lig_base, cfg.mode = seed, lig_base, mode
+    cfg.warps_per_block, cfg.use_graph = warps_per_block, int(use_graph)
+    out = {"dof": dof, "state": state, "energy": energy}
+    if trace_poses is not None:
+        tp = np.asarray(trace_poses, dtype=np.int64)
+        slot = torch.full((n_lig * poses,), -1, dtype=torch.int32)
+        slot[torch.as_tensor(tp)] = torch.arange(len(tp), dtype=torch.int32)
+        slot = slot.to(dev)
+        rec = 2 * batch.max_tor + 14
+        trace = torch.full(((step_end - step_begin), len(tp), rec), float("nan"), device=dev)
+        cfg.trace, cfg.trace_slot, cfg.n_trace = trace.data_ptr(), slot.data_ptr(), len(tp)
+        out["trace"], out["trace_slot"] = trace, slot
+    if count_pairs:
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        cfg.pair_count = cnt.data_ptr()
+        out["pair_count"] = cnt
+    check(_lib.lib().trids_sample(pocket.handle, batch.handle, C.byref(cfg), _ptr(dof), _ptr(state),
+                                  _ptr(energy), _stream(stream)))
+    return out
+
+
+def topk(batch: Batch, energy: torch.Tensor, dof: torch.Tensor, k: int, rmsd: float = 1.0, stream=None):
+    """Rank + cluster + cut (trids_topk).  Returns (idx [n_lig, k] int32, energies [n_lig, k])."""
+    _require_cuda()
+    _check_dev(energy, "energy")
+    _check_dev(dof, "dof")
+    n_lig, P = energy.shape
+    idx = torch.empty(n_lig, k, dtype=torch.int32, device=energy.device)
+    e = torch.empty(n_lig, k, device=energy.device)
+    check(_lib.lib().trids_topk(batch.handle, P, _ptr(energy), _ptr(dof), k, float(rmsd), _ptr(idx), _ptr(e),
+                                _stream(stream)))
+    return idx, e
+
+
+def sync(batch: Batch, poses: int, state: Optional[torch.Tensor] = None, timeout_ms: float = 0.0, stream=None) -> int:
+    """Wait for the stream (bounded) and check per-pose status words (trids_sync).  Returns the code."""
+    return _lib.lib().trids_sync(batch.handle, poses, _ptr(state), _stream(stream), float(timeout_ms))

@@ -1,0 +1,266 @@
+// Host-side ligand packing: torsion tree, packed atom order, intra-ligand pair list.
+//
+// The paper fixes the degrees of freedom (Sec. 2 "Conformation sampling":
+// translation, rotation, torsion angles of rotatable bonds) and counts N_tor
+// (Eq. E_screen) but not the tree layout.  Rules used (also stated in trids.h):
+// fragments are the components left after cutting rotatable bonds; the root is
+// the fragment of minimum height in the fragment tree (ties: smallest input atom
+// index); torsions are numbered in BFS order from the root with children ordered
+// by their smallest input atom index; atoms are laid out in DFS pre-order of
+// fragments (same child order, ascending input index inside a fragment) so each
+// torsion's moving subtree is one contiguous index range; intra-ligand pairs are
+// atoms in different fragments at least 4 bonds apart.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <functional>
+#include <numeric>
+#include <queue>
+
+#include "trids_internal.h"
+
+namespace trids {
+
+namespace {
+
+struct DisjointSets {
+    std::vector<int> up;
+    explicit DisjointSets(int n) : up(n) { std::iota(up.begin(), up.end(), 0); }
+    int find(int a) {
+        while (up[a] != a) a = up[a] = up[up[a]];
+        return a;
+    }
+    void join(int a, int b) { up[find(a)] = find(b); }
+};
+
+std::string fmt(const char* f, int a, int b = 0) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, f, a, b);
+    return buf;
+}
+
+}  // namespace
+
+std::string pack_ligand(int n, const float* xyz, const int32_t* type, int n_types, int nb,
+                        const int32_t* bonds, const uint8_t* rot, PackedLigand* out) {
+    if (n < 1 || n > kLmax) return fmt("ligand has %d atoms (allowed 1..%d)", n, kLmax);
+    if (nb < 0) return "negative bond count";
+    for (int i = 0; i < n; ++i) {
+        if (type[i] < 0 || type[i] >= n_types) return fmt("atom %d has type %d out of range", i, type[i]);
+        if (!std::isfinite(xyz[3 * i]) || !std::isfinite(xyz[3 * i + 1]) || !std::isfinite(xyz[3 * i + 2]))
+            return fmt("atom %d has a non-finite coordinate", i);
+    }
+    // bond matrix: 0 none, 1 rigid, 2 rotatable
+    std::vector<uint8_t> bm(n * n, 0);
+    int n_rot = 0;
+    for (int b = 0; b < nb; ++b) {
+        int a0 = bonds[2 * b], a1 = bonds[2 * b + 1];
+        if (a0 < 0 || a1 < 0 || a0 >= n || a1 >= n) return fmt("bond %d has an atom index out of range", b);
+        if (a0 == a1) return fmt("bond %d joins atom %d to itself", b, a0);
+        if (bm[a0 * n + a1]) return fmt("bond %d duplicates an earlier bond", b);
+        uint8_t kind = rot[b] ? 2 : 1;
+        bm[a0 * n + a1] = bm[a1 * n + a0] = kind;
+        n_rot += rot[b] ? 1 : 0;
+    }
+    if (n_rot > kTmax) return fmt("%d rotatable bonds (at most %d)", n_rot, kTmax);
+
+    // bond distances: breadth-first search from every atom over adjacency lists
+    const int INF = 1 << 20;
+    std::vector<std::vector<int>> adj(n);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (bm[i * n + j]) adj[i].push_back(j);
+    std::vector<int> D(n * n, INF);
+    std::vector<int> frontier;
+    frontier.reserve(n);
+    for (int s = 0; s < n; ++s) {
+        int* row = &D[s * n];
+        row[s] = 0;
+        frontier.assign(1, s);
+        for (size_t h = 0; h < frontier.size(); ++h) {
+            const int u = frontier[h];
+            for (int v : adj[u])
+                if (row[v] == INF) { row[v] = row[u] + 1; frontier.push_back(v); }
+        }
+    }
+    for (int i = 1; i < n; ++i)
+        if (D[i] >= INF) return fmt("atom %d is not connected to atom 0", i);
+
+    // fragments: union over rigid bonds, numbered by their smallest atom index
+    DisjointSets ds(n);
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            if (bm[i * n + j] == 1) ds.join(i, j);
+    std::vector<int> rep_to_frag(n, -1), fragof(n);
+    int nf = 0;
+    for (int i = 0; i < n; ++i) {   // ascending i: first atom seen is the fragment minimum
+        int r = ds.find(i);
+        if (rep_to_frag[r] < 0) rep_to_frag[r] = nf++;
+        fragof[i] = rep_to_frag[r];
+    }
+    if (n_rot != nf - 1) return "a rotatable bond lies in a ring (the fragments do not form a tree)";
+    // fragment tree edges with the bond atoms on each side
+    std::vector<std::vector<std::pair<int, int>>> nbr(nf);  // (other fragment, my atom)
+    std::vector<std::vector<int>> other_atom(nf, std::vector<int>(nf, -1));
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (bm[i * n + j] == 2) {
+                int fi = fragof[i], fj = fragof[j];
+                if (fi == fj) return "a rotatable bond lies inside a rigid fragment (ring)";
+                if (other_atom[fi][fj] >= 0 && other_atom[fi][fj] != i)
+                    return "two rotatable bonds join the same pair of fragments (ring)";
+                if (other_atom[fi][fj] < 0) nbr[fi].push_back({fj, i});
+                other_atom[fi][fj] = i;
+            }
+    for (auto& v : nbr) std::sort(v.begin(), v.end());
+
+    // root: smallest height (eccentricity in the fragment tree), ties by fragment number
+    auto height = [&](int s) {
+        std::vector<int> d(nf, -1);
+        std::queue<int> q;
+        d[s] = 0;
+        q.push(s);
+        int h = 0;
+        while (!q.empty()) {
+            int u = q.front();
+            q.pop();
+            h = std::max(h, d[u]);
+            for (auto& e : nbr[u])
+                if (d[e.first] < 0) { d[e.first] = d[u] + 1; q.push(e.first); }
+        }
+        return h;
+    };
+    int root = 0, best = INF;
+    for (int f = 0; f < nf; ++f) {
+        int h = height(f);
+        if (h < best) { best = h; root = f; }
+    }
+    // BFS: torsion numbers and parents
+    std::vector<int> parent(nf, -2), tor_of(nf, -1), bfs;
+    parent[root] = -1;
+    bfs.push_back(root);
+    for (size_t h = 0; h < bfs.size(); ++h) {
+        int u = bfs[h];
+        for (auto& e : nbr[u])
+            if (parent[e.first] == -2) {
+                parent[e.first] = u;
+                tor_of[e.first] = (int)bfs.size() - 1;
+                bfs.push_back(e.first);
+            }
+    }
+    // DFS pre-order layout and subtree atom counts
+    std::vector<int> first(nf), count(nf, 0), sub(nf, 0);
+    for (int i = 0; i < n; ++i) count[fragof[i]]++;
+    out->perm.clear();
+    std::function<void(int)> dfs = [&](int u) {
+        first[u] = (int)out->perm.size();
+        for (int i = 0; i < n; ++i)
+            if (fragof[i] == u) out->perm.push_back(i);
+        sub[u] = count[u];
+        for (auto& e : nbr[u])
+            if (parent[e.first] == u) {
+                dfs(e.first);
+                sub[u] += sub[e.first];
+            }
+    };
+    dfs(root);
+    std::vector<int> packed_of(n);
+    for (int k = 0; k < n; ++k) packed_of[out->perm[k]] = k;
+
+    int T = nf - 1;
+    out->n_atoms = n;
+    out->n_tor = T;
+    out->frag.assign(n, 0);
+    for (int k = 0; k < n; ++k) {
+        int f = fragof[out->perm[k]];
+        out->frag[k] = (f == root) ? 0 : tor_of[f] + 1;
+    }
+    out->tp.assign(T, 0); out->th.assign(T, 0); out->tpar.assign(T, -1);
+    out->sb.assign(T, 0); out->se.assign(T, 0);
+    for (int f = 0; f < nf; ++f) {
+        if (f == root) continue;
+        int k = tor_of[f], p = parent[f];
+        out->tp[k] = packed_of[other_atom[p][f]];
+        out->th[k] = packed_of[other_atom[f][p]];
+        out->tpar[k] = (p == root) ? -1 : tor_of[p];
+        out->sb[k] = first[f];
+        out->se[k] = first[f] + sub[f];
+    }
+    double s[3] = {0, 0, 0};
+    int cnt = 0;
+    for (int i = 0; i < n; ++i)
+        if (fragof[i] == root) {
+            for (int d = 0; d < 3; ++d) s[d] += (double)xyz[3 * i + d];
+            ++cnt;
+        }
+    for (int d = 0; d < 3; ++d) out->c[d] = s[d] / cnt;
+    out->pairs.clear();
+    for (int a = 0; a < n; ++a)
+        for (int b = a + 1; b < n; ++b)
+            if (out->frag[a] != out->frag[b] && D[out->perm[a] * n + out->perm[b]] >= 4)
+                out->pairs.push_back({a, b});
+    return "";
+}
+
+void topology_ints(const PackedLigand& lg, std::vector<int32_t>* o) {
+    o->clear();
+    o->push_back(lg.n_atoms);
+    o->push_back(lg.n_tor);
+    o->push_back((int)lg.pairs.size());
+    o->insert(o->end(), lg.perm.begin(), lg.perm.end());
+    o->insert(o->end(), lg.frag.begin(), lg.frag.end());
+    for (int k = 0; k < lg.n_tor; ++k) {
+        o->push_back(lg.tp[k]); o->push_back(lg.th[k]); o->push_back(lg.tpar[k]);
+        o->push_back(lg.sb[k]); o->push_back(lg.se[k]);
+    }
+    for (auto& p : lg.pairs) { o->push_back(p.first); o->push_back(p.second); }
+}
+
+// ---------------------------------------------------------------- candidate grid
+void build_grid(int M, const float* xyz, float cutoff, float h, CandidateGrid* g) {
+    double lo[3] = {1e30, 1e30, 1e30}, hi[3] = {-1e30, -1e30, -1e30};
+    for (int j = 0; j < M; ++j)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], (double)xyz[3 * j + d]);
+            hi[d] = std::max(hi[d], (double)xyz[3 * j + d]);
+        }
+    for (int d = 0; d < 3; ++d) {
+        double a = lo[d] - cutoff - h, b = hi[d] + cutoff + h;
+        g->lo[d] = (float)a;
+        g->dims[d] = (int)std::ceil((b - (double)g->lo[d]) / h);
+    }
+    g->h = h;
+    const int nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
+    const size_t ncell = (size_t)nx * ny * nz;
+    // a point in a cell is within h*sqrt(3)/2 of its centre; the margin covers float rounding
+    const double reach = cutoff + 0.5 * std::sqrt(3.0) * h + 1e-3 * h + 1e-4;
+    const double reach2 = reach * reach;
+    const int span = (int)std::ceil(reach / h) + 1;
+    std::vector<std::vector<uint16_t>> lists(ncell);
+    for (int j = 0; j < M; ++j) {
+        double p[3] = {xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2]};
+        int c[3];
+        for (int d = 0; d < 3; ++d) c[d] = (int)std::floor((p[d] - g->lo[d]) / h);
+        for (int iz = std::max(0, c[2] - span); iz <= std::min(nz - 1, c[2] + span); ++iz)
+            for (int iy = std::max(0, c[1] - span); iy <= std::min(ny - 1, c[1] + span); ++iy)
+                for (int ix = std::max(0, c[0] - span); ix <= std::min(nx - 1, c[0] + span); ++ix) {
+                    double cx = g->lo[0] + (ix + 0.5) * h - p[0];
+                    double cy = g->lo[1] + (iy + 0.5) * h - p[1];
+                    double cz = g->lo[2] + (iz + 0.5) * h - p[2];
+                    if (cx * cx + cy * cy + cz * cz <= reach2)
+                        lists[((size_t)iz * ny + iy) * nx + ix].push_back((uint16_t)j);
+                }
+    }
+    g->start.assign(ncell + 1, 0);
+    size_t total = 0;
+    for (size_t c = 0; c < ncell; ++c) {
+        g->start[c] = (uint32_t)total;
+        total += (lists[c].size() + 7) / 8 * 8;
+    }
+    g->start[ncell] = (uint32_t)total;
+    g->cand.assign(total, (uint16_t)M);
+    for (size_t c = 0; c < ncell; ++c)
+        std::copy(lists[c].begin(), lists[c].end(), g->cand.begin() + g->start[c]);
+}
+
+}  // namespace trids

@@ -1,0 +1,1616 @@
+// libtrids: device code and C-ABI entry points for gradient-guided pose sampling
+// (TRIDS, arXiv 2510.24186, Sec. 2 "Scoring functions" and "Conformation sampling",
+// Sec. 4 items 1-4) on sm_103a.
+//
+// Thread mapping: one thread per pose.  A warp owns 32 poses of ONE ligand, so all
+// lanes run the same topology (forward kinematics, intra-ligand pair list, adjoint
+// and update loops are uniform across the warp) and only the ligand-pocket pair loop
+// diverges.  Per-warp shared memory holds the poses' coordinates and forces as
+// [component][atom][lane] (conflict-free); every block stages the scoring tables and
+// the pocket (float4 per atom) into shared memory with one bulk asynchronous copy.
+// Ligand-pocket pairs are culled by a precomputed candidate grid (each cell lists the
+// pocket atoms that can lie within the cutoff of any point of the cell).  Every sum
+// runs in a fixed order inside one thread, so results are bit-reproducible and the
+// persistent and per-launch forms agree bit for bit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "trids_internal.h"
+
+using namespace trids;
+
+// =============================================================== error handling
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const char* f, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, f);
+    std::vsnprintf(buf, sizeof buf, f, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+}  // namespace
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(TRIDS_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+// =============================================================== device helpers
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kTwoPi = 6.28318530717958647692f;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    // Salmon et al., SC'11: ten rounds of two 32x32->64 products, key bumped by the
+    // Weyl constants between rounds.
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Block `blk` of the random stream (seed, ligand, pose, loop, purpose).
+__device__ __forceinline__ uint4 rand_block(uint64_t seed, uint32_t lig, uint32_t pose, uint32_t loop,
+                                            uint32_t purpose, uint32_t blk) {
+    return philox4x32_10(make_uint4(pose, lig, (loop << 16) | (purpose << 8) | blk, 0u),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+__device__ __forceinline__ float u01(uint32_t w) { return (float)(w >> 8) * (1.0f / 16777216.0f); }
+
+__device__ __forceinline__ uint32_t pick(uint4 v, int i) {
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// quaternion (w,x,y,z) -> rotation matrix of q/|q|
+__device__ __forceinline__ void quat_to_mat(const float q[4], float R[9]) {
+    float n = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    float w = q[0] * n, x = q[1] * n, y = q[2] * n, z = q[3] * n;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// q <- normalize(r (x) q)
+__device__ __forceinline__ void quat_premul(const float r[4], float q[4]) {
+    float o0 = r[0] * q[0] - r[1] * q[1] - r[2] * q[2] - r[3] * q[3];
+    float o1 = r[0] * q[1] + q[0] * r[1] + r[2] * q[3] - r[3] * q[2];
+    float o2 = r[0] * q[2] + q[0] * r[2] + r[3] * q[1] - r[1] * q[3];
+    float o3 = r[0] * q[3] + q[0] * r[3] + r[1] * q[2] - r[2] * q[1];
+    float n = rsqrtf(o0 * o0 + o1 * o1 + o2 * o2 + o3 * o3);
+    q[0] = o0 * n; q[1] = o1 * n; q[2] = o2 * n; q[3] = o3 * n;
+}
+
+__device__ __forceinline__ float wrap_pi(float a) { return a - kTwoPi * floorf((a + kPi) * (1.0f / kTwoPi)); }
+
+// ------------------------------------------------------------------ pair terms
+// Vina form on the surface distance d = r - R_a - R_b (see trids.h).  Returns the
+// weighted energy; fr = (dE/dr)/r.  With TERMS, et[t] gets the unweighted term values
+// and dRs = dE/d(R_a + R_b).
+template <bool TERMS>
+__device__ __forceinline__ float pair_vina(float r2, float rsum, int pf, const float* __restrict__ w,
+                                           float& fr, float* et, float& dRs) {
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float d = r - rsum;
+    const float g1 = __expf(-4.f * d * d);
+    const float b = fmaf(0.5f, d, -1.5f);
+    const float g2 = __expf(-b * b);
+    const float dn = fminf(d, 0.f);
+    float hy = 0.f, dhy = 0.f, hb = 0.f, dhb = 0.f;
+    if (pf & 1) {
+        hy = d < 0.5f ? 1.f : (d < 1.5f ? 1.5f - d : 0.f);
+        dhy = (d >= 0.5f && d < 1.5f) ? -1.f : 0.f;
+    }
+    if (pf & 2) {
+        hb = d < -0.7f ? 1.f : (d < 0.f ? d * (-1.f / 0.7f) : 0.f);
+        dhb = (d >= -0.7f && d < 0.f) ? (-1.f / 0.7f) : 0.f;
+    }
+    float e = w[0] * g1;
+    e = fmaf(w[1], g2, e);
+    e = fmaf(w[2], dn * dn, e);
+    e = fmaf(w[3], hy, e);
+    e = fmaf(w[4], hb, e);
+    float dd = w[0] * (-8.f * d * g1);
+    dd = fmaf(w[1], -b * g2, dd);
+    dd = fmaf(w[2], 2.f * dn, dd);
+    dd = fmaf(w[3], dhy, dd);
+    dd = fmaf(w[4], dhb, dd);
+    fr = dd * rinv;
+    if (TERMS) {
+        et[0] = g1; et[1] = g2; et[2] = dn * dn; et[3] = hy; et[4] = hb;
+        dRs = -dd;
+    }
+    return e;
+}
+
+// TRIDS E_dock terms on r (see trids.h).
+template <bool TERMS>
+__device__ __forceinline__ float pair_trids(float r2, float rsum, int pf, const float4* __restrict__ gmm,
+                                            int K, bool inter, const float* __restrict__ w, float& fr,
+                                            float* et, float& dRs) {
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    float e0 = 0.f, d0 = 0.f, e1 = 0.f, d1 = 0.f, e2 = 0.f, d2 = 0.f, r2d = 0.f, e3 = 0.f, d3 = 0.f;
+    if (inter && r < 5.f) {
+        for (int k = 0; k < K; ++k) {
+            const float4 g = gmm[k];
+            const float z = r - g.y;
+            const float ex = g.x * __expf(g.z * z * z);
+            e0 -= ex;
+            d0 = fmaf(ex * z, g.w, d0);
+        }
+    }
+    if (r < 10.f) {
+        const float z = r - rsum - 3.f;
+        const float gl = __expf(-0.25f * z * z);
+        e1 = -gl;
+        d1 = 0.5f * gl * z;
+    }
+    const float dcl = (pf & 2) ? 2.6f : rsum;
+    if (r < dcl) {
+        const float rr = r < 0.5f ? 0.5f : r;
+        e2 = -logf(rr / dcl);
+        d2 = r < 0.5f ? 0.f : -rinv;
+        r2d = (pf & 2) ? 0.f : 1.f / dcl;
+    }
+    if ((pf & 2) && r < 3.4f) {
+        const float z = r - 2.88f;
+        const float gh = __expf(z * z * (-1.f / 0.18f));
+        e3 = -gh;
+        d3 = gh * z * (1.f / 0.09f);
+    }
+    const float e = w[0] * e0 + w[1] * e1 + w[2] * e2 + w[3] * e3;
+    fr = (w[0] * d0 + w[1] * d1 + w[2] * d2 + w[3] * d3) * rinv;
+    if (TERMS) {
+        et[0] = e0; et[1] = e1; et[2] = e2; et[3] = e3; et[4] = 0.f;
+        dRs = w[1] * (-d1) + w[2] * r2d;
+    }
+    return e;
+}
+
+// ------------------------------------------------------------------ shared layout
+struct Smem {
+    const DevParams* P;
+    const float4* pocket;
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    size_t params_bytes, pocket_off, pocket_bytes, mbar_off, warp_off, warp_bytes, total;
+};
+
+__host__ __device__ inline size_t warp_smem_bytes(int Lmax, int Tmax, bool params) {
+    return (size_t)(6 * Lmax + Tmax + (params ? kNT : 0)) * 32 * sizeof(float);
+}
+
+inline Layout make_layout(int term_set, int M, int Lmax, int Tmax, int warps, bool params) {
+    Layout L;
+    L.params_bytes = term_set == TRIDS_TERMS_TRIDS ? sizeof(DevParams) : offsetof(DevParams, gmm);
+    L.pocket_off = align_up(L.params_bytes, 128);
+    L.pocket_bytes = (size_t)(M + 1) * sizeof(float4);
+    L.mbar_off = align_up(L.pocket_off + L.pocket_bytes, 16);
+    L.warp_off = align_up(L.mbar_off + 16, 128);
+    L.warp_bytes = warp_smem_bytes(Lmax, Tmax, params);
+    L.total = L.warp_off + L.warp_bytes * warps;
+    return L;
+}
+
+// Stage the scoring tables and the pocket into shared memory with bulk async copies
+// completing on one mbarrier.  Returns false (and sets *err) if the copy did not
+// complete within a bounded wait.
+__device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t params_bytes, size_t pocket_off,
+                            size_t mbar_off, int* err) {
+    const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(smem + mbar_off);
+    const uint32_t bytes_p = (uint32_t)params_bytes;
+    const uint32_t bytes_k = (uint32_t)((size_t)(pk.M + 1) * sizeof(float4));
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes_p + bytes_k)
+                     : "memory");
+        const uint32_t dp = (uint32_t)__cvta_generic_to_shared(smem);
+        const uint32_t dk = (uint32_t)__cvta_generic_to_shared(smem + pocket_off);
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dp),
+            "l"(pk.params), "r"(bytes_p), "r"(mbar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dk),
+            "l"(pk.atoms), "r"(bytes_k), "r"(mbar)
+            : "memory");
+    }
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(mbar)
+            : "memory");
+    }
+    const int ok = __syncthreads_and(done ? 1 : 0);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    return ok != 0;
+}
+
+// ------------------------------------------------------------------ per-warp pose work
+struct Warp {
+    float* xs;    // [3][Lmax][32]
+    float* gs;    // [3][Lmax][32]
+    float* ths;   // [Tmax][32]
+    float* grs;   // [kNT][32] (parameter-gradient kernels only)
+    int Lmax, lane;
+    __device__ float& X(int c, int i) const { return xs[(c * Lmax + i) * 32 + lane]; }
+    __device__ float& G(int c, int i) const { return gs[(c * Lmax + i) * 32 + lane]; }
+    __device__ float& TH(int k) const { return ths[k * 32 + lane]; }
+};
+
+// Forward kinematics: local coordinates, torsions deepest first (reverse BFS order)
+// about their input-geometry axes -- the axis atoms of a torsion are never moved by
+// the torsions below it -- then x = t + R(q) z.
+__device__ void forward_kinematics(const DevBatch& B, const LigHdr& h, const Warp& W, const float t[3],
+                                   const float q[4]) {
+    for (int i = 0; i < h.n_atoms; ++i) {
+        const float4 y = __ldg(&B.atom_y[h.atom_off + i]);
+        W.X(0, i) = y.x; W.X(1, i) = y.y; W.X(2, i) = y.z;
+    }
+    for (int k = h.n_tor - 1; k >= 0; --k) {
+        const int4 ti = __ldg(&B.tor_idx[h.tor_off + k]);
+        const float4 u = __ldg(&B.tor_u[h.tor_off + k]);
+        const float4 p = __ldg(&B.tor_p[h.tor_off + k]);
+        float s, c;
+        sincosf(W.TH(k), &s, &c);
+        const float kc = 1.f - c;
+        const float R0 = c + kc * u.x * u.x, R1 = kc * u.x * u.y - s * u.z, R2 = kc * u.x * u.z + s * u.y;
+        const float R3 = kc * u.y * u.x + s * u.z, R4 = c + kc * u.y * u.y, R5 = kc * u.y * u.z - s * u.x;
+        const float R6 = kc * u.z * u.x - s * u.y, R7 = kc * u.z * u.y + s * u.x, R8 = c + kc * u.z * u.z;
+        for (int i = ti.z; i < ti.w; ++i) {
+            const float vx = W.X(0, i) - p.x, vy = W.X(1, i) - p.y, vz = W.X(2, i) - p.z;
+            W.X(0, i) = p.x + (R0 * vx + R1 * vy + R2 * vz);
+            W.X(1, i) = p.y + (R3 * vx + R4 * vy + R5 * vz);
+            W.X(2, i) = p.z + (R6 * vx + R7 * vy + R8 * vz);
+        }
+    }
+    float R[9];
+    quat_to_mat(q, R);
+    for (int i = 0; i < h.n_atoms; ++i) {
+        const float vx = W.X(0, i), vy = W.X(1, i), vz = W.X(2, i);
+        W.X(0, i) = t[0] + (R[0] * vx + R[1] * vy + R[2] * vz);
+        W.X(1, i) = t[1] + (R[3] * vx + R[4] * vy + R[5] * vz);
+        W.X(2, i) = t[2] + (R[6] * vx + R[7] * vy + R[8] * vz);
+    }
+}
+
+struct ParamAcc {
+    float gw[5];
+};
+
+// Score and per-atom forces of the warp's poses.  Forces go to W.G, the returned value
+// is E_total; *e_inter gets the ligand-pocket part.  With PARAMS, the per-term sums
+// (scaled by ebar) go to acc.gw and the radius derivatives to W.grs.
+template <int TS, bool PARAMS, bool COUNT>
+__device__ float score_pose(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h,
+                            const Warp& W, float ebar, ParamAcc& acc, float* e_inter, uint32_t& npairs) {
+    const DevParams& P = *S.P;
+    const float cut2 = P.cut2;
+    float w[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) w[t] = P.w[t];
+    for (int i = 0; i < h.n_atoms; ++i) { W.G(0, i) = 0.f; W.G(1, i) = 0.f; W.G(2, i) = 0.f; }
+    float et[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float dRs = 0.f;
+    // intra-ligand pairs (uniform list across the warp)
+    float e_intra = 0.f;
+    for (int q = 0; q < h.n_pairs; ++q) {
+        const uint32_t pw = __ldg(&B.pairs[h.pair_off + q]);
+        const int i = pw & 0xff, j = (pw >> 8) & 0xff, ti = (pw >> 16) & 0xff, tj = pw >> 24;
+        const float dx = W.X(0, i) - W.X(0, j), dy = W.X(1, i) - W.X(1, j), dz = W.X(2, i) - W.X(2, j);
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (r2 < cut2) {
+            const float2 pt = P.pairtab[ti][tj];
+            const int pf = __float_as_int(pt.y);
+            float fr;
+            float e;
+            if (TS == TRIDS_TERMS_VINA5)
+                e = pair_vina<PARAMS>(fmaxf(r2, 1e-12f), pt.x, pf, w, fr, et, dRs);
+            else
+                e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, pf, nullptr, 0, false, w, fr, et, dRs);
+            e_intra += e;
+            W.G(0, i) = fmaf(fr, dx, W.G(0, i)); W.G(1, i) = fmaf(fr, dy, W.G(1, i)); W.G(2, i) = fmaf(fr, dz, W.G(2, i));
+            W.G(0, j) = fmaf(-fr, dx, W.G(0, j)); W.G(1, j) = fmaf(-fr, dy, W.G(1, j)); W.G(2, j) = fmaf(-fr, dz, W.G(2, j));
+            if (PARAMS) {
+#pragma unroll
+                for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
+                W.grs[ti * 32 + W.lane] += ebar * dRs;
+                W.grs[tj * 32 + W.lane] += ebar * dRs;
+            }
+            if (COUNT) ++npairs;
+        }
+    }
+    // ligand-pocket pairs through the candidate grid
+    float e_lp = 0.f;
+    const float4* __restrict__ pocket = S.pocket;
+    for (int i = 0; i < h.n_atoms; ++i) {
+        const float4 ya = __ldg(&B.atom_y[h.atom_off + i]);
+        const int ti = __float_as_int(ya.w);
+        const float xi = W.X(0, i), yi = W.X(1, i), zi = W.X(2, i);
+        const float fx = (xi - pk.gx) * pk.inv_h, fy = (yi - pk.gy) * pk.inv_h, fz = (zi - pk.gz) * pk.inv_h;
+        uint32_t beg = 0, end = 0;
+        if (fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)pk.nx && fy < (float)pk.ny && fz < (float)pk.nz) {
+            const int cx = min((int)fx, pk.nx - 1), cy = min((int)fy, pk.ny - 1), cz = min((int)fz, pk.nz - 1);
+            const size_t cell = ((size_t)cz * pk.ny + cy) * pk.nx + cx;
+            beg = __ldg(&pk.cell_start[cell]);
+            end = __ldg(&pk.cell_start[cell + 1]);
+        }
+        const float2* __restrict__ prow = P.pairtab[ti];
+        const float4* __restrict__ grow = (TS == TRIDS_TERMS_TRIDS) ? &P.gmm[ti][0][0] : nullptr;
+        float ax = 0.f, ay = 0.f, az = 0.f, ae = 0.f;
+        for (uint32_t k = beg; k < end; k += 8) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(pk.cand + k));
+            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const int j = (s & 1) ? (int)(wv[s >> 1] >> 16) : (int)(wv[s >> 1] & 0xffff);
+                const float4 a = pocket[j];
+                const float dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                if (r2 < cut2) {
+                    const int tj = __float_as_int(a.w);
+                    const float2 pt = prow[tj];
+                    const int pf = __float_as_int(pt.y);
+                    float fr;
+                    float e;
+                    if (TS == TRIDS_TERMS_VINA5)
+                        e = pair_vina<PARAMS>(fmaxf(r2, 1e-12f), pt.x, pf, w, fr, et, dRs);
+                    else
+                        e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, pf, grow + tj * kK, P.gmm_k, true, w, fr,
+                                               et, dRs);
+                    ae += e;
+                    ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
+                    if (PARAMS) {
+#pragma unroll
+                        for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
+                        W.grs[ti * 32 + W.lane] += ebar * dRs;
+                        W.grs[tj * 32 + W.lane] += ebar * dRs;
+                    }
+                    if (COUNT) ++npairs;
+                }
+            }
+        }
+        e_lp += ae;
+        W.G(0, i) += ax; W.G(1, i) += ay; W.G(2, i) += az;
+    }
+    *e_inter = e_lp;
+    return e_lp + e_intra;
+}
+
+// dE/dt = sum g_i, world torque tau = sum (x_i - t) x g_i.
+__device__ void rigid_adjoint(const LigHdr& h, const Warp& W, const float t[3], float gt[3], float tau[3]) {
+    gt[0] = gt[1] = gt[2] = tau[0] = tau[1] = tau[2] = 0.f;
+    for (int i = 0; i < h.n_atoms; ++i) {
+        const float gx = W.G(0, i), gy = W.G(1, i), gz = W.G(2, i);
+        const float rx = W.X(0, i) - t[0], ry = W.X(1, i) - t[1], rz = W.X(2, i) - t[2];
+        gt[0] += gx; gt[1] += gy; gt[2] += gz;
+        tau[0] += ry * gz - rz * gy;
+        tau[1] += rz * gx - rx * gz;
+        tau[2] += rx * gy - ry * gx;
+    }
+}
+
+// dE/dtheta_k = a_k . sum over the moving subtree of (x_i - p_k) x g_i, with a_k the
+// world axis (parent atom -> child atom) and p_k the world parent atom.
+__device__ float torsion_grad(const DevBatch& B, const LigHdr& h, const Warp& W, int k) {
+    const int4 ti = __ldg(&B.tor_idx[h.tor_off + k]);
+    const float px = W.X(0, ti.x), py = W.X(1, ti.x), pz = W.X(2, ti.x);
+    float ax = W.X(0, ti.y) - px, ay = W.X(1, ti.y) - py, az = W.X(2, ti.y) - pz;
+    const float n = rsqrtf(ax * ax + ay * ay + az * az);
+    ax *= n; ay *= n; az *= n;
+    float s = 0.f;
+    for (int i = ti.z; i < ti.w; ++i) {
+        const float rx = W.X(0, i) - px, ry = W.X(1, i) - py, rz = W.X(2, i) - pz;
+        const float gx = W.G(0, i), gy = W.G(1, i), gz = W.G(2, i);
+        s += ax * (ry * gz - rz * gy) + ay * (rz * gx - rx * gz) + az * (rx * gy - ry * gx);
+    }
+    return s;
+}
+
+// ------------------------------------------------------------------ sampler state
+struct PoseState {
+    float t[3], q[4], m[6], v[6], st[3], sq[4];
+    float ecur, esaved;
+    int status;
+};
+
+struct SampleArgs {
+    DevPocket pk;
+    DevBatch B;
+    int P, S, step_begin, step_end, Lmc;
+    float lr, b1, b2, eps, beta;
+    uint64_t seed;
+    int lig_base;
+    float* dof;
+    float* state;
+    float* energy;
+    float* trace;
+    const int* trace_slot;
+    int n_trace;
+    unsigned long long* pair_count;
+    const int2* items;
+    int n_items;
+    unsigned int* counter;
+    int* err;
+    size_t params_bytes, pocket_off, mbar_off, warp_off, warp_bytes;
+};
+
+struct Sched {
+    int loop, j, n;
+};
+
+__device__ __forceinline__ Sched schedule(int S, int Lmc, int s) {
+    const int base = S / Lmc, rem = S % Lmc;
+    Sched r;
+    const int head = rem * (base + 1);
+    if (s < head) {
+        r.loop = s / (base + 1); r.j = s % (base + 1); r.n = base + 1;
+    } else {
+        const int s2 = s - head;
+        r.loop = rem + s2 / base; r.j = s2 % base; r.n = base;
+    }
+    return r;
+}
+
+__device__ __forceinline__ float& fld(const SampleArgs& A, int l, int f, int p) {
+    return A.state[((size_t)l * A.B.n_fields + f) * A.P + p];
+}
+
+__device__ void init_pose(const SampleArgs& A, const LigHdr& h, const Warp& W, int l, int p, PoseState& st) {
+    const uint32_t lig = (uint32_t)(A.lig_base + l);
+    float u[6 + kTmax];
+    for (int b = 0; b * 4 < 6 + h.n_tor; ++b) {
+        const uint4 r = rand_block(A.seed, lig, (uint32_t)p, 0u, 0u, (uint32_t)b);
+        for (int c = 0; c < 4 && b * 4 + c < 6 + h.n_tor; ++c) u[b * 4 + c] = u01(pick(r, c));
+    }
+    for (int d = 0; d < 3; ++d) st.t[d] = fmaf(u[d], A.pk.box_hi[d] - A.pk.box_lo[d], A.pk.box_lo[d]);
+    const float a = sqrtf(1.f - u[3]), b = sqrtf(u[3]);
+    float s1, c1, s2, c2;
+    sincospif(2.f * u[4], &s1, &c1);
+    sincospif(2.f * u[5], &s2, &c2);
+    st.q[0] = a * s1; st.q[1] = a * c1; st.q[2] = b * s2; st.q[3] = b * c2;
+    for (int k = 0; k < h.n_tor; ++k) W.TH(k) = fmaf(u[6 + k], kTwoPi, -kPi);
+    for (int d = 0; d < 6; ++d) { st.m[d] = 0.f; st.v[d] = 0.f; }
+    for (int d = 0; d < 3; ++d) st.st[d] = st.t[d];
+    for (int d = 0; d < 4; ++d) st.sq[d] = st.q[d];
+    st.ecur = __int_as_float(0x7fc00000);
+    st.esaved = st.ecur;
+    st.status = 0;
+}
+
+__device__ void load_pose(const SampleArgs& A, const LigHdr& h, const Warp& W, int l, int p, PoseState& st) {
+    const float* row = A.dof + ((size_t)l * A.P + p) * A.B.dof_stride;
+    for (int d = 0; d < 3; ++d) st.t[d] = row[d];
+    for (int d = 0; d < 4; ++d) st.q[d] = row[3 + d];
+    for (int k = 0; k < h.n_tor; ++k) W.TH(k) = row[7 + k];
+    for (int d = 0; d < 6; ++d) { st.m[d] = fld(A, l, kFieldM + d, p); st.v[d] = fld(A, l, kFieldV + d, p); }
+    for (int d = 0; d < 3; ++d) st.st[d] = fld(A, l, kFieldSaved + d, p);
+    for (int d = 0; d < 4; ++d) st.sq[d] = fld(A, l, kFieldSaved + 3 + d, p);
+    st.ecur = fld(A, l, kFieldEcur, p);
+    st.esaved = fld(A, l, kFieldEsaved, p);
+    st.status = __float_as_int(fld(A, l, kFieldStatus, p));
+}
+
+__device__ void store_pose(const SampleArgs& A, const LigHdr& h, const Warp& W, int l, int p, const PoseState& st) {
+    float* row = A.dof + ((size_t)l * A.P + p) * A.B.dof_stride;
+    for (int d = 0; d < 3; ++d) row[d] = st.t[d];
+    for (int d = 0; d < 4; ++d) row[3 + d] = st.q[d];
+    for (int k = 0; k < A.B.max_tor; ++k) row[7 + k] = k < h.n_tor ? W.TH(k) : 0.f;
+    for (int d = 0; d < 6; ++d) { fld(A, l, kFieldM + d, p) = st.m[d]; fld(A, l, kFieldV + d, p) = st.v[d]; }
+    for (int d = 0; d < 3; ++d) fld(A, l, kFieldSaved + d, p) = st.st[d];
+    for (int d = 0; d < 4; ++d) fld(A, l, kFieldSaved + 3 + d, p) = st.sq[d];
+    fld(A, l, kFieldEcur, p) = st.ecur;
+    fld(A, l, kFieldEsaved, p) = st.esaved;
+    fld(A, l, kFieldStatus, p) = __int_as_float(st.status);
+    A.energy[(size_t)l * A.P + p] = st.ecur;
+}
+
+__device__ __forceinline__ float adam_delta(const SampleArgs& A, float g, float& m, float& v, float bc1, float sbc2) {
+    m = fmaf(A.b1, m, (1.f - A.b1) * g);
+    v = fmaf(A.b2, v, (1.f - A.b2) * g * g);
+    const float denom = sqrtf(v) / sbc2 + A.eps;
+    return -(A.lr / bc1) * m / denom;
+}
+
+// One evaluation (and its update or acceptance test) of one pose; s is the global
+// evaluation index of the schedule.
+template <int TS, bool COUNT>
+__device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h, const Warp& W, int l, int p,
+                            bool live, int s, PoseState& st, uint32_t& npairs) {
+    if (st.status & 1) return;  // frozen after a non-finite energy
+    const Sched sc = schedule(A.S, A.Lmc, s);
+    const int T = h.n_tor;
+    const uint32_t lig = (uint32_t)(A.lig_base + l);
+    if (sc.j == 0) {
+        if (sc.loop > 0) {
+            // save the state, then resample one of the 6+T variables in its range
+            for (int d = 0; d < 3; ++d) st.st[d] = st.t[d];
+            for (int d = 0; d < 4; ++d) st.sq[d] = st.q[d];
+            if (live)
+                for (int k = 0; k < T; ++k) fld(A, l, kFieldTheta + 2 * A.B.max_tor + k, p) = W.TH(k);
+            st.esaved = st.ecur;
+            const uint4 r = rand_block(A.seed, lig, (uint32_t)p, (uint32_t)sc.loop, 1u, 0u);
+            const int c = (int)(((unsigned long long)(r.x >> 8) * (unsigned long long)(6 + T)) >> 24);
+            const float u1 = u01(r.y);
+            if (c < 3) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    if (d == c) st.t[d] = fmaf(u1, A.pk.box_hi[d] - A.pk.box_lo[d], A.pk.box_lo[d]);
+            } else if (c < 6) {
+                const float ang = fmaf(u1, kTwoPi, -kPi);
+                float sh, ch;
+                sincosf(0.5f * ang, &sh, &ch);
+                const float rq[4] = {ch, c == 3 ? sh : 0.f, c == 4 ? sh : 0.f, c == 5 ? sh : 0.f};
+                quat_premul(rq, st.q);
+            } else {
+                W.TH(c - 6) = fmaf(u1, kTwoPi, -kPi);
+            }
+        }
+        for (int d = 0; d < 6; ++d) { st.m[d] = 0.f; st.v[d] = 0.f; }
+        if (live)
+            for (int k = 0; k < T; ++k) {
+                fld(A, l, kFieldTheta + k, p) = 0.f;
+                fld(A, l, kFieldTheta + A.B.max_tor + k, p) = 0.f;
+            }
+    }
+    // evaluate
+    forward_kinematics(A.B, h, W, st.t, st.q);
+    ParamAcc acc;
+    float e_inter;
+    const float E = score_pose<TS, false, COUNT>(A.B, A.pk, S, h, W, 1.f, acc, &e_inter, npairs);
+    float gt[3], tau[3];
+    rigid_adjoint(h, W, st.t, gt, tau);
+    float* rec = nullptr;
+    if (A.trace && live) {
+        const int slot = A.trace_slot[(size_t)l * A.P + p];
+        if (slot >= 0) {
+            rec = A.trace + ((size_t)(s - A.step_begin) * A.n_trace + slot) * trace_record(A.B.max_tor);
+            for (int d = 0; d < 3; ++d) rec[d] = st.t[d];
+            for (int d = 0; d < 4; ++d) rec[3 + d] = st.q[d];
+            for (int k = 0; k < A.B.max_tor; ++k) rec[7 + k] = k < T ? W.TH(k) : 0.f;
+            const int o = A.B.dof_stride;
+            rec[o] = E;
+            for (int d = 0; d < 3; ++d) { rec[o + 1 + d] = gt[d]; rec[o + 4 + d] = tau[d]; }
+            for (int k = T; k < A.B.max_tor; ++k) rec[o + 7 + k] = 0.f;
+        }
+    }
+    if (!isfinite(E)) {
+        st.status |= 1;
+        st.ecur = E;
+        return;
+    }
+    const bool update = sc.j < sc.n - 1;
+    float bc1 = 1.f, sbc2 = 1.f;
+    if (update) {
+        const int ta = sc.j + 1;
+        bc1 = 1.f - powf(A.b1, (float)ta);
+        sbc2 = sqrtf(1.f - powf(A.b2, (float)ta));
+    }
+    for (int k = 0; k < T; ++k) {
+        const float g = torsion_grad(A.B, h, W, k);
+        if (rec) rec[A.B.dof_stride + 7 + k] = g;
+        if (update) {
+            float& m = fld(A, l, kFieldTheta + k, p);
+            float& v = fld(A, l, kFieldTheta + A.B.max_tor + k, p);
+            float mm = m, vv = v;
+            const float dlt = adam_delta(A, g, mm, vv, bc1, sbc2);
+            if (live) { m = mm; v = vv; }
+            W.TH(k) = wrap_pi(W.TH(k) + dlt);
+        }
+    }
+    if (update) {
+        for (int d = 0; d < 3; ++d) {
+            const float dlt = adam_delta(A, gt[d], st.m[d], st.v[d], bc1, sbc2);
+            st.t[d] = fminf(fmaxf(st.t[d] + dlt, A.pk.box_lo[d]), A.pk.box_hi[d]);
+        }
+        float dw[3];
+        for (int d = 0; d < 3; ++d) dw[d] = adam_delta(A, tau[d], st.m[3 + d], st.v[3 + d], bc1, sbc2);
+        const float phi = sqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
+        if (phi > 0.f) {
+            float sh, ch;
+            sincosf(0.5f * phi, &sh, &ch);
+            const float sc2 = sh / phi;
+            const float rq[4] = {ch, sc2 * dw[0], sc2 * dw[1], sc2 * dw[2]};
+            quat_premul(rq, st.q);
+        }
+    } else {
+        st.ecur = E;
+        if (sc.loop > 0) {
+            const uint4 r = rand_block(A.seed, lig, (uint32_t)p, (uint32_t)sc.loop, 2u, 0u);
+            const float u = u01(r.x);
+            if (!(u < expf(-A.beta * (E - st.esaved)))) {
+                for (int d = 0; d < 3; ++d) st.t[d] = st.st[d];
+                for (int d = 0; d < 4; ++d) st.q[d] = st.sq[d];
+                for (int k = 0; k < T; ++k) W.TH(k) = fld(A, l, kFieldTheta + 2 * A.B.max_tor + k, p);
+                st.ecur = st.esaved;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ Warp make_warp(unsigned char* smem, size_t warp_off, size_t warp_bytes, int Lmax, int Tmax,
+                                          bool params) {
+    Warp W;
+    const int wid = threadIdx.x >> 5;
+    float* base = reinterpret_cast<float*>(smem + warp_off + warp_bytes * wid);
+    W.xs = base;
+    W.gs = base + 3 * Lmax * 32;
+    W.ths = W.gs + 3 * Lmax * 32;
+    W.grs = params ? W.ths + Tmax * 32 : nullptr;
+    W.Lmax = Lmax;
+    W.lane = threadIdx.x & 31;
+    return W;
+}
+
+__device__ __forceinline__ void flush_count(unsigned long long* cnt, uint32_t n) {
+    unsigned long long v = n;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(cnt, v);
+}
+
+// Persistent fused sampler: each warp pops (ligand, 32-pose tile) items from a global
+// counter and runs every evaluation of its poses with the state held on chip.
+template <int TS, bool COUNT>
+__global__ void __launch_bounds__(256) k_sample_persistent(SampleArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.mbar_off, A.err)) return;
+    Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off)};
+    const Warp W = make_warp(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor, false);
+    uint32_t npairs = 0;
+    for (;;) {
+        int it = 0;
+        if (W.lane == 0) it = (int)atomicAdd(A.counter, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= A.n_items) break;
+        const int2 item = A.items[it];
+        const int l = item.x;
+        const LigHdr h = A.B.lig[l];
+        const int p = min(item.y + W.lane, A.P - 1);
+        const bool live = item.y + W.lane < A.P;
+        PoseState st;
+        if (A.step_begin == 0) init_pose(A, h, W, l, p, st);
+        else load_pose(A, h, W, l, p, st);
+        for (int s = A.step_begin; s < A.step_end; ++s) sample_step<TS, COUNT>(A, S, h, W, l, p, live, s, st, npairs);
+        if (live) store_pose(A, h, W, l, p, st);
+        __syncwarp();
+    }
+    if (COUNT) flush_count(A.pair_count, npairs);
+}
+
+// Plain form: one launch per (ligand, evaluation) with the state in global memory,
+// the same device code as the persistent sampler.
+template <int TS, bool COUNT>
+__global__ void __launch_bounds__(256) k_sample_step(SampleArgs A, int l, int s) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.mbar_off, A.err)) return;
+    Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off)};
+    const Warp W = make_warp(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor, false);
+    const int p0 = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+    if (p0 >= A.P) return;
+    const LigHdr h = A.B.lig[l];
+    const int p = min(p0 + W.lane, A.P - 1);
+    const bool live = p0 + W.lane < A.P;
+    uint32_t npairs = 0;
+    PoseState st;
+    if (s == 0) init_pose(A, h, W, l, p, st);
+    else load_pose(A, h, W, l, p, st);
+    sample_step<TS, COUNT>(A, S, h, W, l, p, live, s, st, npairs);
+    if (live) store_pose(A, h, W, l, p, st);
+    if (COUNT) flush_count(A.pair_count, npairs);
+}
+
+// ------------------------------------------------------------------ score + gradient
+struct ScoreArgs {
+    DevPocket pk;
+    DevBatch B;
+    int P;
+    const float* dof;
+    float* energy;
+    float* e_inter;
+    float* g_dof;
+    float* g_xyz;
+    const float* e_bar;
+    float* partials;   // [n_items][5 + kNT]
+    const int2* items;
+    int n_items;
+    unsigned int* counter;
+    int* err;
+    size_t params_bytes, pocket_off, mbar_off, warp_off, warp_bytes;
+};
+
+template <int TS, bool PARAMS>
+__global__ void __launch_bounds__(256) k_score(ScoreArgs A) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.mbar_off, A.err)) return;
+    Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off)};
+    const Warp W = make_warp(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor, PARAMS);
+    const int D = A.B.dof_stride;
+    for (;;) {
+        int it = 0;
+        if (W.lane == 0) it = (int)atomicAdd(A.counter, 1u);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= A.n_items) break;
+        const int2 item = A.items[it];
+        const int l = item.x;
+        const LigHdr h = A.B.lig[l];
+        const int p = min(item.y + W.lane, A.P - 1);
+        const bool live = item.y + W.lane < A.P;
+        const size_t gp = (size_t)l * A.P + p;
+        const float* row = A.dof + gp * D;
+        float t[3] = {row[0], row[1], row[2]};
+        float q[4] = {row[3], row[4], row[5], row[6]};
+        for (int k = 0; k < h.n_tor; ++k) W.TH(k) = row[7 + k];
+        const float ebar = (A.e_bar && live) ? A.e_bar[gp] : (live ? 1.f : 0.f);
+        ParamAcc acc;
+        for (int t5 = 0; t5 < 5; ++t5) acc.gw[t5] = 0.f;
+        if (PARAMS)
+            for (int a = 0; a < kNT; ++a) W.grs[a * 32 + W.lane] = 0.f;
+        forward_kinematics(A.B, h, W, t, q);
+        float e_inter;
+        uint32_t np = 0;
+        const float E = score_pose<TS, PARAMS, false>(A.B, A.pk, S, h, W, ebar, acc, &e_inter, np);
+        if (live) {
+            A.energy[gp] = E;
+            if (A.e_inter) A.e_inter[gp] = e_inter;
+        }
+        if (A.g_dof && live) {
+            float gt[3], tau[3];
+            rigid_adjoint(h, W, t, gt, tau);
+            float* o = A.g_dof + gp * D;
+            const float sc = A.e_bar ? ebar : 1.f;
+            for (int d = 0; d < 3; ++d) o[d] = sc * gt[d];
+            // dE/dq of E(q/|q|) = 4 M(qhat) tau / |q|, M(q) = 1/2 [-v^T ; w I - [v]x]
+            const float n = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+            const float w = q[0] * n, vx = q[1] * n, vy = q[2] * n, vz = q[3] * n;
+            const float c0 = vy * tau[2] - vz * tau[1], c1 = vz * tau[0] - vx * tau[2], c2 = vx * tau[1] - vy * tau[0];
+            o[3] = sc * 2.f * n * (-(vx * tau[0] + vy * tau[1] + vz * tau[2]));
+            o[4] = sc * 2.f * n * (w * tau[0] - c0);
+            o[5] = sc * 2.f * n * (w * tau[1] - c1);
+            o[6] = sc * 2.f * n * (w * tau[2] - c2);
+            for (int k = 0; k < A.B.max_tor; ++k) o[7 + k] = k < h.n_tor ? sc * torsion_grad(A.B, h, W, k) : 0.f;
+        }
+        if (A.g_xyz && live) {
+            const float sc = A.e_bar ? ebar : 1.f;
+            float* o = A.g_xyz + gp * A.B.max_atoms * 3;
+            for (int i = 0; i < A.B.max_atoms * 3; ++i) o[i] = 0.f;
+            for (int i = 0; i < h.n_atoms; ++i) {
+                const int oi = __ldg(&A.B.atom_orig[h.atom_off + i]);
+                o[3 * oi] = sc * W.G(0, i); o[3 * oi + 1] = sc * W.G(1, i); o[3 * oi + 2] = sc * W.G(2, i);
+            }
+        }
+        if (PARAMS) {
+            // fixed-order warp reductions; one partial row per item
+            float* prow = A.partials + (size_t)it * (5 + kNT);
+            for (int t5 = 0; t5 < 5; ++t5) {
+                float v = acc.gw[t5];
+                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+                if (W.lane == 0) prow[t5] = v;
+            }
+            for (int a = 0; a < kNT; ++a) {
+                float v = W.grs[a * 32 + W.lane];
+                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+                if (W.lane == 0) prow[5 + a] = v;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Sum item partials in item order: out_w[5], out_r[n_types].
+__global__ void k_reduce_params(const float* partials, int n_items, float* g_w, float* g_r, int n_types) {
+    const int c = threadIdx.x;
+    if (c >= 5 + n_types) return;
+    float s = 0.f;
+    for (int i = 0; i < n_items; ++i) s += partials[(size_t)i * (5 + kNT) + c];
+    if (c < 5) { if (g_w) g_w[c] = s; }
+    else if (g_r) g_r[c - 5] = s;
+}
+
+// ------------------------------------------------------------------ top-k
+// One block per ligand: rank by (E, index) with non-finite energies last, then walk
+// the ranking and keep a pose unless its RMSD to a kept pose is below rho.
+__global__ void __launch_bounds__(128) k_topk(DevBatch B, int P, const float* energy, const float* dof, int k,
+                                              float rho, int* idx, float* e_out) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int l = blockIdx.x;
+    const LigHdr h = B.lig[l];
+    const int L = h.n_atoms;
+    int* order = reinterpret_cast<int*>(smem);
+    float* cand = reinterpret_cast<float*>(order + align_up(P, 4));
+    float* kept = cand + 3 * kLmax;
+    float* red = kept + (size_t)k * 3 * kLmax;
+    __shared__ int s_flag;
+    const float* E = energy + (size_t)l * P;
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const float ep = E[p];
+        const bool fp = isfinite(ep);
+        int rank = 0;
+        for (int q = 0; q < P; ++q) {
+            const float eq = E[q];
+            const bool fq = isfinite(eq);
+            bool before;
+            if (fq != fp) before = fq;
+            else if (fq && eq != ep) before = eq < ep;
+            else before = q < p;
+            rank += before ? 1 : 0;
+        }
+        order[rank] = p;
+    }
+    __syncthreads();
+    int nk = 0;
+    for (int n = 0; n < P && nk < k; ++n) {
+        const int p = order[n];
+        if (!isfinite(E[p])) break;
+        // coordinates of pose p: torsions deepest first, then the rigid placement
+        const float* row = dof + ((size_t)l * P + p) * B.dof_stride;
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            const float4 y = B.atom_y[h.atom_off + i];
+            float x0 = y.x, x1 = y.y, x2 = y.z;
+            for (int kk = h.n_tor - 1; kk >= 0; --kk) {
+                const int4 ti = B.tor_idx[h.tor_off + kk];
+                if (i < ti.z || i >= ti.w) continue;
+                const float4 u = B.tor_u[h.tor_off + kk];
+                const float4 pp = B.tor_p[h.tor_off + kk];
+                float s, c;
+                sincosf(row[7 + kk], &s, &c);
+                const float kc = 1.f - c;
+                const float vx = x0 - pp.x, vy = x1 - pp.y, vz = x2 - pp.z;
+                x0 = pp.x + ((c + kc * u.x * u.x) * vx + (kc * u.x * u.y - s * u.z) * vy + (kc * u.x * u.z + s * u.y) * vz);
+                x1 = pp.y + ((kc * u.y * u.x + s * u.z) * vx + (c + kc * u.y * u.y) * vy + (kc * u.y * u.z - s * u.x) * vz);
+                x2 = pp.z + ((kc * u.z * u.x - s * u.y) * vx + (kc * u.z * u.y + s * u.x) * vy + (c + kc * u.z * u.z) * vz);
+            }
+            float q[4] = {row[3], row[4], row[5], row[6]}, R[9];
+            quat_to_mat(q, R);
+            cand[i] = row[0] + (R[0] * x0 + R[1] * x1 + R[2] * x2);
+            cand[kLmax + i] = row[1] + (R[3] * x0 + R[4] * x1 + R[5] * x2);
+            cand[2 * kLmax + i] = row[2] + (R[6] * x0 + R[7] * x1 + R[8] * x2);
+        }
+        if (threadIdx.x == 0) s_flag = 0;
+        __syncthreads();
+        for (int m = 0; m < nk; ++m) {
+            float acc = 0.f;
+            for (int i = threadIdx.x; i < L; i += blockDim.x)
+                for (int c = 0; c < 3; ++c) {
+                    const float d = cand[c * kLmax + i] - kept[((size_t)m * 3 + c) * kLmax + i];
+                    acc = fmaf(d, d, acc);
+                }
+            for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float s = 0.f;
+                for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += red[wv];
+                if (s < rho * rho * (float)L) s_flag = 1;
+            }
+            __syncthreads();
+        }
+        if (!s_flag) {
+            for (int i = threadIdx.x; i < L; i += blockDim.x)
+                for (int c = 0; c < 3; ++c) kept[((size_t)nk * 3 + c) * kLmax + i] = cand[c * kLmax + i];
+            if (threadIdx.x == 0) {
+                idx[(size_t)l * k + nk] = p;
+                if (e_out) e_out[(size_t)l * k + nk] = E[p];
+            }
+            ++nk;
+        }
+        __syncthreads();
+    }
+    for (int m = nk + threadIdx.x; m < k; m += blockDim.x) {
+        idx[(size_t)l * k + m] = -1;
+        if (e_out) e_out[(size_t)l * k + m] = __int_as_float(0x7fc00000);
+    }
+}
+
+__global__ void k_status(const float* state, int n_lig, int P, int n_fields, int* out) {
+    const size_t n = (size_t)n_lig * P;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t l = i / P, p = i % P;
+        const int s = __float_as_int(state[(l * n_fields + kFieldStatus) * P + p]);
+        if (s) atomicOr(out, s);
+    }
+}
+
+}  // namespace
+
+// =============================================================== host objects
+struct trids_pocket {
+    int device = 0;
+    int M = 0;
+    float cutoff_built = 0.f;
+    float cell = 1.f;
+    float box_lo[3], box_hi[3];
+    trids_params prm;
+    DevParams hp;
+    CandidateGrid grid;
+    float4* d_atoms = nullptr;
+    uint32_t* d_cell = nullptr;
+    uint16_t* d_cand = nullptr;
+    DevParams* d_params = nullptr;
+    DevPocket view() const {
+        DevPocket v;
+        v.atoms = d_atoms; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
+        v.nx = grid.dims[0]; v.ny = grid.dims[1]; v.nz = grid.dims[2];
+        v.gx = grid.lo[0]; v.gy = grid.lo[1]; v.gz = grid.lo[2]; v.inv_h = 1.f / grid.h;
+        for (int d = 0; d < 3; ++d) { v.box_lo[d] = box_lo[d]; v.box_hi[d] = box_hi[d]; }
+        return v;
+    }
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned char> key;
+};
+
+struct trids_batch {
+    int device = 0;
+    int n_types = 0;
+    trids_batch_dims dims{};
+    std::vector<PackedLigand> ligs;
+    std::vector<LigHdr> hdr;
+    LigHdr* d_lig = nullptr;
+    float4* d_atom_y = nullptr;
+    int* d_atom_orig = nullptr;
+    int4* d_tor_idx = nullptr;
+    float4* d_tor_u = nullptr;
+    float4* d_tor_p = nullptr;
+    uint32_t* d_pairs = nullptr;
+    // per-pose-count caches
+    int items_P = -1;
+    int2* d_items = nullptr;
+    int n_items = 0;
+    unsigned int* d_counter = nullptr;   // [4]
+    int* d_err = nullptr;                // [2]: staging timeout, status OR
+    float* d_partials = nullptr;
+    size_t partials_cap = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    GraphCache graph;
+    DevBatch view() const {
+        DevBatch v;
+        v.n_lig = dims.n_lig; v.max_atoms = dims.max_atoms; v.max_tor = dims.max_tor;
+        v.dof_stride = dims.dof_stride; v.n_fields = dims.state_fields;
+        v.lig = d_lig; v.atom_y = d_atom_y; v.atom_orig = d_atom_orig; v.tor_idx = d_tor_idx;
+        v.tor_u = d_tor_u; v.tor_p = d_tor_p; v.pairs = d_pairs;
+        return v;
+    }
+};
+
+namespace {
+
+template <class T>
+int upload(T** dst, const std::vector<T>& src) {
+    size_t n = std::max<size_t>(src.size(), 1) * sizeof(T);
+    if (cudaMalloc(dst, n) != cudaSuccess) return fail(TRIDS_ENOMEM, "cudaMalloc of %zu bytes failed", n);
+    if (!src.empty()) CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return TRIDS_OK;
+}
+
+int check_params(const trids_params* p) {
+    if (!p) return fail(TRIDS_EINVAL, "params is NULL");
+    if (p->term_set != TRIDS_TERMS_VINA5 && p->term_set != TRIDS_TERMS_TRIDS)
+        return fail(TRIDS_EINVAL, "term_set %d unknown", p->term_set);
+    if (p->n_types < 1 || p->n_types > kNT) return fail(TRIDS_EINVAL, "n_types %d outside 1..%d", p->n_types, kNT);
+    if (!(p->cutoff > 0.f) || !std::isfinite(p->cutoff) || p->cutoff > 64.f)
+        return fail(TRIDS_EINVAL, "cutoff must be in (0, 64]");
+    for (int t = 0; t < 5; ++t)
+        if (!std::isfinite(p->w[t])) return fail(TRIDS_EINVAL, "weight %d is not finite", t);
+    for (int a = 0; a < p->n_types; ++a)
+        if (!std::isfinite(p->radius[a]) || p->radius[a] < 0.f) return fail(TRIDS_EINVAL, "radius %d invalid", a);
+    if (p->gmm_k < 0 || p->gmm_k > kK) return fail(TRIDS_EINVAL, "gmm_k %d outside 0..%d", p->gmm_k, kK);
+    for (int a = 0; a < p->n_types; ++a)
+        for (int b = 0; b < p->n_types; ++b)
+            for (int k = 0; k < p->gmm_k; ++k) {
+                const float* g = p->gmm[a][b][k];
+                if (!std::isfinite(g[0]) || !std::isfinite(g[1]) || !(g[2] > 0.f) || !std::isfinite(g[2]))
+                    return fail(TRIDS_EINVAL, "gmm[%d][%d][%d] invalid (sigma must be > 0)", a, b, k);
+            }
+    return TRIDS_OK;
+}
+
+void fill_dev_params(const trids_params* p, DevParams* d) {
+    std::memset(d, 0, sizeof *d);
+    d->term_set = p->term_set;
+    d->n_types = p->n_types;
+    d->gmm_k = p->gmm_k;
+    for (int t = 0; t < 5; ++t) d->w[t] = p->w[t];
+    d->cutoff = p->cutoff;
+    d->cut2 = p->cutoff * p->cutoff;
+    d->w_tor = p->w_tor;
+    for (int a = 0; a < kNT; ++a) d->radius[a] = a < p->n_types ? p->radius[a] : 0.f;
+    for (int a = 0; a < kNT; ++a)
+        for (int b = 0; b < kNT; ++b) {
+            const bool in = a < p->n_types && b < p->n_types;
+            const int fa = in ? p->flags[a] : 0, fb = in ? p->flags[b] : 0;
+            const int hyd = (fa & 1) && (fb & 1);
+            const int hb = ((fa & 2) && (fb & 4)) || ((fa & 4) && (fb & 2));
+            int bits = (hyd ? 1 : 0) | (hb ? 2 : 0);
+            float rs = in ? p->radius[a] + p->radius[b] : 0.f;
+            float fb_bits;
+            std::memcpy(&fb_bits, &bits, 4);
+            d->pairtab[a][b] = make_float2(rs, fb_bits);
+            for (int k = 0; k < kK; ++k) {
+                if (in && k < p->gmm_k) {
+                    const float* g = p->gmm[a][b][k];
+                    d->gmm[a][b][k] = make_float4(g[0], g[1], -1.f / (2.f * g[2] * g[2]), 1.f / (g[2] * g[2]));
+                } else {
+                    d->gmm[a][b][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        }
+}
+
+int device_guard(int dev) {
+    int cur = -1;
+    CK(cudaGetDevice(&cur));
+    if (cur != dev) CK(cudaSetDevice(dev));
+    return TRIDS_OK;
+}
+
+int ensure_items(trids_batch* b, int P) {
+    if (b->items_P == P) return TRIDS_OK;
+    const int tiles = (P + 31) / 32;
+    std::vector<std::pair<double, int2>> it;
+    it.reserve((size_t)b->dims.n_lig * tiles);
+    for (int l = 0; l < b->dims.n_lig; ++l) {
+        const LigHdr& h = b->hdr[l];
+        const double cost = 60.0 * h.n_atoms + 1.0 * h.n_pairs + 20.0 * h.n_tor + 10.0;
+        for (int t = 0; t < tiles; ++t) it.push_back({cost, make_int2(l, t * 32)});
+    }
+    std::stable_sort(it.begin(), it.end(), [](const std::pair<double, int2>& a, const std::pair<double, int2>& c) {
+        return a.first > c.first;
+    });
+    std::vector<int2> items(it.size());
+    for (size_t i = 0; i < it.size(); ++i) items[i] = it[i].second;
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_items = nullptr;
+    int rc = upload(&b->d_items, items);
+    if (rc) return rc;
+    b->n_items = (int)items.size();
+    b->items_P = P;
+    return TRIDS_OK;
+}
+
+int n_sms(int dev) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+size_t max_smem(int dev) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return (size_t)v;
+}
+
+// Pick warps per block: the requested count, capped so the block fits in shared memory.
+int pick_warps(int requested, const trids_pocket* pk, const trids_batch* b, bool params, Layout* L) {
+    const size_t cap = max_smem(pk->device);
+    int w = requested > 0 ? std::min(requested, 8) : 4;
+    for (; w >= 1; --w) {
+        *L = make_layout(pk->prm.term_set, pk->M, b->dims.max_atoms, b->dims.max_tor, w, params);
+        if (L->total <= cap) return w;
+    }
+    return 0;
+}
+
+template <class K>
+int grid_for(K kernel, int warps, size_t smem, int dev, int n_items, int* grid) {
+    CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps, smem));
+    if (per_sm < 1) return fail(TRIDS_EINVAL, "kernel does not fit on an SM (shared memory %zu bytes)", smem);
+    const int need = (n_items + warps - 1) / warps;
+    *grid = std::max(1, std::min(need, per_sm * n_sms(dev)));
+    return TRIDS_OK;
+}
+
+int check_device_ptr(const void* p, const char* name, bool nullable) {
+    if (!p) return nullable ? TRIDS_OK : fail(TRIDS_EINVAL, "%s is NULL", name);
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TRIDS_EINVAL, "%s is not a CUDA pointer", name);
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(TRIDS_EINVAL, "%s must be device memory", name);
+    return TRIDS_OK;
+}
+
+}  // namespace
+
+// =============================================================== C-ABI
+extern "C" {
+
+const char* trids_last_error(void) { return g_err.c_str(); }
+
+int trids_version(void) { return 100; }
+
+int trids_make_pocket(const float* xyz, const int32_t* type, int32_t n_atoms, const float box_center[3],
+                      const float box_size[3], float cell, const trids_params* prm, trids_pocket** out) {
+    g_err.clear();
+    if (!out) return fail(TRIDS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!xyz || !type || !box_center || !box_size) return fail(TRIDS_EINVAL, "NULL input array");
+    if (n_atoms < 1 || n_atoms > 65535) return fail(TRIDS_EINVAL, "pocket has %d atoms (allowed 1..65535)", n_atoms);
+    int rc = check_params(prm);
+    if (rc) return rc;
+    for (int j = 0; j < n_atoms; ++j) {
+        if (type[j] < 0 || type[j] >= prm->n_types) return fail(TRIDS_EINVAL, "pocket atom %d type out of range", j);
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(xyz[3 * j + d])) return fail(TRIDS_EINVAL, "pocket atom %d non-finite", j);
+    }
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(box_center[d]) || !(box_size[d] >= 0.f) || !std::isfinite(box_size[d]))
+            return fail(TRIDS_EINVAL, "box must be finite with size >= 0");
+    if (cell < 0.f || !std::isfinite(cell) || (cell > 0.f && cell < 0.25f))
+        return fail(TRIDS_EINVAL, "cell must be 0 (default) or >= 0.25 A");
+    std::unique_ptr<trids_pocket> pk(new trids_pocket());
+    CK(cudaGetDevice(&pk->device));
+    pk->M = n_atoms;
+    pk->prm = *prm;
+    pk->cutoff_built = prm->cutoff;
+    pk->cell = cell > 0.f ? cell : 1.0f;
+    for (int d = 0; d < 3; ++d) {
+        pk->box_lo[d] = box_center[d] - 0.5f * box_size[d];
+        pk->box_hi[d] = box_center[d] + 0.5f * box_size[d];
+    }
+    build_grid(n_atoms, xyz, prm->cutoff, pk->cell, &pk->grid);
+    if (pk->grid.cand.size() >= (1ull << 32)) return fail(TRIDS_ENOMEM, "candidate grid too large");
+    std::vector<float4> atoms(n_atoms + 1);
+    for (int j = 0; j < n_atoms; ++j) {
+        float tb;
+        int t = type[j];
+        std::memcpy(&tb, &t, 4);
+        atoms[j] = make_float4(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], tb);
+    }
+    atoms[n_atoms] = make_float4(1e6f, 1e6f, 1e6f, 0.f);  // sentinel: never within the cutoff
+    fill_dev_params(prm, &pk->hp);
+    std::vector<DevParams> hp(1, pk->hp);
+    if ((rc = upload(&pk->d_atoms, atoms)) || (rc = upload(&pk->d_cell, pk->grid.start)) ||
+        (rc = upload(&pk->d_cand, pk->grid.cand)) || (rc = upload(&pk->d_params, hp))) {
+        trids_free_pocket(pk.release());
+        return rc;
+    }
+    *out = pk.release();
+    return TRIDS_OK;
+}
+
+int trids_set_params(trids_pocket* pk, const trids_params* prm, void* stream) {
+    g_err.clear();
+    if (!pk) return fail(TRIDS_EINVAL, "pocket is NULL");
+    int rc = check_params(prm);
+    if (rc) return rc;
+    if (prm->cutoff > pk->cutoff_built)
+        return fail(TRIDS_EINVAL, "cutoff %.3f exceeds the %.3f the pocket grid was built for", prm->cutoff,
+                    pk->cutoff_built);
+    if ((rc = device_guard(pk->device))) return rc;
+    pk->prm = *prm;
+    fill_dev_params(prm, &pk->hp);
+    CK(cudaMemcpyAsync(pk->d_params, &pk->hp, sizeof(DevParams), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return TRIDS_OK;
+}
+
+int trids_free_pocket(trids_pocket* pk) {
+    if (!pk) return TRIDS_OK;
+    cudaFree(pk->d_atoms);
+    cudaFree(pk->d_cell);
+    cudaFree(pk->d_cand);
+    cudaFree(pk->d_params);
+    delete pk;
+    return TRIDS_OK;
+}
+
+int trids_pack_topology(int32_t n_atoms, const float* xyz, const int32_t* type, int32_t n_types, int32_t n_bonds,
+                        const int32_t* bonds, const uint8_t* rotatable, int32_t* topo, int32_t topo_cap,
+                        int32_t* topo_len) {
+    g_err.clear();
+    if (!xyz || !type || (n_bonds > 0 && (!bonds || !rotatable)) || !topo)
+        return fail(TRIDS_EINVAL, "NULL input array");
+    if (n_types < 1 || n_types > kNT) return fail(TRIDS_EINVAL, "n_types outside 1..%d", kNT);
+    PackedLigand lg;
+    std::string m = pack_ligand(n_atoms, xyz, type, n_types, n_bonds, bonds, rotatable, &lg);
+    if (!m.empty()) return fail(TRIDS_EINVAL, "%s", m.c_str());
+    std::vector<int32_t> v;
+    topology_ints(lg, &v);
+    if ((int)v.size() > topo_cap) return fail(TRIDS_EINVAL, "topology needs %zu ints", v.size());
+    std::copy(v.begin(), v.end(), topo);
+    if (topo_len) *topo_len = (int32_t)v.size();
+    return TRIDS_OK;
+}
+
+int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_atoms, const float* xyz,
+                       const int32_t* type, const int32_t* n_bonds, const int32_t* bonds,
+                       const uint8_t* rotatable, trids_batch** out) {
+    g_err.clear();
+    if (!out) return fail(TRIDS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!pk) return fail(TRIDS_EINVAL, "pocket is NULL");
+    if (n_lig < 1) return fail(TRIDS_EINVAL, "n_lig must be >= 1");
+    if (!n_atoms || !xyz || !type || !n_bonds) return fail(TRIDS_EINVAL, "NULL input array");
+    int rc = device_guard(pk->device);
+    if (rc) return rc;
+    std::unique_ptr<trids_batch> b(new trids_batch());
+    b->device = pk->device;
+    b->n_types = pk->prm.n_types;
+    b->ligs.resize(n_lig);
+    size_t ao = 0, bo = 0;
+    int Lmax = 1, Tmax = 0;
+    int64_t npairs = 0;
+    for (int l = 0; l < n_lig; ++l) {
+        if (n_bonds[l] < 0) return fail(TRIDS_EINVAL, "ligand %d: negative bond count", l);
+        if (n_bonds[l] > 0 && (!bonds || !rotatable)) return fail(TRIDS_EINVAL, "bonds is NULL");
+        std::string m = pack_ligand(n_atoms[l], xyz + 3 * ao, type + ao, pk->prm.n_types, n_bonds[l],
+                                    bonds ? bonds + 2 * bo : nullptr, rotatable ? rotatable + bo : nullptr,
+                                    &b->ligs[l]);
+        if (!m.empty()) return fail(TRIDS_EINVAL, "ligand %d: %s", l, m.c_str());
+        Lmax = std::max(Lmax, n_atoms[l]);
+        Tmax = std::max(Tmax, b->ligs[l].n_tor);
+        npairs += (int64_t)b->ligs[l].pairs.size();
+        ao += n_atoms[l];
+        bo += n_bonds[l];
+    }
+    b->dims.n_lig = n_lig;
+    b->dims.max_atoms = Lmax;
+    b->dims.max_tor = Tmax;
+    b->dims.dof_stride = 7 + Tmax;
+    b->dims.state_fields = state_fields(Tmax);
+    b->dims.n_intra = npairs;
+    std::vector<float4> ay;
+    std::vector<int> aorig;
+    std::vector<int4> tidx;
+    std::vector<float4> tu, tp;
+    std::vector<uint32_t> pairs;
+    ao = 0;
+    for (int l = 0; l < n_lig; ++l) {
+        const PackedLigand& lg = b->ligs[l];
+        LigHdr h{};
+        h.n_atoms = lg.n_atoms;
+        h.n_tor = lg.n_tor;
+        h.atom_off = (int)ay.size();
+        h.tor_off = (int)tidx.size();
+        h.pair_off = (int)pairs.size();
+        h.n_pairs = (int)lg.pairs.size();
+        const float* X = xyz + 3 * ao;
+        const int32_t* Ty = type + ao;
+        for (int i = 0; i < lg.n_atoms; ++i) {
+            const int a = lg.perm[i];
+            float tb;
+            int t = Ty[a];
+            std::memcpy(&tb, &t, 4);
+            ay.push_back(make_float4((float)((double)X[3 * a] - lg.c[0]), (float)((double)X[3 * a + 1] - lg.c[1]),
+                                     (float)((double)X[3 * a + 2] - lg.c[2]), tb));
+            aorig.push_back(a);
+        }
+        for (int k = 0; k < lg.n_tor; ++k) {
+            const int pa = lg.perm[lg.tp[k]], ha = lg.perm[lg.th[k]];
+            double u[3], nn = 0;
+            for (int d = 0; d < 3; ++d) {
+                u[d] = (double)X[3 * ha + d] - (double)X[3 * pa + d];
+                nn += u[d] * u[d];
+            }
+            nn = std::sqrt(nn);
+            if (!(nn > 1e-6)) return fail(TRIDS_EINVAL, "ligand %d: rotatable bond %d has zero length", l, k);
+            tidx.push_back(make_int4(lg.tp[k], lg.th[k], lg.sb[k], lg.se[k]));
+            tu.push_back(make_float4((float)(u[0] / nn), (float)(u[1] / nn), (float)(u[2] / nn), 0.f));
+            tp.push_back(make_float4((float)((double)X[3 * pa] - lg.c[0]), (float)((double)X[3 * pa + 1] - lg.c[1]),
+                                     (float)((double)X[3 * pa + 2] - lg.c[2]), 0.f));
+        }
+        for (auto& pr : lg.pairs) {
+            const uint32_t ti = (uint32_t)Ty[lg.perm[pr.first]], tj = (uint32_t)Ty[lg.perm[pr.second]];
+            pairs.push_back((uint32_t)pr.first | ((uint32_t)pr.second << 8) | (ti << 16) | (tj << 24));
+        }
+        b->hdr.push_back(h);
+        ao += n_atoms[l];
+    }
+    if ((rc = upload(&b->d_lig, b->hdr)) || (rc = upload(&b->d_atom_y, ay)) || (rc = upload(&b->d_atom_orig, aorig)) ||
+        (rc = upload(&b->d_tor_idx, tidx)) || (rc = upload(&b->d_tor_u, tu)) || (rc = upload(&b->d_tor_p, tp)) ||
+        (rc = upload(&b->d_pairs, pairs))) {
+        trids_free_batch(b.release());
+        return rc;
+    }
+    std::vector<unsigned int> zeros(4, 0u);
+    std::vector<int> zi(2, 0);
+    if ((rc = upload(&b->d_counter, zeros)) || (rc = upload(&b->d_err, zi))) {
+        trids_free_batch(b.release());
+        return rc;
+    }
+    *out = b.release();
+    return TRIDS_OK;
+}
+
+int trids_free_batch(trids_batch* b) {
+    if (!b) return TRIDS_OK;
+    if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->ev_a) cudaEventDestroy(b->ev_a);
+    if (b->ev_b) cudaEventDestroy(b->ev_b);
+    cudaFree(b->d_lig); cudaFree(b->d_atom_y); cudaFree(b->d_atom_orig); cudaFree(b->d_tor_idx);
+    cudaFree(b->d_tor_u); cudaFree(b->d_tor_p); cudaFree(b->d_pairs); cudaFree(b->d_items);
+    cudaFree(b->d_counter); cudaFree(b->d_err); cudaFree(b->d_partials);
+    delete b;
+    return TRIDS_OK;
+}
+
+int trids_batch_info(const trids_batch* b, trids_batch_dims* dims) {
+    if (!b || !dims) return fail(TRIDS_EINVAL, "NULL argument");
+    *dims = b->dims;
+    return TRIDS_OK;
+}
+
+int trids_batch_query(const trids_batch* b, int32_t* n_tor, int32_t* n_atoms, int32_t lig, int32_t* topo,
+                      int32_t topo_cap) {
+    g_err.clear();
+    if (!b) return fail(TRIDS_EINVAL, "batch is NULL");
+    for (int l = 0; l < b->dims.n_lig; ++l) {
+        if (n_tor) n_tor[l] = b->ligs[l].n_tor;
+        if (n_atoms) n_atoms[l] = b->ligs[l].n_atoms;
+    }
+    if (topo) {
+        if (lig < 0 || lig >= b->dims.n_lig) return fail(TRIDS_EINVAL, "ligand %d out of range", lig);
+        std::vector<int32_t> v;
+        topology_ints(b->ligs[lig], &v);
+        if ((int)v.size() > topo_cap) return fail(TRIDS_EINVAL, "topology needs %zu ints", v.size());
+        std::copy(v.begin(), v.end(), topo);
+    }
+    return TRIDS_OK;
+}
+
+int64_t trids_state_floats(const trids_batch* b, int32_t poses) {
+    if (!b || poses < 1) return 0;
+    return (int64_t)b->dims.n_lig * poses * b->dims.state_fields;
+}
+
+int trids_score_grad(const trids_pocket* pk, const trids_batch* bc, int32_t poses, const float* dof, float* energy,
+                     float* e_inter, float* g_dof, float* g_xyz, const float* e_bar, float* g_w, float* g_radius,
+                     void* stream) {
+    g_err.clear();
+    trids_batch* b = const_cast<trids_batch*>(bc);
+    if (!pk || !b) return fail(TRIDS_EINVAL, "pocket or batch is NULL");
+    if (pk->device != b->device) return fail(TRIDS_EINVAL, "pocket and batch live on different devices");
+    if (poses < 1) return fail(TRIDS_EINVAL, "poses must be >= 1");
+    int rc = device_guard(pk->device);
+    if (rc) return rc;
+    if ((rc = check_device_ptr(dof, "dof", false)) || (rc = check_device_ptr(energy, "energy", false)) ||
+        (rc = check_device_ptr(e_inter, "e_inter", true)) || (rc = check_device_ptr(g_dof, "g_dof", true)) ||
+        (rc = check_device_ptr(g_xyz, "g_xyz", true)) || (rc = check_device_ptr(e_bar, "e_bar", true)) ||
+        (rc = check_device_ptr(g_w, "g_w", true)) || (rc = check_device_ptr(g_radius, "g_radius", true)))
+        return rc;
+    if ((rc = ensure_items(b, poses))) return rc;
+    const bool params = g_w || g_radius;
+    if (params) {
+        const size_t need = (size_t)b->n_items * (5 + kNT);
+        if (need > b->partials_cap) {
+            cudaFree(b->d_partials);
+            b->d_partials = nullptr;
+            if (cudaMalloc(&b->d_partials, need * sizeof(float)) != cudaSuccess)
+                return fail(TRIDS_ENOMEM, "cudaMalloc of parameter partials failed");
+            b->partials_cap = need;
+        }
+    }
+    Layout L;
+    const int warps = pick_warps(4, pk, b, params, &L);
+    if (!warps) return fail(TRIDS_EINVAL, "pocket of %d atoms does not fit in shared memory", pk->M);
+    ScoreArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.pk = pk->view(); A.B = b->view(); A.P = poses; A.dof = dof; A.energy = energy; A.e_inter = e_inter;
+    A.g_dof = g_dof; A.g_xyz = g_xyz; A.e_bar = e_bar; A.partials = b->d_partials; A.items = b->d_items;
+    A.n_items = b->n_items; A.counter = b->d_counter + 1; A.err = b->d_err;
+    A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.mbar_off = L.mbar_off;
+    A.warp_off = L.warp_off; A.warp_bytes = L.warp_bytes;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(A.counter, 0, sizeof(unsigned int), st));
+    int grid = 0;
+    const bool trids_terms = pk->prm.term_set == TRIDS_TERMS_TRIDS;
+#define LAUNCH_SCORE(TS, PR)                                                                  \
+    do {                                                                                      \
+        auto kern = k_score<TS, PR>;                                                          \
+        if ((rc = grid_for(kern, warps, L.total, pk->device, b->n_items, &grid))) return rc;  \
+        kern<<<grid, 32 * warps, L.total, st>>>(A);                                           \
+    } while (0)
+    if (trids_terms) {
+        if (params) LAUNCH_SCORE(TRIDS_TERMS_TRIDS, true); else LAUNCH_SCORE(TRIDS_TERMS_TRIDS, false);
+    } else {
+        if (params) LAUNCH_SCORE(TRIDS_TERMS_VINA5, true); else LAUNCH_SCORE(TRIDS_TERMS_VINA5, false);
+    }
+#undef LAUNCH_SCORE
+    CK(cudaGetLastError());
+    if (params) {
+        k_reduce_params<<<1, 32, 0, st>>>(b->d_partials, b->n_items, g_w, g_radius, b->n_types);
+        CK(cudaGetLastError());
+    }
+    return TRIDS_OK;
+}
+
+int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_sample_cfg* cfg, float* dof, float* state,
+                 float* energy, void* stream) {
+    g_err.clear();
+    trids_batch* b = const_cast<trids_batch*>(bc);
+    if (!pk || !b || !cfg) return fail(TRIDS_EINVAL, "pocket, batch or cfg is NULL");
+    if (pk->device != b->device) return fail(TRIDS_EINVAL, "pocket and batch live on different devices");
+    const trids_sample_cfg& c = *cfg;
+    if (c.poses < 1) return fail(TRIDS_EINVAL, "poses must be >= 1");
+    if (c.steps < 1 || c.mc_loops < 1) return fail(TRIDS_EINVAL, "steps and mc_loops must be >= 1");
+    if (c.step_begin < 0 || c.step_end > c.steps || c.step_begin >= c.step_end)
+        return fail(TRIDS_EINVAL, "need 0 <= step_begin < step_end <= steps");
+    if (!(c.lr > 0.f) || !std::isfinite(c.lr) || !(c.beta1 >= 0.f && c.beta1 < 1.f) ||
+        !(c.beta2 >= 0.f && c.beta2 < 1.f) || !(c.eps > 0.f) || !std::isfinite(c.beta))
+        return fail(TRIDS_EINVAL, "invalid Adam or Metropolis parameters");
+    if (c.mode != TRIDS_MODE_PERSISTENT && c.mode != TRIDS_MODE_PER_LIGAND)
+        return fail(TRIDS_EINVAL, "unknown mode %d", c.mode);
+    if (c.trace && (!c.trace_slot || c.n_trace < 1))
+        return fail(TRIDS_EINVAL, "trace needs trace_slot and n_trace >= 1");
+    int rc = device_guard(pk->device);
+    if (rc) return rc;
+    if ((rc = check_device_ptr(dof, "dof", false)) || (rc = check_device_ptr(state, "state", false)) ||
+        (rc = check_device_ptr(energy, "energy", false)) || (rc = check_device_ptr(c.trace, "trace", true)) ||
+        (rc = check_device_ptr(c.trace_slot, "trace_slot", true)) ||
+        (rc = check_device_ptr(c.pair_count, "pair_count", true)))
+        return rc;
+    if ((rc = ensure_items(b, c.poses))) return rc;
+    Layout L;
+    const int warps = pick_warps(c.warps_per_block, pk, b, false, &L);
+    if (!warps) return fail(TRIDS_EINVAL, "pocket of %d atoms does not fit in shared memory", pk->M);
+    SampleArgs A;
+    std::memset(&A, 0, sizeof A);  // the bytes form the graph-cache key
+    A.pk = pk->view(); A.B = b->view(); A.P = c.poses; A.S = c.steps; A.step_begin = c.step_begin;
+    A.step_end = c.step_end; A.Lmc = c.mc_loops; A.lr = c.lr; A.b1 = c.beta1; A.b2 = c.beta2; A.eps = c.eps;
+    A.beta = c.beta; A.seed = c.seed; A.lig_base = c.lig_base; A.dof = dof; A.state = state; A.energy = energy;
+    A.trace = c.trace; A.trace_slot = c.trace_slot; A.n_trace = c.n_trace; A.pair_count = c.pair_count;
+    A.items = b->d_items; A.n_items = b->n_items; A.counter = b->d_counter; A.err = b->d_err;
+    A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.mbar_off = L.mbar_off;
+    A.warp_off = L.warp_off; A.warp_bytes = L.warp_bytes;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool tt = pk->prm.term_set == TRIDS_TERMS_TRIDS;
+    const bool cnt = c.pair_count != nullptr;
+    if (c.mode == TRIDS_MODE_PER_LIGAND) {
+        auto kern = tt ? (cnt ? k_sample_step<TRIDS_TERMS_TRIDS, true> : k_sample_step<TRIDS_TERMS_TRIDS, false>)
+                       : (cnt ? k_sample_step<TRIDS_TERMS_VINA5, true> : k_sample_step<TRIDS_TERMS_VINA5, false>);
+        CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+        const int tiles = (c.poses + 31) / 32;
+        const int blocks = (tiles + warps - 1) / warps;
+        for (int s = c.step_begin; s < c.step_end; ++s)
+            for (int l = 0; l < b->dims.n_lig; ++l) kern<<<blocks, 32 * warps, L.total, st>>>(A, l, s);
+        CK(cudaGetLastError());
+        return TRIDS_OK;
+    }
+    auto kern = tt ? (cnt ? k_sample_persistent<TRIDS_TERMS_TRIDS, true> : k_sample_persistent<TRIDS_TERMS_TRIDS, false>)
+                   : (cnt ? k_sample_persistent<TRIDS_TERMS_VINA5, true> : k_sample_persistent<TRIDS_TERMS_VINA5, false>);
+    int grid = 0;
+    if ((rc = grid_for(kern, warps, L.total, pk->device, b->n_items, &grid))) return rc;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap));
+    if (!c.use_graph || cap != cudaStreamCaptureStatusNone) {
+        CK(cudaMemsetAsync(A.counter, 0, sizeof(unsigned int), st));
+        kern<<<grid, 32 * warps, L.total, st>>>(A);
+        CK(cudaGetLastError());
+        return TRIDS_OK;
+    }
+    // CUDA graph (Sec. 4 item 2): counter reset + persistent launch, captured once per
+    // argument set and replayed on the caller's stream.  The legacy default stream
+    // cannot be captured; for it capture and replay run on a side stream ordered
+    // against the caller's by events.
+    std::vector<unsigned char> key(sizeof(SampleArgs) + 4 * sizeof(int));
+    std::memcpy(key.data(), &A, sizeof(SampleArgs));
+    const int extra[4] = {grid, warps, tt ? 1 : 0, cnt ? 1 : 0};
+    std::memcpy(key.data() + sizeof(SampleArgs), extra, sizeof extra);
+    const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
+    if (legacy && !b->side) {
+        CK(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming));
+    }
+    cudaStream_t run = legacy ? b->side : st;
+    if (!b->graph.exec || b->graph.key != key) {
+        if (b->graph.exec) { cudaGraphExecDestroy(b->graph.exec); b->graph.exec = nullptr; }
+        if (!b->side) CK(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+        cudaStream_t cs = b->side;
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaMemsetAsync(A.counter, 0, sizeof(unsigned int), cs);
+        kern<<<grid, 32 * warps, L.total, cs>>>(A);
+        cudaError_t le = cudaGetLastError();
+        CK(cudaStreamEndCapture(cs, &g));
+        if (le != cudaSuccess) { cudaGraphDestroy(g); return fail(TRIDS_ECUDA, "launch during capture: %s", cudaGetErrorString(le)); }
+        cudaError_t ie = cudaGraphInstantiate(&b->graph.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return fail(TRIDS_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+        b->graph.key = key;
+    }
+    if (!legacy) {
+        CK(cudaGraphLaunch(b->graph.exec, run));
+        return TRIDS_OK;
+    }
+    CK(cudaEventRecord(b->ev_a, st));
+    CK(cudaStreamWaitEvent(run, b->ev_a, 0));
+    CK(cudaGraphLaunch(b->graph.exec, run));
+    CK(cudaEventRecord(b->ev_b, run));
+    CK(cudaStreamWaitEvent(st, b->ev_b, 0));
+    return TRIDS_OK;
+}
+
+int trids_topk(const trids_batch* b, int32_t poses, const float* energy, const float* dof, int32_t k, float rmsd,
+               int32_t* idx, float* e_out, void* stream) {
+    g_err.clear();
+    if (!b) return fail(TRIDS_EINVAL, "batch is NULL");
+    if (poses < 1 || k < 1 || k > 64) return fail(TRIDS_EINVAL, "need poses >= 1 and 1 <= k <= 64");
+    if (!(rmsd >= 0.f) || !std::isfinite(rmsd)) return fail(TRIDS_EINVAL, "rmsd must be finite and >= 0");
+    int rc = device_guard(b->device);
+    if (rc) return rc;
+    if ((rc = check_device_ptr(energy, "energy", false)) || (rc = check_device_ptr(dof, "dof", false)) ||
+        (rc = check_device_ptr(idx, "idx", false)) || (rc = check_device_ptr(e_out, "e_out", true)))
+        return rc;
+    const size_t smem = align_up((size_t)poses, 4) * sizeof(int) +
+                        (size_t)(3 * kLmax + (size_t)k * 3 * kLmax + 8) * sizeof(float);
+    if (smem > max_smem(b->device)) return fail(TRIDS_EINVAL, "too many poses for top-k");
+    CK(cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_topk<<<b->dims.n_lig, 128, smem, (cudaStream_t)stream>>>(b->view(), poses, energy, dof, k, rmsd, idx, e_out);
+    CK(cudaGetLastError());
+    return TRIDS_OK;
+}
+
+int trids_sync(const trids_batch* b, int32_t poses, const float* state, void* stream, double timeout_ms) {
+    g_err.clear();
+    if (!b) return fail(TRIDS_EINVAL, "batch is NULL");
+    int rc = device_guard(b->device);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (state) {
+        CK(cudaMemsetAsync(b->d_err + 1, 0, sizeof(int), st));
+        k_status<<<64, 256, 0, st>>>(state, b->dims.n_lig, poses, b->dims.state_fields, b->d_err + 1);
+        CK(cudaGetLastError());
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaStreamQuery(st);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return fail(TRIDS_ECUDA, "stream failed: %s", cudaGetErrorString(q));
+        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (timeout_ms > 0 && ms > timeout_ms) return fail(TRIDS_ETIMEOUT, "stream not done after %.1f ms", ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    int flags[2] = {0, 0};
+    CK(cudaMemcpy(flags, b->d_err, sizeof flags, cudaMemcpyDeviceToHost));
+    if (flags[0]) return fail(TRIDS_ECUDA, "shared-memory staging did not complete");
+    if (state && flags[1]) return fail(TRIDS_ENONFINITE, "a pose produced a non-finite energy (status %d)", flags[1]);
+    return TRIDS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Internal structures of libtrids shared by its host and device translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <vector_types.h>
+
+#include "trids.h"
+
+#ifdef __CUDACC__
+#define TRIDS_HD __host__ __device__
+#else
+#define TRIDS_HD
+#endif
+
+namespace trids {
+
+constexpr int kLmax = TRIDS_MAX_ATOMS;
+constexpr int kTmax = TRIDS_MAX_TOR;
+constexpr int kNT = TRIDS_MAX_TYPES;
+constexpr int kK = TRIDS_MAX_GMM;
+
+// ---------------------------------------------------------------- host-side pack
+// Packed torsion tree of one ligand (rules in trids.h, trids_pack_ligands).
+struct PackedLigand {
+    int n_atoms = 0, n_tor = 0;
+    std::vector<int> perm;          // packed -> input index
+    std::vector<int> frag;          // packed atom -> 0 (root) or k+1
+    std::vector<int> tp, th, tpar, sb, se;
+    std::vector<std::pair<int, int>> pairs;  // intra pairs, packed indices, i < j
+    double c[3] = {0, 0, 0};        // root-fragment centroid (input frame)
+};
+
+// Returns "" on success, else a message.  xyz: [n][3].
+std::string pack_ligand(int n, const float* xyz, const int32_t* type, int n_types, int nb,
+                        const int32_t* bonds, const uint8_t* rot, PackedLigand* out);
+void topology_ints(const PackedLigand& lg, std::vector<int32_t>* out);
+
+// ---------------------------------------------------------------- candidate grid
+// Uniform grid over the pocket's bounding box grown by the cutoff.  Each cell lists
+// every pocket atom within cutoff + half the cell diagonal (+ a small margin) of the
+// cell centre, ascending, padded to a multiple of 8 with the sentinel index M.  A
+// ligand atom outside the grid has no pocket atom within the cutoff.
+struct CandidateGrid {
+    float lo[3];
+    float h;
+    int dims[3];
+    std::vector<uint32_t> start;    // [ncell + 1], offsets in entries (multiples of 8)
+    std::vector<uint16_t> cand;
+};
+void build_grid(int M, const float* xyz, float cutoff, float h, CandidateGrid* g);
+
+// ---------------------------------------------------------------- device views
+// Staged into shared memory by every block: the Vina-form path copies the prefix up
+// to `gmm`, the TRIDS path the whole struct.
+struct alignas(16) DevParams {
+    int term_set, n_types, gmm_k, pad0;
+    float w[5];
+    float cutoff, cut2, w_tor;
+    float radius[kNT];
+    float2 pairtab[kNT][kNT];      // (R_a + R_b, pair flags as int bits: 1 hydrophobic, 2 donor-acceptor)
+    float4 gmm[kNT][kNT][kK];      // (pi, mu, -1/(2 sigma^2), 1/sigma^2)
+};
+
+struct DevPocket {
+    const float4* atoms;           // [M + 1]: (x, y, z, type bits); atoms[M] = far sentinel
+    const uint32_t* cell_start;
+    const uint16_t* cand;
+    const DevParams* params;
+    int M;
+    int nx, ny, nz;
+    float gx, gy, gz, inv_h;
+    float box_lo[3], box_hi[3];
+};
+
+struct LigHdr {
+    int n_atoms, n_tor, atom_off, tor_off;
+    int pair_off, n_pairs, pad0, pad1;
+};
+
+struct DevBatch {
+    int n_lig, max_atoms, max_tor, dof_stride, n_fields;
+    const LigHdr* lig;
+    const float4* atom_y;          // local coords about the root centroid, w = type bits
+    const int* atom_orig;          // input index of each packed atom
+    const int4* tor_idx;           // (parent atom, child atom, subtree begin, subtree end)
+    const float4* tor_u;           // unit axis, input geometry
+    const float4* tor_p;           // parent atom, local coords
+    const uint32_t* pairs;         // i | j << 8 | ti << 16 | tj << 24
+};
+
+// Sampler state fields per pose (SoA over poses inside each ligand):
+//   [0,6) Adam m of (t, w); [6,12) Adam v; [12,19) saved (t, q); 19 E_cur; 20 E_saved;
+//   21 status bits; then T_max each of m_theta, v_theta, saved theta.
+constexpr int kFieldM = 0, kFieldV = 6, kFieldSaved = 12, kFieldEcur = 19, kFieldEsaved = 20,
+              kFieldStatus = 21, kFieldTheta = 22;
+TRIDS_HD inline int state_fields(int max_tor) { return kFieldTheta + 3 * max_tor; }
+TRIDS_HD inline int trace_record(int max_tor) { return 2 * max_tor + 14; }
+
+}  // namespace trids

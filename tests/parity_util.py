@@ -1,0 +1,210 @@
+"""Shared helpers of the GPU parity tests: build inputs, run the oracle, compare.
+
+Tolerances (stated for the method's FP32 results against the FP64 oracle):
+  energy    |dE| <= max(1e-3 kcal/mol, 1e-5 |E|) + straddle slack
+  gradient  per block (t, rotation, torsions): |g - g_ref| / max(|g_ref|, 1e-3) <= 1e-3,
+            plus slack for pairs sitting on a cutoff or kink
+  states    t and theta within 1e-4 (theta on the circle), q within 1e-4 as a rotation
+Integer results (topology, top-k indices, perturbed variable, acceptance decisions)
+must match exactly, except decisions the oracle marks as near ties.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+import oracle
+from paper_2510_24186_b300 import synth
+
+E_ABS, E_REL, G_REL, G_FLOOR, S_TOL = 1e-3, 1e-5, 1e-3, 1e-3, 1e-4
+
+
+def score_params(term_set=0, cutoff=8.0, seed=7, K=2):
+    from paper_2510_24186_b300 import api
+    if term_set == 0:
+        return api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, cutoff)
+    return api.ScoreParams(1, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.TRIDS_WEIGHTS, cutoff, gmm=gmm_table(seed, K))
+
+
+def gmm_table(seed=7, K=2):
+    rng = np.random.default_rng(seed)
+    g = np.zeros((8, 8, K, 3))
+    g[..., 0] = rng.uniform(0.2, 1.0, (8, 8, K))
+    g[..., 1] = rng.uniform(2.0, 4.5, (8, 8, K))
+    g[..., 2] = rng.uniform(0.4, 1.2, (8, 8, K))
+    return g.astype(np.float32).astype(np.float64)
+
+
+def oracle_params(sp):
+    """Oracle parameter block holding the same float32 values the GPU uses."""
+    f = lambda v: [float(np.float32(x)) for x in v]
+    return oracle.make_params(sp.term_set, f(sp.radius), sp.flags, f(sp.w), float(np.float32(sp.cutoff)),
+                              float(np.float32(sp.w_tor)), gmm=None if sp.gmm is None else np.asarray(sp.gmm))
+
+
+def oracle_ligands(ligs):
+    out = []
+    for lg in ligs:
+        st, ol = oracle.pack(lg.xyz.astype(np.float32).astype(np.float64), lg.type, lg.bonds, lg.rotatable)
+        assert st == 0
+        out.append(ol)
+    return out
+
+
+def pocket_arrays(pk):
+    return pk.xyz.astype(np.float32).astype(np.float64), pk.type.astype(np.int32)
+
+
+@dataclasses.dataclass
+class Stats:
+    n: int = 0
+    e_abs: float = 0.0
+    e_rel: float = 0.0
+    g_rel: float = 0.0
+    s_err: float = 0.0
+    straddles: int = 0
+    near_ties: int = 0
+    fails: list = dataclasses.field(default_factory=list)
+
+    def fail(self, msg):
+        if len(self.fails) < 20:
+            self.fails.append(msg)
+
+
+def energy_ok(e_gpu, ev, st: Stats, what=""):
+    d = abs(e_gpu - ev.e_total)
+    st.e_abs = max(st.e_abs, d)
+    st.e_rel = max(st.e_rel, d / max(abs(ev.e_total), 1e-30))
+    st.straddles += ev.n_straddle
+    tol = max(E_ABS, E_REL * abs(ev.e_total)) + ev.e_slack
+    if not (d <= tol) or not math.isfinite(e_gpu):
+        st.fail(f"{what}: E gpu {e_gpu!r} oracle {ev.e_total!r}")
+
+
+def block_ok(g_gpu, g_ref, slack, st: Stats, what=""):
+    g_gpu = np.asarray(g_gpu, dtype=np.float64)
+    g_ref = np.asarray(g_ref, dtype=np.float64)
+    if g_ref.size == 0:
+        return
+    num = np.linalg.norm(g_gpu - g_ref)
+    den = max(np.linalg.norm(g_ref), G_FLOOR)
+    st.g_rel = max(st.g_rel, num / den)
+    if not (num <= G_REL * den + slack):
+        st.fail(f"{what}: |dg| {num:.3e} |g| {np.linalg.norm(g_ref):.3e} slack {slack:.2e}")
+
+
+def grad_slack(ev):
+    # a force jump J on one atom moves a rotation or torsion gradient by at most J times
+    # the lever arm (< 40 A inside a pocket)
+    return 40.0 * ev.g_slack
+
+
+def quat_angle(a, b):
+    a = np.asarray(a, dtype=np.float64) / np.linalg.norm(a)
+    b = np.asarray(b, dtype=np.float64) / np.linalg.norm(b)
+    return 2.0 * math.acos(min(1.0, abs(float(np.dot(a, b)))))
+
+
+def state_err(d_gpu, d_ref, T):
+    d_gpu = np.asarray(d_gpu, dtype=np.float64)
+    d_ref = np.asarray(d_ref, dtype=np.float64)
+    e = float(np.abs(d_gpu[:3] - d_ref[:3]).max())
+    e = max(e, quat_angle(d_gpu[3:7], d_ref[3:7]))
+    if T:
+        dt = (d_gpu[7:7 + T] - d_ref[7:7 + T] + math.pi) % (2 * math.pi) - math.pi
+        e = max(e, float(np.abs(dt).max()))
+    return e
+
+
+def check_trace(trace, poses_g, P, ligs_or, pxyz, ptype, op, cfg_or, S, Lmc, seed, dof_final, e_final,
+                lig_base=0, st: Stats | None = None) -> Stats:
+    """Per-evaluation parity of a sampler trace.
+
+    trace [S, n_trace, rec] (GPU float32), poses_g = global pose ids (l * P + p) of the slots.
+    For every traced pose and evaluation: the oracle re-scores the GPU's state in FP64 and
+    compares energy and gradient; it then applies the method's next action (Adam update,
+    or Metropolis decision + perturbation at a loop boundary) in FP64 to the GPU's state
+    and gradient and compares with the GPU's next state; finally the returned state and
+    energy are checked.
+    """
+    st = st or Stats()
+    trace = np.asarray(trace, dtype=np.float64)
+    D = (trace.shape[2] - 14) // 2 + 7
+    sched = []
+    for l in range(Lmc):
+        for j in range(oracle.loop_steps(S, Lmc, l)):
+            sched.append((l, j, oracle.loop_steps(S, Lmc, l)))
+    for slot, g in enumerate(poses_g):
+        l, p = divmod(int(g), P)
+        lg = ligs_or[l]
+        T = lg.n_tor
+        lig_id = lig_base + l
+        init = oracle.init_pose(cfg_or, T, lig_id, p)
+        e0 = state_err(trace[0, slot, :7 + T], init, T)
+        st.s_err = max(st.s_err, e0)
+        if e0 > S_TOL:
+            st.fail(f"pose {g}: initial state differs by {e0:.2e}")
+        m = v = None
+        e_cur = e_saved = None
+        saved = None
+        for s in range(S):
+            rec = trace[s, slot]
+            dof = rec[:7 + T]
+            E = rec[D]
+            gt, tau, gth = rec[D + 1:D + 4], rec[D + 4:D + 7], rec[D + 7:D + 7 + T]
+            stt, ev = oracle.score(op, pxyz, ptype, lg, dof)
+            st.n += 1
+            energy_ok(E, ev, st, f"pose {g} step {s}")
+            sl = grad_slack(ev)
+            block_ok(gt, ev.g_dof[:3], sl, st, f"pose {g} step {s} dE/dt")
+            block_ok(tau, ev.tau[:], sl, st, f"pose {g} step {s} torque")
+            block_ok(gth, ev.g_dof[7:7 + T], sl, st, f"pose {g} step {s} dE/dtheta")
+            loop, j, n = sched[s]
+            if j == 0:
+                m, v = np.zeros(6 + T), np.zeros(6 + T)
+            grad = np.concatenate([gt, tau, gth]).astype(np.float64)
+            if j < n - 1:
+                nxt = dof.copy()
+                oracle.adam_step(cfg_or, T, j + 1, grad, m, v, nxt)
+            else:
+                e_new = float(E)
+                if loop == 0:
+                    base, e_cur = dof.copy(), e_new
+                else:
+                    u = oracle.metropolis_u(seed, lig_id, p, loop)
+                    acc = oracle.metropolis_accept(e_new, e_saved, cfg_or.beta, u)
+                    thr = math.exp(min(50.0, -cfg_or.beta * (e_new - e_saved)))
+                    near = abs(u - thr) < 1e-5
+                    alt_base = saved.copy() if acc else dof.copy()
+                    base = dof.copy() if acc else saved.copy()
+                    e_cur = e_new if acc else e_saved
+                    alt_e = e_saved if acc else e_new
+                nxt = None
+                if s + 1 < S:
+                    l2 = sched[s + 1][0]
+                    saved, e_saved = base.copy(), e_cur
+                    _, nxt = oracle.perturb(cfg_or, T, lig_id, p, l2, base)
+                    if loop > 0 and near:
+                        _, alt = oracle.perturb(cfg_or, T, lig_id, p, l2, alt_base)
+                        if state_err(trace[s + 1, slot, :7 + T], alt, T) <= S_TOL:
+                            st.near_ties += 1
+                            nxt, saved, e_saved, e_cur = alt, alt_base.copy(), alt_e, alt_e
+                else:
+                    fin = base
+                    if loop > 0 and near and state_err(dof_final[l, p, :7 + T], alt_base, T) <= S_TOL:
+                        st.near_ties += 1
+                        fin, e_cur = alt_base, alt_e
+                    ef = state_err(dof_final[l, p, :7 + T], fin, T)
+                    st.s_err = max(st.s_err, ef)
+                    if ef > S_TOL:
+                        st.fail(f"pose {g}: final state differs by {ef:.2e}")
+                    if float(e_final[l, p]) != float(np.float32(e_cur)):
+                        st.fail(f"pose {g}: final energy {float(e_final[l, p])} vs {e_cur}")
+            if nxt is not None and s + 1 < S:
+                es = state_err(trace[s + 1, slot, :7 + T], nxt, T)
+                st.s_err = max(st.s_err, es)
+                if es > S_TOL:
+                    st.fail(f"pose {g} step {s}->{s + 1}: state differs by {es:.2e}")
+    return st

@@ -1,0 +1,71 @@
+"""Host-side checks of libtrids that need no GPU: exports, packing, argument errors."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2510_24186_b300 import _lib, api, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "trids.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(trids_\w+)\s*\(", hdr, re.M))
+    assert declared == set(_lib.EXPORTS)
+    L = _lib.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert L.trids_version() >= 100
+
+
+def test_host_pack_matches_oracle_bit_exact(orc):
+    rng = np.random.default_rng(21)
+    ligs = [synth.workload(1).ligands[0]]
+    ligs += [synth.gen_ligand(rng, int(rng.integers(1, 71)), int(rng.integers(0, 21))) for _ in range(60)]
+    ligs += [synth.gen_ligand(rng, 70, 20), synth.gen_ligand(rng, 1, 0), synth.gen_ligand(rng, 2, 0)]
+    for lg in ligs:
+        a = api.pack_topology(lg.xyz, lg.type, lg.bonds, lg.rotatable)
+        st, ol = orc.pack(lg.xyz.astype(np.float32).astype(np.float64), lg.type, lg.bonds, lg.rotatable)
+        assert st == 0
+        np.testing.assert_array_equal(a, orc.topology(ol))
+
+
+@pytest.mark.parametrize("case", ["ring_rot", "disconnected", "dup", "type", "nan", "big", "self"])
+def test_host_pack_rejects_bad_ligands(case):
+    lg = synth.workload(1).ligands[0]
+    xyz, t, b, r = lg.xyz.copy(), lg.type.copy(), lg.bonds.copy(), lg.rotatable.copy()
+    if case == "ring_rot":
+        b = np.vstack([b, [[0, 9]]]) if not any((b == [0, 9]).all(1)) else b
+        r = np.concatenate([r, [1]])
+    elif case == "disconnected":
+        b, r = b[1:], r[1:]
+    elif case == "dup":
+        b, r = np.vstack([b, b[:1]]), np.concatenate([r, [0]])
+    elif case == "type":
+        t[0] = 8
+    elif case == "nan":
+        xyz[1, 1] = np.inf
+    elif case == "big":
+        big = synth.gen_ligand(np.random.default_rng(0), 71, 0)
+        xyz, t, b, r = big.xyz, big.type, big.bonds, big.rotatable
+    elif case == "self":
+        b = np.vstack([b, [[3, 3]]])
+        r = np.concatenate([r, [0]])
+    with pytest.raises(_lib.TridsError) as e:
+        api.pack_topology(xyz, t, b, r)
+    assert e.value.code == _lib.EINVAL
+    assert _lib.lib().trids_last_error().decode() != ""
+
+
+def test_null_arguments_are_rejected_without_a_gpu():
+    L = _lib.lib()
+    assert L.trids_score_grad(None, None, 1, None, None, None, None, None, None, None, None, None) == _lib.EINVAL
+    assert L.trids_sample(None, None, None, None, None, None, None) == _lib.EINVAL
+    assert L.trids_topk(None, 1, None, None, 1, 1.0, None, None, None) == _lib.EINVAL
+    assert L.trids_state_floats(None, 4) == 0
+    out = C.c_void_p()
+    assert L.trids_pack_ligands(None, 1, None, None, None, None, None, None, C.byref(out)) == _lib.EINVAL
+    assert out.value is None
