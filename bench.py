@@ -169,6 +169,7 @@ def main():
     ap.add_argument("--per-ligand-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--n-lig", type=int, default=0, help="first N ligands only (small profiling case)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -184,7 +185,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = synth.workload(2)
+    w = synth.workload(2, n_lig=args.n_lig or None)
     sp = api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, w.cutoff)
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
     arrays = synth.concat_ligands(w.ligands)
