@@ -218,6 +218,36 @@ int trids_score_grad(const trids_pocket* pk, const trids_batch* b, int32_t poses
                      float* g_xyz, const float* e_bar, float* g_w, float* g_radius,
                      void* stream);
 
+/*
+ * trids_score_grad_noalloc -- the same energies and gradients as trids_score_grad, but
+ * the call allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ * The paper has no counterpart; this entry point exists for callers that cannot let a
+ * library allocate device memory in the middle of their work: programs that hand out
+ * all device memory from their own pool or a fixed arena reserved at start-up, code
+ * recording work into a CUDA stream capture (where an allocation would break or
+ * serialise the capture), and latency-sensitive loops that cannot afford the device-wide
+ * synchronisation an allocation can cause.  (trids_score_grad allocates its work list and
+ * its parameter-gradient partials on first use of a pose count.)
+ *   Arguments, layouts and results are those of trids_score_grad; the caller still owns
+ *   and passes every input and output buffer.  Parameter sums are reduced in a fixed
+ *   order, which differs from trids_score_grad's, so g_w and g_radius agree with it to
+ *   rounding, not bit for bit.
+ *   Scratch: a 1 MiB array compiled into the library, one per device that loads it, held
+ *   until the process exits.  It holds 256 bytes of work counter, 8 bytes per work item
+ *   (one item = one ligand x 32 poses) and, when g_w or g_radius is requested, 84 more
+ *   bytes per item.  Larger requests fail with TRIDS_EINVAL and a message giving the
+ *   bytes needed; split the batch or use trids_score_grad.
+ *   The first call on a device looks up the array's device address; make that first call
+ *   before any stream capture that includes this entry point.  Every call reuses the same
+ *   array (it keeps the previous call's contents; each call resets what must start at
+ *   zero), so calls that can overlap on the GPU -- on two streams, or from two host
+ *   threads -- race with each other and must be serialised by the caller.
+ */
+int trids_score_grad_noalloc(const trids_pocket* pk, const trids_batch* b, int32_t poses,
+                             const float* dof, float* energy, float* e_inter, float* g_dof,
+                             float* g_xyz, const float* e_bar, float* g_w, float* g_radius,
+                             void* stream);
+
 /* Floats of sampler state per batch: n_lig * poses * dims.state_fields. */
 int64_t trids_state_floats(const trids_batch* b, int32_t poses);
 

@@ -13,8 +13,8 @@ MODE_PERSISTENT, MODE_PER_LIGAND = 0, 1
 
 EXPORTS = ("trids_last_error", "trids_version", "trids_make_pocket", "trids_set_params", "trids_free_pocket",
            "trids_pack_ligands", "trids_free_batch", "trids_batch_info", "trids_batch_query",
-           "trids_pack_topology", "trids_score_grad", "trids_state_floats", "trids_sample", "trids_topk",
-           "trids_sync")
+           "trids_pack_topology", "trids_score_grad", "trids_score_grad_noalloc", "trids_state_floats",
+           "trids_sample", "trids_topk", "trids_sync")
 
 
 class Params(C.Structure):
@@ -70,6 +70,7 @@ def lib(build_if_missing: bool = True):
     L.trids_batch_query.argtypes = [vp, vp, vp, i32, vp, i32]
     L.trids_pack_topology.argtypes = [i32, vp, vp, i32, i32, vp, vp, vp, i32, P(i32)]
     L.trids_score_grad.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.trids_score_grad_noalloc.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.trids_state_floats.argtypes = [vp, i32]
     L.trids_state_floats.restype = i64
     L.trids_sample.argtypes = [vp, vp, P(SampleCfg), vp, vp, vp, vp]

@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -947,7 +948,20 @@ __global__ void k_status(const float* state, int n_lig, int P, int n_fields, int
     }
 }
 
+// Item list in plain (ligand, tile) order, written into caller-independent scratch.
+__global__ void k_items_natural(int2* items, int n_lig, int tiles) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_lig * tiles) items[i] = make_int2(i / tiles, (i % tiles) * 32);
+}
+
 }  // namespace
+
+// =============================================================== allocation-free scoring
+// Scratch of trids_score_grad_noalloc: one statically sized device array per device
+// that loads the library (kept until the process exits).  Layout: work counter at
+// offset 0, item list at 256, parameter partials after it (256-aligned).
+constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // =============================================================== host objects
 struct trids_pocket {
@@ -1610,6 +1624,91 @@ int trids_sync(const trids_batch* b, int32_t poses, const float* state, void* st
     CK(cudaMemcpy(flags, b->d_err, sizeof flags, cudaMemcpyDeviceToHost));
     if (flags[0]) return fail(TRIDS_ECUDA, "shared-memory staging did not complete");
     if (state && flags[1]) return fail(TRIDS_ENONFINITE, "a pose produced a non-finite energy (status %d)", flags[1]);
+    return TRIDS_OK;
+}
+
+// Device address of g_noalloc_scratch for `dev`, looked up once per device with that
+// device current (host code cannot use the symbol itself as a device address).
+static int noalloc_scratch(int dev, unsigned char** out) {
+    static std::mutex mu;
+    static void* addr[256] = {};
+    if (dev < 0 || dev >= 256) return fail(TRIDS_EINVAL, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(TRIDS_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+        addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(addr[dev]);
+    return TRIDS_OK;
+}
+
+int trids_score_grad_noalloc(const trids_pocket* pk, const trids_batch* b, int32_t poses, const float* dof,
+                             float* energy, float* e_inter, float* g_dof, float* g_xyz, const float* e_bar,
+                             float* g_w, float* g_radius, void* stream) {
+    g_err.clear();
+    if (!pk || !b) return fail(TRIDS_EINVAL, "pocket or batch is NULL");
+    if (pk->device != b->device) return fail(TRIDS_EINVAL, "pocket and batch live on different devices");
+    if (poses < 1) return fail(TRIDS_EINVAL, "poses must be >= 1");
+    int rc = device_guard(pk->device);
+    if (rc) return rc;
+    if ((rc = check_device_ptr(dof, "dof", false)) || (rc = check_device_ptr(energy, "energy", false)) ||
+        (rc = check_device_ptr(e_inter, "e_inter", true)) || (rc = check_device_ptr(g_dof, "g_dof", true)) ||
+        (rc = check_device_ptr(g_xyz, "g_xyz", true)) || (rc = check_device_ptr(e_bar, "e_bar", true)) ||
+        (rc = check_device_ptr(g_w, "g_w", true)) || (rc = check_device_ptr(g_radius, "g_radius", true)))
+        return rc;
+    const bool params = g_w || g_radius;
+    const int tiles = (poses + 31) / 32;
+    const size_t n_items = (size_t)b->dims.n_lig * tiles;
+    const size_t items_off = 256;
+    const size_t partials_off = align_up(items_off + n_items * sizeof(int2), 256);
+    const size_t need = params ? partials_off + n_items * (5 + kNT) * sizeof(float) : items_off + n_items * sizeof(int2);
+    if (n_items > (size_t)INT32_MAX || need > kNoAllocScratchBytes)
+        return fail(TRIDS_EINVAL,
+                    "trids_score_grad_noalloc needs %zu bytes of static scratch for %d ligands x %d poses%s; "
+                    "the limit is %zu bytes: split the batch or call trids_score_grad",
+                    need, b->dims.n_lig, poses, params ? " with parameter gradients" : "", kNoAllocScratchBytes);
+    unsigned char* scratch = nullptr;
+    if ((rc = noalloc_scratch(pk->device, &scratch))) return rc;
+    Layout L;
+    const int warps = pick_warps(4, pk, b, params, &L);
+    if (!warps) return fail(TRIDS_EINVAL, "pocket of %d atoms does not fit in shared memory", pk->M);
+    ScoreArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.pk = pk->view(); A.B = b->view(); A.P = poses; A.dof = dof; A.energy = energy; A.e_inter = e_inter;
+    A.g_dof = g_dof; A.g_xyz = g_xyz; A.e_bar = e_bar;
+    A.partials = reinterpret_cast<float*>(scratch + partials_off);
+    A.items = reinterpret_cast<const int2*>(scratch + items_off);
+    A.n_items = (int)n_items; A.counter = reinterpret_cast<unsigned int*>(scratch); A.err = b->d_err;
+    A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.mbar_off = L.mbar_off;
+    A.warp_off = L.warp_off; A.warp_bytes = L.warp_bytes;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: reset the counter, rewrite the items
+    CK(cudaMemsetAsync(A.counter, 0, sizeof(unsigned int), st));
+    k_items_natural<<<(int)((n_items + 255) / 256), 256, 0, st>>>(reinterpret_cast<int2*>(scratch + items_off),
+                                                                  b->dims.n_lig, tiles);
+    CK(cudaGetLastError());
+    int grid = 0;
+    const bool trids_terms = pk->prm.term_set == TRIDS_TERMS_TRIDS;
+#define LAUNCH_SCORE_NA(TS, PR)                                                                \
+    do {                                                                                       \
+        auto kern = k_score<TS, PR>;                                                           \
+        if ((rc = grid_for(kern, warps, L.total, pk->device, (int)n_items, &grid))) return rc; \
+        kern<<<grid, 32 * warps, L.total, st>>>(A);                                            \
+    } while (0)
+    if (trids_terms) {
+        if (params) LAUNCH_SCORE_NA(TRIDS_TERMS_TRIDS, true); else LAUNCH_SCORE_NA(TRIDS_TERMS_TRIDS, false);
+    } else {
+        if (params) LAUNCH_SCORE_NA(TRIDS_TERMS_VINA5, true); else LAUNCH_SCORE_NA(TRIDS_TERMS_VINA5, false);
+    }
+#undef LAUNCH_SCORE_NA
+    CK(cudaGetLastError());
+    if (params) {
+        k_reduce_params<<<1, 32, 0, st>>>(A.partials, (int)n_items, g_w, g_radius, b->n_types);
+        CK(cudaGetLastError());
+    }
     return TRIDS_OK;
 }
 
