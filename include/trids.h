@@ -133,7 +133,7 @@ int trids_version(void);
  * receptor atoms near the reference ligand; translation range [box_min, box_max]
  * with box_min = center - size/2 and box_max = center + size/2).
  *   xyz   host [n_atoms][3] float32 coordinates (A), type host [n_atoms] int32 in
- *         [0, prm->n_types); n_atoms in [1, 65535].
+ *         [0, prm->n_types); n_atoms in [1, 8191].
  *   cell  edge (A) of the candidate grid used to cull ligand-pocket pairs; 0 selects
  *         1.0 A.  The grid changes no result, only which pairs are tested.
  *   prm   scoring parameters, copied.

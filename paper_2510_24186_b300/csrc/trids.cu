@@ -107,46 +107,6 @@ __device__ __forceinline__ void quat_premul(const float r[4], float q[4]) {
 __device__ __forceinline__ float wrap_pi(float a) { return a - kTwoPi * floorf((a + kPi) * (1.0f / kTwoPi)); }
 
 // ------------------------------------------------------------------ pair terms
-// Vina form on the surface distance d = r - R_a - R_b (see trids.h).  Returns the
-// weighted energy; fr = (dE/dr)/r.  With TERMS, et[t] gets the unweighted term values
-// and dRs = dE/d(R_a + R_b).
-template <bool TERMS>
-__device__ __forceinline__ float pair_vina(float r2, float rsum, int pf, const float* __restrict__ w,
-                                           float& fr, float* et, float& dRs) {
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    const float d = r - rsum;
-    const float g1 = __expf(-4.f * d * d);
-    const float b = fmaf(0.5f, d, -1.5f);
-    const float g2 = __expf(-b * b);
-    const float dn = fminf(d, 0.f);
-    float hy = 0.f, dhy = 0.f, hb = 0.f, dhb = 0.f;
-    if (pf & 1) {
-        hy = d < 0.5f ? 1.f : (d < 1.5f ? 1.5f - d : 0.f);
-        dhy = (d >= 0.5f && d < 1.5f) ? -1.f : 0.f;
-    }
-    if (pf & 2) {
-        hb = d < -0.7f ? 1.f : (d < 0.f ? d * (-1.f / 0.7f) : 0.f);
-        dhb = (d >= -0.7f && d < 0.f) ? (-1.f / 0.7f) : 0.f;
-    }
-    float e = w[0] * g1;
-    e = fmaf(w[1], g2, e);
-    e = fmaf(w[2], dn * dn, e);
-    e = fmaf(w[3], hy, e);
-    e = fmaf(w[4], hb, e);
-    float dd = w[0] * (-8.f * d * g1);
-    dd = fmaf(w[1], -b * g2, dd);
-    dd = fmaf(w[2], 2.f * dn, dd);
-    dd = fmaf(w[3], dhy, dd);
-    dd = fmaf(w[4], dhb, dd);
-    fr = dd * rinv;
-    if (TERMS) {
-        et[0] = g1; et[1] = g2; et[2] = dn * dn; et[3] = hy; et[4] = hb;
-        dRs = -dd;
-    }
-    return e;
-}
-
 // TRIDS E_dock terms on r (see trids.h).
 template <bool TERMS>
 __device__ __forceinline__ float pair_trids(float r2, float rsum, int pf, const float4* __restrict__ gmm,
@@ -195,13 +155,14 @@ __device__ __forceinline__ float pair_trids(float r2, float rsum, int pf, const 
 // ------------------------------------------------------------------ shared layout
 struct Smem {
     const DevParams* P;
-    const float4* pocket;
+    const float4* pocket;      // (x, y, z, radius), [M + 1]
+    const uint8_t* ptype;      // pocket atom types, [M + 1]
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-    size_t params_bytes, pocket_off, pocket_bytes, mbar_off, warp_off, warp_bytes, total;
+    size_t params_bytes, pocket_off, pocket_bytes, ptype_off, ptype_bytes, mbar_off, warp_off, warp_bytes, total;
 };
 
 __host__ __device__ inline size_t warp_smem_bytes(int Lmax, int Tmax, bool params) {
@@ -213,7 +174,9 @@ inline Layout make_layout(int term_set, int M, int Lmax, int Tmax, int warps, bo
     L.params_bytes = term_set == TRIDS_TERMS_TRIDS ? sizeof(DevParams) : offsetof(DevParams, gmm);
     L.pocket_off = align_up(L.params_bytes, 128);
     L.pocket_bytes = (size_t)(M + 1) * sizeof(float4);
-    L.mbar_off = align_up(L.pocket_off + L.pocket_bytes, 16);
+    L.ptype_off = L.pocket_off + L.pocket_bytes;
+    L.ptype_bytes = align_up((size_t)(M + 1), 16);
+    L.mbar_off = align_up(L.ptype_off + L.ptype_bytes, 16);
     L.warp_off = align_up(L.mbar_off + 16, 128);
     L.warp_bytes = warp_smem_bytes(Lmax, Tmax, params);
     L.total = L.warp_off + L.warp_bytes * warps;
@@ -224,10 +187,11 @@ inline Layout make_layout(int term_set, int M, int Lmax, int Tmax, int warps, bo
 // completing on one mbarrier.  Returns false (and sets *err) if the copy did not
 // complete within a bounded wait.
 __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t params_bytes, size_t pocket_off,
-                            size_t mbar_off, int* err) {
+                            size_t ptype_off, size_t mbar_off, int* err) {
     const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(smem + mbar_off);
     const uint32_t bytes_p = (uint32_t)params_bytes;
     const uint32_t bytes_k = (uint32_t)((size_t)(pk.M + 1) * sizeof(float4));
+    const uint32_t bytes_t = (uint32_t)align_up((size_t)(pk.M + 1), 16);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -235,7 +199,8 @@ __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t par
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes_p + bytes_k)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
+                     "r"(bytes_p + bytes_k + bytes_t)
                      : "memory");
         const uint32_t dp = (uint32_t)__cvta_generic_to_shared(smem);
         const uint32_t dk = (uint32_t)__cvta_generic_to_shared(smem + pocket_off);
@@ -246,6 +211,11 @@ __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t par
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dk),
             "l"(pk.atoms), "r"(bytes_k), "r"(mbar)
+            : "memory");
+        const uint32_t dt = (uint32_t)__cvta_generic_to_shared(smem + ptype_off);
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dt),
+            "l"(pk.ptype), "r"(bytes_t), "r"(mbar)
             : "memory");
     }
     uint32_t done = 0;
@@ -315,6 +285,161 @@ struct ParamAcc {
     float gw[5];
 };
 
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Branch-free Vina-form pair on surface distance d = r - rsum.  hyd / hb are 1 for a
+// hydrophobic / donor-acceptor pair, else 0.  Returns the weighted energy and its
+// derivative dd = dE/dd (= dE/dr); rinv = 1/r.  With TERMS, et[] gets the unweighted
+// terms.  Piecewise pieces use saturate(): the kinks sit where the clamp engages.
+template <bool TERMS>
+__device__ __forceinline__ float vina_eval(float r2, float rsum, float hyd, float hb, const float w[5], float& dd,
+                                           float& rinv, float* et) {
+    constexpr float kC1 = -5.770780163555854f;   // -4 log2(e): exp(-(d/0.5)^2) = 2^(kC1 d^2)
+    constexpr float kC2 = -1.4426950408889634f;  // -log2(e)
+    const float rr = fmaxf(r2, 1e-12f);
+    rinv = rsqrtf(rr);
+    const float d = rr * rinv - rsum;
+    const float g1 = ex2_approx(d * d * kC1);
+    const float b = fmaf(0.5f, d, -1.5f);
+    const float g2 = ex2_approx(b * b * kC2);
+    const float dn = fminf(d, 0.f);
+    const float w3h = w[3] * hyd, w4h = w[4] * hb;
+    const float hraw = 1.5f - d;
+    const float hy = __saturatef(hraw);
+    const float hbraw = d * (-1.f / 0.7f);
+    const float hbv = __saturatef(hbraw);
+    float e = w[0] * g1;
+    e = fmaf(w[1], g2, e);
+    e = fmaf(w[2], dn * dn, e);
+    e = fmaf(w3h, hy, e);
+    e = fmaf(w4h, hbv, e);
+    float g = w[0] * (-8.f * d * g1);
+    g = fmaf(w[1], -b * g2, g);
+    g = fmaf(w[2], 2.f * dn, g);
+    g -= (hy == hraw) ? w3h : 0.f;
+    g -= (hbv == hbraw) ? w4h * (1.f / 0.7f) : 0.f;
+    dd = g;
+    if (TERMS) {
+        et[0] = g1; et[1] = g2; et[2] = dn * dn; et[3] = hyd * hy; et[4] = hb * hbv;
+    }
+    return e;
+}
+
+// Candidate-grid cell range (entries [beg, end) of pk.cand) of a point; empty outside
+// the grid, where no pocket atom lies within the cutoff.
+__device__ __forceinline__ void cell_range(const DevPocket& pk, float x, float y, float z, uint32_t& beg,
+                                           uint32_t& end) {
+    const float fx = (x - pk.gx) * pk.inv_h, fy = (y - pk.gy) * pk.inv_h, fz = (z - pk.gz) * pk.inv_h;
+    beg = end = 0;
+    if (fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)pk.nx && fy < (float)pk.ny && fz < (float)pk.nz) {
+        const int cx = min((int)fx, pk.nx - 1), cy = min((int)fy, pk.ny - 1), cz = min((int)fz, pk.nz - 1);
+        const size_t cell = ((size_t)cz * pk.ny + cy) * pk.nx + cx;
+        beg = __ldg(&pk.cell_start[cell]);
+        end = __ldg(&pk.cell_start[cell + 1]);
+    }
+}
+
+// Ligand-pocket pairs of each lane's pose.  Each lane walks its own stream of
+// (atom, 8-candidate block) so the lanes of a warp stay busy until the whole pose is
+// done; the next atom's cell range is fetched one atom ahead.  A candidate entry is
+// the pocket index (13 bits) with the pocket atom's flags in the top 3 bits; the pocket
+// float4 carries (x, y, z, radius).  The Vina-form block is branch-free: every
+// candidate is evaluated and masked by r^2 < cutoff^2, so the eight pairs of a block
+// are independent instruction streams.  Forces accumulate per atom in registers and
+// are added to W.G when the lane leaves the atom.  Returns the lane's ligand-pocket
+// energy.
+template <int TS, bool PARAMS, bool COUNT>
+__device__ float inter_pass(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const Warp& W,
+                            const float w[5], float ebar, ParamAcc& acc, uint32_t& npairs) {
+    const DevParams& P = *S.P;
+    const float cut2 = P.cut2;
+    const int L = h.n_atoms;
+    const float4* __restrict__ pocket = S.pocket;
+    const uint16_t* __restrict__ cand = pk.cand;
+    float e_sum = 0.f;
+    int i = 0;
+    float xi = W.X(0, 0), yi = W.X(1, 0), zi = W.X(2, 0);
+    int ti = __float_as_int(__ldg(&B.atom_y[h.atom_off]).w);
+    uint32_t cur, end, nb = 0, ne = 0;
+    cell_range(pk, xi, yi, zi, cur, end);
+    if (L > 1) cell_range(pk, W.X(0, 1), W.X(1, 1), W.X(2, 1), nb, ne);
+    float ri = P.radius[ti];
+    uint32_t fi = P.tflags[ti];
+    float ax = 0.f, ay = 0.f, az = 0.f, ae = 0.f;
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    uint4 v = cur < end ? __ldg(reinterpret_cast<const uint4*>(cand + cur)) : zero4;   // block at cur
+    uint4 vn = nb < ne ? __ldg(reinterpret_cast<const uint4*>(cand + nb)) : zero4;     // first block of atom i+1
+    for (;;) {
+        while (cur >= end) {                     // leave atom i (per lane)
+            W.G(0, i) += ax; W.G(1, i) += ay; W.G(2, i) += az;
+            e_sum += ae;
+            ax = ay = az = ae = 0.f;
+            if (++i >= L) return e_sum;
+            xi = W.X(0, i); yi = W.X(1, i); zi = W.X(2, i);
+            ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
+            ri = P.radius[ti];
+            fi = P.tflags[ti];
+            cur = nb; end = ne; v = vn;
+            nb = ne = 0;
+            if (i + 1 < L) cell_range(pk, W.X(0, i + 1), W.X(1, i + 1), W.X(2, i + 1), nb, ne);
+            vn = nb < ne ? __ldg(reinterpret_cast<const uint4*>(cand + nb)) : zero4;
+        }
+        const uint4 vc = v;
+        if (cur + 8 < end) v = __ldg(reinterpret_cast<const uint4*>(cand + cur + 8));   // prefetch
+        cur += 8;
+        const uint32_t wv[4] = {vc.x, vc.y, vc.z, vc.w};
+        // pair-flag selectors: hydrophobic needs both bit0; donor-acceptor needs
+        // (donor_i & acceptor_j) | (acceptor_i & donor_j)
+        const uint32_t f_hyd = fi & 1u;
+        const uint32_t f_hb = ((fi & 2u) << 1) | ((fi & 4u) >> 1);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const uint32_t ent = (s & 1) ? (wv[s >> 1] >> 16) : (wv[s >> 1] & 0xffffu);
+            const int j = (int)(ent & 0x1fffu);
+            const uint32_t fj = ent >> 13;
+            const float4 a = pocket[j];
+            const float dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const bool in = r2 < cut2;
+            if (TS == TRIDS_TERMS_VINA5) {
+                float dd, rinv, et[5];
+                const float e = vina_eval<PARAMS>(r2, ri + a.w, (f_hyd & fj) ? 1.f : 0.f, (f_hb & fj) ? 1.f : 0.f,
+                                                  w, dd, rinv, et);
+                const float fr = in ? dd * rinv : 0.f;
+                ae += in ? e : 0.f;
+                ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
+                if (PARAMS && in) {
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
+                    const int tj = S.ptype[j];
+                    W.grs[ti * 32 + W.lane] -= ebar * dd;
+                    W.grs[tj * 32 + W.lane] -= ebar * dd;
+                }
+            } else if (in) {
+                const int tj = S.ptype[j];
+                const float2 pt = P.pairtab[ti][tj];
+                float fr, dRs;
+                float et[5];
+                const float e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, __float_as_int(pt.y), &P.gmm[ti][tj][0],
+                                                   P.gmm_k, true, w, fr, et, dRs);
+                ae += e;
+                ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
+                if (PARAMS) {
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
+                    W.grs[ti * 32 + W.lane] += ebar * dRs;
+                    W.grs[tj * 32 + W.lane] += ebar * dRs;
+                }
+            }
+            if (COUNT) npairs += in ? 1u : 0u;
+        }
+    }
+}
+
 // Score and per-atom forces of the warp's poses.  Forces go to W.G, the returned value
 // is E_total; *e_inter gets the ligand-pocket part.  With PARAMS, the per-term sums
 // (scaled by ebar) go to acc.gw and the radius derivatives to W.grs.
@@ -331,85 +456,69 @@ __device__ float score_pose(const DevBatch& B, const DevPocket& pk, const Smem& 
     float dRs = 0.f;
     // intra-ligand pairs (uniform list across the warp)
     float e_intra = 0.f;
-    for (int q = 0; q < h.n_pairs; ++q) {
-        const uint32_t pw = __ldg(&B.pairs[h.pair_off + q]);
-        const int i = pw & 0xff, j = (pw >> 8) & 0xff, ti = (pw >> 16) & 0xff, tj = pw >> 24;
-        const float dx = W.X(0, i) - W.X(0, j), dy = W.X(1, i) - W.X(1, j), dz = W.X(2, i) - W.X(2, j);
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        if (r2 < cut2) {
-            const float2 pt = P.pairtab[ti][tj];
-            const int pf = __float_as_int(pt.y);
-            float fr;
-            float e;
-            if (TS == TRIDS_TERMS_VINA5)
-                e = pair_vina<PARAMS>(fmaxf(r2, 1e-12f), pt.x, pf, w, fr, et, dRs);
-            else
-                e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, pf, nullptr, 0, false, w, fr, et, dRs);
-            e_intra += e;
-            W.G(0, i) = fmaf(fr, dx, W.G(0, i)); W.G(1, i) = fmaf(fr, dy, W.G(1, i)); W.G(2, i) = fmaf(fr, dz, W.G(2, i));
-            W.G(0, j) = fmaf(-fr, dx, W.G(0, j)); W.G(1, j) = fmaf(-fr, dy, W.G(1, j)); W.G(2, j) = fmaf(-fr, dz, W.G(2, j));
-            if (PARAMS) {
+    if (TS == TRIDS_TERMS_VINA5) {
+        // four pairs at a time: independent loads and pair math, then the force updates
+        // in list order (pairs of a chunk may share atoms)
+        for (int q0 = 0; q0 < h.n_pairs; q0 += 4) {
+            uint32_t pw[4];
 #pragma unroll
-                for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
-                W.grs[ti * 32 + W.lane] += ebar * dRs;
-                W.grs[tj * 32 + W.lane] += ebar * dRs;
+            for (int u = 0; u < 4; ++u) pw[u] = q0 + u < h.n_pairs ? __ldg(&B.pairs[h.pair_off + q0 + u]) : 0u;
+            float fx[4], fy[4], fz[4], ee[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = pw[u] & 0xff, j = (pw[u] >> 8) & 0xff, ti = (pw[u] >> 16) & 0xff, tj = pw[u] >> 24;
+                const float dx = W.X(0, i) - W.X(0, j), dy = W.X(1, i) - W.X(1, j), dz = W.X(2, i) - W.X(2, j);
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                const bool in = (q0 + u < h.n_pairs) && r2 < cut2;
+                const float2 pt = P.pairtab[ti][tj];
+                const int pf = __float_as_int(pt.y);
+                float dd, rinv;
+                const float e = vina_eval<PARAMS>(r2, pt.x, (pf & 1) ? 1.f : 0.f, (pf & 2) ? 1.f : 0.f, w, dd, rinv, et);
+                const float fr = in ? dd * rinv : 0.f;
+                fx[u] = fr * dx; fy[u] = fr * dy; fz[u] = fr * dz;
+                ee[u] = in ? e : 0.f;
+                if (PARAMS && in) {
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
+                    W.grs[ti * 32 + W.lane] -= ebar * dd;
+                    W.grs[tj * 32 + W.lane] -= ebar * dd;
+                }
+                if (COUNT) npairs += in ? 1u : 0u;
             }
-            if (COUNT) ++npairs;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = pw[u] & 0xff, j = (pw[u] >> 8) & 0xff;
+                e_intra += ee[u];
+                W.G(0, i) += fx[u]; W.G(1, i) += fy[u]; W.G(2, i) += fz[u];
+                W.G(0, j) -= fx[u]; W.G(1, j) -= fy[u]; W.G(2, j) -= fz[u];
+            }
+        }
+    } else {
+        for (int q = 0; q < h.n_pairs; ++q) {
+            const uint32_t pw = __ldg(&B.pairs[h.pair_off + q]);
+            const int i = pw & 0xff, j = (pw >> 8) & 0xff, ti = (pw >> 16) & 0xff, tj = pw >> 24;
+            const float dx = W.X(0, i) - W.X(0, j), dy = W.X(1, i) - W.X(1, j), dz = W.X(2, i) - W.X(2, j);
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (r2 < cut2) {
+                const float2 pt = P.pairtab[ti][tj];
+                float fr;
+                const float e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, __float_as_int(pt.y), nullptr, 0, false, w,
+                                                   fr, et, dRs);
+                e_intra += e;
+                W.G(0, i) = fmaf(fr, dx, W.G(0, i)); W.G(1, i) = fmaf(fr, dy, W.G(1, i)); W.G(2, i) = fmaf(fr, dz, W.G(2, i));
+                W.G(0, j) = fmaf(-fr, dx, W.G(0, j)); W.G(1, j) = fmaf(-fr, dy, W.G(1, j)); W.G(2, j) = fmaf(-fr, dz, W.G(2, j));
+                if (PARAMS) {
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
+                    W.grs[ti * 32 + W.lane] += ebar * dRs;
+                    W.grs[tj * 32 + W.lane] += ebar * dRs;
+                }
+                if (COUNT) ++npairs;
+            }
         }
     }
     // ligand-pocket pairs through the candidate grid
-    float e_lp = 0.f;
-    const float4* __restrict__ pocket = S.pocket;
-    for (int i = 0; i < h.n_atoms; ++i) {
-        const float4 ya = __ldg(&B.atom_y[h.atom_off + i]);
-        const int ti = __float_as_int(ya.w);
-        const float xi = W.X(0, i), yi = W.X(1, i), zi = W.X(2, i);
-        const float fx = (xi - pk.gx) * pk.inv_h, fy = (yi - pk.gy) * pk.inv_h, fz = (zi - pk.gz) * pk.inv_h;
-        uint32_t beg = 0, end = 0;
-        if (fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)pk.nx && fy < (float)pk.ny && fz < (float)pk.nz) {
-            const int cx = min((int)fx, pk.nx - 1), cy = min((int)fy, pk.ny - 1), cz = min((int)fz, pk.nz - 1);
-            const size_t cell = ((size_t)cz * pk.ny + cy) * pk.nx + cx;
-            beg = __ldg(&pk.cell_start[cell]);
-            end = __ldg(&pk.cell_start[cell + 1]);
-        }
-        const float2* __restrict__ prow = P.pairtab[ti];
-        const float4* __restrict__ grow = (TS == TRIDS_TERMS_TRIDS) ? &P.gmm[ti][0][0] : nullptr;
-        float ax = 0.f, ay = 0.f, az = 0.f, ae = 0.f;
-        for (uint32_t k = beg; k < end; k += 8) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(pk.cand + k));
-            const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const int j = (s & 1) ? (int)(wv[s >> 1] >> 16) : (int)(wv[s >> 1] & 0xffff);
-                const float4 a = pocket[j];
-                const float dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                if (r2 < cut2) {
-                    const int tj = __float_as_int(a.w);
-                    const float2 pt = prow[tj];
-                    const int pf = __float_as_int(pt.y);
-                    float fr;
-                    float e;
-                    if (TS == TRIDS_TERMS_VINA5)
-                        e = pair_vina<PARAMS>(fmaxf(r2, 1e-12f), pt.x, pf, w, fr, et, dRs);
-                    else
-                        e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, pf, grow + tj * kK, P.gmm_k, true, w, fr,
-                                               et, dRs);
-                    ae += e;
-                    ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
-                    if (PARAMS) {
-#pragma unroll
-                        for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
-                        W.grs[ti * 32 + W.lane] += ebar * dRs;
-                        W.grs[tj * 32 + W.lane] += ebar * dRs;
-                    }
-                    if (COUNT) ++npairs;
-                }
-            }
-        }
-        e_lp += ae;
-        W.G(0, i) += ax; W.G(1, i) += ay; W.G(2, i) += az;
-    }
+    const float e_lp = inter_pass<TS, PARAMS, COUNT>(B, pk, S, h, W, w, ebar, acc, npairs);
     *e_inter = e_lp;
     return e_lp + e_intra;
 }
@@ -469,7 +578,7 @@ struct SampleArgs {
     int n_items;
     unsigned int* counter;
     int* err;
-    size_t params_bytes, pocket_off, mbar_off, warp_off, warp_bytes;
+    size_t params_bytes, pocket_off, ptype_off, mbar_off, warp_off, warp_bytes;
 };
 
 struct Sched {
@@ -689,10 +798,11 @@ __device__ __forceinline__ void flush_count(unsigned long long* cnt, uint32_t n)
 // Persistent fused sampler: each warp pops (ligand, 32-pose tile) items from a global
 // counter and runs every evaluation of its poses with the state held on chip.
 template <int TS, bool COUNT>
-__global__ void __launch_bounds__(256) k_sample_persistent(SampleArgs A) {
+__global__ void __launch_bounds__(128, 1) k_sample_persistent(SampleArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.mbar_off, A.err)) return;
-    Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off)};
+    if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
+    Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
+           reinterpret_cast<const uint8_t*>(smem + A.ptype_off)};
     const Warp W = make_warp(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor, false);
     uint32_t npairs = 0;
     for (;;) {
@@ -718,10 +828,11 @@ __global__ void __launch_bounds__(256) k_sample_persistent(SampleArgs A) {
 // Plain form: one launch per (ligand, evaluation) with the state in global memory,
 // the same device code as the persistent sampler.
 template <int TS, bool COUNT>
-__global__ void __launch_bounds__(256) k_sample_step(SampleArgs A, int l, int s) {
+__global__ void __launch_bounds__(128, 1) k_sample_step(SampleArgs A, int l, int s) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.mbar_off, A.err)) return;
-    Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off)};
+    if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
+    Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
+           reinterpret_cast<const uint8_t*>(smem + A.ptype_off)};
     const Warp W = make_warp(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor, false);
     const int p0 = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
     if (p0 >= A.P) return;
@@ -753,14 +864,15 @@ struct ScoreArgs {
     int n_items;
     unsigned int* counter;
     int* err;
-    size_t params_bytes, pocket_off, mbar_off, warp_off, warp_bytes;
+    size_t params_bytes, pocket_off, ptype_off, mbar_off, warp_off, warp_bytes;
 };
 
 template <int TS, bool PARAMS>
 __global__ void __launch_bounds__(256) k_score(ScoreArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.mbar_off, A.err)) return;
-    Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off)};
+    if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
+    Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
+           reinterpret_cast<const uint8_t*>(smem + A.ptype_off)};
     const Warp W = make_warp(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor, PARAMS);
     const int D = A.B.dof_stride;
     for (;;) {
@@ -967,6 +1079,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 struct trids_pocket {
     int device = 0;
     int M = 0;
+    std::vector<float> xyz;
+    std::vector<int> type;
+    uint8_t* d_ptype = nullptr;
     float cutoff_built = 0.f;
     float cell = 1.f;
     float box_lo[3], box_hi[3];
@@ -979,7 +1094,7 @@ struct trids_pocket {
     DevParams* d_params = nullptr;
     DevPocket view() const {
         DevPocket v;
-        v.atoms = d_atoms; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
+        v.atoms = d_atoms; v.ptype = d_ptype; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
         v.nx = grid.dims[0]; v.ny = grid.dims[1]; v.nz = grid.dims[2];
         v.gx = grid.lo[0]; v.gy = grid.lo[1]; v.gz = grid.lo[2]; v.inv_h = 1.f / grid.h;
         for (int d = 0; d < 3; ++d) { v.box_lo[d] = box_lo[d]; v.box_hi[d] = box_hi[d]; }
@@ -1068,6 +1183,7 @@ void fill_dev_params(const trids_params* p, DevParams* d) {
     d->cut2 = p->cutoff * p->cutoff;
     d->w_tor = p->w_tor;
     for (int a = 0; a < kNT; ++a) d->radius[a] = a < p->n_types ? p->radius[a] : 0.f;
+    for (int a = 0; a < kNT; ++a) d->tflags[a] = a < p->n_types ? (uint32_t)(p->flags[a] & 7) : 0u;
     for (int a = 0; a < kNT; ++a)
         for (int b = 0; b < kNT; ++b) {
             const bool in = a < p->n_types && b < p->n_types;
@@ -1088,6 +1204,30 @@ void fill_dev_params(const trids_params* p, DevParams* d) {
                 }
             }
         }
+}
+
+// Pocket arrays that depend on the parameters: atoms as (x, y, z, radius of the type)
+// and candidate entries carrying each atom's flags.  Stream-ordered, then synchronised
+// (the host staging vectors are temporaries).
+int upload_pocket_arrays(trids_pocket* pk, cudaStream_t st) {
+    const int M = pk->M;
+    std::vector<float4> atoms(M + 1);
+    for (int j = 0; j < M; ++j)
+        atoms[j] = make_float4(pk->xyz[3 * j], pk->xyz[3 * j + 1], pk->xyz[3 * j + 2], pk->prm.radius[pk->type[j]]);
+    atoms[M] = make_float4(1e6f, 1e6f, 1e6f, 0.f);  // sentinel: never within the cutoff
+    std::vector<uint16_t> cand(pk->grid.cand.size());
+    for (size_t k = 0; k < cand.size(); ++k) {
+        const int j = pk->grid.cand[k];
+        const uint32_t f = j < M ? (uint32_t)(pk->prm.flags[pk->type[j]] & 7) : 0u;
+        cand[k] = (uint16_t)((uint32_t)j | (f << 13));
+    }
+    fill_dev_params(&pk->prm, &pk->hp);
+    CK(cudaMemcpyAsync(pk->d_atoms, atoms.data(), atoms.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
+    if (!cand.empty())
+        CK(cudaMemcpyAsync(pk->d_cand, cand.data(), cand.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(pk->d_params, &pk->hp, sizeof(DevParams), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return TRIDS_OK;
 }
 
 int device_guard(int dev) {
@@ -1182,7 +1322,7 @@ int trids_make_pocket(const float* xyz, const int32_t* type, int32_t n_atoms, co
     if (!out) return fail(TRIDS_EINVAL, "out is NULL");
     *out = nullptr;
     if (!xyz || !type || !box_center || !box_size) return fail(TRIDS_EINVAL, "NULL input array");
-    if (n_atoms < 1 || n_atoms > 65535) return fail(TRIDS_EINVAL, "pocket has %d atoms (allowed 1..65535)", n_atoms);
+    if (n_atoms < 1 || n_atoms > 8191) return fail(TRIDS_EINVAL, "pocket has %d atoms (allowed 1..8191)", n_atoms);
     int rc = check_params(prm);
     if (rc) return rc;
     for (int j = 0; j < n_atoms; ++j) {
@@ -1201,6 +1341,8 @@ int trids_make_pocket(const float* xyz, const int32_t* type, int32_t n_atoms, co
     pk->prm = *prm;
     pk->cutoff_built = prm->cutoff;
     pk->cell = cell > 0.f ? cell : 1.0f;
+    pk->xyz.assign(xyz, xyz + 3 * (size_t)n_atoms);
+    pk->type.assign(type, type + n_atoms);
     for (int d = 0; d < 3; ++d) {
         pk->box_lo[d] = box_center[d] - 0.5f * box_size[d];
         pk->box_hi[d] = box_center[d] + 0.5f * box_size[d];
@@ -1208,17 +1350,13 @@ int trids_make_pocket(const float* xyz, const int32_t* type, int32_t n_atoms, co
     build_grid(n_atoms, xyz, prm->cutoff, pk->cell, &pk->grid);
     if (pk->grid.cand.size() >= (1ull << 32)) return fail(TRIDS_ENOMEM, "candidate grid too large");
     std::vector<float4> atoms(n_atoms + 1);
-    for (int j = 0; j < n_atoms; ++j) {
-        float tb;
-        int t = type[j];
-        std::memcpy(&tb, &t, 4);
-        atoms[j] = make_float4(xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2], tb);
-    }
-    atoms[n_atoms] = make_float4(1e6f, 1e6f, 1e6f, 0.f);  // sentinel: never within the cutoff
+    std::vector<uint8_t> ptype(align_up((size_t)n_atoms + 1, 16), 0);
+    for (int j = 0; j < n_atoms; ++j) ptype[j] = (uint8_t)type[j];
     fill_dev_params(prm, &pk->hp);
     std::vector<DevParams> hp(1, pk->hp);
-    if ((rc = upload(&pk->d_atoms, atoms)) || (rc = upload(&pk->d_cell, pk->grid.start)) ||
-        (rc = upload(&pk->d_cand, pk->grid.cand)) || (rc = upload(&pk->d_params, hp))) {
+    if ((rc = upload(&pk->d_atoms, atoms)) || (rc = upload(&pk->d_ptype, ptype)) ||
+        (rc = upload(&pk->d_cell, pk->grid.start)) || (rc = upload(&pk->d_cand, pk->grid.cand)) ||
+        (rc = upload(&pk->d_params, hp)) || (rc = upload_pocket_arrays(pk.get(), nullptr))) {
         trids_free_pocket(pk.release());
         return rc;
     }
@@ -1236,15 +1374,13 @@ int trids_set_params(trids_pocket* pk, const trids_params* prm, void* stream) {
                     pk->cutoff_built);
     if ((rc = device_guard(pk->device))) return rc;
     pk->prm = *prm;
-    fill_dev_params(prm, &pk->hp);
-    CK(cudaMemcpyAsync(pk->d_params, &pk->hp, sizeof(DevParams), cudaMemcpyHostToDevice, (cudaStream_t)stream));
-    CK(cudaStreamSynchronize((cudaStream_t)stream));
-    return TRIDS_OK;
+    return upload_pocket_arrays(pk, (cudaStream_t)stream);
 }
 
 int trids_free_pocket(trids_pocket* pk) {
     if (!pk) return TRIDS_OK;
     cudaFree(pk->d_atoms);
+    cudaFree(pk->d_ptype);
     cudaFree(pk->d_cell);
     cudaFree(pk->d_cand);
     cudaFree(pk->d_params);
@@ -1447,7 +1583,8 @@ int trids_score_grad(const trids_pocket* pk, const trids_batch* bc, int32_t pose
     A.pk = pk->view(); A.B = b->view(); A.P = poses; A.dof = dof; A.energy = energy; A.e_inter = e_inter;
     A.g_dof = g_dof; A.g_xyz = g_xyz; A.e_bar = e_bar; A.partials = b->d_partials; A.items = b->d_items;
     A.n_items = b->n_items; A.counter = b->d_counter + 1; A.err = b->d_err;
-    A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.mbar_off = L.mbar_off;
+    A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.ptype_off = L.ptype_off;
+    A.mbar_off = L.mbar_off;
     A.warp_off = L.warp_off; A.warp_bytes = L.warp_bytes;
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemsetAsync(A.counter, 0, sizeof(unsigned int), st));
@@ -1500,7 +1637,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         return rc;
     if ((rc = ensure_items(b, c.poses))) return rc;
     Layout L;
-    const int warps = pick_warps(c.warps_per_block, pk, b, false, &L);
+    const int warps = pick_warps(std::min(c.warps_per_block > 0 ? c.warps_per_block : 4, 4), pk, b, false, &L);
     if (!warps) return fail(TRIDS_EINVAL, "pocket of %d atoms does not fit in shared memory", pk->M);
     SampleArgs A;
     std::memset(&A, 0, sizeof A);  // the bytes form the graph-cache key
@@ -1509,7 +1646,8 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     A.beta = c.beta; A.seed = c.seed; A.lig_base = c.lig_base; A.dof = dof; A.state = state; A.energy = energy;
     A.trace = c.trace; A.trace_slot = c.trace_slot; A.n_trace = c.n_trace; A.pair_count = c.pair_count;
     A.items = b->d_items; A.n_items = b->n_items; A.counter = b->d_counter; A.err = b->d_err;
-    A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.mbar_off = L.mbar_off;
+    A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.ptype_off = L.ptype_off;
+    A.mbar_off = L.mbar_off;
     A.warp_off = L.warp_off; A.warp_bytes = L.warp_bytes;
     cudaStream_t st = (cudaStream_t)stream;
     const bool tt = pk->prm.term_set == TRIDS_TERMS_TRIDS;
@@ -1682,7 +1820,8 @@ int trids_score_grad_noalloc(const trids_pocket* pk, const trids_batch* b, int32
     A.partials = reinterpret_cast<float*>(scratch + partials_off);
     A.items = reinterpret_cast<const int2*>(scratch + items_off);
     A.n_items = (int)n_items; A.counter = reinterpret_cast<unsigned int*>(scratch); A.err = b->d_err;
-    A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.mbar_off = L.mbar_off;
+    A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.ptype_off = L.ptype_off;
+    A.mbar_off = L.mbar_off;
     A.warp_off = L.warp_off; A.warp_bytes = L.warp_bytes;
     cudaStream_t st = (cudaStream_t)stream;
     // the array keeps the previous call's contents: reset the counter, rewrite the items

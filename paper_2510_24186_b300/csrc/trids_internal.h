@@ -42,7 +42,8 @@ void topology_ints(const PackedLigand& lg, std::vector<int32_t>* out);
 // Uniform grid over the pocket's bounding box grown by the cutoff.  Each cell lists
 // every pocket atom within cutoff + half the cell diagonal (+ a small margin) of the
 // cell centre, ascending, padded to a multiple of 8 with the sentinel index M.  A
-// ligand atom outside the grid has no pocket atom within the cutoff.
+// ligand atom outside the grid has no pocket atom within the cutoff.  The device copy
+// carries each atom's flags in the top 3 bits of its entry (so M < 8192).
 struct CandidateGrid {
     float lo[3];
     float h;
@@ -60,14 +61,16 @@ struct alignas(16) DevParams {
     float w[5];
     float cutoff, cut2, w_tor;
     float radius[kNT];
+    uint32_t tflags[kNT];          // per type: bit0 hydrophobic, bit1 donor, bit2 acceptor
     float2 pairtab[kNT][kNT];      // (R_a + R_b, pair flags as int bits: 1 hydrophobic, 2 donor-acceptor)
     float4 gmm[kNT][kNT][kK];      // (pi, mu, -1/(2 sigma^2), 1/sigma^2)
 };
 
 struct DevPocket {
-    const float4* atoms;           // [M + 1]: (x, y, z, type bits); atoms[M] = far sentinel
+    const float4* atoms;           // [M + 1]: (x, y, z, radius); atoms[M] = far sentinel
+    const uint8_t* ptype;          // [M + 1] (padded to 16 bytes): atom types
     const uint32_t* cell_start;
-    const uint16_t* cand;
+    const uint16_t* cand;          // pocket index (13 bits) | flags of that atom << 13
     const DevParams* params;
     int M;
     int nx, ny, nz;
