@@ -165,8 +165,12 @@ struct Layout {
     size_t params_bytes, pocket_off, pocket_bytes, ptype_off, ptype_bytes, mbar_off, warp_off, warp_bytes, total;
 };
 
-__host__ __device__ inline size_t warp_smem_bytes(int Lmax, int Tmax, bool params) {
-    return (size_t)(6 * Lmax + Tmax + (params ? kNT : 0)) * 32 * sizeof(float);
+__host__ __device__ inline size_t pose_warp_bytes(int Lm, int Tm, bool params) {
+    size_t b = 16 * (size_t)Lm * 2 + 48 * (size_t)(Tm > 0 ? Tm : 1) + 16 * (size_t)(Lm + 32);
+    b += 4 * (size_t)Lm + 4 * (size_t)(Lm + 1);
+    b = align_up(b, 16);
+    if (params) b += 4 * (size_t)kNT * 32;
+    return align_up(b, 128);
 }
 
 inline Layout make_layout(int term_set, int M, int Lmax, int Tmax, int warps, bool params) {
@@ -178,7 +182,7 @@ inline Layout make_layout(int term_set, int M, int Lmax, int Tmax, int warps, bo
     L.ptype_bytes = align_up((size_t)(M + 1), 16);
     L.mbar_off = align_up(L.ptype_off + L.ptype_bytes, 16);
     L.warp_off = align_up(L.mbar_off + 16, 128);
-    L.warp_bytes = warp_smem_bytes(Lmax, Tmax, params);
+    L.warp_bytes = pose_warp_bytes(Lmax, Tmax, params);
     L.total = L.warp_off + L.warp_bytes * warps;
     return L;
 }
@@ -234,51 +238,46 @@ __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t par
 }
 
 // ------------------------------------------------------------------ per-warp pose work
-struct Warp {
-    float* xs;    // [3][Lmax][32]
-    float* gs;    // [3][Lmax][32]
-    float* ths;   // [Tmax][32]
-    float* grs;   // [kNT][32] (parameter-gradient kernels only)
-    int Lmax, lane;
-    __device__ float& X(int c, int i) const { return xs[(c * Lmax + i) * 32 + lane]; }
-    __device__ float& G(int c, int i) const { return gs[(c * Lmax + i) * 32 + lane]; }
-    __device__ float& TH(int k) const { return ths[k * 32 + lane]; }
+// One warp owns one pose.  Per-warp shared memory (pose_warp_bytes):
+//   xs  float4[Lm]      world coordinates of the pose's atoms
+//   gs  float4[Lm]      dE/dx_i
+//   rk  float4[3 Tm]    rows of each torsion's rotation matrix
+//   rec float4[Lm + 32] partial ligand-pocket forces, slot (atom + lane)
+//   cs  uint32[Lm]      candidate-list offset of each atom's cell
+//   pre int[Lm + 1]     exclusive prefix of each atom's candidate blocks
+//   grs float[kNT][32]  per-lane dE/dR_a (parameter-gradient kernels only)
+struct PW {
+    float4* xs;
+    float4* gs;
+    float4* rk;
+    float4* rec;
+    uint32_t* cs;
+    int* pre;
+    float* grs;
+    int lane;
 };
 
-// Forward kinematics: local coordinates, torsions deepest first (reverse BFS order)
-// about their input-geometry axes -- the axis atoms of a torsion are never moved by
-// the torsions below it -- then x = t + R(q) z.
-__device__ void forward_kinematics(const DevBatch& B, const LigHdr& h, const Warp& W, const float t[3],
-                                   const float q[4]) {
-    for (int i = 0; i < h.n_atoms; ++i) {
-        const float4 y = __ldg(&B.atom_y[h.atom_off + i]);
-        W.X(0, i) = y.x; W.X(1, i) = y.y; W.X(2, i) = y.z;
-    }
-    for (int k = h.n_tor - 1; k >= 0; --k) {
-        const int4 ti = __ldg(&B.tor_idx[h.tor_off + k]);
-        const float4 u = __ldg(&B.tor_u[h.tor_off + k]);
-        const float4 p = __ldg(&B.tor_p[h.tor_off + k]);
-        float s, c;
-        sincosf(W.TH(k), &s, &c);
-        const float kc = 1.f - c;
-        const float R0 = c + kc * u.x * u.x, R1 = kc * u.x * u.y - s * u.z, R2 = kc * u.x * u.z + s * u.y;
-        const float R3 = kc * u.y * u.x + s * u.z, R4 = c + kc * u.y * u.y, R5 = kc * u.y * u.z - s * u.x;
-        const float R6 = kc * u.z * u.x - s * u.y, R7 = kc * u.z * u.y + s * u.x, R8 = c + kc * u.z * u.z;
-        for (int i = ti.z; i < ti.w; ++i) {
-            const float vx = W.X(0, i) - p.x, vy = W.X(1, i) - p.y, vz = W.X(2, i) - p.z;
-            W.X(0, i) = p.x + (R0 * vx + R1 * vy + R2 * vz);
-            W.X(1, i) = p.y + (R3 * vx + R4 * vy + R5 * vz);
-            W.X(2, i) = p.z + (R6 * vx + R7 * vy + R8 * vz);
-        }
-    }
-    float R[9];
-    quat_to_mat(q, R);
-    for (int i = 0; i < h.n_atoms; ++i) {
-        const float vx = W.X(0, i), vy = W.X(1, i), vz = W.X(2, i);
-        W.X(0, i) = t[0] + (R[0] * vx + R[1] * vy + R[2] * vz);
-        W.X(1, i) = t[1] + (R[3] * vx + R[4] * vy + R[5] * vz);
-        W.X(2, i) = t[2] + (R[6] * vx + R[7] * vy + R[8] * vz);
-    }
+__device__ __forceinline__ PW make_pw(unsigned char* smem, size_t warp_off, size_t warp_bytes, int Lm, int Tm) {
+    PW W;
+    unsigned char* base = smem + warp_off + warp_bytes * (threadIdx.x >> 5);
+    W.xs = reinterpret_cast<float4*>(base);
+    W.gs = W.xs + Lm;
+    W.rk = W.gs + Lm;
+    W.rec = W.rk + 3 * (Tm > 0 ? Tm : 1);
+    W.cs = reinterpret_cast<uint32_t*>(W.rec + Lm + 32);
+    W.pre = reinterpret_cast<int*>(W.cs + Lm);
+    W.grs = reinterpret_cast<float*>(base + align_up(16 * (size_t)Lm * 2 + 48 * (size_t)(Tm > 0 ? Tm : 1) +
+                                                     16 * (size_t)(Lm + 32) + 4 * (size_t)Lm + 4 * (size_t)(Lm + 1),
+                                                 16));
+    W.lane = threadIdx.x & 31;
+    return W;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+    // butterfly: every lane ends with the same, fixed-order sum
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
 }
 
 struct ParamAcc {
@@ -343,221 +342,302 @@ __device__ __forceinline__ void cell_range(const DevPocket& pk, float x, float y
     }
 }
 
-// Ligand-pocket pairs of each lane's pose.  Each lane walks its own stream of
-// (atom, 8-candidate block) so the lanes of a warp stay busy until the whole pose is
-// done; the next atom's cell range is fetched one atom ahead.  A candidate entry is
-// the pocket index (13 bits) with the pocket atom's flags in the top 3 bits; the pocket
-// float4 carries (x, y, z, radius).  The Vina-form block is branch-free: every
-// candidate is evaluated and masked by r^2 < cutoff^2, so the eight pairs of a block
-// are independent instruction streams.  Forces accumulate per atom in registers and
-// are added to W.G when the lane leaves the atom.  Returns the lane's ligand-pocket
-// energy.
+// Forward kinematics of the warp's pose.  Lane k < T builds torsion k's rotation
+// (Rodrigues, angle th held by lane k) into W.rk; then each lane places its atoms:
+// torsions deepest first (reverse BFS order) about their input-geometry axes -- the
+// axis atoms of a torsion are never moved by the torsions below it -- then
+// x = t + R(q) z.
+__device__ void fk_warp(const DevBatch& B, const LigHdr& h, const PW& W, const float t[3], const float q[4], float th) {
+    const int T = h.n_tor, L = h.n_atoms;
+    if (W.lane < T) {
+        const float4 u = __ldg(&B.tor_u[h.tor_off + W.lane]);
+        float s, c;
+        sincosf(th, &s, &c);
+        const float kc = 1.f - c;
+        W.rk[3 * W.lane + 0] = make_float4(c + kc * u.x * u.x, kc * u.x * u.y - s * u.z, kc * u.x * u.z + s * u.y, 0.f);
+        W.rk[3 * W.lane + 1] = make_float4(kc * u.y * u.x + s * u.z, c + kc * u.y * u.y, kc * u.y * u.z - s * u.x, 0.f);
+        W.rk[3 * W.lane + 2] = make_float4(kc * u.z * u.x - s * u.y, kc * u.z * u.y + s * u.x, c + kc * u.z * u.z, 0.f);
+    }
+    __syncwarp();
+    float R[9];
+    quat_to_mat(q, R);
+    for (int i = W.lane; i < L; i += 32) {
+        const float4 y = __ldg(&B.atom_y[h.atom_off + i]);
+        float x0 = y.x, x1 = y.y, x2 = y.z;
+        for (int k = T - 1; k >= 0; --k) {
+            const int4 ti = __ldg(&B.tor_idx[h.tor_off + k]);
+            if (i >= ti.z && i < ti.w) {
+                const float4 p = __ldg(&B.tor_p[h.tor_off + k]);
+                const float4 r0 = W.rk[3 * k], r1 = W.rk[3 * k + 1], r2 = W.rk[3 * k + 2];
+                const float vx = x0 - p.x, vy = x1 - p.y, vz = x2 - p.z;
+                x0 = p.x + (r0.x * vx + r0.y * vy + r0.z * vz);
+                x1 = p.y + (r1.x * vx + r1.y * vy + r1.z * vz);
+                x2 = p.z + (r2.x * vx + r2.y * vy + r2.z * vz);
+            }
+        }
+        W.xs[i] = make_float4(t[0] + (R[0] * x0 + R[1] * x1 + R[2] * x2), t[1] + (R[3] * x0 + R[4] * x1 + R[5] * x2),
+                              t[2] + (R[6] * x0 + R[7] * x1 + R[8] * x2), 0.f);
+    }
+    __syncwarp();
+}
+
+// Ligand-pocket pairs of the warp's pose.  Every atom's cell lists its candidate
+// pocket atoms in blocks of 8; the pose's blocks are numbered atom by atom (prefix in
+// W.pre) and split into 32 equal contiguous segments, one per lane, so the lanes stay
+// balanced whatever the atoms' list lengths.  A lane accumulates the force on its
+// current atom in registers and leaves a partial in slot (atom + lane) of W.rec; the
+// partials of an atom are then added in lane order (bit-reproducible).  A candidate
+// entry is the pocket index (13 bits) with the pocket atom's flags in the top 3 bits;
+// the pocket float4 carries (x, y, z, radius).  The Vina-form block is branch-free:
+// all eight candidates are evaluated and masked by r^2 < cutoff^2.  Writes the
+// ligand-pocket forces to W.gs and returns the lane's share of the energy.
 template <int TS, bool PARAMS, bool COUNT>
-__device__ float inter_pass(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const Warp& W,
+__device__ float inter_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
                             const float w[5], float ebar, ParamAcc& acc, uint32_t& npairs) {
     const DevParams& P = *S.P;
     const float cut2 = P.cut2;
-    const int L = h.n_atoms;
+    const int L = h.n_atoms, lane = W.lane;
     const float4* __restrict__ pocket = S.pocket;
     const uint16_t* __restrict__ cand = pk.cand;
-    float e_sum = 0.f;
-    int i = 0;
-    float xi = W.X(0, 0), yi = W.X(1, 0), zi = W.X(2, 0);
-    int ti = __float_as_int(__ldg(&B.atom_y[h.atom_off]).w);
-    uint32_t cur, end, nb = 0, ne = 0;
-    cell_range(pk, xi, yi, zi, cur, end);
-    if (L > 1) cell_range(pk, W.X(0, 1), W.X(1, 1), W.X(2, 1), nb, ne);
-    float ri = P.radius[ti];
-    uint32_t fi = P.tflags[ti];
-    float ax = 0.f, ay = 0.f, az = 0.f, ae = 0.f;
-    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
-    uint4 v = cur < end ? __ldg(reinterpret_cast<const uint4*>(cand + cur)) : zero4;   // block at cur
-    uint4 vn = nb < ne ? __ldg(reinterpret_cast<const uint4*>(cand + nb)) : zero4;     // first block of atom i+1
-    for (;;) {
-        while (cur >= end) {                     // leave atom i (per lane)
-            W.G(0, i) += ax; W.G(1, i) += ay; W.G(2, i) += az;
-            e_sum += ae;
-            ax = ay = az = ae = 0.f;
-            if (++i >= L) return e_sum;
-            xi = W.X(0, i); yi = W.X(1, i); zi = W.X(2, i);
-            ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
-            ri = P.radius[ti];
-            fi = P.tflags[ti];
-            cur = nb; end = ne; v = vn;
-            nb = ne = 0;
-            if (i + 1 < L) cell_range(pk, W.X(0, i + 1), W.X(1, i + 1), W.X(2, i + 1), nb, ne);
-            vn = nb < ne ? __ldg(reinterpret_cast<const uint4*>(cand + nb)) : zero4;
+    // 1. cell ranges and block prefix
+    int carry = 0;
+    for (int base = 0; base < L; base += 32) {
+        const int i = base + lane;
+        int nblk = 0;
+        if (i < L) {
+            const float4 x = W.xs[i];
+            uint32_t beg, end;
+            cell_range(pk, x.x, x.y, x.z, beg, end);
+            W.cs[i] = beg;
+            nblk = (int)((end - beg) >> 3);
         }
-        const uint4 vc = v;
-        if (cur + 8 < end) v = __ldg(reinterpret_cast<const uint4*>(cand + cur + 8));   // prefetch
-        cur += 8;
-        const uint32_t wv[4] = {vc.x, vc.y, vc.z, vc.w};
-        // pair-flag selectors: hydrophobic needs both bit0; donor-acceptor needs
-        // (donor_i & acceptor_j) | (acceptor_i & donor_j)
-        const uint32_t f_hyd = fi & 1u;
-        const uint32_t f_hb = ((fi & 2u) << 1) | ((fi & 4u) >> 1);
+        int v = nblk;
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const uint32_t ent = (s & 1) ? (wv[s >> 1] >> 16) : (wv[s >> 1] & 0xffffu);
-            const int j = (int)(ent & 0x1fffu);
-            const uint32_t fj = ent >> 13;
-            const float4 a = pocket[j];
-            const float dx = xi - a.x, dy = yi - a.y, dz = zi - a.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const bool in = r2 < cut2;
-            if (TS == TRIDS_TERMS_VINA5) {
-                float dd, rinv, et[5];
-                const float e = vina_eval<PARAMS>(r2, ri + a.w, (f_hyd & fj) ? 1.f : 0.f, (f_hb & fj) ? 1.f : 0.f,
-                                                  w, dd, rinv, et);
-                const float fr = in ? dd * rinv : 0.f;
-                ae += in ? e : 0.f;
-                ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
-                if (PARAMS && in) {
-#pragma unroll
-                    for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
-                    const int tj = S.ptype[j];
-                    W.grs[ti * 32 + W.lane] -= ebar * dd;
-                    W.grs[tj * 32 + W.lane] -= ebar * dd;
-                }
-            } else if (in) {
-                const int tj = S.ptype[j];
-                const float2 pt = P.pairtab[ti][tj];
-                float fr, dRs;
-                float et[5];
-                const float e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, __float_as_int(pt.y), &P.gmm[ti][tj][0],
-                                                   P.gmm_k, true, w, fr, et, dRs);
-                ae += e;
-                ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
-                if (PARAMS) {
-#pragma unroll
-                    for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
-                    W.grs[ti * 32 + W.lane] += ebar * dRs;
-                    W.grs[tj * 32 + W.lane] += ebar * dRs;
-                }
-            }
-            if (COUNT) npairs += in ? 1u : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += n;
         }
+        if (i < L) W.pre[i + 1] = carry + v;
+        carry += __shfl_sync(kFull, v, 31);
     }
-}
-
-// Score and per-atom forces of the warp's poses.  Forces go to W.G, the returned value
-// is E_total; *e_inter gets the ligand-pocket part.  With PARAMS, the per-term sums
-// (scaled by ebar) go to acc.gw and the radius derivatives to W.grs.
-template <int TS, bool PARAMS, bool COUNT>
-__device__ float score_pose(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h,
-                            const Warp& W, float ebar, ParamAcc& acc, float* e_inter, uint32_t& npairs) {
-    const DevParams& P = *S.P;
-    const float cut2 = P.cut2;
-    float w[5];
+    if (lane == 0) W.pre[0] = 0;
+    for (int r = lane; r < L + 32; r += 32) W.rec[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    const int N = carry;
+    const int lo = (int)(((long long)N * lane) >> 5), hi = (int)(((long long)N * (lane + 1)) >> 5);
+    float e_lane = 0.f;
+    if (lo < hi) {
+        int i = 0;
+        {
+            int a = 0, b = L - 1;
+            while (a < b) {
+                const int m = (a + b + 1) >> 1;
+                if (W.pre[m] <= lo) a = m; else b = m - 1;
+            }
+            i = a;
+        }
+        int nxt = W.pre[i + 1];
+        uint32_t cur = W.cs[i] + 8u * (uint32_t)(lo - W.pre[i]);
+        float4 xa = W.xs[i];
+        int ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
+        float ri = P.radius[ti];
+        uint32_t fi = P.tflags[ti];
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        uint4 v = __ldg(reinterpret_cast<const uint4*>(cand + cur));
+        for (int blk = lo; blk < hi; ++blk) {
+            if (blk == nxt) {                      // move to the atom owning block blk
+                W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
+                ax = ay = az = 0.f;
+                do { ++i; } while (W.pre[i + 1] == blk);
+                nxt = W.pre[i + 1];
+                cur = W.cs[i];
+                xa = W.xs[i];
+                ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
+                ri = P.radius[ti];
+                fi = P.tflags[ti];
+                v = __ldg(reinterpret_cast<const uint4*>(cand + cur));
+            }
+            const uint4 vc = v;
+            if (blk + 1 < hi && blk + 1 < nxt) v = __ldg(reinterpret_cast<const uint4*>(cand + cur + 8));
+            cur += 8;
+            const uint32_t wv[4] = {vc.x, vc.y, vc.z, vc.w};
+            // pair-flag selectors: hydrophobic needs both bit0; donor-acceptor needs
+            // (donor_i & acceptor_j) | (acceptor_i & donor_j)
+            const uint32_t f_hyd = fi & 1u;
+            const uint32_t f_hb = ((fi & 2u) << 1) | ((fi & 4u) >> 1);
 #pragma unroll
-    for (int t = 0; t < 5; ++t) w[t] = P.w[t];
-    for (int i = 0; i < h.n_atoms; ++i) { W.G(0, i) = 0.f; W.G(1, i) = 0.f; W.G(2, i) = 0.f; }
-    float et[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    float dRs = 0.f;
-    // intra-ligand pairs (uniform list across the warp)
-    float e_intra = 0.f;
-    if (TS == TRIDS_TERMS_VINA5) {
-        // four pairs at a time: independent loads and pair math, then the force updates
-        // in list order (pairs of a chunk may share atoms)
-        for (int q0 = 0; q0 < h.n_pairs; q0 += 4) {
-            uint32_t pw[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) pw[u] = q0 + u < h.n_pairs ? __ldg(&B.pairs[h.pair_off + q0 + u]) : 0u;
-            float fx[4], fy[4], fz[4], ee[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = pw[u] & 0xff, j = (pw[u] >> 8) & 0xff, ti = (pw[u] >> 16) & 0xff, tj = pw[u] >> 24;
-                const float dx = W.X(0, i) - W.X(0, j), dy = W.X(1, i) - W.X(1, j), dz = W.X(2, i) - W.X(2, j);
+            for (int s = 0; s < 8; ++s) {
+                const uint32_t ent = (s & 1) ? (wv[s >> 1] >> 16) : (wv[s >> 1] & 0xffffu);
+                const int j = (int)(ent & 0x1fffu);
+                const uint32_t fj = ent >> 13;
+                const float4 a = pocket[j];
+                const float dx = xa.x - a.x, dy = xa.y - a.y, dz = xa.z - a.z;
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                const bool in = (q0 + u < h.n_pairs) && r2 < cut2;
-                const float2 pt = P.pairtab[ti][tj];
-                const int pf = __float_as_int(pt.y);
-                float dd, rinv;
-                const float e = vina_eval<PARAMS>(r2, pt.x, (pf & 1) ? 1.f : 0.f, (pf & 2) ? 1.f : 0.f, w, dd, rinv, et);
-                const float fr = in ? dd * rinv : 0.f;
-                fx[u] = fr * dx; fy[u] = fr * dy; fz[u] = fr * dz;
-                ee[u] = in ? e : 0.f;
-                if (PARAMS && in) {
+                const bool in = r2 < cut2;
+                if (TS == TRIDS_TERMS_VINA5) {
+                    float dd, rinv, et[5];
+                    const float e = vina_eval<PARAMS>(r2, ri + a.w, (f_hyd & fj) ? 1.f : 0.f,
+                                                      (f_hb & fj) ? 1.f : 0.f, w, dd, rinv, et);
+                    const float fr = in ? dd * rinv : 0.f;
+                    e_lane += in ? e : 0.f;
+                    ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
+                    if (PARAMS && in) {
 #pragma unroll
-                    for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
-                    W.grs[ti * 32 + W.lane] -= ebar * dd;
-                    W.grs[tj * 32 + W.lane] -= ebar * dd;
+                        for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
+                        const int tj = S.ptype[j];
+                        W.grs[ti * 32 + lane] -= ebar * dd;
+                        W.grs[tj * 32 + lane] -= ebar * dd;
+                    }
+                } else if (in) {
+                    const int tj = S.ptype[j];
+                    const float2 pt = P.pairtab[ti][tj];
+                    float fr, dRs;
+                    float et[5];
+                    const float e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, __float_as_int(pt.y),
+                                                       &P.gmm[ti][tj][0], P.gmm_k, true, w, fr, et, dRs);
+                    e_lane += e;
+                    ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
+                    if (PARAMS) {
+#pragma unroll
+                        for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
+                        W.grs[ti * 32 + lane] += ebar * dRs;
+                        W.grs[tj * 32 + lane] += ebar * dRs;
+                    }
                 }
                 if (COUNT) npairs += in ? 1u : 0u;
             }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int i = pw[u] & 0xff, j = (pw[u] >> 8) & 0xff;
-                e_intra += ee[u];
-                W.G(0, i) += fx[u]; W.G(1, i) += fy[u]; W.G(2, i) += fz[u];
-                W.G(0, j) -= fx[u]; W.G(1, j) -= fy[u]; W.G(2, j) -= fz[u];
+        }
+        W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
+    }
+    __syncwarp();
+    // 2. add each atom's partials in lane order
+    for (int i = lane; i < L; i += 32) {
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        const int b0 = W.pre[i], b1 = W.pre[i + 1];
+        if (b0 < b1) {
+            const int l0 = min(31, (32 * (b0 + 1) - 1) / N), l1 = min(31, (32 * b1 - 1) / N);
+            for (int l = l0; l <= l1; ++l) {
+                const float4 r = W.rec[i + l];
+                gx += r.x; gy += r.y; gz += r.z;
             }
         }
-    } else {
-        for (int q = 0; q < h.n_pairs; ++q) {
-            const uint32_t pw = __ldg(&B.pairs[h.pair_off + q]);
+        W.gs[i] = make_float4(gx, gy, gz, 0.f);
+    }
+    __syncwarp();
+    return e_lane;
+}
+
+// Intra-ligand pairs, in rounds of up to 32 pairs that share no atom (coloured at pack
+// time, padding entries 0xffffffff), one pair per lane: force updates never collide
+// and each atom receives its contributions in round order.  Adds to W.gs and returns
+// the lane's share of the energy.
+template <int TS, bool PARAMS, bool COUNT>
+__device__ float intra_warp(const DevBatch& B, const Smem& S, const LigHdr& h, const PW& W, const float w[5],
+                            float ebar, ParamAcc& acc, uint32_t& npairs) {
+    const DevParams& P = *S.P;
+    const float cut2 = P.cut2;
+    float e_lane = 0.f;
+    for (int c = 0; c < h.n_chunks; ++c) {
+        const uint32_t pw = __ldg(&B.pairs[h.pair_off + c * 32 + W.lane]);
+        if (pw != 0xffffffffu) {
             const int i = pw & 0xff, j = (pw >> 8) & 0xff, ti = (pw >> 16) & 0xff, tj = pw >> 24;
-            const float dx = W.X(0, i) - W.X(0, j), dy = W.X(1, i) - W.X(1, j), dz = W.X(2, i) - W.X(2, j);
+            const float4 xi = W.xs[i], xj = W.xs[j];
+            const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            if (r2 < cut2) {
-                const float2 pt = P.pairtab[ti][tj];
-                float fr;
-                const float e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, __float_as_int(pt.y), nullptr, 0, false, w,
-                                                   fr, et, dRs);
-                e_intra += e;
-                W.G(0, i) = fmaf(fr, dx, W.G(0, i)); W.G(1, i) = fmaf(fr, dy, W.G(1, i)); W.G(2, i) = fmaf(fr, dz, W.G(2, i));
-                W.G(0, j) = fmaf(-fr, dx, W.G(0, j)); W.G(1, j) = fmaf(-fr, dy, W.G(1, j)); W.G(2, j) = fmaf(-fr, dz, W.G(2, j));
-                if (PARAMS) {
+            const bool in = r2 < cut2;
+            const float2 pt = P.pairtab[ti][tj];
+            const int pf = __float_as_int(pt.y);
+            float fr, e, et[5], dRs = 0.f;
+            if (TS == TRIDS_TERMS_VINA5) {
+                float dd, rinv;
+                e = vina_eval<PARAMS>(r2, pt.x, (pf & 1) ? 1.f : 0.f, (pf & 2) ? 1.f : 0.f, w, dd, rinv, et);
+                fr = in ? dd * rinv : 0.f;
+                e = in ? e : 0.f;
+                dRs = -dd;
+            } else {
+                fr = 0.f;
+                e = 0.f;
+                if (in) e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, pf, nullptr, 0, false, w, fr, et, dRs);
+            }
+            e_lane += e;
+            float4 gi = W.gs[i], gj = W.gs[j];
+            gi.x = fmaf(fr, dx, gi.x); gi.y = fmaf(fr, dy, gi.y); gi.z = fmaf(fr, dz, gi.z);
+            gj.x = fmaf(-fr, dx, gj.x); gj.y = fmaf(-fr, dy, gj.y); gj.z = fmaf(-fr, dz, gj.z);
+            W.gs[i] = gi;
+            W.gs[j] = gj;
+            if (PARAMS && in) {
 #pragma unroll
-                    for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
-                    W.grs[ti * 32 + W.lane] += ebar * dRs;
-                    W.grs[tj * 32 + W.lane] += ebar * dRs;
-                }
-                if (COUNT) ++npairs;
+                for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
+                W.grs[ti * 32 + W.lane] += ebar * dRs;
+                W.grs[tj * 32 + W.lane] += ebar * dRs;
+            }
+            if (COUNT) npairs += in ? 1u : 0u;
+        }
+        __syncwarp();
+    }
+    return e_lane;
+}
+
+// E_total of the warp's pose (same value on every lane); forces in W.gs.
+template <int TS, bool PARAMS, bool COUNT>
+__device__ float score_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
+                            float ebar, ParamAcc& acc, float* e_inter, uint32_t& npairs) {
+    float w[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) w[t] = S.P->w[t];
+    const float el = inter_warp<TS, PARAMS, COUNT>(B, pk, S, h, W, w, ebar, acc, npairs);
+    const float ei = intra_warp<TS, PARAMS, COUNT>(B, S, h, W, w, ebar, acc, npairs);
+    const float e_lp = warp_sum(el);
+    *e_inter = e_lp;
+    return e_lp + warp_sum(ei);
+}
+
+// dE/dt = sum g_i and world torque tau = sum (x_i - t) x g_i (every lane), and
+// dE/dtheta_k = a_k . sum over the moving subtree of (x_i - p_k) x g_i with a_k the world
+// axis (parent atom -> child atom) and p_k the world parent atom (lane k).
+__device__ float adjoint_warp(const DevBatch& B, const LigHdr& h, const PW& W, const float t[3], float gt[3],
+                              float tau[3]) {
+    const int L = h.n_atoms, T = h.n_tor;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
+    for (int i = W.lane; i < L; i += 32) {
+        const float4 g = W.gs[i], x = W.xs[i];
+        const float rx = x.x - t[0], ry = x.y - t[1], rz = x.z - t[2];
+        a0 += g.x; a1 += g.y; a2 += g.z;
+        a3 += ry * g.z - rz * g.y;
+        a4 += rz * g.x - rx * g.z;
+        a5 += rx * g.y - ry * g.x;
+    }
+    gt[0] = warp_sum(a0); gt[1] = warp_sum(a1); gt[2] = warp_sum(a2);
+    tau[0] = warp_sum(a3); tau[1] = warp_sum(a4); tau[2] = warp_sum(a5);
+    float mine = 0.f;
+    for (int k = 0; k < T; ++k) {
+        const int4 ti = __ldg(&B.tor_idx[h.tor_off + k]);
+        const float4 p = W.xs[ti.x], c = W.xs[ti.y];
+        float ax = c.x - p.x, ay = c.y - p.y, az = c.z - p.z;
+        const float n = rsqrtf(ax * ax + ay * ay + az * az);
+        ax *= n; ay *= n; az *= n;
+        float s = 0.f;
+        for (int i = W.lane; i < L; i += 32) {
+            if (i >= ti.z && i < ti.w) {
+                const float4 x = W.xs[i], g = W.gs[i];
+                const float rx = x.x - p.x, ry = x.y - p.y, rz = x.z - p.z;
+                s += ax * (ry * g.z - rz * g.y) + ay * (rz * g.x - rx * g.z) + az * (rx * g.y - ry * g.x);
             }
         }
+        s = warp_sum(s);
+        if (W.lane == k) mine = s;
     }
-    // ligand-pocket pairs through the candidate grid
-    const float e_lp = inter_pass<TS, PARAMS, COUNT>(B, pk, S, h, W, w, ebar, acc, npairs);
-    *e_inter = e_lp;
-    return e_lp + e_intra;
-}
-
-// dE/dt = sum g_i, world torque tau = sum (x_i - t) x g_i.
-__device__ void rigid_adjoint(const LigHdr& h, const Warp& W, const float t[3], float gt[3], float tau[3]) {
-    gt[0] = gt[1] = gt[2] = tau[0] = tau[1] = tau[2] = 0.f;
-    for (int i = 0; i < h.n_atoms; ++i) {
-        const float gx = W.G(0, i), gy = W.G(1, i), gz = W.G(2, i);
-        const float rx = W.X(0, i) - t[0], ry = W.X(1, i) - t[1], rz = W.X(2, i) - t[2];
-        gt[0] += gx; gt[1] += gy; gt[2] += gz;
-        tau[0] += ry * gz - rz * gy;
-        tau[1] += rz * gx - rx * gz;
-        tau[2] += rx * gy - ry * gx;
-    }
-}
-
-// dE/dtheta_k = a_k . sum over the moving subtree of (x_i - p_k) x g_i, with a_k the
-// world axis (parent atom -> child atom) and p_k the world parent atom.
-__device__ float torsion_grad(const DevBatch& B, const LigHdr& h, const Warp& W, int k) {
-    const int4 ti = __ldg(&B.tor_idx[h.tor_off + k]);
-    const float px = W.X(0, ti.x), py = W.X(1, ti.x), pz = W.X(2, ti.x);
-    float ax = W.X(0, ti.y) - px, ay = W.X(1, ti.y) - py, az = W.X(2, ti.y) - pz;
-    const float n = rsqrtf(ax * ax + ay * ay + az * az);
-    ax *= n; ay *= n; az *= n;
-    float s = 0.f;
-    for (int i = ti.z; i < ti.w; ++i) {
-        const float rx = W.X(0, i) - px, ry = W.X(1, i) - py, rz = W.X(2, i) - pz;
-        const float gx = W.G(0, i), gy = W.G(1, i), gz = W.G(2, i);
-        s += ax * (ry * gz - rz * gy) + ay * (rz * gx - rx * gz) + az * (rx * gy - ry * gx);
-    }
-    return s;
+    return mine;
 }
 
 // ------------------------------------------------------------------ sampler state
+// Rigid state is held by every lane; lane k < T holds torsion k's angle, Adam moments
+// and saved angle.
 struct PoseState {
     float t[3], q[4], m[6], v[6], st[3], sq[4];
     float ecur, esaved;
     int status;
+    float th, mth, vth, sth;
 };
 
 struct SampleArgs {
@@ -574,7 +654,7 @@ struct SampleArgs {
     const int* trace_slot;
     int n_trace;
     unsigned long long* pair_count;
-    const int2* items;
+    const int* lig_order;      // ligands by decreasing cost; item it = (lig_order[it / P], it % P)
     int n_items;
     unsigned int* counter;
     int* err;
@@ -598,57 +678,78 @@ __device__ __forceinline__ Sched schedule(int S, int Lmc, int s) {
     return r;
 }
 
-__device__ __forceinline__ float& fld(const SampleArgs& A, int l, int f, int p) {
-    return A.state[((size_t)l * A.B.n_fields + f) * A.P + p];
+__device__ __forceinline__ float* fld(const SampleArgs& A, int l, int f, int p) {
+    return A.state + ((size_t)l * A.B.n_fields + f) * A.P + p;
 }
 
-__device__ void init_pose(const SampleArgs& A, const LigHdr& h, const Warp& W, int l, int p, PoseState& st) {
+__device__ void init_pose(const SampleArgs& A, const LigHdr& h, int lane, int l, int p, PoseState& st) {
     const uint32_t lig = (uint32_t)(A.lig_base + l);
-    float u[6 + kTmax];
-    for (int b = 0; b * 4 < 6 + h.n_tor; ++b) {
-        const uint4 r = rand_block(A.seed, lig, (uint32_t)p, 0u, 0u, (uint32_t)b);
-        for (int c = 0; c < 4 && b * 4 + c < 6 + h.n_tor; ++c) u[b * 4 + c] = u01(pick(r, c));
-    }
+    const uint4 r0 = rand_block(A.seed, lig, (uint32_t)p, 0u, 0u, 0u);
+    const uint4 r1 = rand_block(A.seed, lig, (uint32_t)p, 0u, 0u, 1u);
+    const float u[6] = {u01(r0.x), u01(r0.y), u01(r0.z), u01(r0.w), u01(r1.x), u01(r1.y)};
     for (int d = 0; d < 3; ++d) st.t[d] = fmaf(u[d], A.pk.box_hi[d] - A.pk.box_lo[d], A.pk.box_lo[d]);
     const float a = sqrtf(1.f - u[3]), b = sqrtf(u[3]);
     float s1, c1, s2, c2;
     sincospif(2.f * u[4], &s1, &c1);
     sincospif(2.f * u[5], &s2, &c2);
     st.q[0] = a * s1; st.q[1] = a * c1; st.q[2] = b * s2; st.q[3] = b * c2;
-    for (int k = 0; k < h.n_tor; ++k) W.TH(k) = fmaf(u[6 + k], kTwoPi, -kPi);
+    st.th = 0.f;
+    if (lane < h.n_tor) {
+        const int n = 6 + lane;
+        const uint4 r = rand_block(A.seed, lig, (uint32_t)p, 0u, 0u, (uint32_t)(n >> 2));
+        st.th = fmaf(u01(pick(r, n & 3)), kTwoPi, -kPi);
+    }
     for (int d = 0; d < 6; ++d) { st.m[d] = 0.f; st.v[d] = 0.f; }
     for (int d = 0; d < 3; ++d) st.st[d] = st.t[d];
     for (int d = 0; d < 4; ++d) st.sq[d] = st.q[d];
     st.ecur = __int_as_float(0x7fc00000);
     st.esaved = st.ecur;
     st.status = 0;
+    st.mth = st.vth = 0.f;
+    st.sth = st.th;
 }
 
-__device__ void load_pose(const SampleArgs& A, const LigHdr& h, const Warp& W, int l, int p, PoseState& st) {
+__device__ void load_pose(const SampleArgs& A, const LigHdr& h, int lane, int l, int p, PoseState& st) {
     const float* row = A.dof + ((size_t)l * A.P + p) * A.B.dof_stride;
     for (int d = 0; d < 3; ++d) st.t[d] = row[d];
     for (int d = 0; d < 4; ++d) st.q[d] = row[3 + d];
-    for (int k = 0; k < h.n_tor; ++k) W.TH(k) = row[7 + k];
-    for (int d = 0; d < 6; ++d) { st.m[d] = fld(A, l, kFieldM + d, p); st.v[d] = fld(A, l, kFieldV + d, p); }
-    for (int d = 0; d < 3; ++d) st.st[d] = fld(A, l, kFieldSaved + d, p);
-    for (int d = 0; d < 4; ++d) st.sq[d] = fld(A, l, kFieldSaved + 3 + d, p);
-    st.ecur = fld(A, l, kFieldEcur, p);
-    st.esaved = fld(A, l, kFieldEsaved, p);
-    st.status = __float_as_int(fld(A, l, kFieldStatus, p));
+    for (int d = 0; d < 6; ++d) { st.m[d] = *fld(A, l, kFieldM + d, p); st.v[d] = *fld(A, l, kFieldV + d, p); }
+    for (int d = 0; d < 3; ++d) st.st[d] = *fld(A, l, kFieldSaved + d, p);
+    for (int d = 0; d < 4; ++d) st.sq[d] = *fld(A, l, kFieldSaved + 3 + d, p);
+    st.ecur = *fld(A, l, kFieldEcur, p);
+    st.esaved = *fld(A, l, kFieldEsaved, p);
+    st.status = __float_as_int(*fld(A, l, kFieldStatus, p));
+    st.th = st.mth = st.vth = st.sth = 0.f;
+    if (lane < h.n_tor) {
+        const int M = A.B.max_tor;
+        st.th = row[7 + lane];
+        st.mth = *fld(A, l, kFieldTheta + lane, p);
+        st.vth = *fld(A, l, kFieldTheta + M + lane, p);
+        st.sth = *fld(A, l, kFieldTheta + 2 * M + lane, p);
+    }
 }
 
-__device__ void store_pose(const SampleArgs& A, const LigHdr& h, const Warp& W, int l, int p, const PoseState& st) {
+__device__ void store_pose(const SampleArgs& A, const LigHdr& h, int lane, int l, int p, const PoseState& st) {
     float* row = A.dof + ((size_t)l * A.P + p) * A.B.dof_stride;
-    for (int d = 0; d < 3; ++d) row[d] = st.t[d];
-    for (int d = 0; d < 4; ++d) row[3 + d] = st.q[d];
-    for (int k = 0; k < A.B.max_tor; ++k) row[7 + k] = k < h.n_tor ? W.TH(k) : 0.f;
-    for (int d = 0; d < 6; ++d) { fld(A, l, kFieldM + d, p) = st.m[d]; fld(A, l, kFieldV + d, p) = st.v[d]; }
-    for (int d = 0; d < 3; ++d) fld(A, l, kFieldSaved + d, p) = st.st[d];
-    for (int d = 0; d < 4; ++d) fld(A, l, kFieldSaved + 3 + d, p) = st.sq[d];
-    fld(A, l, kFieldEcur, p) = st.ecur;
-    fld(A, l, kFieldEsaved, p) = st.esaved;
-    fld(A, l, kFieldStatus, p) = __int_as_float(st.status);
-    A.energy[(size_t)l * A.P + p] = st.ecur;
+    const int M = A.B.max_tor;
+    if (lane == 0) {
+        for (int d = 0; d < 3; ++d) row[d] = st.t[d];
+        for (int d = 0; d < 4; ++d) row[3 + d] = st.q[d];
+        for (int d = 0; d < 6; ++d) { *fld(A, l, kFieldM + d, p) = st.m[d]; *fld(A, l, kFieldV + d, p) = st.v[d]; }
+        for (int d = 0; d < 3; ++d) *fld(A, l, kFieldSaved + d, p) = st.st[d];
+        for (int d = 0; d < 4; ++d) *fld(A, l, kFieldSaved + 3 + d, p) = st.sq[d];
+        *fld(A, l, kFieldEcur, p) = st.ecur;
+        *fld(A, l, kFieldEsaved, p) = st.esaved;
+        *fld(A, l, kFieldStatus, p) = __int_as_float(st.status);
+        A.energy[(size_t)l * A.P + p] = st.ecur;
+    }
+    if (lane < M) {
+        const bool own = lane < h.n_tor;
+        row[7 + lane] = own ? st.th : 0.f;
+        *fld(A, l, kFieldTheta + lane, p) = own ? st.mth : 0.f;
+        *fld(A, l, kFieldTheta + M + lane, p) = own ? st.vth : 0.f;
+        *fld(A, l, kFieldTheta + 2 * M + lane, p) = own ? st.sth : 0.f;
+    }
 }
 
 __device__ __forceinline__ float adam_delta(const SampleArgs& A, float g, float& m, float& v, float bc1, float sbc2) {
@@ -658,22 +759,23 @@ __device__ __forceinline__ float adam_delta(const SampleArgs& A, float g, float&
     return -(A.lr / bc1) * m / denom;
 }
 
-// One evaluation (and its update or acceptance test) of one pose; s is the global
-// evaluation index of the schedule.
+// One evaluation (and its update or acceptance test) of the warp's pose; s is the
+// global evaluation index of the schedule.  Every branch below is uniform across the
+// warp except the per-torsion lanes.
 template <int TS, bool COUNT>
-__device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h, const Warp& W, int l, int p,
-                            bool live, int s, PoseState& st, uint32_t& npairs) {
+__device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h, const PW& W, int l, int p, int s,
+                            PoseState& st, uint32_t& npairs) {
     if (st.status & 1) return;  // frozen after a non-finite energy
     const Sched sc = schedule(A.S, A.Lmc, s);
-    const int T = h.n_tor;
+    const int T = h.n_tor, lane = W.lane;
+    const bool own = lane < T;
     const uint32_t lig = (uint32_t)(A.lig_base + l);
     if (sc.j == 0) {
         if (sc.loop > 0) {
             // save the state, then resample one of the 6+T variables in its range
             for (int d = 0; d < 3; ++d) st.st[d] = st.t[d];
             for (int d = 0; d < 4; ++d) st.sq[d] = st.q[d];
-            if (live)
-                for (int k = 0; k < T; ++k) fld(A, l, kFieldTheta + 2 * A.B.max_tor + k, p) = W.TH(k);
+            st.sth = st.th;
             st.esaved = st.ecur;
             const uint4 r = rand_block(A.seed, lig, (uint32_t)p, (uint32_t)sc.loop, 1u, 0u);
             const int c = (int)(((unsigned long long)(r.x >> 8) * (unsigned long long)(6 + T)) >> 24);
@@ -688,36 +790,35 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
                 sincosf(0.5f * ang, &sh, &ch);
                 const float rq[4] = {ch, c == 3 ? sh : 0.f, c == 4 ? sh : 0.f, c == 5 ? sh : 0.f};
                 quat_premul(rq, st.q);
-            } else {
-                W.TH(c - 6) = fmaf(u1, kTwoPi, -kPi);
+            } else if (lane == c - 6) {
+                st.th = fmaf(u1, kTwoPi, -kPi);
             }
         }
         for (int d = 0; d < 6; ++d) { st.m[d] = 0.f; st.v[d] = 0.f; }
-        if (live)
-            for (int k = 0; k < T; ++k) {
-                fld(A, l, kFieldTheta + k, p) = 0.f;
-                fld(A, l, kFieldTheta + A.B.max_tor + k, p) = 0.f;
-            }
+        st.mth = st.vth = 0.f;
     }
     // evaluate
-    forward_kinematics(A.B, h, W, st.t, st.q);
+    fk_warp(A.B, h, W, st.t, st.q, st.th);
     ParamAcc acc;
     float e_inter;
-    const float E = score_pose<TS, false, COUNT>(A.B, A.pk, S, h, W, 1.f, acc, &e_inter, npairs);
+    const float E = score_warp<TS, false, COUNT>(A.B, A.pk, S, h, W, 1.f, acc, &e_inter, npairs);
     float gt[3], tau[3];
-    rigid_adjoint(h, W, st.t, gt, tau);
-    float* rec = nullptr;
-    if (A.trace && live) {
+    const float gth = adjoint_warp(A.B, h, W, st.t, gt, tau);
+    if (A.trace) {
         const int slot = A.trace_slot[(size_t)l * A.P + p];
         if (slot >= 0) {
-            rec = A.trace + ((size_t)(s - A.step_begin) * A.n_trace + slot) * trace_record(A.B.max_tor);
-            for (int d = 0; d < 3; ++d) rec[d] = st.t[d];
-            for (int d = 0; d < 4; ++d) rec[3 + d] = st.q[d];
-            for (int k = 0; k < A.B.max_tor; ++k) rec[7 + k] = k < T ? W.TH(k) : 0.f;
+            float* rec = A.trace + ((size_t)(s - A.step_begin) * A.n_trace + slot) * trace_record(A.B.max_tor);
             const int o = A.B.dof_stride;
-            rec[o] = E;
-            for (int d = 0; d < 3; ++d) { rec[o + 1 + d] = gt[d]; rec[o + 4 + d] = tau[d]; }
-            for (int k = T; k < A.B.max_tor; ++k) rec[o + 7 + k] = 0.f;
+            if (lane == 0) {
+                for (int d = 0; d < 3; ++d) rec[d] = st.t[d];
+                for (int d = 0; d < 4; ++d) rec[3 + d] = st.q[d];
+                rec[o] = E;
+                for (int d = 0; d < 3; ++d) { rec[o + 1 + d] = gt[d]; rec[o + 4 + d] = tau[d]; }
+            }
+            if (lane < A.B.max_tor) {
+                rec[7 + lane] = own ? st.th : 0.f;
+                rec[o + 7 + lane] = own ? gth : 0.f;
+            }
         }
     }
     if (!isfinite(E)) {
@@ -725,26 +826,11 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
         st.ecur = E;
         return;
     }
-    const bool update = sc.j < sc.n - 1;
-    float bc1 = 1.f, sbc2 = 1.f;
-    if (update) {
+    if (sc.j < sc.n - 1) {
         const int ta = sc.j + 1;
-        bc1 = 1.f - powf(A.b1, (float)ta);
-        sbc2 = sqrtf(1.f - powf(A.b2, (float)ta));
-    }
-    for (int k = 0; k < T; ++k) {
-        const float g = torsion_grad(A.B, h, W, k);
-        if (rec) rec[A.B.dof_stride + 7 + k] = g;
-        if (update) {
-            float& m = fld(A, l, kFieldTheta + k, p);
-            float& v = fld(A, l, kFieldTheta + A.B.max_tor + k, p);
-            float mm = m, vv = v;
-            const float dlt = adam_delta(A, g, mm, vv, bc1, sbc2);
-            if (live) { m = mm; v = vv; }
-            W.TH(k) = wrap_pi(W.TH(k) + dlt);
-        }
-    }
-    if (update) {
+        const float bc1 = 1.f - powf(A.b1, (float)ta);
+        const float sbc2 = sqrtf(1.f - powf(A.b2, (float)ta));
+        if (own) st.th = wrap_pi(st.th + adam_delta(A, gth, st.mth, st.vth, bc1, sbc2));
         for (int d = 0; d < 3; ++d) {
             const float dlt = adam_delta(A, gt[d], st.m[d], st.v[d], bc1, sbc2);
             st.t[d] = fminf(fmaxf(st.t[d] + dlt, A.pk.box_lo[d]), A.pk.box_hi[d]);
@@ -767,25 +853,11 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
             if (!(u < expf(-A.beta * (E - st.esaved)))) {
                 for (int d = 0; d < 3; ++d) st.t[d] = st.st[d];
                 for (int d = 0; d < 4; ++d) st.q[d] = st.sq[d];
-                for (int k = 0; k < T; ++k) W.TH(k) = fld(A, l, kFieldTheta + 2 * A.B.max_tor + k, p);
+                st.th = st.sth;
                 st.ecur = st.esaved;
             }
         }
     }
-}
-
-__device__ __forceinline__ Warp make_warp(unsigned char* smem, size_t warp_off, size_t warp_bytes, int Lmax, int Tmax,
-                                          bool params) {
-    Warp W;
-    const int wid = threadIdx.x >> 5;
-    float* base = reinterpret_cast<float*>(smem + warp_off + warp_bytes * wid);
-    W.xs = base;
-    W.gs = base + 3 * Lmax * 32;
-    W.ths = W.gs + 3 * Lmax * 32;
-    W.grs = params ? W.ths + Tmax * 32 : nullptr;
-    W.Lmax = Lmax;
-    W.lane = threadIdx.x & 31;
-    return W;
 }
 
 __device__ __forceinline__ void flush_count(unsigned long long* cnt, uint32_t n) {
@@ -795,56 +867,52 @@ __device__ __forceinline__ void flush_count(unsigned long long* cnt, uint32_t n)
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(cnt, v);
 }
 
-// Persistent fused sampler: each warp pops (ligand, 32-pose tile) items from a global
-// counter and runs every evaluation of its poses with the state held on chip.
+// Persistent fused sampler: each warp pops poses from a global counter (ligands in
+// decreasing-cost order) and runs every evaluation of the pose with its state on chip.
 template <int TS, bool COUNT>
-__global__ void __launch_bounds__(128, 1) k_sample_persistent(SampleArgs A) {
+__global__ void __launch_bounds__(256, 2) k_sample_persistent(SampleArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
     Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
            reinterpret_cast<const uint8_t*>(smem + A.ptype_off)};
-    const Warp W = make_warp(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor, false);
+    const PW W = make_pw(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor);
     uint32_t npairs = 0;
     for (;;) {
         int it = 0;
         if (W.lane == 0) it = (int)atomicAdd(A.counter, 1u);
         it = __shfl_sync(kFull, it, 0);
         if (it >= A.n_items) break;
-        const int2 item = A.items[it];
-        const int l = item.x;
+        const int l = A.lig_order[it / A.P];
+        const int p = it % A.P;
         const LigHdr h = A.B.lig[l];
-        const int p = min(item.y + W.lane, A.P - 1);
-        const bool live = item.y + W.lane < A.P;
         PoseState st;
-        if (A.step_begin == 0) init_pose(A, h, W, l, p, st);
-        else load_pose(A, h, W, l, p, st);
-        for (int s = A.step_begin; s < A.step_end; ++s) sample_step<TS, COUNT>(A, S, h, W, l, p, live, s, st, npairs);
-        if (live) store_pose(A, h, W, l, p, st);
+        if (A.step_begin == 0) init_pose(A, h, W.lane, l, p, st);
+        else load_pose(A, h, W.lane, l, p, st);
+        for (int s = A.step_begin; s < A.step_end; ++s) sample_step<TS, COUNT>(A, S, h, W, l, p, s, st, npairs);
+        store_pose(A, h, W.lane, l, p, st);
         __syncwarp();
     }
     if (COUNT) flush_count(A.pair_count, npairs);
 }
 
-// Plain form: one launch per (ligand, evaluation) with the state in global memory,
-// the same device code as the persistent sampler.
+// Plain form: one launch per (ligand, evaluation), one warp per pose, the state in
+// global memory between launches; the same device code as the persistent sampler.
 template <int TS, bool COUNT>
-__global__ void __launch_bounds__(128, 1) k_sample_step(SampleArgs A, int l, int s) {
+__global__ void __launch_bounds__(256, 2) k_sample_step(SampleArgs A, int l, int s) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
     Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
            reinterpret_cast<const uint8_t*>(smem + A.ptype_off)};
-    const Warp W = make_warp(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor, false);
-    const int p0 = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
-    if (p0 >= A.P) return;
+    const PW W = make_pw(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor);
+    const int p = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    if (p >= A.P) return;
     const LigHdr h = A.B.lig[l];
-    const int p = min(p0 + W.lane, A.P - 1);
-    const bool live = p0 + W.lane < A.P;
     uint32_t npairs = 0;
     PoseState st;
-    if (s == 0) init_pose(A, h, W, l, p, st);
-    else load_pose(A, h, W, l, p, st);
-    sample_step<TS, COUNT>(A, S, h, W, l, p, live, s, st, npairs);
-    if (live) store_pose(A, h, W, l, p, st);
+    if (s == 0) init_pose(A, h, W.lane, l, p, st);
+    else load_pose(A, h, W.lane, l, p, st);
+    sample_step<TS, COUNT>(A, S, h, W, l, p, s, st, npairs);
+    store_pose(A, h, W.lane, l, p, st);
     if (COUNT) flush_count(A.pair_count, npairs);
 }
 
@@ -860,86 +928,94 @@ struct ScoreArgs {
     float* g_xyz;
     const float* e_bar;
     float* partials;   // [n_items][5 + kNT]
-    const int2* items;
+    const int2* items; // (ligand, first pose of a 32-pose tile)
     int n_items;
     unsigned int* counter;
     int* err;
     size_t params_bytes, pocket_off, ptype_off, mbar_off, warp_off, warp_bytes;
 };
 
+// Each warp takes a (ligand, 32-pose tile) item and scores its poses one after another;
+// parameter-gradient sums of the tile are reduced in a fixed order into one row.
 template <int TS, bool PARAMS>
-__global__ void __launch_bounds__(256) k_score(ScoreArgs A) {
+__global__ void __launch_bounds__(256, 2) k_score(ScoreArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
     Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
            reinterpret_cast<const uint8_t*>(smem + A.ptype_off)};
-    const Warp W = make_warp(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor, PARAMS);
-    const int D = A.B.dof_stride;
+    const PW W = make_pw(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor);
+    const int D = A.B.dof_stride, lane = W.lane;
     for (;;) {
         int it = 0;
-        if (W.lane == 0) it = (int)atomicAdd(A.counter, 1u);
+        if (lane == 0) it = (int)atomicAdd(A.counter, 1u);
         it = __shfl_sync(kFull, it, 0);
         if (it >= A.n_items) break;
         const int2 item = A.items[it];
         const int l = item.x;
         const LigHdr h = A.B.lig[l];
-        const int p = min(item.y + W.lane, A.P - 1);
-        const bool live = item.y + W.lane < A.P;
-        const size_t gp = (size_t)l * A.P + p;
-        const float* row = A.dof + gp * D;
-        float t[3] = {row[0], row[1], row[2]};
-        float q[4] = {row[3], row[4], row[5], row[6]};
-        for (int k = 0; k < h.n_tor; ++k) W.TH(k) = row[7 + k];
-        const float ebar = (A.e_bar && live) ? A.e_bar[gp] : (live ? 1.f : 0.f);
         ParamAcc acc;
         for (int t5 = 0; t5 < 5; ++t5) acc.gw[t5] = 0.f;
         if (PARAMS)
-            for (int a = 0; a < kNT; ++a) W.grs[a * 32 + W.lane] = 0.f;
-        forward_kinematics(A.B, h, W, t, q);
-        float e_inter;
-        uint32_t np = 0;
-        const float E = score_pose<TS, PARAMS, false>(A.B, A.pk, S, h, W, ebar, acc, &e_inter, np);
-        if (live) {
-            A.energy[gp] = E;
-            if (A.e_inter) A.e_inter[gp] = e_inter;
-        }
-        if (A.g_dof && live) {
-            float gt[3], tau[3];
-            rigid_adjoint(h, W, t, gt, tau);
-            float* o = A.g_dof + gp * D;
-            const float sc = A.e_bar ? ebar : 1.f;
-            for (int d = 0; d < 3; ++d) o[d] = sc * gt[d];
-            // dE/dq of E(q/|q|) = 4 M(qhat) tau / |q|, M(q) = 1/2 [-v^T ; w I - [v]x]
-            const float n = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-            const float w = q[0] * n, vx = q[1] * n, vy = q[2] * n, vz = q[3] * n;
-            const float c0 = vy * tau[2] - vz * tau[1], c1 = vz * tau[0] - vx * tau[2], c2 = vx * tau[1] - vy * tau[0];
-            o[3] = sc * 2.f * n * (-(vx * tau[0] + vy * tau[1] + vz * tau[2]));
-            o[4] = sc * 2.f * n * (w * tau[0] - c0);
-            o[5] = sc * 2.f * n * (w * tau[1] - c1);
-            o[6] = sc * 2.f * n * (w * tau[2] - c2);
-            for (int k = 0; k < A.B.max_tor; ++k) o[7 + k] = k < h.n_tor ? sc * torsion_grad(A.B, h, W, k) : 0.f;
-        }
-        if (A.g_xyz && live) {
-            const float sc = A.e_bar ? ebar : 1.f;
-            float* o = A.g_xyz + gp * A.B.max_atoms * 3;
-            for (int i = 0; i < A.B.max_atoms * 3; ++i) o[i] = 0.f;
-            for (int i = 0; i < h.n_atoms; ++i) {
-                const int oi = __ldg(&A.B.atom_orig[h.atom_off + i]);
-                o[3 * oi] = sc * W.G(0, i); o[3 * oi + 1] = sc * W.G(1, i); o[3 * oi + 2] = sc * W.G(2, i);
+            for (int a = 0; a < kNT; ++a) W.grs[a * 32 + lane] = 0.f;
+        const int p_end = min(item.y + 32, A.P);
+        for (int p = item.y; p < p_end; ++p) {
+            const size_t gp = (size_t)l * A.P + p;
+            const float* row = A.dof + gp * D;
+            const float t[3] = {row[0], row[1], row[2]};
+            const float q[4] = {row[3], row[4], row[5], row[6]};
+            const float th = lane < h.n_tor ? row[7 + lane] : 0.f;
+            const float ebar = A.e_bar ? A.e_bar[gp] : 1.f;
+            fk_warp(A.B, h, W, t, q, th);
+            float e_inter;
+            uint32_t np = 0;
+            const float E = score_warp<TS, PARAMS, false>(A.B, A.pk, S, h, W, ebar, acc, &e_inter, np);
+            if (lane == 0) {
+                A.energy[gp] = E;
+                if (A.e_inter) A.e_inter[gp] = e_inter;
             }
+            if (A.g_dof) {
+                float gt[3], tau[3];
+                const float gth = adjoint_warp(A.B, h, W, t, gt, tau);
+                float* o = A.g_dof + gp * D;
+                const float sc = A.e_bar ? ebar : 1.f;
+                if (lane == 0) {
+                    for (int d = 0; d < 3; ++d) o[d] = sc * gt[d];
+                    // dE/dq of E(q/|q|) = 4 M(qhat) tau / |q|, M(q) = 1/2 [-v^T ; w I - [v]x]
+                    const float n = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+                    const float w = q[0] * n, vx = q[1] * n, vy = q[2] * n, vz = q[3] * n;
+                    const float c0 = vy * tau[2] - vz * tau[1], c1 = vz * tau[0] - vx * tau[2],
+                                c2 = vx * tau[1] - vy * tau[0];
+                    o[3] = sc * 2.f * n * (-(vx * tau[0] + vy * tau[1] + vz * tau[2]));
+                    o[4] = sc * 2.f * n * (w * tau[0] - c0);
+                    o[5] = sc * 2.f * n * (w * tau[1] - c1);
+                    o[6] = sc * 2.f * n * (w * tau[2] - c2);
+                }
+                if (lane < A.B.max_tor) o[7 + lane] = lane < h.n_tor ? sc * gth : 0.f;
+            }
+            if (A.g_xyz) {
+                const float sc = A.e_bar ? ebar : 1.f;
+                float* o = A.g_xyz + gp * A.B.max_atoms * 3;
+                for (int i = lane; i < A.B.max_atoms; i += 32) {
+                    if (i < h.n_atoms) {
+                        const int oi = __ldg(&A.B.atom_orig[h.atom_off + i]);
+                        const float4 g = W.gs[i];
+                        o[3 * oi] = sc * g.x; o[3 * oi + 1] = sc * g.y; o[3 * oi + 2] = sc * g.z;
+                    } else {
+                        o[3 * i] = 0.f; o[3 * i + 1] = 0.f; o[3 * i + 2] = 0.f;
+                    }
+                }
+            }
+            __syncwarp();
         }
         if (PARAMS) {
-            // fixed-order warp reductions; one partial row per item
             float* prow = A.partials + (size_t)it * (5 + kNT);
             for (int t5 = 0; t5 < 5; ++t5) {
-                float v = acc.gw[t5];
-                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-                if (W.lane == 0) prow[t5] = v;
+                const float v = warp_sum(acc.gw[t5]);
+                if (lane == 0) prow[t5] = v;
             }
             for (int a = 0; a < kNT; ++a) {
-                float v = W.grs[a * 32 + W.lane];
-                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-                if (W.lane == 0) prow[5 + a] = v;
+                const float v = warp_sum(W.grs[a * 32 + lane]);
+                if (lane == 0) prow[5 + a] = v;
             }
         }
         __syncwarp();
@@ -1122,8 +1198,9 @@ struct trids_batch {
     uint32_t* d_pairs = nullptr;
     // per-pose-count caches
     int items_P = -1;
-    int2* d_items = nullptr;
+    int2* d_items = nullptr;        // (ligand, first pose of a 32-pose tile), by decreasing cost
     int n_items = 0;
+    int* d_lig_order = nullptr;     // ligands by decreasing cost
     unsigned int* d_counter = nullptr;   // [4]
     int* d_err = nullptr;                // [2]: staging timeout, status OR
     float* d_partials = nullptr;
@@ -1240,22 +1317,28 @@ int device_guard(int dev) {
 int ensure_items(trids_batch* b, int P) {
     if (b->items_P == P) return TRIDS_OK;
     const int tiles = (P + 31) / 32;
-    std::vector<std::pair<double, int2>> it;
-    it.reserve((size_t)b->dims.n_lig * tiles);
+    std::vector<std::pair<double, int>> lc(b->dims.n_lig);
     for (int l = 0; l < b->dims.n_lig; ++l) {
         const LigHdr& h = b->hdr[l];
-        const double cost = 60.0 * h.n_atoms + 1.0 * h.n_pairs + 20.0 * h.n_tor + 10.0;
-        for (int t = 0; t < tiles; ++t) it.push_back({cost, make_int2(l, t * 32)});
+        lc[l] = {60.0 * h.n_atoms + 2.0 * h.n_pairs + 20.0 * h.n_tor + 10.0, l};
     }
-    std::stable_sort(it.begin(), it.end(), [](const std::pair<double, int2>& a, const std::pair<double, int2>& c) {
+    std::stable_sort(lc.begin(), lc.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& c) {
         return a.first > c.first;
     });
-    std::vector<int2> items(it.size());
-    for (size_t i = 0; i < it.size(); ++i) items[i] = it[i].second;
-    if (b->d_items) cudaFree(b->d_items);
+    std::vector<int> order(lc.size());
+    std::vector<int2> items;
+    items.reserve((size_t)b->dims.n_lig * tiles);
+    for (size_t i = 0; i < lc.size(); ++i) {
+        order[i] = lc[i].second;
+        for (int t = 0; t < tiles; ++t) items.push_back(make_int2(lc[i].second, t * 32));
+    }
+    cudaFree(b->d_items);
+    cudaFree(b->d_lig_order);
     b->d_items = nullptr;
+    b->d_lig_order = nullptr;
     int rc = upload(&b->d_items, items);
     if (rc) return rc;
+    if ((rc = upload(&b->d_lig_order, order))) return rc;
     b->n_items = (int)items.size();
     b->items_P = P;
     return TRIDS_OK;
@@ -1276,7 +1359,7 @@ size_t max_smem(int dev) {
 // Pick warps per block: the requested count, capped so the block fits in shared memory.
 int pick_warps(int requested, const trids_pocket* pk, const trids_batch* b, bool params, Layout* L) {
     const size_t cap = max_smem(pk->device);
-    int w = requested > 0 ? std::min(requested, 8) : 4;
+    int w = requested > 0 ? std::min(requested, 8) : 8;
     for (; w >= 1; --w) {
         *L = make_layout(pk->prm.term_set, pk->M, b->dims.max_atoms, b->dims.max_tor, w, params);
         if (L->total <= cap) return w;
@@ -1483,9 +1566,35 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
             tp.push_back(make_float4((float)((double)X[3 * pa] - lg.c[0]), (float)((double)X[3 * pa + 1] - lg.c[1]),
                                      (float)((double)X[3 * pa + 2] - lg.c[2]), 0.f));
         }
-        for (auto& pr : lg.pairs) {
-            const uint32_t ti = (uint32_t)Ty[lg.perm[pr.first]], tj = (uint32_t)Ty[lg.perm[pr.second]];
-            pairs.push_back((uint32_t)pr.first | ((uint32_t)pr.second << 8) | (ti << 16) | (tj << 24));
+        // intra pairs in rounds of <= 32 pairs sharing no atom (first fit in list order)
+        {
+            std::vector<std::vector<uint32_t>> rounds;
+            std::vector<std::pair<uint64_t, uint64_t>> used;
+            for (auto& pr : lg.pairs) {
+                const uint32_t ti = (uint32_t)Ty[lg.perm[pr.first]], tj = (uint32_t)Ty[lg.perm[pr.second]];
+                const uint32_t word = (uint32_t)pr.first | ((uint32_t)pr.second << 8) | (ti << 16) | (tj << 24);
+                auto bit = [](int a) {
+                    return a < 64 ? std::make_pair(1ull << a, 0ull) : std::make_pair(0ull, 1ull << (a - 64));
+                };
+                const auto ba = bit(pr.first), bb = bit(pr.second);
+                size_t r = 0;
+                for (; r < rounds.size(); ++r)
+                    if (rounds[r].size() < 32 && !((used[r].first & (ba.first | bb.first)) ||
+                                                   (used[r].second & (ba.second | bb.second))))
+                        break;
+                if (r == rounds.size()) {
+                    rounds.emplace_back();
+                    used.push_back({0ull, 0ull});
+                }
+                rounds[r].push_back(word);
+                used[r].first |= ba.first | bb.first;
+                used[r].second |= ba.second | bb.second;
+            }
+            h.n_chunks = (int)rounds.size();
+            for (auto& rd : rounds) {
+                for (uint32_t wd : rd) pairs.push_back(wd);
+                for (size_t k = rd.size(); k < 32; ++k) pairs.push_back(0xffffffffu);
+            }
         }
         b->hdr.push_back(h);
         ao += n_atoms[l];
@@ -1513,7 +1622,7 @@ int trids_free_batch(trids_batch* b) {
     if (b->ev_a) cudaEventDestroy(b->ev_a);
     if (b->ev_b) cudaEventDestroy(b->ev_b);
     cudaFree(b->d_lig); cudaFree(b->d_atom_y); cudaFree(b->d_atom_orig); cudaFree(b->d_tor_idx);
-    cudaFree(b->d_tor_u); cudaFree(b->d_tor_p); cudaFree(b->d_pairs); cudaFree(b->d_items);
+    cudaFree(b->d_tor_u); cudaFree(b->d_tor_p); cudaFree(b->d_pairs); cudaFree(b->d_items); cudaFree(b->d_lig_order);
     cudaFree(b->d_counter); cudaFree(b->d_err); cudaFree(b->d_partials);
     delete b;
     return TRIDS_OK;
@@ -1576,7 +1685,7 @@ int trids_score_grad(const trids_pocket* pk, const trids_batch* bc, int32_t pose
         }
     }
     Layout L;
-    const int warps = pick_warps(4, pk, b, params, &L);
+    const int warps = pick_warps(8, pk, b, params, &L);
     if (!warps) return fail(TRIDS_EINVAL, "pocket of %d atoms does not fit in shared memory", pk->M);
     ScoreArgs A;
     std::memset(&A, 0, sizeof A);
@@ -1637,7 +1746,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         return rc;
     if ((rc = ensure_items(b, c.poses))) return rc;
     Layout L;
-    const int warps = pick_warps(std::min(c.warps_per_block > 0 ? c.warps_per_block : 4, 4), pk, b, false, &L);
+    const int warps = pick_warps(c.warps_per_block, pk, b, false, &L);
     if (!warps) return fail(TRIDS_EINVAL, "pocket of %d atoms does not fit in shared memory", pk->M);
     SampleArgs A;
     std::memset(&A, 0, sizeof A);  // the bytes form the graph-cache key
@@ -1645,7 +1754,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     A.step_end = c.step_end; A.Lmc = c.mc_loops; A.lr = c.lr; A.b1 = c.beta1; A.b2 = c.beta2; A.eps = c.eps;
     A.beta = c.beta; A.seed = c.seed; A.lig_base = c.lig_base; A.dof = dof; A.state = state; A.energy = energy;
     A.trace = c.trace; A.trace_slot = c.trace_slot; A.n_trace = c.n_trace; A.pair_count = c.pair_count;
-    A.items = b->d_items; A.n_items = b->n_items; A.counter = b->d_counter; A.err = b->d_err;
+    A.lig_order = b->d_lig_order; A.n_items = b->dims.n_lig * c.poses; A.counter = b->d_counter; A.err = b->d_err;
     A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.ptype_off = L.ptype_off;
     A.mbar_off = L.mbar_off;
     A.warp_off = L.warp_off; A.warp_bytes = L.warp_bytes;
@@ -1656,8 +1765,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         auto kern = tt ? (cnt ? k_sample_step<TRIDS_TERMS_TRIDS, true> : k_sample_step<TRIDS_TERMS_TRIDS, false>)
                        : (cnt ? k_sample_step<TRIDS_TERMS_VINA5, true> : k_sample_step<TRIDS_TERMS_VINA5, false>);
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-        const int tiles = (c.poses + 31) / 32;
-        const int blocks = (tiles + warps - 1) / warps;
+        const int blocks = (c.poses + warps - 1) / warps;
         for (int s = c.step_begin; s < c.step_end; ++s)
             for (int l = 0; l < b->dims.n_lig; ++l) kern<<<blocks, 32 * warps, L.total, st>>>(A, l, s);
         CK(cudaGetLastError());
@@ -1666,7 +1774,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     auto kern = tt ? (cnt ? k_sample_persistent<TRIDS_TERMS_TRIDS, true> : k_sample_persistent<TRIDS_TERMS_TRIDS, false>)
                    : (cnt ? k_sample_persistent<TRIDS_TERMS_VINA5, true> : k_sample_persistent<TRIDS_TERMS_VINA5, false>);
     int grid = 0;
-    if ((rc = grid_for(kern, warps, L.total, pk->device, b->n_items, &grid))) return rc;
+    if ((rc = grid_for(kern, warps, L.total, pk->device, A.n_items, &grid))) return rc;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(st, &cap));
     if (!c.use_graph || cap != cudaStreamCaptureStatusNone) {
@@ -1811,7 +1919,7 @@ int trids_score_grad_noalloc(const trids_pocket* pk, const trids_batch* b, int32
     unsigned char* scratch = nullptr;
     if ((rc = noalloc_scratch(pk->device, &scratch))) return rc;
     Layout L;
-    const int warps = pick_warps(4, pk, b, params, &L);
+    const int warps = pick_warps(8, pk, b, params, &L);
     if (!warps) return fail(TRIDS_EINVAL, "pocket of %d atoms does not fit in shared memory", pk->M);
     ScoreArgs A;
     std::memset(&A, 0, sizeof A);

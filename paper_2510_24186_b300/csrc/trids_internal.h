@@ -80,7 +80,7 @@ struct DevPocket {
 
 struct LigHdr {
     int n_atoms, n_tor, atom_off, tor_off;
-    int pair_off, n_pairs, pad0, pad1;
+    int pair_off, n_pairs, n_chunks, pad0;   // intra pairs: n_chunks rounds of 32 slots at pair_off
 };
 
 struct DevBatch {
@@ -91,7 +91,7 @@ struct DevBatch {
     const int4* tor_idx;           // (parent atom, child atom, subtree begin, subtree end)
     const float4* tor_u;           // unit axis, input geometry
     const float4* tor_p;           // parent atom, local coords
-    const uint32_t* pairs;         // i | j << 8 | ti << 16 | tj << 24
+    const uint32_t* pairs;         // i | j << 8 | ti << 16 | tj << 24; 0xffffffff = empty slot
 };
 
 // Sampler state fields per pose (SoA over poses inside each ligand):
