@@ -170,6 +170,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--n-lig", type=int, default=0, help="first N ligands only (small profiling case)")
+    ap.add_argument("--cell", type=float, default=0.0, help="candidate-grid cell edge in A (0 = library default)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -187,7 +188,7 @@ def main():
 
     w = synth.workload(2, n_lig=args.n_lig or None)
     sp = api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, w.cutoff)
-    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
+    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, cell=args.cell)
     arrays = synth.concat_ligands(w.ligands)
     b = api.Batch(pk, *arrays)
     P, S, Lm = w.poses, w.steps, w.mc_loops
@@ -308,7 +309,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "n_lig": n_lig, "poses": P, "steps": S, "mc_loops": Lm,
                    "pocket_atoms": len(w.pocket.type), "top_k": w.topk, "term_set": "vina5",
-                   "graph": True, "l2": "flushed between steps (256 MB write)",
+                   "graph": True, "l2": "flushed between steps (256 MB write)", "cell": args.cell or 0.5,
                    "parallelism": f"ligand shards x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,

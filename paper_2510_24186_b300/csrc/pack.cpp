@@ -236,31 +236,36 @@ void build_grid(int M, const float* xyz, float cutoff, float h, CandidateGrid* g
     const double reach = cutoff + 0.5 * std::sqrt(3.0) * h + 1e-3 * h + 1e-4;
     const double reach2 = reach * reach;
     const int span = (int)std::ceil(reach / h) + 1;
-    std::vector<std::vector<uint16_t>> lists(ncell);
-    for (int j = 0; j < M; ++j) {
-        double p[3] = {xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2]};
+    // two passes over (atom, nearby cell): count, then fill in ascending atom order
+    auto visit = [&](int j, auto&& fn) {
+        const double p[3] = {xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2]};
         int c[3];
         for (int d = 0; d < 3; ++d) c[d] = (int)std::floor((p[d] - g->lo[d]) / h);
-        for (int iz = std::max(0, c[2] - span); iz <= std::min(nz - 1, c[2] + span); ++iz)
-            for (int iy = std::max(0, c[1] - span); iy <= std::min(ny - 1, c[1] + span); ++iy)
+        for (int iz = std::max(0, c[2] - span); iz <= std::min(nz - 1, c[2] + span); ++iz) {
+            const double cz = g->lo[2] + (iz + 0.5) * h - p[2];
+            for (int iy = std::max(0, c[1] - span); iy <= std::min(ny - 1, c[1] + span); ++iy) {
+                const double cy = g->lo[1] + (iy + 0.5) * h - p[1];
+                const double r2yz = cy * cy + cz * cz;
+                if (r2yz > reach2) continue;
                 for (int ix = std::max(0, c[0] - span); ix <= std::min(nx - 1, c[0] + span); ++ix) {
-                    double cx = g->lo[0] + (ix + 0.5) * h - p[0];
-                    double cy = g->lo[1] + (iy + 0.5) * h - p[1];
-                    double cz = g->lo[2] + (iz + 0.5) * h - p[2];
-                    if (cx * cx + cy * cy + cz * cz <= reach2)
-                        lists[((size_t)iz * ny + iy) * nx + ix].push_back((uint16_t)j);
+                    const double cx = g->lo[0] + (ix + 0.5) * h - p[0];
+                    if (cx * cx + r2yz <= reach2) fn(((size_t)iz * ny + iy) * nx + ix);
                 }
-    }
+            }
+        }
+    };
+    std::vector<uint32_t> count(ncell, 0);
+    for (int j = 0; j < M; ++j) visit(j, [&](size_t cell) { ++count[cell]; });
     g->start.assign(ncell + 1, 0);
     size_t total = 0;
-    for (size_t c = 0; c < ncell; ++c) {
-        g->start[c] = (uint32_t)total;
-        total += (lists[c].size() + 7) / 8 * 8;
+    for (size_t cidx = 0; cidx < ncell; ++cidx) {
+        g->start[cidx] = (uint32_t)total;
+        total += (count[cidx] + 7) / 8 * 8;
     }
     g->start[ncell] = (uint32_t)total;
     g->cand.assign(total, (uint16_t)M);
-    for (size_t c = 0; c < ncell; ++c)
-        std::copy(lists[c].begin(), lists[c].end(), g->cand.begin() + g->start[c]);
+    std::vector<uint32_t> fill(g->start.begin(), g->start.end() - 1);
+    for (int j = 0; j < M; ++j) visit(j, [&](size_t cell) { g->cand[fill[cell]++] = (uint16_t)j; });
 }
 
 }  // namespace trids

@@ -460,13 +460,17 @@ __device__ float inter_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             const uint4 vc = v;
             if (blk + 1 < hi && blk + 1 < nxt) v = __ldg(reinterpret_cast<const uint4*>(cand + cur + 8));
             cur += 8;
-            const uint32_t wv[4] = {vc.x, vc.y, vc.z, vc.w};
             // pair-flag selectors: hydrophobic needs both bit0; donor-acceptor needs
             // (donor_i & acceptor_j) | (acceptor_i & donor_j)
             const uint32_t f_hyd = fi & 1u;
             const uint32_t f_hb = ((fi & 2u) << 1) | ((fi & 4u) >> 1);
+            // two halves of four candidates: the loop body stays small for the
+            // instruction cache, which the 16 resident warps share across all phases
+#pragma unroll 1
+            for (int hv = 0; hv < 2; ++hv) {
+            const uint32_t wv[2] = {hv ? vc.z : vc.x, hv ? vc.w : vc.y};
 #pragma unroll
-            for (int s = 0; s < 8; ++s) {
+            for (int s = 0; s < 4; ++s) {
                 const uint32_t ent = (s & 1) ? (wv[s >> 1] >> 16) : (wv[s >> 1] & 0xffffu);
                 const int j = (int)(ent & 0x1fffu);
                 const uint32_t fj = ent >> 13;
@@ -505,6 +509,7 @@ __device__ float inter_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                     }
                 }
                 if (COUNT) npairs += in ? 1u : 0u;
+            }
             }
         }
         W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
@@ -1423,7 +1428,7 @@ int trids_make_pocket(const float* xyz, const int32_t* type, int32_t n_atoms, co
     pk->M = n_atoms;
     pk->prm = *prm;
     pk->cutoff_built = prm->cutoff;
-    pk->cell = cell > 0.f ? cell : 1.0f;
+    pk->cell = cell > 0.f ? cell : 0.5f;
     pk->xyz.assign(xyz, xyz + 3 * (size_t)n_atoms);
     pk->type.assign(type, type + n_atoms);
     for (int d = 0; d < 3; ++d) {
