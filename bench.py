@@ -179,7 +179,7 @@ def main():
         return run_reference(args, rank)
 
     import torch
-    from paper_2510_24186_b300 import api
+    from paper_2510_24186_b300 import api, parallel
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -233,11 +233,7 @@ def main():
         dist.barrier()
     t_sample = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
     t_step = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
-    total_ms = sum(t_step)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = parallel.max_over_ranks(sum(t_step), device="cuda")
     rc = api.sync(b, P, state, timeout_ms=60000)
 
     # in-cutoff pair counts of the same trajectories (untimed counting variant; the
