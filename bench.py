@@ -188,8 +188,13 @@ def main():
 
     w = synth.workload(2, n_lig=args.n_lig or None)
     sp = api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, w.cutoff)
-    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, cell=args.cell)
     arrays = synth.concat_ligands(w.ligands)
+    tuned = None
+    if not args.cell and not args.warps:
+        from paper_2510_24186_b300 import autotune
+        tuned = autotune.autotune(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, arrays, w.poses)
+        args.cell, args.warps = tuned.cell, tuned.warps_per_block
+    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, cell=args.cell)
     b = api.Batch(pk, *arrays)
     P, S, Lm = w.poses, w.steps, w.mc_loops
     n_lig = b.n_lig
@@ -306,6 +311,9 @@ def main():
         "config": {"workload": w.name, "n_lig": n_lig, "poses": P, "steps": S, "mc_loops": Lm,
                    "pocket_atoms": len(w.pocket.type), "top_k": w.topk, "term_set": "vina5",
                    "graph": True, "l2": "flushed between steps (256 MB write)", "cell": args.cell or 0.5,
+                   "warps_per_block": args.warps or 8,
+                   "autotuned": None if tuned is None else {"table_ms": tuned.table, "probe": "256 ligands x 6 "
+                                                            "evaluations per shape"},
                    "parallelism": f"ligand shards x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,

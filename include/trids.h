@@ -46,6 +46,7 @@ extern "C" {
 #define TRIDS_MAX_GMM 4
 #define TRIDS_MAX_ATOMS 70    /* heavy atoms per ligand */
 #define TRIDS_MAX_TOR 20      /* rotatable bonds per ligand */
+#define TRIDS_MAX_BOXES 8     /* docking boxes per pocket */
 
 #define TRIDS_TERMS_VINA5 0
 #define TRIDS_TERMS_TRIDS 1
@@ -147,6 +148,15 @@ int trids_make_pocket(const float* xyz, const int32_t* type, int32_t n_atoms,
 /* Replace the scoring parameters (weights, radii, flags, GMM).  The cutoff may not
  * exceed the one the pocket was built with.  Stream-ordered on `stream`. */
 int trids_set_params(trids_pocket* pk, const trids_params* prm, void* stream);
+
+/*
+ * Several docking boxes, e.g. one per candidate cavity of a receptor region (the paper
+ * defines one box per task, Sec. 2 "Conformation sampling"; several boxes let one call
+ * sample several cavities).  Pose p samples, is perturbed and is clamped in box
+ * p mod n_boxes.  centers, sizes: host [n_boxes][3]; 1 <= n_boxes <= TRIDS_MAX_BOXES.
+ * Takes effect for launches issued after the call.
+ */
+int trids_set_boxes(trids_pocket* pk, int32_t n_boxes, const float* centers, const float* sizes);
 
 int trids_free_pocket(trids_pocket* pk);
 

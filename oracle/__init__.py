@@ -41,13 +41,18 @@ class Eval(C.Structure):
                 ("g_x", (C.c_double * 3) * LMAX), ("x", (C.c_double * 3) * LMAX),
                 ("g_w", C.c_double * 5), ("g_R", C.c_double * NT),
                 ("n_inter", C.c_int64), ("n_intra", C.c_int64), ("n_straddle", C.c_int32),
-                ("e_slack", C.c_double), ("g_slack", C.c_double)]
+                ("e_slack", C.c_double), ("g_slack", C.c_double), ("e_mag", C.c_double),
+                ("g_mag", C.c_double * (7 + TMAX))]
+
+
+MAX_BOXES = 8
 
 
 class SampleCfg(C.Structure):
     _fields_ = [("steps", C.c_int32), ("mc_loops", C.c_int32), ("lr", C.c_double), ("b1", C.c_double),
                 ("b2", C.c_double), ("eps", C.c_double), ("beta", C.c_double), ("seed", C.c_uint64),
-                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3)]
+                ("n_boxes", C.c_int32), ("box_lo", (C.c_double * 3) * MAX_BOXES),
+                ("box_hi", (C.c_double * 3) * MAX_BOXES)]
 
 
 def build(force: bool = False) -> str:
@@ -87,7 +92,7 @@ def lib():
         L.or_metropolis_u.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
         L.or_metropolis_u.restype = C.c_double
         L.or_metropolis_accept.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
-        L.or_adam_step.argtypes = [P(SampleCfg), C.c_int, C.c_int, P(C.c_double), P(C.c_double),
+        L.or_adam_step.argtypes = [P(SampleCfg), C.c_int, C.c_int, C.c_uint32, P(C.c_double), P(C.c_double),
                                    P(C.c_double), P(C.c_double)]
         L.or_sample_pose.argtypes = [P(SampleCfg), P(Params), C.c_int, P(C.c_double), P(C.c_int32),
                                      P(Ligand), C.c_uint32, C.c_uint32, P(C.c_double), P(C.c_int64)]
@@ -206,11 +211,16 @@ def philox(ctr, key):
 
 def sample_cfg(steps=30, mc_loops=8, lr=0.1, b1=0.9, b2=0.999, eps=1e-8, beta=0.069, seed=0,
                box_lo=(-11.25,) * 3, box_hi=(11.25,) * 3):
+    """box_lo / box_hi: one box (3 values) or several ([n][3]); pose p uses box p mod n."""
     c = SampleCfg()
     c.steps, c.mc_loops, c.lr, c.b1, c.b2, c.eps, c.beta, c.seed = steps, mc_loops, lr, b1, b2, eps, beta, seed
-    for d in range(3):
-        c.box_lo[d] = box_lo[d]
-        c.box_hi[d] = box_hi[d]
+    lo = np.atleast_2d(np.asarray(box_lo, dtype=np.float64))
+    hi = np.atleast_2d(np.asarray(box_hi, dtype=np.float64))
+    c.n_boxes = len(lo)
+    for b in range(len(lo)):
+        for d in range(3):
+            c.box_lo[b][d] = lo[b, d]
+            c.box_hi[b][d] = hi[b, d]
     return c
 
 
@@ -234,9 +244,9 @@ def metropolis_accept(e_new, e_old, beta, u):
     return bool(lib().or_metropolis_accept(e_new, e_old, beta, u))
 
 
-def adam_step(cfg, T, ta, g, m, v, dof):
+def adam_step(cfg, T, ta, g, m, v, dof, pose=0):
     """In-place FP64 Adam update of (m, v, dof); g = (dE/dt, tau, dE/dtheta)."""
-    lib().or_adam_step(C.byref(cfg), T, ta, _dp(g), _dp(m), _dp(v), _dp(dof))
+    lib().or_adam_step(C.byref(cfg), T, ta, pose, _dp(g), _dp(m), _dp(v), _dp(dof))
 
 
 def loop_steps(S, Lmc, l):

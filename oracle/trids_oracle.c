@@ -74,13 +74,20 @@ typedef struct {
     int64_t n_inter, n_intra;    /* pairs inside the cutoff */
     int32_t n_straddle;          /* pairs within OR_STRADDLE of a cutoff or a kink */
     double e_slack, g_slack;     /* summed |value jump| and |dE/dr jump| of those pairs */
+    /* condition magnitudes for a rounding bound: sum |pair energy|, and for each DOF the
+     * sum over atoms of |lever arm| * (sum of |dE/dr| of the atom's pairs) (t: lever 1;
+     * q: the lever about t; theta: the lever about the torsion's parent atom) */
+    double e_mag;
+    double g_mag[7 + OR_TMAX];
 } or_eval;
 
+#define OR_MAX_BOXES 8
 typedef struct {
     int32_t steps, mc_loops;
     double lr, b1, b2, eps, beta;
     uint64_t seed;
-    double box_lo[3], box_hi[3];
+    int32_t n_boxes;                          /* pose p uses box p mod n_boxes */
+    double box_lo[OR_MAX_BOXES][3], box_hi[OR_MAX_BOXES][3];
 } or_sample_cfg;
 
 #define OR_STRADDLE 1e-4
@@ -554,7 +561,8 @@ void or_pair(const or_params* p, int ti, int tj, double r, int inter,
 /* E_total = inter (ligand-pocket) + intra (ligand-ligand pair list).          */
 /* ------------------------------------------------------------------------- */
 static void accumulate_pair(const or_params* p, int ti, int tj, const double* xi, const double* xj,
-                            int inter, double* E, double* gi, double* gj, or_eval* ev, double scale)
+                            int inter, double* E, double* gi, double* gj, or_eval* ev, double scale,
+                            double* mi, double* mj)
 {
     double dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
     double r = sqrt(dx * dx + dy * dy + dz * dz);
@@ -579,6 +587,9 @@ static void accumulate_pair(const or_params* p, int ti, int tj, const double* xi
     ev->g_R[ti] += scale * dEdR;
     ev->g_R[tj] += scale * dEdR;
     *E += es;
+    ev->e_mag += fabs(es);
+    *mi += fabs(dEdr);
+    if (mj) *mj += fabs(dEdr);
     if (r > 0) {
         double f = dEdr / r;
         gi[0] += f * dx; gi[1] += f * dy; gi[2] += f * dz;
@@ -596,14 +607,30 @@ int or_score(const or_params* p, int M, const double* pxyz, const int32_t* ptype
     fk_frames(lg, dof, Rf, of);
     or_quat_mat(dof + 3, Rq);
     or_fk(lg, dof, &ev->x[0][0]);
+    double gm[OR_LMAX];
+    for (int i = 0; i < L; ++i) gm[i] = 0;
     for (int i = 0; i < L; ++i)
         for (int j = 0; j < M; ++j)
             accumulate_pair(p, lg->type[i], ptype[j], ev->x[i], pxyz + 3 * j, 1,
-                            &ev->e_inter, ev->g_x[i], NULL, ev, 1.0);
+                            &ev->e_inter, ev->g_x[i], NULL, ev, 1.0, &gm[i], NULL);
     for (int k = 0; k < lg->n_pairs; ++k) {
         int i = lg->pi[k], j = lg->pj[k];
         accumulate_pair(p, lg->type[i], lg->type[j], ev->x[i], ev->x[j], 0,
-                        &ev->e_intra, ev->g_x[i], ev->g_x[j], ev, 1.0);
+                        &ev->e_intra, ev->g_x[i], ev->g_x[j], ev, 1.0, &gm[i], &gm[j]);
+    }
+    for (int i = 0; i < L; ++i) {
+        double lt = sqrt((ev->x[i][0] - dof[0]) * (ev->x[i][0] - dof[0]) + (ev->x[i][1] - dof[1]) * (ev->x[i][1] - dof[1]) +
+                         (ev->x[i][2] - dof[2]) * (ev->x[i][2] - dof[2]));
+        for (int d = 0; d < 3; ++d) ev->g_mag[d] += gm[i];
+        for (int d = 0; d < 4; ++d) ev->g_mag[3 + d] += 2.0 * lt * gm[i];
+    }
+    for (int k = 0; k < T; ++k) {
+        const double* pk0 = ev->x[lg->tp[k]];
+        for (int i = lg->sb[k]; i < lg->se[k]; ++i) {
+            double lv = sqrt((ev->x[i][0] - pk0[0]) * (ev->x[i][0] - pk0[0]) + (ev->x[i][1] - pk0[1]) * (ev->x[i][1] - pk0[1]) +
+                             (ev->x[i][2] - pk0[2]) * (ev->x[i][2] - pk0[2]));
+            ev->g_mag[7 + k] += lv * gm[i];
+        }
     }
     ev->e_total = ev->e_inter + ev->e_intra;
     /* adjoint: translation, rotation tangent, torsions */
@@ -658,11 +685,23 @@ int or_loop_steps(int S, int Lmc, int l) { return S / Lmc + ((l < S % Lmc) ? 1 :
 
 static double wrap_pi(double a) { return a - 2.0 * M_PI * floor((a + M_PI) / (2.0 * M_PI)); }
 
+/* Translation range of a pose (Sec. 2: t in [box_min, box_max]); with several docking
+ * boxes (one per candidate cavity) pose p samples in box p mod n_boxes. */
+static const double* box_lo(const or_sample_cfg* cfg, uint32_t pose)
+{
+    return cfg->box_lo[cfg->n_boxes > 1 ? pose % (uint32_t)cfg->n_boxes : 0];
+}
+static const double* box_hi(const or_sample_cfg* cfg, uint32_t pose)
+{
+    return cfg->box_hi[cfg->n_boxes > 1 ? pose % (uint32_t)cfg->n_boxes : 0];
+}
+
 void or_init_pose(const or_sample_cfg* cfg, int T, uint32_t lig, uint32_t pose, double* dof)
 {
     double u[3 + 3 + OR_TMAX];
+    const double *lo = box_lo(cfg, pose), *hi = box_hi(cfg, pose);
     for (int n = 0; n < 6 + T; ++n) u[n] = u01(or_rand_word(cfg->seed, lig, pose, 0, 0, (uint32_t)n));
-    for (int d = 0; d < 3; ++d) dof[d] = cfg->box_lo[d] + u[d] * (cfg->box_hi[d] - cfg->box_lo[d]);
+    for (int d = 0; d < 3; ++d) dof[d] = lo[d] + u[d] * (hi[d] - lo[d]);
     /* Shoemake's subgroup method for a uniform unit quaternion */
     double a = sqrt(1.0 - u[3]), b = sqrt(u[3]);
     dof[3] = a * sin(2.0 * M_PI * u[4]);
@@ -679,7 +718,7 @@ int or_perturb(const or_sample_cfg* cfg, int T, uint32_t lig, uint32_t pose, uin
     double u1 = u01(or_rand_word(cfg->seed, lig, pose, loop, 1, 1));
     int c = (int)(((uint64_t)(w0 >> 8) * (uint64_t)(6 + T)) >> 24);
     if (c < 3) {
-        dof[c] = cfg->box_lo[c] + u1 * (cfg->box_hi[c] - cfg->box_lo[c]);
+        dof[c] = box_lo(cfg, pose)[c] + u1 * (box_hi(cfg, pose)[c] - box_lo(cfg, pose)[c]);
     } else if (c < 6) {
         double ang = -M_PI + 2.0 * M_PI * u1;
         double r[4] = {cos(0.5 * ang), 0, 0, 0};
@@ -702,9 +741,12 @@ int or_metropolis_accept(double e_new, double e_old, double beta, double u)
     return u < exp(-beta * (e_new - e_old));
 }
 
-/* Adam (bias-corrected, the PyTorch form) on g = (dE/dt, tau, dE/dtheta), step count ta >= 1. */
-void or_adam_step(const or_sample_cfg* cfg, int T, int ta, const double* g, double* m, double* v, double* dof)
+/* Adam (bias-corrected, the PyTorch form) on g = (dE/dt, tau, dE/dtheta), step count ta >= 1;
+ * t is clamped into the pose's box. */
+void or_adam_step(const or_sample_cfg* cfg, int T, int ta, uint32_t pose, const double* g, double* m, double* v,
+                  double* dof)
 {
+    const double *lo = box_lo(cfg, pose), *hi = box_hi(cfg, pose);
     double bc1 = 1.0 - pow(cfg->b1, ta), bc2 = 1.0 - pow(cfg->b2, ta);
     double step[6 + OR_TMAX];
     for (int j = 0; j < 6 + T; ++j) {
@@ -715,8 +757,8 @@ void or_adam_step(const or_sample_cfg* cfg, int T, int ta, const double* g, doub
     }
     for (int d = 0; d < 3; ++d) {
         double t = dof[d] + step[d];
-        if (t < cfg->box_lo[d]) t = cfg->box_lo[d];
-        if (t > cfg->box_hi[d]) t = cfg->box_hi[d];
+        if (t < lo[d]) t = lo[d];
+        if (t > hi[d]) t = hi[d];
         dof[d] = t;
     }
     double phi = sqrt(step[3] * step[3] + step[4] * step[4] + step[5] * step[5]);
@@ -761,7 +803,7 @@ double or_sample_pose(const or_sample_cfg* cfg, const or_params* p, int M, const
             if (j < n - 1) {
                 for (int d = 0; d < 3; ++d) { g[d] = ev->g_dof[d]; g[3 + d] = ev->tau[d]; }
                 for (int k = 0; k < T; ++k) g[6 + k] = ev->g_dof[7 + k];
-                or_adam_step(cfg, T, j + 1, g, m, v, dof);
+                or_adam_step(cfg, T, j + 1, pose, g, m, v, dof);
             } else {
                 e_cur = ev->e_total;
             }

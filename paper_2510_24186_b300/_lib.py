@@ -11,7 +11,8 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE = 0, -1, -2, -3, -4, -5
 TERMS_VINA5, TERMS_TRIDS = 0, 1
 MODE_PERSISTENT, MODE_PER_LIGAND = 0, 1
 
-EXPORTS = ("trids_last_error", "trids_version", "trids_make_pocket", "trids_set_params", "trids_free_pocket",
+EXPORTS = ("trids_last_error", "trids_version", "trids_make_pocket", "trids_set_params", "trids_set_boxes",
+           "trids_free_pocket",
            "trids_pack_ligands", "trids_free_batch", "trids_batch_info", "trids_batch_query",
            "trids_pack_topology", "trids_score_grad", "trids_score_grad_noalloc", "trids_state_floats",
            "trids_sample", "trids_topk", "trids_sync")
@@ -63,6 +64,7 @@ def lib(build_if_missing: bool = True):
     L.trids_version.restype = C.c_int
     L.trids_make_pocket.argtypes = [vp, vp, i32, P(C.c_float * 3), P(C.c_float * 3), fp, P(Params), P(vp)]
     L.trids_set_params.argtypes = [vp, P(Params), vp]
+    L.trids_set_boxes.argtypes = [vp, i32, vp, vp]
     L.trids_free_pocket.argtypes = [vp]
     L.trids_pack_ligands.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, P(vp)]
     L.trids_free_batch.argtypes = [vp]

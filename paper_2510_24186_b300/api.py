@@ -88,6 +88,13 @@ class Pocket:
         check(_lib.lib().trids_set_params(self.handle, C.byref(cp), _stream(stream)))
         self.params = params
 
+    def set_boxes(self, centers, sizes):
+        """Several docking boxes: pose p samples in box p mod len(centers) (trids_set_boxes)."""
+        c = np.ascontiguousarray(np.atleast_2d(centers), dtype=np.float32)
+        s = np.ascontiguousarray(np.atleast_2d(sizes), dtype=np.float32)
+        check(_lib.lib().trids_set_boxes(self.handle, len(c), c.ctypes.data, s.ctypes.data))
+        self.box_center, self.box_size = c, s
+
     def close(self):
         if getattr(self, "handle", None):
             _lib.lib().trids_free_pocket(self.handle)
@@ -262,3 +269,49 @@ def topk(batch: Batch, energy: torch.Tensor, dof: torch.Tensor, k: int, rmsd: fl
 def sync(batch: Batch, poses: int, state: Optional[torch.Tensor] = None, timeout_ms: float = 0.0, stream=None) -> int:
     """Wait for the stream (bounded) and check per-pose status words (trids_sync).  Returns the code."""
     return _lib.lib().trids_sync(batch.handle, poses, _ptr(state), _stream(stream), float(timeout_ms))
+
+
+def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd: float = 1.0, seed: int = 0,
+                  mc_loops: int = 8, warps_per_block: int = 0, stream=None):
+    """Screen an iterable of ligand batches (each a tuple of arrays as for Batch) through one
+    pocket.  The next batch is packed on a host thread while the current one samples; the
+    DOF, state and energy buffers stay on the device and are reused.  Yields
+    (first ligand id, top-k indices [n, k], top-k energies [n, k]) per batch as numpy arrays.
+    Ligand ids (the random-stream ids) run on across batches."""
+    import concurrent.futures as cf
+    _require_cuda()
+    st = stream or torch.cuda.current_stream()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    bufs = {"dof": torch.empty(0, device=dev), "state": torch.empty(0, device=dev),
+            "energy": torch.empty(0, device=dev)}
+
+    def view(name, n):
+        if bufs[name].numel() < n:
+            bufs[name] = torch.empty(int(n * 1.25) + 1024, device=dev)
+        return bufs[name][:n]
+
+    it = iter(batches)
+    base = 0
+    with cf.ThreadPoolExecutor(max_workers=1) as ex:
+        nxt = next(it, None)
+        fut = ex.submit(Batch, pocket, *nxt) if nxt is not None else None
+        while fut is not None:
+            b = fut.result()
+            nxt = next(it, None)
+            fut = ex.submit(Batch, pocket, *nxt) if nxt is not None else None
+            D = b.dof_stride
+            dof = view("dof", b.n_lig * poses * D).view(b.n_lig, poses, D)
+            state = view("state", b.state_floats(poses))
+            energy = view("energy", b.n_lig * poses).view(b.n_lig, poses)
+            with torch.cuda.stream(st):
+                sample(pocket, b, poses, steps, mc_loops=mc_loops, seed=seed, lig_base=base, dof=dof, state=state,
+                       energy=energy, warps_per_block=warps_per_block, stream=st)
+                idx, e = topk(b, energy, dof, k, rmsd, stream=st)
+                idx_h = torch.empty(idx.shape, dtype=idx.dtype, pin_memory=True)
+                e_h = torch.empty(e.shape, dtype=e.dtype, pin_memory=True)
+                idx_h.copy_(idx, non_blocking=True)
+                e_h.copy_(e, non_blocking=True)
+            st.synchronize()
+            yield base, idx_h.numpy().copy(), e_h.numpy().copy()
+            base += b.n_lig
+            b.close()

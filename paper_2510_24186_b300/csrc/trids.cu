@@ -692,7 +692,9 @@ __device__ void init_pose(const SampleArgs& A, const LigHdr& h, int lane, int l,
     const uint4 r0 = rand_block(A.seed, lig, (uint32_t)p, 0u, 0u, 0u);
     const uint4 r1 = rand_block(A.seed, lig, (uint32_t)p, 0u, 0u, 1u);
     const float u[6] = {u01(r0.x), u01(r0.y), u01(r0.z), u01(r0.w), u01(r1.x), u01(r1.y)};
-    for (int d = 0; d < 3; ++d) st.t[d] = fmaf(u[d], A.pk.box_hi[d] - A.pk.box_lo[d], A.pk.box_lo[d]);
+    const int bx = A.pk.n_boxes > 1 ? p % A.pk.n_boxes : 0;
+    for (int d = 0; d < 3; ++d)
+        st.t[d] = fmaf(u[d], A.pk.box_hi[bx][d] - A.pk.box_lo[bx][d], A.pk.box_lo[bx][d]);
     const float a = sqrtf(1.f - u[3]), b = sqrtf(u[3]);
     float s1, c1, s2, c2;
     sincospif(2.f * u[4], &s1, &c1);
@@ -773,6 +775,7 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
     if (st.status & 1) return;  // frozen after a non-finite energy
     const Sched sc = schedule(A.S, A.Lmc, s);
     const int T = h.n_tor, lane = W.lane;
+    const int bx = A.pk.n_boxes > 1 ? p % A.pk.n_boxes : 0;   // the pose's docking box
     const bool own = lane < T;
     const uint32_t lig = (uint32_t)(A.lig_base + l);
     if (sc.j == 0) {
@@ -788,7 +791,7 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
             if (c < 3) {
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
-                    if (d == c) st.t[d] = fmaf(u1, A.pk.box_hi[d] - A.pk.box_lo[d], A.pk.box_lo[d]);
+                    if (d == c) st.t[d] = fmaf(u1, A.pk.box_hi[bx][d] - A.pk.box_lo[bx][d], A.pk.box_lo[bx][d]);
             } else if (c < 6) {
                 const float ang = fmaf(u1, kTwoPi, -kPi);
                 float sh, ch;
@@ -838,7 +841,7 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
         if (own) st.th = wrap_pi(st.th + adam_delta(A, gth, st.mth, st.vth, bc1, sbc2));
         for (int d = 0; d < 3; ++d) {
             const float dlt = adam_delta(A, gt[d], st.m[d], st.v[d], bc1, sbc2);
-            st.t[d] = fminf(fmaxf(st.t[d] + dlt, A.pk.box_lo[d]), A.pk.box_hi[d]);
+            st.t[d] = fminf(fmaxf(st.t[d] + dlt, A.pk.box_lo[bx][d]), A.pk.box_hi[bx][d]);
         }
         float dw[3];
         for (int d = 0; d < 3; ++d) dw[d] = adam_delta(A, tau[d], st.m[3 + d], st.v[3 + d], bc1, sbc2);
@@ -875,7 +878,7 @@ __device__ __forceinline__ void flush_count(unsigned long long* cnt, uint32_t n)
 // Persistent fused sampler: each warp pops poses from a global counter (ligands in
 // decreasing-cost order) and runs every evaluation of the pose with its state on chip.
 template <int TS, bool COUNT>
-__global__ void __launch_bounds__(256, 2) k_sample_persistent(SampleArgs A) {
+__global__ void __launch_bounds__(512, 1) k_sample_persistent(SampleArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
     Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
@@ -903,7 +906,7 @@ __global__ void __launch_bounds__(256, 2) k_sample_persistent(SampleArgs A) {
 // Plain form: one launch per (ligand, evaluation), one warp per pose, the state in
 // global memory between launches; the same device code as the persistent sampler.
 template <int TS, bool COUNT>
-__global__ void __launch_bounds__(256, 2) k_sample_step(SampleArgs A, int l, int s) {
+__global__ void __launch_bounds__(512, 1) k_sample_step(SampleArgs A, int l, int s) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
     Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
@@ -943,7 +946,7 @@ struct ScoreArgs {
 // Each warp takes a (ligand, 32-pose tile) item and scores its poses one after another;
 // parameter-gradient sums of the tile are reduced in a fixed order into one row.
 template <int TS, bool PARAMS>
-__global__ void __launch_bounds__(256, 2) k_score(ScoreArgs A) {
+__global__ void __launch_bounds__(512, 1) k_score(ScoreArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
     Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
@@ -1165,7 +1168,8 @@ struct trids_pocket {
     uint8_t* d_ptype = nullptr;
     float cutoff_built = 0.f;
     float cell = 1.f;
-    float box_lo[3], box_hi[3];
+    int n_boxes = 1;
+    float box_lo[kMaxBoxes][3], box_hi[kMaxBoxes][3];
     trids_params prm;
     DevParams hp;
     CandidateGrid grid;
@@ -1178,7 +1182,9 @@ struct trids_pocket {
         v.atoms = d_atoms; v.ptype = d_ptype; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
         v.nx = grid.dims[0]; v.ny = grid.dims[1]; v.nz = grid.dims[2];
         v.gx = grid.lo[0]; v.gy = grid.lo[1]; v.gz = grid.lo[2]; v.inv_h = 1.f / grid.h;
-        for (int d = 0; d < 3; ++d) { v.box_lo[d] = box_lo[d]; v.box_hi[d] = box_hi[d]; }
+        v.n_boxes = n_boxes;
+        for (int b = 0; b < kMaxBoxes; ++b)
+            for (int d = 0; d < 3; ++d) { v.box_lo[b][d] = box_lo[b][d]; v.box_hi[b][d] = box_hi[b][d]; }
         return v;
     }
 };
@@ -1225,11 +1231,22 @@ struct trids_batch {
 
 namespace {
 
+// Device copy of a host vector.  The copy goes through a private non-blocking stream so it
+// does not wait for (or stall) kernels running on other streams, e.g. while the next
+// batch of a screening stream is packed during sampling.
 template <class T>
 int upload(T** dst, const std::vector<T>& src) {
     size_t n = std::max<size_t>(src.size(), 1) * sizeof(T);
     if (cudaMalloc(dst, n) != cudaSuccess) return fail(TRIDS_ENOMEM, "cudaMalloc of %zu bytes failed", n);
-    if (!src.empty()) CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    if (!src.empty()) {
+        cudaStream_t s;
+        CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        cudaError_t e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(TRIDS_ECUDA, "upload failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
     return TRIDS_OK;
 }
 
@@ -1364,7 +1381,7 @@ size_t max_smem(int dev) {
 // Pick warps per block: the requested count, capped so the block fits in shared memory.
 int pick_warps(int requested, const trids_pocket* pk, const trids_batch* b, bool params, Layout* L) {
     const size_t cap = max_smem(pk->device);
-    int w = requested > 0 ? std::min(requested, 8) : 8;
+    int w = requested > 0 ? std::min(requested, 16) : 8;
     for (; w >= 1; --w) {
         *L = make_layout(pk->prm.term_set, pk->M, b->dims.max_atoms, b->dims.max_tor, w, params);
         if (L->total <= cap) return w;
@@ -1432,8 +1449,10 @@ int trids_make_pocket(const float* xyz, const int32_t* type, int32_t n_atoms, co
     pk->xyz.assign(xyz, xyz + 3 * (size_t)n_atoms);
     pk->type.assign(type, type + n_atoms);
     for (int d = 0; d < 3; ++d) {
-        pk->box_lo[d] = box_center[d] - 0.5f * box_size[d];
-        pk->box_hi[d] = box_center[d] + 0.5f * box_size[d];
+        for (int b = 0; b < kMaxBoxes; ++b) {
+            pk->box_lo[b][d] = box_center[d] - 0.5f * box_size[d];
+            pk->box_hi[b][d] = box_center[d] + 0.5f * box_size[d];
+        }
     }
     build_grid(n_atoms, xyz, prm->cutoff, pk->cell, &pk->grid);
     if (pk->grid.cand.size() >= (1ull << 32)) return fail(TRIDS_ENOMEM, "candidate grid too large");
@@ -1463,6 +1482,25 @@ int trids_set_params(trids_pocket* pk, const trids_params* prm, void* stream) {
     if ((rc = device_guard(pk->device))) return rc;
     pk->prm = *prm;
     return upload_pocket_arrays(pk, (cudaStream_t)stream);
+}
+
+int trids_set_boxes(trids_pocket* pk, int32_t n_boxes, const float* centers, const float* sizes) {
+    g_err.clear();
+    if (!pk || !centers || !sizes) return fail(TRIDS_EINVAL, "NULL argument");
+    if (n_boxes < 1 || n_boxes > kMaxBoxes) return fail(TRIDS_EINVAL, "n_boxes must be in 1..%d", kMaxBoxes);
+    for (int b = 0; b < n_boxes; ++b)
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(centers[3 * b + d]) || !(sizes[3 * b + d] >= 0.f) || !std::isfinite(sizes[3 * b + d]))
+                return fail(TRIDS_EINVAL, "box %d must be finite with size >= 0", b);
+    pk->n_boxes = n_boxes;
+    for (int b = 0; b < kMaxBoxes; ++b) {
+        const int s = b < n_boxes ? b : 0;
+        for (int d = 0; d < 3; ++d) {
+            pk->box_lo[b][d] = centers[3 * s + d] - 0.5f * sizes[3 * s + d];
+            pk->box_hi[b][d] = centers[3 * s + d] + 0.5f * sizes[3 * s + d];
+        }
+    }
+    return TRIDS_OK;
 }
 
 int trids_free_pocket(trids_pocket* pk) {

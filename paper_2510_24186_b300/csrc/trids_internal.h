@@ -21,6 +21,7 @@ constexpr int kLmax = TRIDS_MAX_ATOMS;
 constexpr int kTmax = TRIDS_MAX_TOR;
 constexpr int kNT = TRIDS_MAX_TYPES;
 constexpr int kK = TRIDS_MAX_GMM;
+constexpr int kMaxBoxes = TRIDS_MAX_BOXES;
 
 // ---------------------------------------------------------------- host-side pack
 // Packed torsion tree of one ligand (rules in trids.h, trids_pack_ligands).
@@ -75,7 +76,8 @@ struct DevPocket {
     int M;
     int nx, ny, nz;
     float gx, gy, gz, inv_h;
-    float box_lo[3], box_hi[3];
+    int n_boxes;                   // pose p samples in box p mod n_boxes
+    float box_lo[kMaxBoxes][3], box_hi[kMaxBoxes][3];
 };
 
 struct LigHdr {

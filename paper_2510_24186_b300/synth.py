@@ -256,7 +256,8 @@ class Workload:
     topk: int
     seed: int
     cell: float = 0.0
-    pose_cavity: bool = False   # pose p is placed in cavity p mod n_cav
+    box_centers: np.ndarray | None = None   # several docking boxes: pose p uses box p mod n
+    box_sizes: np.ndarray | None = None
 
 
 def concat_ligands(ligs):
@@ -321,6 +322,6 @@ def workload(k: int, n_lig: int | None = None) -> Workload:
         pk = gen_pocket(rng, 6000, cav)
         ligs = _ligand_set(rng, n_lig or 4096, (20, 60), (0, 15), UNIFORM_MIX, c0)
         return Workload("blind-docking scale: 6,000-atom region, 3 cavities, 4,096 ligands x 512 poses "
-                        "x 100 steps", pk, ligs, c0, np.full(3, 22.5 + side), 512, 100, 8, 8.0, 9,
-                        seed, cell=4.0, pose_cavity=True)
+                        "x 100 steps", pk, ligs, c0, np.full(3, 22.5), 512, 100, 8, 8.0, 9,
+                        seed, cell=1.0, box_centers=cav, box_sizes=np.full((3, 3), 22.5))
     raise ValueError(f"unknown workload {k}")

@@ -3,7 +3,10 @@
 Tolerances (stated for the method's FP32 results against the FP64 oracle):
   energy    |dE| <= max(1e-3 kcal/mol, 1e-5 |E|) + straddle slack
   gradient  per block (t, rotation, torsions): |g - g_ref| / max(|g_ref|, 1e-3) <= 1e-3,
-            plus slack for pairs sitting on a cutoff or kink
+            plus slack for pairs sitting on a cutoff or kink, plus the FP32 rounding bound
+            4 * 2^-24 * (sum over the block's DOFs of the oracle's condition magnitudes,
+            sum over atoms of |lever| * sum of |dE/dr| of the atom's pairs): a gradient that is
+            a small difference of large terms cannot be closer than this in float32
   states    t and theta within 1e-4 (theta on the circle), q within 1e-4 as a rotation
 Integer results (topology, top-k indices, perturbed variable, acceptance decisions)
 must match exactly, except decisions the oracle marks as near ties.
@@ -95,10 +98,18 @@ def block_ok(g_gpu, g_ref, slack, st: Stats, what=""):
         st.fail(f"{what}: |dg| {num:.3e} |g| {np.linalg.norm(g_ref):.3e} slack {slack:.2e}")
 
 
+EPS32 = 2.0 ** -24
+
+
 def grad_slack(ev):
     # a force jump J on one atom moves a rotation or torsion gradient by at most J times
     # the lever arm (< 40 A inside a pocket)
     return 40.0 * ev.g_slack
+
+
+def round_slack(ev, lo, hi):
+    """float32 rounding allowance for DOF components [lo, hi) (see module docstring)."""
+    return 4.0 * EPS32 * float(np.linalg.norm(np.array(ev.g_mag[lo:hi])))
 
 
 def quat_angle(a, b):
@@ -158,16 +169,16 @@ def check_trace(trace, poses_g, P, ligs_or, pxyz, ptype, op, cfg_or, S, Lmc, see
             st.n += 1
             energy_ok(E, ev, st, f"pose {g} step {s}")
             sl = grad_slack(ev)
-            block_ok(gt, ev.g_dof[:3], sl, st, f"pose {g} step {s} dE/dt")
-            block_ok(tau, ev.tau[:], sl, st, f"pose {g} step {s} torque")
-            block_ok(gth, ev.g_dof[7:7 + T], sl, st, f"pose {g} step {s} dE/dtheta")
+            block_ok(gt, ev.g_dof[:3], sl + round_slack(ev, 0, 3), st, f"pose {g} step {s} dE/dt")
+            block_ok(tau, ev.tau[:], sl + round_slack(ev, 3, 7), st, f"pose {g} step {s} torque")
+            block_ok(gth, ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"pose {g} step {s} dE/dtheta")
             loop, j, n = sched[s]
             if j == 0:
                 m, v = np.zeros(6 + T), np.zeros(6 + T)
             grad = np.concatenate([gt, tau, gth]).astype(np.float64)
             if j < n - 1:
                 nxt = dof.copy()
-                oracle.adam_step(cfg_or, T, j + 1, grad, m, v, nxt)
+                oracle.adam_step(cfg_or, T, j + 1, grad, m, v, nxt, pose=p)
             else:
                 e_new = float(E)
                 if loop == 0:

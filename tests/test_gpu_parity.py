@@ -8,7 +8,7 @@ import oracle
 from paper_2510_24186_b300 import synth
 
 from parity_util import (Stats, block_ok, check_trace, energy_ok, grad_slack, oracle_ligands, oracle_params,
-                         pocket_arrays, score_params, state_err)
+                         pocket_arrays, round_slack, score_params, state_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -84,9 +84,9 @@ def test_score_grad_parity_single_ligand(api, term_set):
         energy_ok(out["energy"][0, p], ev, st, f"pose {p}")
         sl = grad_slack(ev)
         assert abs(out["e_inter"][0, p] - ev.e_inter) <= max(1e-3, 1e-5 * abs(ev.e_inter)) + ev.e_slack
-        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], sl, st, f"pose {p} t")
-        block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl, st, f"pose {p} q")
-        block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl, st, f"pose {p} theta")
+        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], sl + round_slack(ev, 0, 3), st, f"pose {p} t")
+        block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"pose {p} q")
+        block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"pose {p} theta")
         assert np.all(out["g_dof"][0, p, 7 + T:] == 0)
         gx = np.zeros((b.max_atoms, 3))
         gx[perm] = np.array(ev.g_x)[:lg.n_atoms]
@@ -112,9 +112,10 @@ def test_score_grad_parity_batch_ragged(api, term_set):
             st.n += 1
             energy_ok(out["energy"][l, p], ev, st, f"lig {l} pose {p}")
             sl = grad_slack(ev)
-            block_ok(out["g_dof"][l, p, :3], ev.g_dof[:3], sl, st, f"lig {l} pose {p} t")
-            block_ok(out["g_dof"][l, p, 3:7], ev.g_dof[3:7], sl, st, f"lig {l} pose {p} q")
-            block_ok(out["g_dof"][l, p, 7:7 + T], ev.g_dof[7:7 + T], sl, st, f"lig {l} pose {p} theta")
+            block_ok(out["g_dof"][l, p, :3], ev.g_dof[:3], sl + round_slack(ev, 0, 3), st, f"lig {l} pose {p} t")
+            block_ok(out["g_dof"][l, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"lig {l} pose {p} q")
+            block_ok(out["g_dof"][l, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st,
+                     f"lig {l} pose {p} theta")
     report(st, f"score batch term_set={term_set}")
 
 
@@ -148,7 +149,7 @@ def test_parameter_gradients_and_autograd(api, term_set):
             stt, ev = oracle.score(op, pxyz, ptype, ligs[l], dof[l, p, :7 + T])
             gw += eb[l, p] * np.array(ev.g_w)
             gr += eb[l, p] * np.array(ev.g_R)
-            sl = abs(eb[l, p]) * grad_slack(ev)
+            sl = abs(eb[l, p]) * (grad_slack(ev) + round_slack(ev, 0, 7 + T))
             block_ok(gd[l, p, :7 + T], eb[l, p] * np.array(ev.g_dof[:7 + T]), sl, st, f"lig {l} pose {p}")
     block_ok(W.grad.numpy(), gw, 0.0, st, "dE/dw")
     block_ok(R.grad.numpy(), gr[:8], 0.0, st, "dE/dR")
@@ -292,3 +293,102 @@ def test_config2_full_size_sampled(api):
         ref, near = oracle.topk(E[l], X, w.topk, 1.0)
         if near == 0:
             np.testing.assert_array_equal(idx[l], ref)
+
+
+def test_config3_full_size_score_sampled(api):
+    """Config 3 at full size (256 ligands x 64 random poses) through the autograd Function:
+    energies, DOF gradients (t, q, theta) and parameter gradients against the oracle on a
+    seeded sample of 192 poses, plus dE/dw, dE/dR summed over every pose."""
+    from paper_2510_24186_b300.autograd import score as tscore
+    w = synth.workload(3)
+    sp, pk, b = make(api, w)
+    rng = np.random.default_rng(33)
+    P = 64
+    dof = synth.random_dofs(rng, b.n_tor, P, w.box_center - w.box_size / 2, w.box_center + w.box_size / 2,
+                            b.dof_stride)
+    d = torch.from_numpy(dof).cuda().requires_grad_(True)
+    W = torch.tensor(list(sp.w), dtype=torch.float64, requires_grad=True)
+    R = torch.tensor(list(sp.radius), dtype=torch.float64, requires_grad=True)
+    E = tscore(d, W, R, pk, b)
+    E.sum().backward()
+    Eh, gd = E.detach().cpu().numpy(), d.grad.cpu().numpy()
+    op = oracle_params(sp)
+    pxyz, ptype = pocket_arrays(w.pocket)
+    ligs = oracle_ligands(w.ligands)
+    st = Stats()
+    picks = rng.choice(b.n_lig * P, 192, replace=False)
+    for g in picks:
+        l, p = divmod(int(g), P)
+        T = ligs[l].n_tor
+        stt, ev = oracle.score(op, pxyz, ptype, ligs[l], dof[l, p, :7 + T])
+        st.n += 1
+        energy_ok(Eh[l, p], ev, st, f"lig {l} pose {p}")
+        sl = grad_slack(ev)
+        block_ok(gd[l, p, :3], ev.g_dof[:3], sl + round_slack(ev, 0, 3), st, f"lig {l} pose {p} t")
+        block_ok(gd[l, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"lig {l} pose {p} q")
+        block_ok(gd[l, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"lig {l} pose {p} theta")
+    # parameter gradients over every pose: oracle sums over all 16,384 poses
+    gw = np.zeros(5)
+    gr = np.zeros(16)
+    for l in range(b.n_lig):
+        for p in range(P):
+            T = ligs[l].n_tor
+            ev = oracle.score(op, pxyz, ptype, ligs[l], dof[l, p, :7 + T])[1]
+            gw += np.array(ev.g_w)
+            gr += np.array(ev.g_R)
+    block_ok(W.grad.numpy(), gw, 0.0, st, "dE/dw")
+    block_ok(R.grad.numpy(), gr[:8], 0.0, st, "dE/dR")
+    report(st, "config 3 full size")
+
+
+def test_config5_three_cavities_sampled(api):
+    """Config 5 shapes: 6,000-atom region around three cavities, one docking box per
+    cavity (pose p in box p mod 3), 512 poses; 48 ligands x 100 evaluations, 96 traced
+    poses checked per evaluation against the oracle."""
+    w = synth.workload(5, n_lig=48)
+    sp = score_params(0)
+    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, cell=1.0)
+    pk.set_boxes(w.box_centers, w.box_sizes)
+    b = api.Batch.from_ligands(pk, w.ligands)
+    P, S, seed = w.poses, w.steps, 5005
+    rng = np.random.default_rng(5)
+    poses_g = np.sort(rng.choice(b.n_lig * P, 96, replace=False))
+    out = api.sample(pk, b, P, S, mc_loops=w.mc_loops, seed=seed, trace_poses=poses_g.tolist())
+    assert api.sync(b, P, out["state"], timeout_ms=120000) == 0
+    lo = (w.box_centers - w.box_sizes / 2).astype(np.float32).astype(np.float64)
+    hi = (w.box_centers + w.box_sizes / 2).astype(np.float32).astype(np.float64)
+    cfg = oracle.sample_cfg(steps=S, mc_loops=w.mc_loops, lr=float(np.float32(0.1)), b1=float(np.float32(0.9)),
+                            b2=float(np.float32(0.999)), eps=float(np.float32(1e-8)), beta=float(np.float32(0.069)),
+                            seed=seed, box_lo=lo, box_hi=hi)
+    dof = out["dof"].cpu().numpy()
+    st = check_trace(out["trace"].cpu().numpy(), poses_g, P, oracle_ligands(w.ligands), *pocket_arrays(w.pocket),
+                     oracle_params(sp), cfg, S, w.mc_loops, seed, dof, out["energy"].cpu().numpy())
+    report(st, "config 5 sampled")
+    # every final translation lies in its pose's box
+    p_of = np.arange(P) % 3
+    assert (dof[:, :, :3] >= lo[p_of][None] - 1e-4).all() and (dof[:, :, :3] <= hi[p_of][None] + 1e-4).all()
+
+
+def test_config4_stream_matches_separate_batches(api):
+    """Config 4 shapes (drug-like mix, 2,000-atom pocket, 64 poses x 40 evaluations) as a
+    stream of uneven batches with device-resident buffers and host packing overlapped:
+    identical to sampling each batch on its own with the same ligand ids."""
+    w = synth.workload(4, n_lig=300)
+    sp = score_params(0)
+    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
+    sizes = [70, 130, 100]
+    chunks, o = [], 0
+    for s in sizes:
+        chunks.append(synth.concat_ligands(w.ligands[o:o + s]))
+        o += s
+    got = list(api.screen_stream(pk, chunks, w.poses, w.steps, w.topk, seed=44))
+    assert [g[0] for g in got] == [0, 70, 200]
+    base = 0
+    for (b0, idx, e), arr in zip(got, chunks):
+        b = api.Batch(pk, *arr)
+        out = api.sample(pk, b, w.poses, w.steps, mc_loops=w.mc_loops, seed=44, lig_base=base)
+        i2, e2 = api.topk(b, out["energy"], out["dof"], w.topk, 1.0)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(idx, i2.cpu().numpy())
+        np.testing.assert_array_equal(e, e2.cpu().numpy())
+        base += b.n_lig

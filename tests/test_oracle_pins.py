@@ -563,3 +563,23 @@ def test_topk_matches_brute_force(orc):
     E = np.array([2.0, 1.0, 1.0, 0.5])
     X = np.zeros((4, 2, 3))
     assert orc.topk(E, X, 3, 0.0)[0].tolist() == [3, 1, 2]
+
+
+def test_multiple_boxes_assign_pose_p_to_box_p_mod_n(orc):
+    """Several docking boxes: init, perturbation and the Adam clamp of pose p use box p mod n."""
+    lo = np.array([[-30, -5, -5], [10, 10, 10], [-2, 20, -40]], dtype=float)
+    hi = lo + np.array([[4, 4, 4], [2, 3, 4], [5, 5, 5]], dtype=float)
+    cfg = orc.sample_cfg(seed=5, box_lo=lo, box_hi=hi, lr=5.0)
+    T = 2
+    rng = np.random.default_rng(0)
+    for p in range(30):
+        b = p % 3
+        d = orc.init_pose(cfg, T, 1, p)
+        assert (d[:3] >= lo[b]).all() and (d[:3] < hi[b]).all()
+        for loop in range(1, 6):
+            c, d2 = orc.perturb(cfg, T, 1, p, loop, d)
+            assert (d2[:3] >= lo[b]).all() and (d2[:3] <= hi[b]).all()
+        m, v = np.zeros(6 + T), np.zeros(6 + T)
+        g = rng.normal(size=6 + T) * 100
+        orc.adam_step(cfg, T, 1, g, m, v, d, pose=p)
+        assert (d[:3] >= lo[b]).all() and (d[:3] <= hi[b]).all()
