@@ -165,10 +165,13 @@ struct Layout {
     size_t params_bytes, pocket_off, pocket_bytes, ptype_off, ptype_bytes, mbar_off, warp_off, warp_bytes, total;
 };
 
+__host__ __device__ inline size_t pose_warp_core_bytes(int Lm, int Tm) {
+    return 16 * (size_t)(Lm + 1) + 16 * (size_t)Lm + 48 * (size_t)(Tm > 0 ? Tm : 1) + 16 * (size_t)(Lm + 32) +
+           12 * (size_t)Lm + 4 * (size_t)(Lm + 1);
+}
+
 __host__ __device__ inline size_t pose_warp_bytes(int Lm, int Tm, bool params) {
-    size_t b = 16 * (size_t)Lm * 2 + 48 * (size_t)(Tm > 0 ? Tm : 1) + 16 * (size_t)(Lm + 32);
-    b += 4 * (size_t)Lm + 4 * (size_t)(Lm + 1);
-    b = align_up(b, 16);
+    size_t b = align_up(pose_warp_core_bytes(Lm, Tm), 16);
     if (params) b += 4 * (size_t)kNT * 32;
     return align_up(b, 128);
 }
@@ -247,11 +250,13 @@ __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t par
 //   pre int[Lm + 1]     exclusive prefix of each atom's candidate blocks
 //   grs float[kNT][32]  per-lane dE/dR_a (parameter-gradient kernels only)
 struct PW {
-    float4* xs;
+    float4* xs;     // [Lm + 1] (x, y, z, radius); xs[Lm] is a far sentinel
     float4* gs;
     float4* rk;
     float4* rec;
-    uint32_t* cs;
+    uint32_t* cs;   // per atom: candidate-list offset of its cell
+    int* cb;        // per atom: candidate blocks of its cell
+    int* ip;        // per atom: first intra-partner block
     int* pre;
     float* grs;
     int lane;
@@ -261,14 +266,14 @@ __device__ __forceinline__ PW make_pw(unsigned char* smem, size_t warp_off, size
     PW W;
     unsigned char* base = smem + warp_off + warp_bytes * (threadIdx.x >> 5);
     W.xs = reinterpret_cast<float4*>(base);
-    W.gs = W.xs + Lm;
+    W.gs = W.xs + Lm + 1;
     W.rk = W.gs + Lm;
     W.rec = W.rk + 3 * (Tm > 0 ? Tm : 1);
     W.cs = reinterpret_cast<uint32_t*>(W.rec + Lm + 32);
-    W.pre = reinterpret_cast<int*>(W.cs + Lm);
-    W.grs = reinterpret_cast<float*>(base + align_up(16 * (size_t)Lm * 2 + 48 * (size_t)(Tm > 0 ? Tm : 1) +
-                                                     16 * (size_t)(Lm + 32) + 4 * (size_t)Lm + 4 * (size_t)(Lm + 1),
-                                                 16));
+    W.cb = reinterpret_cast<int*>(W.cs + Lm);
+    W.ip = W.cb + Lm;
+    W.pre = W.ip + Lm;
+    W.grs = reinterpret_cast<float*>(base + align_up(pose_warp_core_bytes(Lm, Tm), 16));
     W.lane = threadIdx.x & 31;
     return W;
 }
@@ -347,7 +352,8 @@ __device__ __forceinline__ void cell_range(const DevPocket& pk, float x, float y
 // torsions deepest first (reverse BFS order) about their input-geometry axes -- the
 // axis atoms of a torsion are never moved by the torsions below it -- then
 // x = t + R(q) z.
-__device__ void fk_warp(const DevBatch& B, const LigHdr& h, const PW& W, const float t[3], const float q[4], float th) {
+__device__ void fk_warp(const DevBatch& B, const LigHdr& h, const PW& W, const float t[3], const float q[4], float th,
+                        const float* __restrict__ rad) {
     const int T = h.n_tor, L = h.n_atoms;
     if (W.lane < T) {
         const float4 u = __ldg(&B.tor_u[h.tor_off + W.lane]);
@@ -376,30 +382,33 @@ __device__ void fk_warp(const DevBatch& B, const LigHdr& h, const PW& W, const f
             }
         }
         W.xs[i] = make_float4(t[0] + (R[0] * x0 + R[1] * x1 + R[2] * x2), t[1] + (R[3] * x0 + R[4] * x1 + R[5] * x2),
-                              t[2] + (R[6] * x0 + R[7] * x1 + R[8] * x2), 0.f);
+                              t[2] + (R[6] * x0 + R[7] * x1 + R[8] * x2), rad[__float_as_int(y.w)]);
     }
+    if (W.lane == 0) W.xs[B.max_atoms] = make_float4(1e6f, 1e6f, 1e6f, 0.f);   // padding target
     __syncwarp();
 }
 
-// Ligand-pocket pairs of the warp's pose.  Every atom's cell lists its candidate
-// pocket atoms in blocks of 8; the pose's blocks are numbered atom by atom (prefix in
-// W.pre) and split into 32 equal contiguous segments, one per lane, so the lanes stay
-// balanced whatever the atoms' list lengths.  A lane accumulates the force on its
-// current atom in registers and leaves a partial in slot (atom + lane) of W.rec; the
-// partials of an atom are then added in lane order (bit-reproducible).  A candidate
-// entry is the pocket index (13 bits) with the pocket atom's flags in the top 3 bits;
-// the pocket float4 carries (x, y, z, radius).  The Vina-form block is branch-free:
-// all eight candidates are evaluated and masked by r^2 < cutoff^2.  Writes the
-// ligand-pocket forces to W.gs and returns the lane's share of the energy.
+// All pairs of the warp's pose.  Atom i's work list is its cell's candidate pocket atoms
+// followed by its intra-ligand partners (every intra pair appears once from each side),
+// both in blocks of 8 uint16 entries (target index, 13 bits | target's flags << 13;
+// padding points at a far sentinel).  Pocket targets are read from the block's staged
+// pocket, ligand targets from the pose's own coordinates (W.xs); both float4 carry
+// (x, y, z, radius).  The pose's blocks are numbered atom by atom (prefix in W.pre) and
+// split into 32 equal contiguous segments, one per lane, so the lanes stay balanced
+// whatever the atoms' list lengths.  A lane accumulates the force on its current atom
+// in registers and leaves a partial in slot (atom + lane) of W.rec; the partials of an
+// atom are added in lane order (bit-reproducible).  The Vina-form block is branch-free:
+// all candidates are evaluated and masked by r^2 < cutoff^2.  Writes the forces to W.gs;
+// returns the lane's ligand-pocket energy and, in *e_in2, twice its intra energy.
 template <int TS, bool PARAMS, bool COUNT>
-__device__ float inter_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
-                            const float w[5], float ebar, ParamAcc& acc, uint32_t& npairs) {
+__device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
+                           const float w[5], float ebar, ParamAcc& acc, uint32_t& npairs, float* e_in2) {
     const DevParams& P = *S.P;
     const float cut2 = P.cut2;
     const int L = h.n_atoms, lane = W.lane;
-    const float4* __restrict__ pocket = S.pocket;
     const uint16_t* __restrict__ cand = pk.cand;
-    // 1. cell ranges and block prefix
+    const uint16_t* __restrict__ ient = B.ient + h.ient_off;
+    // 1. per-atom work: candidate blocks of the cell + intra-partner blocks; prefix
     int carry = 0;
     for (int base = 0; base < L; base += 32) {
         const int i = base + lane;
@@ -408,8 +417,12 @@ __device__ float inter_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             const float4 x = W.xs[i];
             uint32_t beg, end;
             cell_range(pk, x.x, x.y, x.z, beg, end);
+            const int i0 = __ldg(&B.ipre[h.ipre_off + i]), i1 = __ldg(&B.ipre[h.ipre_off + i + 1]);
+            const int cbk = (int)((end - beg) >> 3);
             W.cs[i] = beg;
-            nblk = (int)((end - beg) >> 3);
+            W.cb[i] = cbk;
+            W.ip[i] = i0;
+            nblk = cbk + (i1 - i0);
         }
         int v = nblk;
 #pragma unroll
@@ -425,7 +438,7 @@ __device__ float inter_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
     __syncwarp();
     const int N = carry;
     const int lo = (int)(((long long)N * lane) >> 5), hi = (int)(((long long)N * (lane + 1)) >> 5);
-    float e_lane = 0.f;
+    float e_lp = 0.f, e_in = 0.f;
     if (lo < hi) {
         int i = 0;
         {
@@ -436,81 +449,93 @@ __device__ float inter_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             }
             i = a;
         }
-        int nxt = W.pre[i + 1];
-        uint32_t cur = W.cs[i] + 8u * (uint32_t)(lo - W.pre[i]);
+        int first = W.pre[i], nxt = W.pre[i + 1], cbk = W.cb[i], ipb = W.ip[i];
+        uint32_t csb = W.cs[i];
         float4 xa = W.xs[i];
         int ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
-        float ri = P.radius[ti];
+        float ri = xa.w;
         uint32_t fi = P.tflags[ti];
         float ax = 0.f, ay = 0.f, az = 0.f;
-        uint4 v = __ldg(reinterpret_cast<const uint4*>(cand + cur));
+        auto block_ptr = [&](int blk) -> const uint4* {
+            const int loc = blk - first;
+            return loc < cbk ? reinterpret_cast<const uint4*>(cand + csb + 8u * (uint32_t)loc)
+                             : reinterpret_cast<const uint4*>(ient + 8 * (ipb + loc - cbk));
+        };
+        uint4 v = __ldg(block_ptr(lo));
         for (int blk = lo; blk < hi; ++blk) {
             if (blk == nxt) {                      // move to the atom owning block blk
                 W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
                 ax = ay = az = 0.f;
                 do { ++i; } while (W.pre[i + 1] == blk);
+                first = W.pre[i];
                 nxt = W.pre[i + 1];
-                cur = W.cs[i];
+                cbk = W.cb[i];
+                ipb = W.ip[i];
+                csb = W.cs[i];
                 xa = W.xs[i];
                 ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
-                ri = P.radius[ti];
+                ri = xa.w;
                 fi = P.tflags[ti];
-                v = __ldg(reinterpret_cast<const uint4*>(cand + cur));
+                v = __ldg(block_ptr(blk));
             }
             const uint4 vc = v;
-            if (blk + 1 < hi && blk + 1 < nxt) v = __ldg(reinterpret_cast<const uint4*>(cand + cur + 8));
-            cur += 8;
+            const bool intra = blk - first >= cbk;
+            if (blk + 1 < hi && blk + 1 < nxt) v = __ldg(block_ptr(blk + 1));
+            const float4* __restrict__ src = intra ? W.xs : S.pocket;
             // pair-flag selectors: hydrophobic needs both bit0; donor-acceptor needs
             // (donor_i & acceptor_j) | (acceptor_i & donor_j)
             const uint32_t f_hyd = fi & 1u;
             const uint32_t f_hb = ((fi & 2u) << 1) | ((fi & 4u) >> 1);
+            float eb = 0.f;
             // two halves of four candidates: the loop body stays small for the
             // instruction cache, which the 16 resident warps share across all phases
 #pragma unroll 1
             for (int hv = 0; hv < 2; ++hv) {
-            const uint32_t wv[2] = {hv ? vc.z : vc.x, hv ? vc.w : vc.y};
+                const uint32_t wv[2] = {hv ? vc.z : vc.x, hv ? vc.w : vc.y};
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                const uint32_t ent = (s & 1) ? (wv[s >> 1] >> 16) : (wv[s >> 1] & 0xffffu);
-                const int j = (int)(ent & 0x1fffu);
-                const uint32_t fj = ent >> 13;
-                const float4 a = pocket[j];
-                const float dx = xa.x - a.x, dy = xa.y - a.y, dz = xa.z - a.z;
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                const bool in = r2 < cut2;
-                if (TS == TRIDS_TERMS_VINA5) {
-                    float dd, rinv, et[5];
-                    const float e = vina_eval<PARAMS>(r2, ri + a.w, (f_hyd & fj) ? 1.f : 0.f,
-                                                      (f_hb & fj) ? 1.f : 0.f, w, dd, rinv, et);
-                    const float fr = in ? dd * rinv : 0.f;
-                    e_lane += in ? e : 0.f;
-                    ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
-                    if (PARAMS && in) {
+                for (int s = 0; s < 4; ++s) {
+                    const uint32_t ent = (s & 1) ? (wv[s >> 1] >> 16) : (wv[s >> 1] & 0xffffu);
+                    const int j = (int)(ent & 0x1fffu);
+                    const uint32_t fj = ent >> 13;
+                    const float4 a = src[j];
+                    const float dx = xa.x - a.x, dy = xa.y - a.y, dz = xa.z - a.z;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    const bool in = r2 < cut2;
+                    if (TS == TRIDS_TERMS_VINA5) {
+                        float dd, rinv, et[5];
+                        const float e = vina_eval<PARAMS>(r2, ri + a.w, (f_hyd & fj) ? 1.f : 0.f,
+                                                          (f_hb & fj) ? 1.f : 0.f, w, dd, rinv, et);
+                        const float fr = in ? dd * rinv : 0.f;
+                        eb += in ? e : 0.f;
+                        ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
+                        if (PARAMS && in) {
+                            const float sc = intra ? 0.5f * ebar : ebar;
 #pragma unroll
-                        for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
-                        const int tj = S.ptype[j];
-                        W.grs[ti * 32 + lane] -= ebar * dd;
-                        W.grs[tj * 32 + lane] -= ebar * dd;
+                            for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(sc, et[t], acc.gw[t]);
+                            W.grs[ti * 32 + lane] -= ebar * dd;
+                            if (!intra) W.grs[S.ptype[j] * 32 + lane] -= ebar * dd;
+                        }
+                    } else if (in) {
+                        const int tj = intra ? 0 : S.ptype[j];
+                        float fr, dRs;
+                        float et[5];
+                        const float e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), ri + a.w, (f_hb & fj) ? 2 : 0,
+                                                           intra ? nullptr : &P.gmm[ti][tj][0], P.gmm_k, !intra, w, fr,
+                                                           et, dRs);
+                        eb += e;
+                        ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
+                        if (PARAMS) {
+                            const float sc = intra ? 0.5f * ebar : ebar;
+#pragma unroll
+                            for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(sc, et[t], acc.gw[t]);
+                            W.grs[ti * 32 + lane] += ebar * dRs;
+                            if (!intra) W.grs[tj * 32 + lane] += ebar * dRs;
+                        }
                     }
-                } else if (in) {
-                    const int tj = S.ptype[j];
-                    const float2 pt = P.pairtab[ti][tj];
-                    float fr, dRs;
-                    float et[5];
-                    const float e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, __float_as_int(pt.y),
-                                                       &P.gmm[ti][tj][0], P.gmm_k, true, w, fr, et, dRs);
-                    e_lane += e;
-                    ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
-                    if (PARAMS) {
-#pragma unroll
-                        for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
-                        W.grs[ti * 32 + lane] += ebar * dRs;
-                        W.grs[tj * 32 + lane] += ebar * dRs;
-                    }
+                    if (COUNT) npairs += in ? (intra ? 1u : 2u) : 0u;   // doubled: intra pairs come twice
                 }
-                if (COUNT) npairs += in ? 1u : 0u;
             }
-            }
+            if (intra) e_in += eb; else e_lp += eb;
         }
         W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
     }
@@ -529,58 +554,8 @@ __device__ float inter_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
         W.gs[i] = make_float4(gx, gy, gz, 0.f);
     }
     __syncwarp();
-    return e_lane;
-}
-
-// Intra-ligand pairs, in rounds of up to 32 pairs that share no atom (coloured at pack
-// time, padding entries 0xffffffff), one pair per lane: force updates never collide
-// and each atom receives its contributions in round order.  Adds to W.gs and returns
-// the lane's share of the energy.
-template <int TS, bool PARAMS, bool COUNT>
-__device__ float intra_warp(const DevBatch& B, const Smem& S, const LigHdr& h, const PW& W, const float w[5],
-                            float ebar, ParamAcc& acc, uint32_t& npairs) {
-    const DevParams& P = *S.P;
-    const float cut2 = P.cut2;
-    float e_lane = 0.f;
-    for (int c = 0; c < h.n_chunks; ++c) {
-        const uint32_t pw = __ldg(&B.pairs[h.pair_off + c * 32 + W.lane]);
-        if (pw != 0xffffffffu) {
-            const int i = pw & 0xff, j = (pw >> 8) & 0xff, ti = (pw >> 16) & 0xff, tj = pw >> 24;
-            const float4 xi = W.xs[i], xj = W.xs[j];
-            const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            const bool in = r2 < cut2;
-            const float2 pt = P.pairtab[ti][tj];
-            const int pf = __float_as_int(pt.y);
-            float fr, e, et[5], dRs = 0.f;
-            if (TS == TRIDS_TERMS_VINA5) {
-                float dd, rinv;
-                e = vina_eval<PARAMS>(r2, pt.x, (pf & 1) ? 1.f : 0.f, (pf & 2) ? 1.f : 0.f, w, dd, rinv, et);
-                fr = in ? dd * rinv : 0.f;
-                e = in ? e : 0.f;
-                dRs = -dd;
-            } else {
-                fr = 0.f;
-                e = 0.f;
-                if (in) e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), pt.x, pf, nullptr, 0, false, w, fr, et, dRs);
-            }
-            e_lane += e;
-            float4 gi = W.gs[i], gj = W.gs[j];
-            gi.x = fmaf(fr, dx, gi.x); gi.y = fmaf(fr, dy, gi.y); gi.z = fmaf(fr, dz, gi.z);
-            gj.x = fmaf(-fr, dx, gj.x); gj.y = fmaf(-fr, dy, gj.y); gj.z = fmaf(-fr, dz, gj.z);
-            W.gs[i] = gi;
-            W.gs[j] = gj;
-            if (PARAMS && in) {
-#pragma unroll
-                for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(ebar, et[t], acc.gw[t]);
-                W.grs[ti * 32 + W.lane] += ebar * dRs;
-                W.grs[tj * 32 + W.lane] += ebar * dRs;
-            }
-            if (COUNT) npairs += in ? 1u : 0u;
-        }
-        __syncwarp();
-    }
-    return e_lane;
+    *e_in2 = e_in;
+    return e_lp;
 }
 
 // E_total of the warp's pose (same value on every lane); forces in W.gs.
@@ -590,11 +565,11 @@ __device__ float score_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
     float w[5];
 #pragma unroll
     for (int t = 0; t < 5; ++t) w[t] = S.P->w[t];
-    const float el = inter_warp<TS, PARAMS, COUNT>(B, pk, S, h, W, w, ebar, acc, npairs);
-    const float ei = intra_warp<TS, PARAMS, COUNT>(B, S, h, W, w, ebar, acc, npairs);
+    float ein2;
+    const float el = pairs_warp<TS, PARAMS, COUNT>(B, pk, S, h, W, w, ebar, acc, npairs, &ein2);
     const float e_lp = warp_sum(el);
     *e_inter = e_lp;
-    return e_lp + warp_sum(ei);
+    return e_lp + 0.5f * warp_sum(ein2);
 }
 
 // dE/dt = sum g_i and world torque tau = sum (x_i - t) x g_i (every lane), and
@@ -806,7 +781,7 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
         st.mth = st.vth = 0.f;
     }
     // evaluate
-    fk_warp(A.B, h, W, st.t, st.q, st.th);
+    fk_warp(A.B, h, W, st.t, st.q, st.th, S.P->radius);
     ParamAcc acc;
     float e_inter;
     const float E = score_warp<TS, false, COUNT>(A.B, A.pk, S, h, W, 1.f, acc, &e_inter, npairs);
@@ -868,11 +843,13 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
     }
 }
 
+// Pair counts are kept doubled per lane (an intra pair is seen from both of its atoms,
+// possibly by different lanes); the warp total is halved here.
 __device__ __forceinline__ void flush_count(unsigned long long* cnt, uint32_t n) {
     unsigned long long v = n;
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(cnt, v);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(cnt, v >> 1);
 }
 
 // Persistent fused sampler: each warp pops poses from a global counter (ligands in
@@ -973,7 +950,7 @@ __global__ void __launch_bounds__(512, 1) k_score(ScoreArgs A) {
             const float q[4] = {row[3], row[4], row[5], row[6]};
             const float th = lane < h.n_tor ? row[7 + lane] : 0.f;
             const float ebar = A.e_bar ? A.e_bar[gp] : 1.f;
-            fk_warp(A.B, h, W, t, q, th);
+            fk_warp(A.B, h, W, t, q, th, S.P->radius);
             float e_inter;
             uint32_t np = 0;
             const float E = score_warp<TS, PARAMS, false>(A.B, A.pk, S, h, W, ebar, acc, &e_inter, np);
@@ -1166,6 +1143,7 @@ struct trids_pocket {
     std::vector<float> xyz;
     std::vector<int> type;
     uint8_t* d_ptype = nullptr;
+    std::vector<trids_batch*> batches;   // batches whose intra entries carry this pocket's flags
     float cutoff_built = 0.f;
     float cell = 1.f;
     int n_boxes = 1;
@@ -1206,7 +1184,11 @@ struct trids_batch {
     int4* d_tor_idx = nullptr;
     float4* d_tor_u = nullptr;
     float4* d_tor_p = nullptr;
-    uint32_t* d_pairs = nullptr;
+    int* d_ipre = nullptr;
+    uint16_t* d_ient = nullptr;
+    std::vector<uint16_t> ient_j;     // intra partner lists: target index (pad = max_atoms)
+    std::vector<uint8_t> ient_type;   // target type (for re-encoding flags)
+    trids_pocket* owner = nullptr;    // pocket whose flags are encoded in d_ient
     // per-pose-count caches
     int items_P = -1;
     int2* d_items = nullptr;        // (ligand, first pose of a 32-pose tile), by decreasing cost
@@ -1224,7 +1206,7 @@ struct trids_batch {
         v.n_lig = dims.n_lig; v.max_atoms = dims.max_atoms; v.max_tor = dims.max_tor;
         v.dof_stride = dims.dof_stride; v.n_fields = dims.state_fields;
         v.lig = d_lig; v.atom_y = d_atom_y; v.atom_orig = d_atom_orig; v.tor_idx = d_tor_idx;
-        v.tor_u = d_tor_u; v.tor_p = d_tor_p; v.pairs = d_pairs;
+        v.tor_u = d_tor_u; v.tor_p = d_tor_p; v.ipre = d_ipre; v.ient = d_ient;
         return v;
     }
 };
@@ -1326,6 +1308,18 @@ int upload_pocket_arrays(trids_pocket* pk, cudaStream_t st) {
         CK(cudaMemcpyAsync(pk->d_cand, cand.data(), cand.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(pk->d_params, &pk->hp, sizeof(DevParams), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
+    return TRIDS_OK;
+}
+
+// (Re-)encode a batch's intra partner entries with the pocket's current type flags.
+int encode_intra(const trids_pocket* pk, trids_batch* b, bool allocate) {
+    std::vector<uint16_t> ent(b->ient_j.size());
+    for (size_t k = 0; k < ent.size(); ++k) {
+        const uint32_t f = b->ient_type[k] == 0xff ? 0u : (uint32_t)(pk->prm.flags[b->ient_type[k]] & 7);
+        ent[k] = (uint16_t)((uint32_t)b->ient_j[k] | (f << 13));
+    }
+    if (allocate) return upload(&b->d_ient, ent);
+    if (!ent.empty()) CK(cudaMemcpy(b->d_ient, ent.data(), ent.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
     return TRIDS_OK;
 }
 
@@ -1480,8 +1474,13 @@ int trids_set_params(trids_pocket* pk, const trids_params* prm, void* stream) {
         return fail(TRIDS_EINVAL, "cutoff %.3f exceeds the %.3f the pocket grid was built for", prm->cutoff,
                     pk->cutoff_built);
     if ((rc = device_guard(pk->device))) return rc;
+    const bool flags_changed = std::memcmp(pk->prm.flags, prm->flags, sizeof prm->flags) != 0;
     pk->prm = *prm;
-    return upload_pocket_arrays(pk, (cudaStream_t)stream);
+    if ((rc = upload_pocket_arrays(pk, (cudaStream_t)stream))) return rc;
+    if (flags_changed)
+        for (trids_batch* b : pk->batches)
+            if ((rc = encode_intra(pk, b, false))) return rc;
+    return TRIDS_OK;
 }
 
 int trids_set_boxes(trids_pocket* pk, int32_t n_boxes, const float* centers, const float* sizes) {
@@ -1505,6 +1504,7 @@ int trids_set_boxes(trids_pocket* pk, int32_t n_boxes, const float* centers, con
 
 int trids_free_pocket(trids_pocket* pk) {
     if (!pk) return TRIDS_OK;
+    for (trids_batch* b : pk->batches) b->owner = nullptr;
     cudaFree(pk->d_atoms);
     cudaFree(pk->d_ptype);
     cudaFree(pk->d_cell);
@@ -1573,7 +1573,7 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
     std::vector<int> aorig;
     std::vector<int4> tidx;
     std::vector<float4> tu, tp;
-    std::vector<uint32_t> pairs;
+    std::vector<int> ipre;
     ao = 0;
     for (int l = 0; l < n_lig; ++l) {
         const PackedLigand& lg = b->ligs[l];
@@ -1582,7 +1582,8 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
         h.n_tor = lg.n_tor;
         h.atom_off = (int)ay.size();
         h.tor_off = (int)tidx.size();
-        h.pair_off = (int)pairs.size();
+        h.ipre_off = (int)ipre.size();
+        h.ient_off = (int)b->ient_j.size();
         h.n_pairs = (int)lg.pairs.size();
         const float* X = xyz + 3 * ao;
         const int32_t* Ty = type + ao;
@@ -1609,42 +1610,37 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
             tp.push_back(make_float4((float)((double)X[3 * pa] - lg.c[0]), (float)((double)X[3 * pa + 1] - lg.c[1]),
                                      (float)((double)X[3 * pa + 2] - lg.c[2]), 0.f));
         }
-        // intra pairs in rounds of <= 32 pairs sharing no atom (first fit in list order)
+        // intra partner lists: per atom, every partner (both directions, ascending) in
+        // blocks of 8, padded with the far sentinel index max_atoms
         {
-            std::vector<std::vector<uint32_t>> rounds;
-            std::vector<std::pair<uint64_t, uint64_t>> used;
+            std::vector<std::vector<int>> part(lg.n_atoms);
             for (auto& pr : lg.pairs) {
-                const uint32_t ti = (uint32_t)Ty[lg.perm[pr.first]], tj = (uint32_t)Ty[lg.perm[pr.second]];
-                const uint32_t word = (uint32_t)pr.first | ((uint32_t)pr.second << 8) | (ti << 16) | (tj << 24);
-                auto bit = [](int a) {
-                    return a < 64 ? std::make_pair(1ull << a, 0ull) : std::make_pair(0ull, 1ull << (a - 64));
-                };
-                const auto ba = bit(pr.first), bb = bit(pr.second);
-                size_t r = 0;
-                for (; r < rounds.size(); ++r)
-                    if (rounds[r].size() < 32 && !((used[r].first & (ba.first | bb.first)) ||
-                                                   (used[r].second & (ba.second | bb.second))))
-                        break;
-                if (r == rounds.size()) {
-                    rounds.emplace_back();
-                    used.push_back({0ull, 0ull});
+                part[pr.first].push_back(pr.second);
+                part[pr.second].push_back(pr.first);
+            }
+            int blocks = 0;
+            for (int i = 0; i < lg.n_atoms; ++i) {
+                std::sort(part[i].begin(), part[i].end());
+                ipre.push_back(blocks);
+                for (int j : part[i]) {
+                    b->ient_j.push_back((uint16_t)j);
+                    b->ient_type.push_back((uint8_t)Ty[lg.perm[j]]);
                 }
-                rounds[r].push_back(word);
-                used[r].first |= ba.first | bb.first;
-                used[r].second |= ba.second | bb.second;
+                const size_t pad = (8 - part[i].size() % 8) % 8;
+                for (size_t k = 0; k < pad; ++k) {
+                    b->ient_j.push_back((uint16_t)Lmax);
+                    b->ient_type.push_back(0xff);
+                }
+                blocks += (int)((part[i].size() + 7) / 8);
             }
-            h.n_chunks = (int)rounds.size();
-            for (auto& rd : rounds) {
-                for (uint32_t wd : rd) pairs.push_back(wd);
-                for (size_t k = rd.size(); k < 32; ++k) pairs.push_back(0xffffffffu);
-            }
+            ipre.push_back(blocks);
         }
         b->hdr.push_back(h);
         ao += n_atoms[l];
     }
     if ((rc = upload(&b->d_lig, b->hdr)) || (rc = upload(&b->d_atom_y, ay)) || (rc = upload(&b->d_atom_orig, aorig)) ||
         (rc = upload(&b->d_tor_idx, tidx)) || (rc = upload(&b->d_tor_u, tu)) || (rc = upload(&b->d_tor_p, tp)) ||
-        (rc = upload(&b->d_pairs, pairs))) {
+        (rc = upload(&b->d_ipre, ipre)) || (rc = encode_intra(pk, b.get(), true))) {
         trids_free_batch(b.release());
         return rc;
     }
@@ -1654,18 +1650,24 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
         trids_free_batch(b.release());
         return rc;
     }
+    b->owner = const_cast<trids_pocket*>(pk);
+    b->owner->batches.push_back(b.get());
     *out = b.release();
     return TRIDS_OK;
 }
 
 int trids_free_batch(trids_batch* b) {
     if (!b) return TRIDS_OK;
+    if (b->owner) {
+        auto& v = b->owner->batches;
+        v.erase(std::remove(v.begin(), v.end(), b), v.end());
+    }
     if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
     if (b->side) cudaStreamDestroy(b->side);
     if (b->ev_a) cudaEventDestroy(b->ev_a);
     if (b->ev_b) cudaEventDestroy(b->ev_b);
     cudaFree(b->d_lig); cudaFree(b->d_atom_y); cudaFree(b->d_atom_orig); cudaFree(b->d_tor_idx);
-    cudaFree(b->d_tor_u); cudaFree(b->d_tor_p); cudaFree(b->d_pairs); cudaFree(b->d_items); cudaFree(b->d_lig_order);
+    cudaFree(b->d_tor_u); cudaFree(b->d_tor_p); cudaFree(b->d_ipre); cudaFree(b->d_ient); cudaFree(b->d_items); cudaFree(b->d_lig_order);
     cudaFree(b->d_counter); cudaFree(b->d_err); cudaFree(b->d_partials);
     delete b;
     return TRIDS_OK;

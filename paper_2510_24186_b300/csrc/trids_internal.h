@@ -82,7 +82,8 @@ struct DevPocket {
 
 struct LigHdr {
     int n_atoms, n_tor, atom_off, tor_off;
-    int pair_off, n_pairs, n_chunks, pad0;   // intra pairs: n_chunks rounds of 32 slots at pair_off
+    int ipre_off, ient_off, n_pairs, pad0;   // intra partner lists: per-atom block prefix at ipre_off
+                                             // (L + 1 ints), entries at ient_off (8 per block)
 };
 
 struct DevBatch {
@@ -93,7 +94,9 @@ struct DevBatch {
     const int4* tor_idx;           // (parent atom, child atom, subtree begin, subtree end)
     const float4* tor_u;           // unit axis, input geometry
     const float4* tor_p;           // parent atom, local coords
-    const uint32_t* pairs;         // i | j << 8 | ti << 16 | tj << 24; 0xffffffff = empty slot
+    const int* ipre;               // per atom: first block of its intra partner list
+    const uint16_t* ient;          // partner index | partner flags << 13; each intra pair appears
+                                   // once from each side; padding = max_atoms (far sentinel)
 };
 
 // Sampler state fields per pose (SoA over poses inside each ligand):
