@@ -333,6 +333,90 @@ __device__ __forceinline__ float vina_eval(float r2, float rsum, float hyd, floa
     return e;
 }
 
+// Constants of the paired Vina-form evaluation; both halves of each float2 are equal.
+struct VinaX2 {
+    float2 w0, w1, w2, n0, n2, c1, c2, half, m15, m1, p15, m07, k07, tiny;
+    float w3, w4;
+};
+
+__device__ __forceinline__ VinaX2 make_vina_x2(const float w[5]) {
+    VinaX2 K;
+    K.w0 = make_float2(w[0], w[0]);
+    K.w1 = make_float2(w[1], w[1]);
+    K.w2 = make_float2(w[2], w[2]);
+    K.n0 = make_float2(8.f * w[0], 8.f * w[0]);
+    K.n2 = make_float2(-2.f * w[2], -2.f * w[2]);
+    K.c1 = make_float2(-5.770780163555854f, -5.770780163555854f);
+    K.c2 = make_float2(-1.4426950408889634f, -1.4426950408889634f);
+    K.half = make_float2(0.5f, 0.5f);
+    K.m15 = make_float2(-1.5f, -1.5f);
+    K.m1 = make_float2(-1.f, -1.f);
+    K.p15 = make_float2(1.5f, 1.5f);
+    K.m07 = make_float2(-1.f / 0.7f, -1.f / 0.7f);
+    K.k07 = make_float2(1.f / 0.7f, 1.f / 0.7f);
+    K.tiny = make_float2(1e-12f, 1e-12f);
+    K.w3 = w[3];
+    K.w4 = w[4];
+    return K;
+}
+
+// The same Vina-form pair as vina_eval, for the two candidates packed in one 32-bit
+// candidate-list word, on the packed FP32 pipe (f32x2).  The gradient's sign is folded
+// into the constants so that no operand needs negating: with p = x_j - x_i and
+// ng = -dE/dd, the force on atom i gains ng / r * p.  nxy = -(x_i, y_i) and
+// nzr = -(z_i, R_i); mh / mb select the candidate's hydrophobic / donor-acceptor flag
+// bits (low entry; shifted by 16 for the high entry).  in-cutoff pairs are masked by
+// multiplying with 0/1, which is exact for the finite values every candidate (the far
+// sentinel included) produces.
+template <bool COUNT>
+__device__ __forceinline__ void vina_x2(uint32_t wd, const float4* __restrict__ src, float2 nxy, float2 nzr,
+                                        float cut2, const VinaX2& K, uint32_t mh, uint32_t mb, float2& eb,
+                                        float& ax, float& ay, float& az, uint32_t& cnt, uint32_t cw) {
+    const float4 a = src[wd & 0x1fffu], c = src[(wd >> 16) & 0x1fffu];
+    const float2 pm = make_float2(1.f, -1.f);
+    const float2 pa = __fadd2_rn(make_float2(a.x, a.y), nxy);
+    const float2 qa = __ffma2_rn(make_float2(a.z, a.w), pm, nzr);     // (z_j - z_i, -(R_i + R_j))
+    const float2 pc = __fadd2_rn(make_float2(c.x, c.y), nxy);
+    const float2 qc = __ffma2_rn(make_float2(c.z, c.w), pm, nzr);
+    const float2 sa = __fmul2_rn(pa, pa), sc = __fmul2_rn(pc, pc);
+    const float2 r2 = make_float2(fmaf(qa.x, qa.x, sa.x) + sa.y, fmaf(qc.x, qc.x, sc.x) + sc.y);
+    const float2 in = make_float2(r2.x < cut2 ? 1.f : 0.f, r2.y < cut2 ? 1.f : 0.f);
+    const float2 rr = __fadd2_rn(r2, K.tiny);
+    const float2 ri = make_float2(rsqrtf(rr.x), rsqrtf(rr.y));
+    const float2 d = make_float2(fmaf(rr.x, ri.x, qa.y), fmaf(rr.y, ri.y, qc.y));
+    const float2 q1 = __fmul2_rn(__fmul2_rn(d, d), K.c1);
+    const float2 g1 = make_float2(ex2_approx(q1.x), ex2_approx(q1.y));
+    const float2 b = __ffma2_rn(d, K.half, K.m15);
+    const float2 q2 = __fmul2_rn(__fmul2_rn(b, b), K.c2);
+    const float2 g2 = make_float2(ex2_approx(q2.x), ex2_approx(q2.y));
+    const float2 dn = make_float2(fminf(d.x, 0.f), fminf(d.y, 0.f));
+    const float2 hr = __ffma2_rn(d, K.m1, K.p15);                      // 1.5 - d
+    const float2 hy = make_float2(__saturatef(hr.x), __saturatef(hr.y));
+    const float2 ih = make_float2(hy.x == hr.x ? 1.f : 0.f, hy.y == hr.y ? 1.f : 0.f);
+    const float2 br = __fmul2_rn(d, K.m07);                            // -d / 0.7
+    const float2 hb = make_float2(__saturatef(br.x), __saturatef(br.y));
+    const float2 ib = make_float2(hb.x == br.x ? 1.f : 0.f, hb.y == br.y ? 1.f : 0.f);
+    const float2 w3h = make_float2((wd & mh) ? K.w3 : 0.f, (wd & (mh << 16)) ? K.w3 : 0.f);
+    const float2 w4h = make_float2((wd & mb) ? K.w4 : 0.f, (wd & (mb << 16)) ? K.w4 : 0.f);
+    float2 e = __fmul2_rn(K.w0, g1);
+    e = __ffma2_rn(K.w1, g2, e);
+    e = __ffma2_rn(K.w2, __fmul2_rn(dn, dn), e);
+    e = __ffma2_rn(w3h, hy, e);
+    e = __ffma2_rn(w4h, hb, e);
+    float2 ng = __fmul2_rn(__fmul2_rn(d, K.n0), g1);                    // 8 w0 d g1
+    ng = __ffma2_rn(__fmul2_rn(b, K.w1), g2, ng);                       // + w1 b g2
+    ng = __ffma2_rn(K.n2, dn, ng);                                      // - 2 w2 dn
+    ng = __ffma2_rn(ih, w3h, ng);
+    ng = __ffma2_rn(ib, __fmul2_rn(w4h, K.k07), ng);
+    eb = __ffma2_rn(e, in, eb);
+    const float2 f = __fmul2_rn(__fmul2_rn(ng, in), ri);
+    float2 axy = make_float2(ax, ay);
+    axy = __ffma2_rn(make_float2(f.x, f.x), pa, axy); az = fmaf(f.x, qa.x, az);
+    axy = __ffma2_rn(make_float2(f.y, f.y), pc, axy); az = fmaf(f.y, qc.x, az);
+    ax = axy.x; ay = axy.y;
+    if (COUNT) cnt += ((r2.x < cut2) + (r2.y < cut2)) * cw;
+}
+
 // Candidate-grid cell range (entries [beg, end) of pk.cand) of a point; empty outside
 // the grid, where no pocket atom lies within the cutoff.
 __device__ __forceinline__ void cell_range(const DevPocket& pk, float x, float y, float z, uint32_t& beg,
@@ -405,6 +489,7 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                            const float w[5], float ebar, ParamAcc& acc, uint32_t& npairs, float* e_in2) {
     const DevParams& P = *S.P;
     const float cut2 = P.cut2;
+    const VinaX2 K = make_vina_x2(w);
     const int L = h.n_atoms, lane = W.lane;
     const uint16_t* __restrict__ cand = pk.cand;
     const uint16_t* __restrict__ ient = B.ient + h.ient_off;
@@ -487,54 +572,65 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             const uint32_t f_hyd = fi & 1u;
             const uint32_t f_hb = ((fi & 2u) << 1) | ((fi & 4u) >> 1);
             float eb = 0.f;
+            float2 eb2 = make_float2(0.f, 0.f);
+            const float2 nxy = make_float2(-xa.x, -xa.y), nzr = make_float2(-xa.z, -ri);
+            const uint32_t mh = f_hyd << 13, mb = f_hb << 13;
             // two halves of four candidates: the loop body stays small for the
             // instruction cache, which the 16 resident warps share across all phases
 #pragma unroll 1
             for (int hv = 0; hv < 2; ++hv) {
                 const uint32_t wv[2] = {hv ? vc.z : vc.x, hv ? vc.w : vc.y};
+                if constexpr (TS == TRIDS_TERMS_VINA5 && !PARAMS) {
 #pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    const uint32_t ent = (s & 1) ? (wv[s >> 1] >> 16) : (wv[s >> 1] & 0xffffu);
-                    const int j = (int)(ent & 0x1fffu);
-                    const uint32_t fj = ent >> 13;
-                    const float4 a = src[j];
-                    const float dx = xa.x - a.x, dy = xa.y - a.y, dz = xa.z - a.z;
-                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                    const bool in = r2 < cut2;
-                    if (TS == TRIDS_TERMS_VINA5) {
-                        float dd, rinv, et[5];
-                        const float e = vina_eval<PARAMS>(r2, ri + a.w, (f_hyd & fj) ? 1.f : 0.f,
-                                                          (f_hb & fj) ? 1.f : 0.f, w, dd, rinv, et);
-                        const float fr = in ? dd * rinv : 0.f;
-                        eb += in ? e : 0.f;
-                        ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
-                        if (PARAMS && in) {
-                            const float sc = intra ? 0.5f * ebar : ebar;
+                    for (int u = 0; u < 2; ++u)
+                        vina_x2<COUNT>(wv[u], src, nxy, nzr, cut2, K, mh, mb, eb2, ax, ay, az, npairs,
+                                       intra ? 1u : 2u);   // doubled: intra pairs come twice
+                } else {
 #pragma unroll
-                            for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(sc, et[t], acc.gw[t]);
-                            W.grs[ti * 32 + lane] -= ebar * dd;
-                            if (!intra) W.grs[S.ptype[j] * 32 + lane] -= ebar * dd;
+                    for (int s = 0; s < 4; ++s) {
+                        const uint32_t ent = (s & 1) ? (wv[s >> 1] >> 16) : (wv[s >> 1] & 0xffffu);
+                        const int j = (int)(ent & 0x1fffu);
+                        const uint32_t fj = ent >> 13;
+                        const float4 a = src[j];
+                        const float dx = xa.x - a.x, dy = xa.y - a.y, dz = xa.z - a.z;
+                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        const bool in = r2 < cut2;
+                        if (TS == TRIDS_TERMS_VINA5) {
+                            float dd, rinv, et[5];
+                            const float e = vina_eval<PARAMS>(r2, ri + a.w, (f_hyd & fj) ? 1.f : 0.f,
+                                                              (f_hb & fj) ? 1.f : 0.f, w, dd, rinv, et);
+                            const float fr = in ? dd * rinv : 0.f;
+                            eb += in ? e : 0.f;
+                            ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
+                            if (PARAMS && in) {
+                                const float sc = intra ? 0.5f * ebar : ebar;
+#pragma unroll
+                                for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(sc, et[t], acc.gw[t]);
+                                W.grs[ti * 32 + lane] -= ebar * dd;
+                                if (!intra) W.grs[S.ptype[j] * 32 + lane] -= ebar * dd;
+                            }
+                        } else if (in) {
+                            const int tj = intra ? 0 : S.ptype[j];
+                            float fr, dRs;
+                            float et[5];
+                            const float e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), ri + a.w, (f_hb & fj) ? 2 : 0,
+                                                               intra ? nullptr : &P.gmm[ti][tj][0], P.gmm_k, !intra, w, fr,
+                                                               et, dRs);
+                            eb += e;
+                            ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
+                            if (PARAMS) {
+                                const float sc = intra ? 0.5f * ebar : ebar;
+#pragma unroll
+                                for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(sc, et[t], acc.gw[t]);
+                                W.grs[ti * 32 + lane] += ebar * dRs;
+                                if (!intra) W.grs[tj * 32 + lane] += ebar * dRs;
+                            }
                         }
-                    } else if (in) {
-                        const int tj = intra ? 0 : S.ptype[j];
-                        float fr, dRs;
-                        float et[5];
-                        const float e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), ri + a.w, (f_hb & fj) ? 2 : 0,
-                                                           intra ? nullptr : &P.gmm[ti][tj][0], P.gmm_k, !intra, w, fr,
-                                                           et, dRs);
-                        eb += e;
-                        ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
-                        if (PARAMS) {
-                            const float sc = intra ? 0.5f * ebar : ebar;
-#pragma unroll
-                            for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(sc, et[t], acc.gw[t]);
-                            W.grs[ti * 32 + lane] += ebar * dRs;
-                            if (!intra) W.grs[tj * 32 + lane] += ebar * dRs;
-                        }
+                        if (COUNT) npairs += in ? (intra ? 1u : 2u) : 0u;   // doubled: intra pairs come twice
                     }
-                    if (COUNT) npairs += in ? (intra ? 1u : 2u) : 0u;   // doubled: intra pairs come twice
                 }
             }
+            if (TS == TRIDS_TERMS_VINA5 && !PARAMS) eb = eb2.x + eb2.y;
             if (intra) e_in += eb; else e_lp += eb;
         }
         W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
