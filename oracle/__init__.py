@@ -42,7 +42,25 @@ class Eval(C.Structure):
                 ("g_w", C.c_double * 5), ("g_R", C.c_double * NT),
                 ("n_inter", C.c_int64), ("n_intra", C.c_int64), ("n_straddle", C.c_int32),
                 ("e_slack", C.c_double), ("g_slack", C.c_double), ("e_mag", C.c_double),
-                ("g_mag", C.c_double * (7 + TMAX))]
+                ("g_mag", C.c_double * (7 + TMAX)), ("n_res_pairs", C.c_int64)]
+
+
+class Mdn(C.Structure):
+    _fields_ = [("n_res", C.c_int32), ("K", C.c_int32), ("res", C.POINTER(C.c_int32)),
+                ("prm", C.POINTER(C.c_double))]
+
+
+def mdn(res, prm):
+    """Residue-level E_MDN inputs: res [M] residue of each pocket atom, prm [L_input, n_res, K, 3]
+    of (pi, mu, sigma).  The arrays are kept alive on the returned object."""
+    res = np.ascontiguousarray(res, dtype=np.int32)
+    prm = np.ascontiguousarray(prm, dtype=np.float64)
+    m = Mdn()
+    m.n_res, m.K = prm.shape[1], prm.shape[2]
+    m.res = res.ctypes.data_as(C.POINTER(C.c_int32))
+    m.prm = prm.ctypes.data_as(C.POINTER(C.c_double))
+    m._keep = (res, prm)
+    return m
 
 
 MAX_BOXES = 8
@@ -86,6 +104,8 @@ def lib():
                               P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_double)]
         L.or_score.argtypes = [P(Params), C.c_int, P(C.c_double), P(C.c_int32), P(Ligand),
                                P(C.c_double), P(Eval)]
+        L.or_score_mdn.argtypes = [P(Params), C.c_int, P(C.c_double), P(C.c_int32), P(Mdn), P(Ligand),
+                                   P(C.c_double), P(Eval)]
         L.or_loop_steps.argtypes = [C.c_int, C.c_int, C.c_int]
         L.or_init_pose.argtypes = [P(SampleCfg), C.c_int, C.c_uint32, C.c_uint32, P(C.c_double)]
         L.or_perturb.argtypes = [P(SampleCfg), C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, P(C.c_double)]
@@ -95,10 +115,10 @@ def lib():
         L.or_adam_step.argtypes = [P(SampleCfg), C.c_int, C.c_int, C.c_uint32, P(C.c_double), P(C.c_double),
                                    P(C.c_double), P(C.c_double)]
         L.or_sample_pose.argtypes = [P(SampleCfg), P(Params), C.c_int, P(C.c_double), P(C.c_int32),
-                                     P(Ligand), C.c_uint32, C.c_uint32, P(C.c_double), P(C.c_int64)]
+                                     P(Mdn), P(Ligand), C.c_uint32, C.c_uint32, P(C.c_double), P(C.c_int64)]
         L.or_sample_pose.restype = C.c_double
         L.or_sample_ligand.argtypes = [P(SampleCfg), P(Params), C.c_int, P(C.c_double), P(C.c_int32),
-                                       P(Ligand), C.c_uint32, C.c_int, C.c_int, P(C.c_double),
+                                       P(Mdn), P(Ligand), C.c_uint32, C.c_int, C.c_int, P(C.c_double),
                                        P(C.c_double), C.c_int]
         L.or_sample_ligand.restype = C.c_int64
         L.or_topk.argtypes = [C.c_int, P(C.c_double), P(C.c_double), C.c_int, C.c_int, C.c_double,
@@ -169,13 +189,14 @@ def fk(lg, dof, brute=False):
     return x
 
 
-def score(p, pxyz, ptype, lg, dof):
-    """Returns an Eval (FP64)."""
+def score(p, pxyz, ptype, lg, dof, md=None):
+    """Returns (status, Eval) in FP64.  md: residue-level E_MDN inputs (term_set 2), see mdn()."""
     ev = Eval()
     pxyz = np.ascontiguousarray(pxyz, dtype=np.float64)
     ptype = np.ascontiguousarray(ptype, dtype=np.int32)
     dof = np.ascontiguousarray(dof, dtype=np.float64)
-    st = lib().or_score(C.byref(p), len(ptype), _dp(pxyz), _ip(ptype), C.byref(lg), _dp(dof), C.byref(ev))
+    st = lib().or_score_mdn(C.byref(p), len(ptype), _dp(pxyz), _ip(ptype), None if md is None else C.byref(md),
+                            C.byref(lg), _dp(dof), C.byref(ev))
     return st, ev
 
 
@@ -253,7 +274,7 @@ def loop_steps(S, Lmc, l):
     return lib().or_loop_steps(S, Lmc, l)
 
 
-def sample_ligand(cfg, p, pxyz, ptype, lg, lig, P, n_threads=1):
+def sample_ligand(cfg, p, pxyz, ptype, lg, lig, P, n_threads=1, md=None):
     """FP64 trajectories of P poses; returns (dof [P, 7+T], energy [P], in-cutoff pair count)."""
     T = lg.n_tor
     dof = np.zeros((P, 7 + T))
@@ -261,7 +282,7 @@ def sample_ligand(cfg, p, pxyz, ptype, lg, lig, P, n_threads=1):
     pxyz = np.ascontiguousarray(pxyz, dtype=np.float64)
     ptype = np.ascontiguousarray(ptype, dtype=np.int32)
     pairs = lib().or_sample_ligand(C.byref(cfg), C.byref(p), len(ptype), _dp(pxyz), _ip(ptype),
-                                   C.byref(lg), lig, P, 7 + T, _dp(dof), _dp(e), n_threads)
+                                   None if md is None else C.byref(md), C.byref(lg), lig, P, 7 + T, _dp(dof), _dp(e), n_threads)
     return dof, e, pairs
 
 

@@ -19,6 +19,8 @@
  *   or_pair                pinned: hand-computed closed forms (tests/golden/terms.txt)
  *   or_fk                  pinned: or_fk_brute (independent algorithm) + invariants
  *   or_score               pinned: rigid-motion invariance, FD of energy, 1+1 atom closed form
+ *   residue E_MDN          pinned: closed forms (tests/golden/terms.txt), a numpy brute force of
+ *                          the residue minimum, FD, rigid-motion invariance, argmin tie rule
  *   or_adam_step           pinned: torch.optim.Adam
  *   or_init/perturb/metro  pinned: Philox pin + Shoemake uniformity + beta property
  *   or_sample              pinned through its parts; end-to-end trajectories are chaotic,
@@ -79,7 +81,17 @@ typedef struct {
      * q: the lever about t; theta: the lever about the torsion's parent atom) */
     double e_mag;
     double g_mag[7 + OR_TMAX];
+    int64_t n_res_pairs;         /* (ligand atom, residue) pairs inside the E_MDN cutoff */
 } or_eval;
+
+/* Residue-level E_MDN inputs (term_set 2).  res[j] = residue of pocket atom j;
+ * prm[((i * n_res) + r) * K + k] = (pi, mu, sigma) of ligand atom i (input order),
+ * residue r, kernel k: the parameters the paper's network predicts per pair. */
+typedef struct {
+    int32_t n_res, K;
+    const int32_t* res;
+    const double* prm;
+} or_mdn;
 
 #define OR_MAX_BOXES 8
 typedef struct {
@@ -473,6 +485,8 @@ static int hb_pair(const or_params* p, int a, int b)
  *   gauss1 = exp(-(d/0.5)^2), gauss2 = exp(-((d-3)/2)^2), repulsion = d^2 (d<0),
  *   hydrophobic (both hydrophobic) = 1 (d<0.5), 1.5-d (d<1.5), else 0,
  *   hbond (donor-acceptor) = 1 (d<-0.7), -d/0.7 (d<0), else 0.
+ * term_set 2: as term_set 1 without the atom-pair e0; E_MDN is then the
+ *   residue-level sum of residue_mdn below.
  * term_set 1, the TRIDS E_dock terms (Sec. 2 "Scoring functions"), on r:
  *   e0 = E_MDN pair = -sum_k pi_k exp(-(r-mu_k)^2 / (2 sigma_k^2)) for r < 5 (inter only);
  *        exponent sign read as negative (Gaussian), no normalisation, as printed;
@@ -508,7 +522,8 @@ void or_pair(const or_params* p, int ti, int tj, double r, int inter,
         }
         for (int t = 0; t < 5; ++t) dR[t] = -dr[t];
     } else {
-        if (inter && r < 5.0) {
+        const int atom_mdn = inter && p->term_set == 1;
+        if (atom_mdn && r < 5.0) {
             const double* g = p->gmm + ((size_t)(ti * OR_NT + tj) * OR_KMAX) * 3;
             double P = 0, dP = 0;
             for (int k = 0; k < p->gmm_k; ++k) {
@@ -518,7 +533,7 @@ void or_pair(const or_params* p, int ti, int tj, double r, int inter,
             }
             e[0] = -P; dr[0] = -dP;
         }
-        if (inter && NEAR(r, 5.0)) {
+        if (atom_mdn && NEAR(r, 5.0)) {
             const double* g = p->gmm + ((size_t)(ti * OR_NT + tj) * OR_KMAX) * 3;
             for (int k = 0; k < p->gmm_k; ++k) {
                 double z = 5.0 - g[3 * k + 1];
@@ -598,10 +613,83 @@ static void accumulate_pair(const or_params* p, int ti, int tj, const double* xi
     if (inter) ev->n_inter++; else ev->n_intra++;
 }
 
+/*
+ * Residue-level E_MDN (Sec. 2, Eqs. P(d) and E_MDN): d_ir = the minimum distance
+ * between ligand atom i and the atoms of pocket residue r; each (i, r) with d_ir < 5 A
+ * adds w0 * (-sum_k pi_k exp(-(d_ir - mu_k)^2 / (2 sigma_k^2))).  Readings: the exponent
+ * is negative (a Gaussian) and P is unnormalised, as for the atom-pair form.  The force
+ * acts along the nearest atom (the subgradient of the minimum; equal distances -> the
+ * lowest atom index).  A pair within OR_STRADDLE of the cutoff, or whose two nearest
+ * atoms are within OR_STRADDLE of each other, is a counted straddle.
+ */
+int or_score_mdn(const or_params* p, int M, const double* pxyz, const int32_t* ptype, const or_mdn* md,
+                 const or_ligand* lg, const double* dof, or_eval* ev);
+
+static void residue_mdn(const or_params* p, int M, const double* pxyz, const or_mdn* md, const or_ligand* lg,
+                        or_eval* ev, double* gm)
+{
+    const int R = md->n_res, K = md->K;
+    double* best = (double*)malloc(sizeof(double) * 2 * R);
+    int* arg = (int*)malloc(sizeof(int) * R);
+    double* second = best + R;
+    for (int i = 0; i < lg->n_atoms; ++i) {
+        const double* x = ev->x[i];
+        for (int r = 0; r < R; ++r) { best[r] = second[r] = INFINITY; arg[r] = -1; }
+        for (int a = 0; a < M; ++a) {
+            const int r = md->res[a];
+            double dx = x[0] - pxyz[3 * a], dy = x[1] - pxyz[3 * a + 1], dz = x[2] - pxyz[3 * a + 2];
+            double d = sqrt(dx * dx + dy * dy + dz * dz);
+            if (d < best[r]) { second[r] = best[r]; best[r] = d; arg[r] = a; }
+            else if (d < second[r]) second[r] = d;
+        }
+        const double* pi_row = md->prm + (size_t)lg->perm[i] * R * K * 3;
+        for (int r = 0; r < R; ++r) {
+            if (arg[r] < 0) continue;
+            const double d = best[r];
+            const double* g = pi_row + (size_t)r * K * 3;
+            double P = 0, dP = 0;
+            for (int k = 0; k < K; ++k) {
+                double z = d - g[3 * k + 1], s2 = g[3 * k + 2] * g[3 * k + 2];
+                double ex = g[3 * k] * exp(-z * z / (2.0 * s2));
+                P += ex;
+                dP -= ex * z / s2;
+            }
+            const double e = -P, dEdd = -dP;   /* unweighted term and its d-derivative */
+            if (fabs(d - 5.0) < OR_STRADDLE) {
+                ev->n_straddle++;
+                ev->e_slack += fabs(p->w[0] * e);
+                ev->g_slack += fabs(p->w[0] * dEdd);
+            }
+            if (!(d < 5.0)) continue;
+            if (second[r] - d < OR_STRADDLE) { ev->n_straddle++; ev->g_slack += 2.0 * fabs(p->w[0] * dEdd); }
+            ev->e_inter += p->w[0] * e;
+            ev->g_w[0] += e;
+            ev->e_mag += fabs(p->w[0] * e);
+            gm[i] += fabs(p->w[0] * dEdd);
+            ev->n_res_pairs++;
+            if (d > 0) {
+                const double* xa = pxyz + 3 * arg[r];
+                double f = p->w[0] * dEdd / d;
+                for (int c = 0; c < 3; ++c) ev->g_x[i][c] += f * (x[c] - xa[c]);
+            }
+        }
+    }
+    free(best);
+    free(arg);
+}
+
 int or_score(const or_params* p, int M, const double* pxyz, const int32_t* ptype,
              const or_ligand* lg, const double* dof, or_eval* ev)
 {
+    return or_score_mdn(p, M, pxyz, ptype, NULL, lg, dof, ev);
+}
+
+/* term_set 2 needs md (residues and per-pair kernels); other term sets ignore it. */
+int or_score_mdn(const or_params* p, int M, const double* pxyz, const int32_t* ptype, const or_mdn* md,
+                 const or_ligand* lg, const double* dof, or_eval* ev)
+{
     memset(ev, 0, sizeof *ev);
+    if (p->term_set == 2 && !md) return OR_EINVAL;
     int L = lg->n_atoms, T = lg->n_tor;
     double Rf[OR_TMAX + 1][9], of[OR_TMAX + 1][3], Rq[9];
     fk_frames(lg, dof, Rf, of);
@@ -618,6 +706,7 @@ int or_score(const or_params* p, int M, const double* pxyz, const int32_t* ptype
         accumulate_pair(p, lg->type[i], lg->type[j], ev->x[i], ev->x[j], 0,
                         &ev->e_intra, ev->g_x[i], ev->g_x[j], ev, 1.0, &gm[i], &gm[j]);
     }
+    if (p->term_set == 2) residue_mdn(p, M, pxyz, md, lg, ev, gm);
     for (int i = 0; i < L; ++i) {
         double lt = sqrt((ev->x[i][0] - dof[0]) * (ev->x[i][0] - dof[0]) + (ev->x[i][1] - dof[1]) * (ev->x[i][1] - dof[1]) +
                          (ev->x[i][2] - dof[2]) * (ev->x[i][2] - dof[2]));
@@ -778,7 +867,7 @@ void or_adam_step(const or_sample_cfg* cfg, int T, int ta, uint32_t pose, const 
  * non-finite energy froze the pose).  pairs (nullable) accumulates the number
  * of pairs inside the cutoff over all evaluations. */
 double or_sample_pose(const or_sample_cfg* cfg, const or_params* p, int M, const double* pxyz,
-                      const int32_t* ptype, const or_ligand* lg, uint32_t lig, uint32_t pose,
+                      const int32_t* ptype, const or_mdn* md, const or_ligand* lg, uint32_t lig, uint32_t pose,
                       double* dof, int64_t* pairs)
 {
     int T = lg->n_tor;
@@ -797,7 +886,7 @@ double or_sample_pose(const or_sample_cfg* cfg, const or_params* p, int M, const
         memset(m, 0, sizeof m);
         memset(v, 0, sizeof v);
         for (int j = 0; j < n; ++j) {
-            int st = or_score(p, M, pxyz, ptype, lg, dof, ev);
+            int st = or_score_mdn(p, M, pxyz, ptype, md, lg, dof, ev);
             if (pairs) *pairs += ev->n_inter + ev->n_intra;
             if (st != OR_OK) { free(ev); return NAN; }
             if (j < n - 1) {
@@ -822,14 +911,14 @@ double or_sample_pose(const or_sample_cfg* cfg, const or_params* p, int M, const
 
 typedef struct {
     const or_sample_cfg* cfg; const or_params* p; int M; const double* pxyz; const int32_t* ptype;
-    const or_ligand* lg; uint32_t lig; int pose0, pose1, dstride; double* dof; double* e; int64_t pairs;
+    const or_mdn* md; const or_ligand* lg; uint32_t lig; int pose0, pose1, dstride; double* dof; double* e; int64_t pairs;
 } or_job;
 
 static void* or_worker(void* arg)
 {
     or_job* j = (or_job*)arg;
     for (int ps = j->pose0; ps < j->pose1; ++ps)
-        j->e[ps] = or_sample_pose(j->cfg, j->p, j->M, j->pxyz, j->ptype, j->lg, j->lig, (uint32_t)ps,
+        j->e[ps] = or_sample_pose(j->cfg, j->p, j->M, j->pxyz, j->ptype, j->md, j->lg, j->lig, (uint32_t)ps,
                                   j->dof + (size_t)ps * j->dstride, &j->pairs);
     return NULL;
 }
@@ -837,7 +926,7 @@ static void* or_worker(void* arg)
 /* Poses [0, P) of one ligand on n_threads POSIX threads (contiguous chunks).
  * dof: [P][dstride], e: [P].  Returns the number of in-cutoff pairs evaluated. */
 int64_t or_sample_ligand(const or_sample_cfg* cfg, const or_params* p, int M, const double* pxyz,
-                         const int32_t* ptype, const or_ligand* lg, uint32_t lig, int P, int dstride,
+                         const int32_t* ptype, const or_mdn* md, const or_ligand* lg, uint32_t lig, int P, int dstride,
                          double* dof, double* e, int n_threads)
 {
     if (n_threads < 1) n_threads = 1;
@@ -846,7 +935,7 @@ int64_t or_sample_ligand(const or_sample_cfg* cfg, const or_params* p, int M, co
     pthread_t th[256];
     if (n_threads > 256) n_threads = 256;
     for (int t = 0; t < n_threads; ++t) {
-        or_job j = {cfg, p, M, pxyz, ptype, lg, lig, (int)((int64_t)P * t / n_threads),
+        or_job j = {cfg, p, M, pxyz, ptype, md, lg, lig, (int)((int64_t)P * t / n_threads),
                     (int)((int64_t)P * (t + 1) / n_threads), dstride, dof, e, 0};
         jobs[t] = j;
         pthread_create(&th[t], NULL, or_worker, &jobs[t]);

@@ -21,6 +21,11 @@ Recipes (all distances in Angstrom):
     cavity centre (or a union of such shells), atoms >= 3 A apart. R_out starts
     at 12 A and grows by 0.5 A after 10,000 consecutive rejections.
   * 8 Vina-style atom types with project-chosen radii and flags (below).
+  * residues (for the residue-level E_MDN): greedy spatial groups of pocket
+    atoms. Seed = the lowest-index unassigned atom; the group takes the seed's
+    nearest unassigned atoms within 6 A, up to a size drawn from U{4..14}.
+  * per-(ligand atom, residue) Gaussian kernels (what the paper's network would
+    predict): pi ~ U(0.05, 1) / K, mu ~ U(2.0, 5.5), sigma ~ U(0.3, 1.5).
 """
 from __future__ import annotations
 
@@ -223,6 +228,35 @@ def gen_pocket(rng: np.random.Generator, n_atoms: int, centers, r_in=4.0, r_out=
     vol = len(centers) * 4.0 / 3.0 * math.pi * (r_out ** 3 - r_in ** 3)
     return Pocket(xyz=pts, type=types, centers=centers, r_out=float(r_out),
                   density=float(n_atoms / vol))
+
+
+def gen_residues(rng: np.random.Generator, xyz: np.ndarray, size_range=(4, 14), reach=6.0) -> np.ndarray:
+    """Residue index of each pocket atom (greedy spatial groups, see the module notes)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    n = len(xyz)
+    res = np.full(n, -1, dtype=np.int32)
+    tree = cKDTree(xyz)
+    r = 0
+    for seed in range(n):
+        if res[seed] >= 0:
+            continue
+        size = int(rng.integers(size_range[0], size_range[1] + 1))
+        near = tree.query_ball_point(xyz[seed], reach)
+        near = [j for j in near if res[j] < 0]
+        near.sort(key=lambda j: (float(np.sum((xyz[j] - xyz[seed]) ** 2)), j))
+        for j in near[:size]:
+            res[j] = r
+        r += 1
+    return res
+
+
+def gen_mdn(rng: np.random.Generator, n_lig_atoms: int, n_res: int, K: int) -> np.ndarray:
+    """Kernels [n_lig_atoms, n_res, K, 3] of (pi, mu, sigma), float32."""
+    out = np.empty((n_lig_atoms, n_res, K, 3), dtype=np.float32)
+    out[..., 0] = rng.uniform(0.05, 1.0, (n_lig_atoms, n_res, K)) / K
+    out[..., 1] = rng.uniform(2.0, 5.5, (n_lig_atoms, n_res, K))
+    out[..., 2] = rng.uniform(0.3, 1.5, (n_lig_atoms, n_res, K))
+    return out
 
 
 def random_dofs(rng: np.random.Generator, n_tor: np.ndarray, poses: int, box_min, box_max,
