@@ -50,6 +50,10 @@ extern "C" {
 
 #define TRIDS_TERMS_VINA5 0
 #define TRIDS_TERMS_TRIDS 1
+#define TRIDS_TERMS_TRIDS_RES 2
+
+#define TRIDS_MAX_MDN_K 16    /* Gaussian kernels per (ligand atom, residue) pair */
+#define TRIDS_MAX_RESIDUES 8191
 
 #define TRIDS_MODE_PERSISTENT 0 /* one persistent fused launch (optionally a CUDA graph) */
 #define TRIDS_MODE_PER_LIGAND 1 /* plain form: one launch per (ligand, step) */
@@ -76,6 +80,18 @@ extern "C" {
  *     w2 E_clash: -ln(max(r,0.5)/d_clash), r < d_clash, d_clash = 2.6 for a donor-acceptor
  *                pair, else R_a + R_b;
  *     w3 E_Hbond: -exp(-(r-2.88)^2/(2*0.3^2)), donor-acceptor pairs, r < 3.4.
+ * term_set TRIDS_TERMS_TRIDS_RES: E_MDN at residue level, the form Sec. 2 defines
+ *   (d_ij in Eq. P(d) is the minimum distance between residue i's atoms and ligand
+ *   atom j):
+ *     w0 E_MDN:  -sum_r sum_j [d_rj < 5] sum_k pi_k exp(-(d_rj - mu_k)^2/(2 sigma_k^2)),
+ *                d_rj = min over the atoms a of residue r of |x_j - x_a|; the force acts
+ *                along the nearest atom (equal distances: the lowest pocket-atom index);
+ *                (pi, mu, sigma) per (ligand atom, residue, k) from trids_set_mdn; the
+ *                5 A cutoff is the paper's and does not depend on `cutoff`;
+ *     w1..w3:    E_long, E_clash, E_Hbond over atom pairs, as for TRIDS_TERMS_TRIDS
+ *                (gmm unused).
+ *   Needs trids_set_residues on the pocket (built with cutoff >= 5) and trids_set_mdn
+ *   on the batch; score and sample calls fail with TRIDS_EINVAL without them.
  * flags[type]: bit0 hydrophobic, bit1 donor, bit2 acceptor.  A donor-acceptor pair
  * is donor on one side and acceptor on the other, either way round.
  */
@@ -161,6 +177,19 @@ int trids_set_boxes(trids_pocket* pk, int32_t n_boxes, const float* centers, con
 int trids_free_pocket(trids_pocket* pk);
 
 /*
+ * Residues of the pocket for the residue-level E_MDN (term set TRIDS_TERMS_TRIDS_RES;
+ * Sec. 2: the MDN scores atom-residue pairs by their minimum distance).
+ *   residue  host [n_atoms] int32, residue index of each pocket atom in [0, n_res);
+ *            a residue may hold any atoms, in any order, or none.
+ *   n_res    1..TRIDS_MAX_RESIDUES.
+ * Builds, per cell of the pocket's candidate grid, the list of residues with an atom
+ * within 5 A of the cell (plus half its diagonal).  Replaces earlier residues.  The
+ * pocket must have been built with cutoff >= 5.  Errors: TRIDS_EINVAL, TRIDS_ENOMEM,
+ * TRIDS_ECUDA.  Synchronous.
+ */
+int trids_set_residues(trids_pocket* pk, int32_t n_res, const int32_t* residue);
+
+/*
  * trids_pack_ligands -- validate ligands, build their torsion trees and upload them.
  * Inputs are host arrays, concatenated over ligands: n_atoms[n_lig]; xyz[sum L][3]
  * float32 input geometry (theta = 0); type[sum L]; n_bonds[n_lig];
@@ -184,6 +213,19 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
                        const int32_t* bonds, const uint8_t* rotatable, trids_batch** out);
 
 int trids_free_batch(trids_batch* b);
+
+/*
+ * Per-pair Gaussian kernels of the residue-level E_MDN (the quantities the paper's
+ * network predicts for each ligand atom / residue pair, Sec. 2 Eq. P(d)).
+ *   mdn    DEVICE float32 [n_atoms_total][n_res][K][3] of (pi, mu, sigma), rows in the
+ *          input atom order of trids_pack_ligands (ligand 0's atoms first); sigma > 0.
+ *   n_res  must equal the pocket's residue count when scoring; K in 1..TRIDS_MAX_MDN_K.
+ * The library keeps its own copy (rows reordered to the packed atom order), so `mdn`
+ * may be freed after the call.  Runs on `stream` and synchronises it.  Errors:
+ * TRIDS_EINVAL (sizes, host pointer, non-finite values or sigma <= 0), TRIDS_ENOMEM,
+ * TRIDS_ECUDA.
+ */
+int trids_set_mdn(trids_batch* b, int32_t n_res, int32_t K, const float* mdn, void* stream);
 
 int trids_batch_info(const trids_batch* b, trids_batch_dims* dims);
 

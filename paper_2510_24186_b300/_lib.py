@@ -8,12 +8,13 @@ from . import build as _build
 
 MAX_TYPES, MAX_GMM, MAX_ATOMS, MAX_TOR = 16, 4, 70, 20
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ENONFINITE = 0, -1, -2, -3, -4, -5
-TERMS_VINA5, TERMS_TRIDS = 0, 1
+TERMS_VINA5, TERMS_TRIDS, TERMS_TRIDS_RES = 0, 1, 2
+MAX_MDN_K, MAX_RESIDUES = 16, 8191
 MODE_PERSISTENT, MODE_PER_LIGAND = 0, 1
 
 EXPORTS = ("trids_last_error", "trids_version", "trids_make_pocket", "trids_set_params", "trids_set_boxes",
-           "trids_free_pocket",
-           "trids_pack_ligands", "trids_free_batch", "trids_batch_info", "trids_batch_query",
+           "trids_free_pocket", "trids_set_residues",
+           "trids_pack_ligands", "trids_free_batch", "trids_set_mdn", "trids_batch_info", "trids_batch_query",
            "trids_pack_topology", "trids_score_grad", "trids_score_grad_noalloc", "trids_state_floats",
            "trids_sample", "trids_topk", "trids_sync")
 
@@ -68,6 +69,8 @@ def lib(build_if_missing: bool = True):
     L.trids_free_pocket.argtypes = [vp]
     L.trids_pack_ligands.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, P(vp)]
     L.trids_free_batch.argtypes = [vp]
+    L.trids_set_residues.argtypes = [vp, i32, vp]
+    L.trids_set_mdn.argtypes = [vp, i32, i32, vp, vp]
     L.trids_batch_info.argtypes = [vp, P(BatchDims)]
     L.trids_batch_query.argtypes = [vp, vp, vp, i32, vp, i32]
     L.trids_pack_topology.argtypes = [i32, vp, vp, i32, i32, vp, vp, vp, i32, P(i32)]

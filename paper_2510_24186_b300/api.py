@@ -95,6 +95,14 @@ class Pocket:
         check(_lib.lib().trids_set_boxes(self.handle, len(c), c.ctypes.data, s.ctypes.data))
         self.box_center, self.box_size = c, s
 
+    def set_residues(self, residue):
+        """Residue index of each pocket atom, for the residue-level E_MDN (trids_set_residues)."""
+        r = np.ascontiguousarray(residue, dtype=np.int32)
+        if len(r) != self.n_atoms:
+            raise ValueError(f"need {self.n_atoms} residue indices, got {len(r)}")
+        self.n_res = int(r.max()) + 1
+        check(_lib.lib().trids_set_residues(self.handle, self.n_res, r.ctypes.data))
+
     def close(self):
         if getattr(self, "handle", None):
             _lib.lib().trids_free_pocket(self.handle)
@@ -147,6 +155,16 @@ class Batch:
 
     def state_floats(self, poses: int) -> int:
         return int(_lib.lib().trids_state_floats(self.handle, poses))
+
+    def set_mdn(self, mdn: torch.Tensor, stream=None):
+        """Residue-level E_MDN kernels (trids_set_mdn): a CUDA float32 tensor
+        [n_atoms_total, n_res, K, 3] of (pi, mu, sigma) in input atom order."""
+        if not (mdn.is_cuda and mdn.dtype == torch.float32 and mdn.dim() == 4 and mdn.shape[3] == 3):
+            raise ValueError("mdn must be a CUDA float32 tensor [n_atoms_total, n_res, K, 3]")
+        if mdn.shape[0] != int(self.n_atoms.sum()):
+            raise ValueError(f"mdn has {mdn.shape[0]} rows, the batch has {int(self.n_atoms.sum())} atoms")
+        m = mdn.contiguous()
+        check(_lib.lib().trids_set_mdn(self.handle, int(m.shape[1]), int(m.shape[2]), _ptr(m), _stream(stream)))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -268,4 +268,62 @@ void build_grid(int M, const float* xyz, float cutoff, float h, CandidateGrid* g
     for (int j = 0; j < M; ++j) visit(j, [&](size_t cell) { g->cand[fill[cell]++] = (uint16_t)j; });
 }
 
+void build_residue_grid(int M, const float* xyz, const int32_t* res, int n_res, const CandidateGrid& g,
+                        ResidueGrid* out) {
+    out->n_res = n_res;
+    out->start.assign(n_res + 1, 0);
+    for (int j = 0; j < M; ++j) ++out->start[res[j] + 1];
+    for (int r = 0; r < n_res; ++r) out->start[r + 1] += out->start[r];
+    out->atoms.assign(M, 0);
+    {
+        std::vector<int32_t> fill(out->start.begin(), out->start.end() - 1);
+        for (int j = 0; j < M; ++j) out->atoms[fill[res[j]]++] = (uint16_t)j;   // ascending j per residue
+    }
+    const int nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
+    const double h = g.h;
+    const size_t ncell = (size_t)nx * ny * nz;
+    const double reach = kMdnCut + 0.5 * std::sqrt(3.0) * h + 1e-3 * h + 1e-4;
+    const double reach2 = reach * reach;
+    const int span = (int)std::ceil(reach / h) + 1;
+    // cells within reach of any atom of residue r, each once (mark = last residue seen)
+    std::vector<int32_t> mark(ncell, -1);
+    auto visit_residue = [&](int r, auto&& fn) {
+        for (int a = out->start[r]; a < out->start[r + 1]; ++a) {
+            const int j = out->atoms[a];
+            const double p[3] = {xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2]};
+            int c[3];
+            for (int d = 0; d < 3; ++d) c[d] = (int)std::floor((p[d] - g.lo[d]) / h);
+            for (int iz = std::max(0, c[2] - span); iz <= std::min(nz - 1, c[2] + span); ++iz) {
+                const double cz = g.lo[2] + (iz + 0.5) * h - p[2];
+                for (int iy = std::max(0, c[1] - span); iy <= std::min(ny - 1, c[1] + span); ++iy) {
+                    const double cy = g.lo[1] + (iy + 0.5) * h - p[1];
+                    const double r2yz = cy * cy + cz * cz;
+                    if (r2yz > reach2) continue;
+                    for (int ix = std::max(0, c[0] - span); ix <= std::min(nx - 1, c[0] + span); ++ix) {
+                        const double cx = g.lo[0] + (ix + 0.5) * h - p[0];
+                        if (cx * cx + r2yz > reach2) continue;
+                        const size_t cell = ((size_t)iz * ny + iy) * nx + ix;
+                        if (mark[cell] == r) continue;
+                        mark[cell] = r;
+                        fn(cell);
+                    }
+                }
+            }
+        }
+    };
+    std::vector<uint32_t> count(ncell, 0);
+    for (int r = 0; r < n_res; ++r) visit_residue(r, [&](size_t cell) { ++count[cell]; });
+    out->cell_start.assign(ncell + 1, 0);
+    size_t total = 0;
+    for (size_t c = 0; c < ncell; ++c) {
+        out->cell_start[c] = (uint32_t)total;
+        total += count[c];
+    }
+    out->cell_start[ncell] = (uint32_t)total;
+    out->list.assign(total, 0);
+    std::fill(mark.begin(), mark.end(), -1);
+    std::vector<uint32_t> fill(out->cell_start.begin(), out->cell_start.end() - 1);
+    for (int r = 0; r < n_res; ++r) visit_residue(r, [&](size_t cell) { out->list[fill[cell]++] = (uint16_t)r; });
+}
+
 }  // namespace trids

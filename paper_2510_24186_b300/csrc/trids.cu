@@ -419,15 +419,15 @@ __device__ __forceinline__ void vina_x2(uint32_t wd, const float4* __restrict__ 
 
 // Candidate-grid cell range (entries [beg, end) of pk.cand) of a point; empty outside
 // the grid, where no pocket atom lies within the cutoff.
-__device__ __forceinline__ void cell_range(const DevPocket& pk, float x, float y, float z, uint32_t& beg,
-                                           uint32_t& end) {
+__device__ __forceinline__ void cell_range(const DevPocket& pk, const uint32_t* __restrict__ starts, float x, float y,
+                                           float z, uint32_t& beg, uint32_t& end) {
     const float fx = (x - pk.gx) * pk.inv_h, fy = (y - pk.gy) * pk.inv_h, fz = (z - pk.gz) * pk.inv_h;
     beg = end = 0;
     if (fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)pk.nx && fy < (float)pk.ny && fz < (float)pk.nz) {
         const int cx = min((int)fx, pk.nx - 1), cy = min((int)fy, pk.ny - 1), cz = min((int)fz, pk.nz - 1);
         const size_t cell = ((size_t)cz * pk.ny + cy) * pk.nx + cx;
-        beg = __ldg(&pk.cell_start[cell]);
-        end = __ldg(&pk.cell_start[cell + 1]);
+        beg = __ldg(&starts[cell]);
+        end = __ldg(&starts[cell + 1]);
     }
 }
 
@@ -501,7 +501,7 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
         if (i < L) {
             const float4 x = W.xs[i];
             uint32_t beg, end;
-            cell_range(pk, x.x, x.y, x.z, beg, end);
+            cell_range(pk, pk.cell_start, x.x, x.y, x.z, beg, end);
             const int i0 = __ldg(&B.ipre[h.ipre_off + i]), i1 = __ldg(&B.ipre[h.ipre_off + i + 1]);
             const int cbk = (int)((end - beg) >> 3);
             W.cs[i] = beg;
@@ -611,10 +611,11 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                             }
                         } else if (in) {
                             const int tj = intra ? 0 : S.ptype[j];
+                            const bool mdn = TS == TRIDS_TERMS_TRIDS && !intra;   // atom-pair E_MDN
                             float fr, dRs;
                             float et[5];
                             const float e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), ri + a.w, (f_hb & fj) ? 2 : 0,
-                                                               intra ? nullptr : &P.gmm[ti][tj][0], P.gmm_k, !intra, w, fr,
+                                                               mdn ? &P.gmm[ti][tj][0] : nullptr, P.gmm_k, mdn, w, fr,
                                                                et, dRs);
                             eb += e;
                             ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
@@ -654,6 +655,60 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
     return e_lp;
 }
 
+// Residue-level E_MDN of the warp's pose (term set 2; Sec. 2, Eqs. P(d) and E_MDN): for
+// each ligand atom (one lane per atom) and each residue listed for its cell, the
+// minimum distance d over the residue's atoms; d < 5 A adds
+// -w0 sum_k pi_k exp(-(d - mu_k)^2 / (2 sigma_k^2)), with the force along the nearest
+// atom (strict < over ascending atom indices keeps the lowest index on ties).  Adds the
+// forces to W.gs (each lane owns its atoms' rows) and returns the lane's energy.
+template <bool PARAMS>
+__device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
+                              float w0, float ebar, ParamAcc& acc) {
+    constexpr float kCut2 = kMdnCut * kMdnCut;
+    const int K = B.mdn_k, R = B.mdn_res;
+    float e = 0.f;
+    for (int i = W.lane; i < h.n_atoms; i += 32) {
+        const float4 x = W.xs[i];
+        uint32_t beg, end;
+        cell_range(pk, pk.rcell_start, x.x, x.y, x.z, beg, end);
+        const float4* __restrict__ kern = B.mdn + (size_t)(h.atom_off + i) * R * K;
+        float gx = 0.f, gy = 0.f, gz = 0.f, ei = 0.f;
+        for (uint32_t q = beg; q < end; ++q) {
+            const int r = __ldg(&pk.rlist[q]);
+            const int a1 = __ldg(&pk.res_start[r + 1]);
+            float best = 3.0e38f, bx = 0.f, by = 0.f, bz = 0.f;
+            for (int a = __ldg(&pk.res_start[r]); a < a1; ++a) {
+                const float4 p = S.pocket[__ldg(&pk.res_atoms[a])];
+                const float dx = x.x - p.x, dy = x.y - p.y, dz = x.z - p.z;
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                if (r2 < best) { best = r2; bx = dx; by = dy; bz = dz; }
+            }
+            if (best < kCut2) {
+                const float rinv = rsqrtf(fmaxf(best, 1e-12f));
+                const float d = best * rinv;
+                float P = 0.f, dP = 0.f;
+                for (int k = 0; k < K; ++k) {
+                    const float4 g = __ldg(&kern[r * K + k]);   // (pi, mu, -1/(2 sigma^2), 1/sigma^2)
+                    const float z = d - g.y;
+                    const float ex = g.x * __expf(g.z * z * z);
+                    P += ex;
+                    dP = fmaf(-ex * z, g.w, dP);                // dP/dd
+                }
+                ei -= P;
+                const float f = -w0 * dP * rinv;                // (dE/dd) / d
+                gx = fmaf(f, bx, gx); gy = fmaf(f, by, gy); gz = fmaf(f, bz, gz);
+            }
+        }
+        float4 g = W.gs[i];
+        g.x += gx; g.y += gy; g.z += gz;
+        W.gs[i] = g;
+        e = fmaf(w0, ei, e);
+        if (PARAMS) acc.gw[0] = fmaf(ebar, ei, acc.gw[0]);
+    }
+    __syncwarp();
+    return e;
+}
+
 // E_total of the warp's pose (same value on every lane); forces in W.gs.
 template <int TS, bool PARAMS, bool COUNT>
 __device__ float score_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
@@ -662,7 +717,8 @@ __device__ float score_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
 #pragma unroll
     for (int t = 0; t < 5; ++t) w[t] = S.P->w[t];
     float ein2;
-    const float el = pairs_warp<TS, PARAMS, COUNT>(B, pk, S, h, W, w, ebar, acc, npairs, &ein2);
+    float el = pairs_warp<TS, PARAMS, COUNT>(B, pk, S, h, W, w, ebar, acc, npairs, &ein2);
+    if constexpr (TS == TRIDS_TERMS_TRIDS_RES) el += residue_warp<PARAMS>(B, pk, S, h, W, w[0], ebar, acc);
     const float e_lp = warp_sum(el);
     *e_inter = e_lp;
     return e_lp + 0.5f * warp_sum(ein2);
@@ -1251,9 +1307,16 @@ struct trids_pocket {
     uint32_t* d_cell = nullptr;
     uint16_t* d_cand = nullptr;
     DevParams* d_params = nullptr;
+    ResidueGrid rgrid;                   // residue-level E_MDN (term set 2)
+    int32_t* d_res_start = nullptr;
+    uint16_t* d_res_atoms = nullptr;
+    uint32_t* d_rcell = nullptr;
+    uint16_t* d_rlist = nullptr;
     DevPocket view() const {
         DevPocket v;
         v.atoms = d_atoms; v.ptype = d_ptype; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
+        v.n_res = rgrid.n_res; v.res_start = d_res_start; v.res_atoms = d_res_atoms; v.rcell_start = d_rcell;
+        v.rlist = d_rlist;
         v.nx = grid.dims[0]; v.ny = grid.dims[1]; v.nz = grid.dims[2];
         v.gx = grid.lo[0]; v.gy = grid.lo[1]; v.gz = grid.lo[2]; v.inv_h = 1.f / grid.h;
         v.n_boxes = n_boxes;
@@ -1297,12 +1360,15 @@ struct trids_batch {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
     GraphCache graph;
+    float4* d_mdn = nullptr;        // residue-level E_MDN kernels, packed rows
+    int mdn_res = 0, mdn_k = 0;
     DevBatch view() const {
         DevBatch v;
         v.n_lig = dims.n_lig; v.max_atoms = dims.max_atoms; v.max_tor = dims.max_tor;
         v.dof_stride = dims.dof_stride; v.n_fields = dims.state_fields;
         v.lig = d_lig; v.atom_y = d_atom_y; v.atom_orig = d_atom_orig; v.tor_idx = d_tor_idx;
         v.tor_u = d_tor_u; v.tor_p = d_tor_p; v.ipre = d_ipre; v.ient = d_ient;
+        v.mdn = d_mdn; v.mdn_res = mdn_res; v.mdn_k = mdn_k;
         return v;
     }
 };
@@ -1330,7 +1396,7 @@ int upload(T** dst, const std::vector<T>& src) {
 
 int check_params(const trids_params* p) {
     if (!p) return fail(TRIDS_EINVAL, "params is NULL");
-    if (p->term_set != TRIDS_TERMS_VINA5 && p->term_set != TRIDS_TERMS_TRIDS)
+    if (p->term_set != TRIDS_TERMS_VINA5 && p->term_set != TRIDS_TERMS_TRIDS && p->term_set != TRIDS_TERMS_TRIDS_RES)
         return fail(TRIDS_EINVAL, "term_set %d unknown", p->term_set);
     if (p->n_types < 1 || p->n_types > kNT) return fail(TRIDS_EINVAL, "n_types %d outside 1..%d", p->n_types, kNT);
     if (!(p->cutoff > 0.f) || !std::isfinite(p->cutoff) || p->cutoff > 64.f)
@@ -1502,6 +1568,58 @@ int check_device_ptr(const void* p, const char* name, bool nullable) {
     return TRIDS_OK;
 }
 
+// Inputs a term set needs beyond the pocket and the batch.
+int check_terms(const trids_pocket* pk, const trids_batch* b) {
+    if (pk->prm.term_set != TRIDS_TERMS_TRIDS_RES) return TRIDS_OK;
+    if (pk->rgrid.n_res < 1) return fail(TRIDS_EINVAL, "term set 2 needs trids_set_residues on the pocket");
+    if (!b->d_mdn) return fail(TRIDS_EINVAL, "term set 2 needs trids_set_mdn on the batch");
+    if (b->mdn_res != pk->rgrid.n_res)
+        return fail(TRIDS_EINVAL, "batch kernels are for %d residues, the pocket has %d", b->mdn_res, pk->rgrid.n_res);
+    return TRIDS_OK;
+}
+
+using PersistentKernel = void (*)(SampleArgs);
+using StepKernel = void (*)(SampleArgs, int, int);
+using ScoreKernel = void (*)(ScoreArgs);
+
+template <int TS>
+PersistentKernel persistent_for(bool cnt) { return cnt ? k_sample_persistent<TS, true> : k_sample_persistent<TS, false>; }
+template <int TS>
+StepKernel step_for(bool cnt) { return cnt ? k_sample_step<TS, true> : k_sample_step<TS, false>; }
+template <int TS>
+ScoreKernel score_for(bool params) { return params ? k_score<TS, true> : k_score<TS, false>; }
+
+PersistentKernel persistent_kernel(int ts, bool cnt) {
+    return ts == TRIDS_TERMS_TRIDS ? persistent_for<TRIDS_TERMS_TRIDS>(cnt)
+         : ts == TRIDS_TERMS_TRIDS_RES ? persistent_for<TRIDS_TERMS_TRIDS_RES>(cnt)
+                                       : persistent_for<TRIDS_TERMS_VINA5>(cnt);
+}
+StepKernel step_kernel(int ts, bool cnt) {
+    return ts == TRIDS_TERMS_TRIDS ? step_for<TRIDS_TERMS_TRIDS>(cnt)
+         : ts == TRIDS_TERMS_TRIDS_RES ? step_for<TRIDS_TERMS_TRIDS_RES>(cnt)
+                                       : step_for<TRIDS_TERMS_VINA5>(cnt);
+}
+ScoreKernel score_kernel(int ts, bool params) {
+    return ts == TRIDS_TERMS_TRIDS ? score_for<TRIDS_TERMS_TRIDS>(params)
+         : ts == TRIDS_TERMS_TRIDS_RES ? score_for<TRIDS_TERMS_TRIDS_RES>(params)
+                                       : score_for<TRIDS_TERMS_VINA5>(params);
+}
+
+// Residue-level E_MDN kernels: input rows (input atom order) -> packed rows as
+// (pi, mu, -1/(2 sigma^2), 1/sigma^2); flags entries with non-finite values or sigma <= 0.
+__global__ void k_mdn_pack(const float* __restrict__ in, const int* __restrict__ in_row, int64_t rows, int RK,
+                           float4* __restrict__ out, int* bad) {
+    const int64_t n = rows * RK;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = e / RK, rk = e - s * RK;
+        const float* g = in + ((int64_t)in_row[s] * RK + rk) * 3;
+        const float pi = g[0], mu = g[1], sg = g[2];
+        if (!isfinite(pi) || !isfinite(mu) || !isfinite(sg) || !(sg > 0.f)) atomicOr(bad, 1);
+        const float is2 = 1.f / (sg * sg);
+        out[e] = make_float4(pi, mu, -0.5f * is2, is2);
+    }
+}
+
 }  // namespace
 
 // =============================================================== C-ABI
@@ -1606,7 +1724,40 @@ int trids_free_pocket(trids_pocket* pk) {
     cudaFree(pk->d_cell);
     cudaFree(pk->d_cand);
     cudaFree(pk->d_params);
+    cudaFree(pk->d_res_start);
+    cudaFree(pk->d_res_atoms);
+    cudaFree(pk->d_rcell);
+    cudaFree(pk->d_rlist);
     delete pk;
+    return TRIDS_OK;
+}
+
+int trids_set_residues(trids_pocket* pk, int32_t n_res, const int32_t* residue) {
+    g_err.clear();
+    if (!pk || !residue) return fail(TRIDS_EINVAL, "NULL argument");
+    if (n_res < 1 || n_res > TRIDS_MAX_RESIDUES)
+        return fail(TRIDS_EINVAL, "n_res %d outside 1..%d", n_res, TRIDS_MAX_RESIDUES);
+    if (pk->cutoff_built < kMdnCut)
+        return fail(TRIDS_EINVAL, "the pocket grid was built for cutoff %.3f; residue terms need >= 5",
+                    pk->cutoff_built);
+    for (int j = 0; j < pk->M; ++j)
+        if (residue[j] < 0 || residue[j] >= n_res) return fail(TRIDS_EINVAL, "atom %d: residue out of range", j);
+    int rc = device_guard(pk->device);
+    if (rc) return rc;
+    ResidueGrid rg;
+    build_residue_grid(pk->M, pk->xyz.data(), residue, n_res, pk->grid, &rg);
+    int32_t* d_start = nullptr;
+    uint16_t *d_atoms = nullptr, *d_list = nullptr;
+    uint32_t* d_cell = nullptr;
+    if ((rc = upload(&d_start, rg.start)) || (rc = upload(&d_atoms, rg.atoms)) || (rc = upload(&d_cell, rg.cell_start)) ||
+        (rc = upload(&d_list, rg.list))) {
+        cudaFree(d_start); cudaFree(d_atoms); cudaFree(d_cell); cudaFree(d_list);
+        return rc;
+    }
+    CK(cudaDeviceSynchronize());   // no launch may still read the arrays being replaced
+    cudaFree(pk->d_res_start); cudaFree(pk->d_res_atoms); cudaFree(pk->d_rcell); cudaFree(pk->d_rlist);
+    pk->d_res_start = d_start; pk->d_res_atoms = d_atoms; pk->d_rcell = d_cell; pk->d_rlist = d_list;
+    pk->rgrid = std::move(rg);
     return TRIDS_OK;
 }
 
@@ -1764,8 +1915,55 @@ int trids_free_batch(trids_batch* b) {
     if (b->ev_b) cudaEventDestroy(b->ev_b);
     cudaFree(b->d_lig); cudaFree(b->d_atom_y); cudaFree(b->d_atom_orig); cudaFree(b->d_tor_idx);
     cudaFree(b->d_tor_u); cudaFree(b->d_tor_p); cudaFree(b->d_ipre); cudaFree(b->d_ient); cudaFree(b->d_items); cudaFree(b->d_lig_order);
-    cudaFree(b->d_counter); cudaFree(b->d_err); cudaFree(b->d_partials);
+    cudaFree(b->d_counter); cudaFree(b->d_err); cudaFree(b->d_partials); cudaFree(b->d_mdn);
     delete b;
+    return TRIDS_OK;
+}
+
+int trids_set_mdn(trids_batch* b, int32_t n_res, int32_t K, const float* mdn, void* stream) {
+    g_err.clear();
+    if (!b) return fail(TRIDS_EINVAL, "batch is NULL");
+    if (n_res < 1 || n_res > TRIDS_MAX_RESIDUES) return fail(TRIDS_EINVAL, "n_res %d outside 1..%d", n_res, TRIDS_MAX_RESIDUES);
+    if (K < 1 || K > TRIDS_MAX_MDN_K) return fail(TRIDS_EINVAL, "K %d outside 1..%d", K, TRIDS_MAX_MDN_K);
+    int rc = device_guard(b->device);
+    if (rc) return rc;
+    if ((rc = check_device_ptr(mdn, "mdn", false))) return rc;
+    std::vector<int> in_row;
+    for (int l = 0; l < b->dims.n_lig; ++l)
+        for (int i = 0; i < b->ligs[l].n_atoms; ++i) in_row.push_back(b->hdr[l].atom_off + b->ligs[l].perm[i]);
+    const int64_t rows = (int64_t)in_row.size(), RK = (int64_t)n_res * K;
+    float4* d_out = nullptr;
+    int* d_row = nullptr;
+    int* d_bad = nullptr;
+    const size_t bytes = (size_t)(rows * RK) * sizeof(float4);
+    if (cudaMalloc(&d_out, bytes) != cudaSuccess) return fail(TRIDS_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+    std::vector<int> zero(1, 0);
+    if ((rc = upload(&d_row, in_row)) || (rc = upload(&d_bad, zero))) {
+        cudaFree(d_out); cudaFree(d_row); cudaFree(d_bad);
+        return rc;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = rows * RK;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 32);
+    k_mdn_pack<<<blocks, 256, 0, st>>>(mdn, d_row, rows, (int)RK, d_out, d_bad);
+    cudaError_t le = cudaGetLastError();
+    int bad = 0;
+    cudaError_t ce = le == cudaSuccess ? cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st) : le;
+    cudaError_t se = cudaStreamSynchronize(st);
+    cudaFree(d_row);
+    cudaFree(d_bad);
+    if (ce != cudaSuccess || se != cudaSuccess) {
+        cudaFree(d_out);
+        return fail(TRIDS_ECUDA, "kernel conversion failed: %s", cudaGetErrorString(ce != cudaSuccess ? ce : se));
+    }
+    if (bad) {
+        cudaFree(d_out);
+        return fail(TRIDS_EINVAL, "mdn holds non-finite values or sigma <= 0");
+    }
+    cudaFree(b->d_mdn);
+    b->d_mdn = d_out;
+    b->mdn_res = n_res;
+    b->mdn_k = K;
     return TRIDS_OK;
 }
 
@@ -1811,7 +2009,8 @@ int trids_score_grad(const trids_pocket* pk, const trids_batch* bc, int32_t pose
     if ((rc = check_device_ptr(dof, "dof", false)) || (rc = check_device_ptr(energy, "energy", false)) ||
         (rc = check_device_ptr(e_inter, "e_inter", true)) || (rc = check_device_ptr(g_dof, "g_dof", true)) ||
         (rc = check_device_ptr(g_xyz, "g_xyz", true)) || (rc = check_device_ptr(e_bar, "e_bar", true)) ||
-        (rc = check_device_ptr(g_w, "g_w", true)) || (rc = check_device_ptr(g_radius, "g_radius", true)))
+        (rc = check_device_ptr(g_w, "g_w", true)) || (rc = check_device_ptr(g_radius, "g_radius", true)) ||
+        (rc = check_terms(pk, b)))
         return rc;
     if ((rc = ensure_items(b, poses))) return rc;
     const bool params = g_w || g_radius;
@@ -1839,19 +2038,11 @@ int trids_score_grad(const trids_pocket* pk, const trids_batch* bc, int32_t pose
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemsetAsync(A.counter, 0, sizeof(unsigned int), st));
     int grid = 0;
-    const bool trids_terms = pk->prm.term_set == TRIDS_TERMS_TRIDS;
-#define LAUNCH_SCORE(TS, PR)                                                                  \
-    do {                                                                                      \
-        auto kern = k_score<TS, PR>;                                                          \
-        if ((rc = grid_for(kern, warps, L.total, pk->device, b->n_items, &grid))) return rc;  \
-        kern<<<grid, 32 * warps, L.total, st>>>(A);                                           \
-    } while (0)
-    if (trids_terms) {
-        if (params) LAUNCH_SCORE(TRIDS_TERMS_TRIDS, true); else LAUNCH_SCORE(TRIDS_TERMS_TRIDS, false);
-    } else {
-        if (params) LAUNCH_SCORE(TRIDS_TERMS_VINA5, true); else LAUNCH_SCORE(TRIDS_TERMS_VINA5, false);
+    {
+        const ScoreKernel kern = score_kernel(pk->prm.term_set, params);
+        if ((rc = grid_for(kern, warps, L.total, pk->device, b->n_items, &grid))) return rc;
+        kern<<<grid, 32 * warps, L.total, st>>>(A);
     }
-#undef LAUNCH_SCORE
     CK(cudaGetLastError());
     if (params) {
         k_reduce_params<<<1, 32, 0, st>>>(b->d_partials, b->n_items, g_w, g_radius, b->n_types);
@@ -1883,7 +2074,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     if ((rc = check_device_ptr(dof, "dof", false)) || (rc = check_device_ptr(state, "state", false)) ||
         (rc = check_device_ptr(energy, "energy", false)) || (rc = check_device_ptr(c.trace, "trace", true)) ||
         (rc = check_device_ptr(c.trace_slot, "trace_slot", true)) ||
-        (rc = check_device_ptr(c.pair_count, "pair_count", true)))
+        (rc = check_device_ptr(c.pair_count, "pair_count", true)) || (rc = check_terms(pk, b)))
         return rc;
     if ((rc = ensure_items(b, c.poses))) return rc;
     Layout L;
@@ -1900,11 +2091,10 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     A.mbar_off = L.mbar_off;
     A.warp_off = L.warp_off; A.warp_bytes = L.warp_bytes;
     cudaStream_t st = (cudaStream_t)stream;
-    const bool tt = pk->prm.term_set == TRIDS_TERMS_TRIDS;
+    const int ts = pk->prm.term_set;
     const bool cnt = c.pair_count != nullptr;
     if (c.mode == TRIDS_MODE_PER_LIGAND) {
-        auto kern = tt ? (cnt ? k_sample_step<TRIDS_TERMS_TRIDS, true> : k_sample_step<TRIDS_TERMS_TRIDS, false>)
-                       : (cnt ? k_sample_step<TRIDS_TERMS_VINA5, true> : k_sample_step<TRIDS_TERMS_VINA5, false>);
+        const StepKernel kern = step_kernel(ts, cnt);
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
         const int blocks = (c.poses + warps - 1) / warps;
         for (int s = c.step_begin; s < c.step_end; ++s)
@@ -1912,8 +2102,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         CK(cudaGetLastError());
         return TRIDS_OK;
     }
-    auto kern = tt ? (cnt ? k_sample_persistent<TRIDS_TERMS_TRIDS, true> : k_sample_persistent<TRIDS_TERMS_TRIDS, false>)
-                   : (cnt ? k_sample_persistent<TRIDS_TERMS_VINA5, true> : k_sample_persistent<TRIDS_TERMS_VINA5, false>);
+    const PersistentKernel kern = persistent_kernel(ts, cnt);
     int grid = 0;
     if ((rc = grid_for(kern, warps, L.total, pk->device, A.n_items, &grid))) return rc;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -1930,7 +2119,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     // against the caller's by events.
     std::vector<unsigned char> key(sizeof(SampleArgs) + 4 * sizeof(int));
     std::memcpy(key.data(), &A, sizeof(SampleArgs));
-    const int extra[4] = {grid, warps, tt ? 1 : 0, cnt ? 1 : 0};
+    const int extra[4] = {grid, warps, ts, cnt ? 1 : 0};
     std::memcpy(key.data() + sizeof(SampleArgs), extra, sizeof extra);
     const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
     if (legacy && !b->side) {
@@ -2044,7 +2233,8 @@ int trids_score_grad_noalloc(const trids_pocket* pk, const trids_batch* b, int32
     if ((rc = check_device_ptr(dof, "dof", false)) || (rc = check_device_ptr(energy, "energy", false)) ||
         (rc = check_device_ptr(e_inter, "e_inter", true)) || (rc = check_device_ptr(g_dof, "g_dof", true)) ||
         (rc = check_device_ptr(g_xyz, "g_xyz", true)) || (rc = check_device_ptr(e_bar, "e_bar", true)) ||
-        (rc = check_device_ptr(g_w, "g_w", true)) || (rc = check_device_ptr(g_radius, "g_radius", true)))
+        (rc = check_device_ptr(g_w, "g_w", true)) || (rc = check_device_ptr(g_radius, "g_radius", true)) ||
+        (rc = check_terms(pk, b)))
         return rc;
     const bool params = g_w || g_radius;
     const int tiles = (poses + 31) / 32;
@@ -2079,19 +2269,11 @@ int trids_score_grad_noalloc(const trids_pocket* pk, const trids_batch* b, int32
                                                                   b->dims.n_lig, tiles);
     CK(cudaGetLastError());
     int grid = 0;
-    const bool trids_terms = pk->prm.term_set == TRIDS_TERMS_TRIDS;
-#define LAUNCH_SCORE_NA(TS, PR)                                                                \
-    do {                                                                                       \
-        auto kern = k_score<TS, PR>;                                                           \
-        if ((rc = grid_for(kern, warps, L.total, pk->device, (int)n_items, &grid))) return rc; \
-        kern<<<grid, 32 * warps, L.total, st>>>(A);                                            \
-    } while (0)
-    if (trids_terms) {
-        if (params) LAUNCH_SCORE_NA(TRIDS_TERMS_TRIDS, true); else LAUNCH_SCORE_NA(TRIDS_TERMS_TRIDS, false);
-    } else {
-        if (params) LAUNCH_SCORE_NA(TRIDS_TERMS_VINA5, true); else LAUNCH_SCORE_NA(TRIDS_TERMS_VINA5, false);
+    {
+        const ScoreKernel kern = score_kernel(pk->prm.term_set, params);
+        if ((rc = grid_for(kern, warps, L.total, pk->device, (int)n_items, &grid))) return rc;
+        kern<<<grid, 32 * warps, L.total, st>>>(A);
     }
-#undef LAUNCH_SCORE_NA
     CK(cudaGetLastError());
     if (params) {
         k_reduce_params<<<1, 32, 0, st>>>(A.partials, (int)n_items, g_w, g_radius, b->n_types);

@@ -54,6 +54,21 @@ struct CandidateGrid {
 };
 void build_grid(int M, const float* xyz, float cutoff, float h, CandidateGrid* g);
 
+// Residue lists of the residue-level E_MDN.  Atoms are grouped by residue (ascending
+// atom index inside a residue, so the first minimum met is the lowest index).  On the
+// candidate grid's cells, each cell lists (ascending) every residue with an atom within
+// kMdnCut + half the cell diagonal (+ a small margin) of the cell centre.
+constexpr float kMdnCut = 5.0f;   // Sec. 2: node pairs closer than d_cutoff = 5 A
+struct ResidueGrid {
+    int n_res = 0;
+    std::vector<int32_t> start;        // [n_res + 1] offsets into atoms
+    std::vector<uint16_t> atoms;       // pocket atom indices grouped by residue
+    std::vector<uint32_t> cell_start;  // [ncell + 1]
+    std::vector<uint16_t> list;        // residue indices
+};
+void build_residue_grid(int M, const float* xyz, const int32_t* res, int n_res, const CandidateGrid& g,
+                        ResidueGrid* out);
+
 // ---------------------------------------------------------------- device views
 // Staged into shared memory by every block: the Vina-form path copies the prefix up
 // to `gmm`, the TRIDS path the whole struct.
@@ -78,6 +93,12 @@ struct DevPocket {
     float gx, gy, gz, inv_h;
     int n_boxes;                   // pose p samples in box p mod n_boxes
     float box_lo[kMaxBoxes][3], box_hi[kMaxBoxes][3];
+    // residue-level E_MDN (term set 2)
+    int n_res;
+    const int32_t* res_start;      // [n_res + 1]
+    const uint16_t* res_atoms;     // atoms grouped by residue
+    const uint32_t* rcell_start;   // [ncell + 1], same cells as cell_start
+    const uint16_t* rlist;         // residues near each cell
 };
 
 struct LigHdr {
@@ -97,6 +118,10 @@ struct DevBatch {
     const int* ipre;               // per atom: first block of its intra partner list
     const uint16_t* ient;          // partner index | partner flags << 13; each intra pair appears
                                    // once from each side; padding = max_atoms (far sentinel)
+    // residue-level E_MDN kernels per packed atom row: [row][n_res][K] of
+    // (pi, mu, -1/(2 sigma^2), 1/sigma^2)
+    const float4* mdn;
+    int mdn_res, mdn_k;
 };
 
 // Sampler state fields per pose (SoA over poses inside each ligand):
