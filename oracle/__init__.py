@@ -70,7 +70,11 @@ class SampleCfg(C.Structure):
     _fields_ = [("steps", C.c_int32), ("mc_loops", C.c_int32), ("lr", C.c_double), ("b1", C.c_double),
                 ("b2", C.c_double), ("eps", C.c_double), ("beta", C.c_double), ("seed", C.c_uint64),
                 ("n_boxes", C.c_int32), ("box_lo", (C.c_double * 3) * MAX_BOXES),
-                ("box_hi", (C.c_double * 3) * MAX_BOXES)]
+                ("box_hi", (C.c_double * 3) * MAX_BOXES), ("optimizer", C.c_int32),
+                ("weight_decay", C.c_double), ("momentum", C.c_double), ("alpha", C.c_double)]
+
+
+OPTIMIZERS = {"adam": 0, "adamw": 1, "rmsprop": 2, "adagrad": 3, "sgd": 4}
 
 
 def build(force: bool = False) -> str:
@@ -112,8 +116,8 @@ def lib():
         L.or_metropolis_u.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
         L.or_metropolis_u.restype = C.c_double
         L.or_metropolis_accept.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
-        L.or_adam_step.argtypes = [P(SampleCfg), C.c_int, C.c_int, C.c_uint32, P(C.c_double), P(C.c_double),
-                                   P(C.c_double), P(C.c_double)]
+        L.or_opt_step.argtypes = [P(SampleCfg), C.c_int, C.c_int, C.c_uint32, P(C.c_double), P(C.c_double),
+                                  P(C.c_double), P(C.c_double)]
         L.or_sample_pose.argtypes = [P(SampleCfg), P(Params), C.c_int, P(C.c_double), P(C.c_int32),
                                      P(Mdn), P(Ligand), C.c_uint32, C.c_uint32, P(C.c_double), P(C.c_int64)]
         L.or_sample_pose.restype = C.c_double
@@ -231,10 +235,14 @@ def philox(ctr, key):
 
 
 def sample_cfg(steps=30, mc_loops=8, lr=0.1, b1=0.9, b2=0.999, eps=1e-8, beta=0.069, seed=0,
-               box_lo=(-11.25,) * 3, box_hi=(11.25,) * 3):
-    """box_lo / box_hi: one box (3 values) or several ([n][3]); pose p uses box p mod n."""
+               box_lo=(-11.25,) * 3, box_hi=(11.25,) * 3, optimizer="adam", weight_decay=0.01, momentum=0.0,
+               alpha=0.99):
+    """box_lo / box_hi: one box (3 values) or several ([n][3]); pose p uses box p mod n.
+    optimizer: adam, adamw, rmsprop, adagrad or sgd (eps is the caller's, as in torch)."""
     c = SampleCfg()
     c.steps, c.mc_loops, c.lr, c.b1, c.b2, c.eps, c.beta, c.seed = steps, mc_loops, lr, b1, b2, eps, beta, seed
+    c.optimizer = OPTIMIZERS[optimizer] if isinstance(optimizer, str) else int(optimizer)
+    c.weight_decay, c.momentum, c.alpha = weight_decay, momentum, alpha
     lo = np.atleast_2d(np.asarray(box_lo, dtype=np.float64))
     hi = np.atleast_2d(np.asarray(box_hi, dtype=np.float64))
     c.n_boxes = len(lo)
@@ -265,9 +273,12 @@ def metropolis_accept(e_new, e_old, beta, u):
     return bool(lib().or_metropolis_accept(e_new, e_old, beta, u))
 
 
-def adam_step(cfg, T, ta, g, m, v, dof, pose=0):
-    """In-place FP64 Adam update of (m, v, dof); g = (dE/dt, tau, dE/dtheta)."""
-    lib().or_adam_step(C.byref(cfg), T, ta, pose, _dp(g), _dp(m), _dp(v), _dp(dof))
+def opt_step(cfg, T, ta, g, m, v, dof, pose=0):
+    """In-place FP64 update of (m, v, dof) with cfg's optimizer; g = (dE/dt, tau, dE/dtheta)."""
+    lib().or_opt_step(C.byref(cfg), T, ta, pose, _dp(g), _dp(m), _dp(v), _dp(dof))
+
+
+adam_step = opt_step
 
 
 def loop_steps(S, Lmc, l):

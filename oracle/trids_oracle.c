@@ -21,7 +21,7 @@
  *   or_score               pinned: rigid-motion invariance, FD of energy, 1+1 atom closed form
  *   residue E_MDN          pinned: closed forms (tests/golden/terms.txt), a numpy brute force of
  *                          the residue minimum, FD, rigid-motion invariance, argmin tie rule
- *   or_adam_step           pinned: torch.optim.Adam
+ *   or_opt_step            pinned: torch.optim.Adam / AdamW / RMSprop / Adagrad / SGD
  *   or_init/perturb/metro  pinned: Philox pin + Shoemake uniformity + beta property
  *   or_sample              pinned through its parts; end-to-end trajectories are chaotic,
  *                          so the whole trajectory is "parity unpinned" beyond per-step checks
@@ -100,7 +100,15 @@ typedef struct {
     uint64_t seed;
     int32_t n_boxes;                          /* pose p uses box p mod n_boxes */
     double box_lo[OR_MAX_BOXES][3], box_hi[OR_MAX_BOXES][3];
+    int32_t optimizer;                        /* OR_OPT_*; the paper samples with Adam */
+    double weight_decay, momentum, alpha;     /* AdamW decay, SGD momentum, RMSprop smoothing */
 } or_sample_cfg;
+
+#define OR_OPT_ADAM 0
+#define OR_OPT_ADAMW 1
+#define OR_OPT_RMSPROP 2
+#define OR_OPT_ADAGRAD 3
+#define OR_OPT_SGD 4
 
 #define OR_STRADDLE 1e-4
 
@@ -830,19 +838,49 @@ int or_metropolis_accept(double e_new, double e_old, double beta, double u)
     return u < exp(-beta * (e_new - e_old));
 }
 
-/* Adam (bias-corrected, the PyTorch form) on g = (dE/dt, tau, dE/dtheta), step count ta >= 1;
- * t is clamped into the pose's box. */
-void or_adam_step(const or_sample_cfg* cfg, int T, int ta, uint32_t pose, const double* g, double* m, double* v,
-                  double* dof)
+/*
+ * One update of the variables from g = (dE/dt, tau, dE/dtheta), step count ta >= 1 inside
+ * the MC loop (the moments m, v restart with every loop).  Sec. 2 samples with Adam
+ * (lr 0.1); Table S5 compares other optimisers.  Each rule is PyTorch's definition:
+ *   Adam     m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ *            step = -(lr / (1 - b1^ta)) m / (sqrt(v) / sqrt(1 - b2^ta) + eps)
+ *   AdamW    the Adam step plus the decoupled decay -lr wd p
+ *   RMSprop  v = a v + (1-a) g^2; step = -lr g / (sqrt(v) + eps)
+ *   Adagrad  v = v + g^2;         step = -lr g / (sqrt(v) + eps)
+ *   SGD      m = mu m + g;        step = -lr m   (m = g on a loop's first step)
+ * Reading for the values p a decay acts on: t - (centre of the pose's box), 0 for the
+ * rotation vector (the tangent is re-centred at the current orientation every step),
+ * and theta.  t is then clamped into the pose's box and theta wrapped to [-pi, pi).
+ */
+void or_opt_step(const or_sample_cfg* cfg, int T, int ta, uint32_t pose, const double* g, double* m, double* v,
+                 double* dof)
 {
     const double *lo = box_lo(cfg, pose), *hi = box_hi(cfg, pose);
     double bc1 = 1.0 - pow(cfg->b1, ta), bc2 = 1.0 - pow(cfg->b2, ta);
     double step[6 + OR_TMAX];
     for (int j = 0; j < 6 + T; ++j) {
-        m[j] = cfg->b1 * m[j] + (1.0 - cfg->b1) * g[j];
-        v[j] = cfg->b2 * v[j] + (1.0 - cfg->b2) * g[j] * g[j];
-        double denom = sqrt(v[j]) / sqrt(bc2) + cfg->eps;
-        step[j] = -(cfg->lr / bc1) * m[j] / denom;
+        double pval = j < 3 ? dof[j] - 0.5 * (lo[j] + hi[j]) : (j < 6 ? 0.0 : dof[7 + (j - 6)]);
+        switch (cfg->optimizer) {
+        case OR_OPT_RMSPROP:
+            v[j] = cfg->alpha * v[j] + (1.0 - cfg->alpha) * g[j] * g[j];
+            step[j] = -cfg->lr * g[j] / (sqrt(v[j]) + cfg->eps);
+            break;
+        case OR_OPT_ADAGRAD:
+            v[j] = v[j] + g[j] * g[j];
+            step[j] = -cfg->lr * g[j] / (sqrt(v[j]) + cfg->eps);
+            break;
+        case OR_OPT_SGD:
+            m[j] = cfg->momentum * m[j] + g[j];
+            step[j] = -cfg->lr * m[j];
+            break;
+        default: {  /* Adam, AdamW */
+            m[j] = cfg->b1 * m[j] + (1.0 - cfg->b1) * g[j];
+            v[j] = cfg->b2 * v[j] + (1.0 - cfg->b2) * g[j] * g[j];
+            double denom = sqrt(v[j]) / sqrt(bc2) + cfg->eps;
+            step[j] = -(cfg->lr / bc1) * m[j] / denom;
+            if (cfg->optimizer == OR_OPT_ADAMW) step[j] -= cfg->lr * cfg->weight_decay * pval;
+        }
+        }
     }
     for (int d = 0; d < 3; ++d) {
         double t = dof[d] + step[d];
@@ -892,7 +930,7 @@ double or_sample_pose(const or_sample_cfg* cfg, const or_params* p, int M, const
             if (j < n - 1) {
                 for (int d = 0; d < 3; ++d) { g[d] = ev->g_dof[d]; g[3 + d] = ev->tau[d]; }
                 for (int k = 0; k < T; ++k) g[6 + k] = ev->g_dof[7 + k];
-                or_adam_step(cfg, T, j + 1, pose, g, m, v, dof);
+                or_opt_step(cfg, T, j + 1, pose, g, m, v, dof);
             } else {
                 e_cur = ev->e_total;
             }
