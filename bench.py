@@ -36,7 +36,32 @@ METRIC = "poses×steps/sec (score + DOF gradient) at 1 B300 vs plain per-ligand 
 UNIT = "pose-steps/s"
 F_PAIR_VINA = 53            # FP32 FLOPs per in-cutoff pair of the Vina-form terms (FMA = 2)
 MUFU_PAIR_VINA = 3          # rsqrt + 2 exp per in-cutoff pair
+F_PAIR_TRIDS = 36           # FP32 FLOPs per in-cutoff atom pair of the TRIDS terms at the E_long cost
 FP32_LANES_PER_SM = 128
+TERMS = {"vina5": 0, "trids": 1, "trids_res": 2}
+GMM_K = 4                   # Gaussian kernels per type pair (term set 1) / per atom-residue pair (2)
+
+
+def score_setup(terms, w):
+    """Scoring parameters of a term set; residues of the pocket for term set 2."""
+    from paper_2510_24186_b300 import api
+    ts = TERMS[terms]
+    if ts == 0:
+        return api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, w.cutoff), None
+    rng = np.random.default_rng(w.seed + 71)
+    gmm = None
+    if ts == 1:
+        gmm = np.empty((synth.N_TYPES, synth.N_TYPES, GMM_K, 3))
+        gmm[..., 0] = rng.uniform(0.05, 1.0, gmm.shape[:3]) / GMM_K
+        gmm[..., 1] = rng.uniform(2.0, 5.5, gmm.shape[:3])
+        gmm[..., 2] = rng.uniform(0.3, 1.5, gmm.shape[:3])
+    sp = api.ScoreParams(ts, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.TRIDS_WEIGHTS, 10.0, gmm=gmm)
+    res = synth.gen_residues(rng, w.pocket.xyz) if ts == 2 else None
+    return sp, res
+
+
+def mdn_kernels(w, n_atoms_total, res):
+    return synth.gen_mdn(np.random.default_rng(w.seed + 72), n_atoms_total, int(res.max()) + 1, GMM_K)
 
 
 def kernel_source_hash():
@@ -113,12 +138,19 @@ def cpu_threads():
         return os.cpu_count() or 1
 
 
-def oracle_sample_rate(w, budget_s=12.0, max_ligs=64, n_threads=None, first=0):
+def oracle_sample_rate(w, budget_s=12.0, max_ligs=64, n_threads=None, first=0, terms="vina5"):
     """FP64 oracle sampler on whole ligands of the workload until ~budget_s of wall time."""
     import oracle
     n_threads = n_threads or cpu_threads()
-    op = oracle.make_params(0, [float(np.float32(x)) for x in synth.TYPE_RADIUS], synth.TYPE_FLAGS,
-                            [float(np.float32(x)) for x in synth.VINA_WEIGHTS], w.cutoff)
+    f32 = lambda v: [float(np.float32(x)) for x in v]
+    sp, res = score_setup(terms, w)
+    op = oracle.make_params(sp.term_set, f32(sp.radius), sp.flags, f32(sp.w), float(np.float32(sp.cutoff)),
+                            gmm=None if sp.gmm is None else np.asarray(sp.gmm, dtype=np.float32).astype(np.float64))
+    mdn = offs = None
+    if res is not None:
+        n_atoms = np.array([len(l.type) for l in w.ligands])
+        offs = np.concatenate([[0], np.cumsum(n_atoms)])
+        mdn = mdn_kernels(w, int(n_atoms.sum()), res)
     lo = w.box_center - w.box_size / 2
     hi = w.box_center + w.box_size / 2
     cfg = oracle.sample_cfg(steps=w.steps, mc_loops=w.mc_loops, seed=7, box_lo=lo, box_hi=hi)
@@ -129,7 +161,8 @@ def oracle_sample_rate(w, budget_s=12.0, max_ligs=64, n_threads=None, first=0):
     for l in range(first, min(len(w.ligands), first + max_ligs)):
         lg = w.ligands[l]
         st, ol = oracle.pack(lg.xyz.astype(np.float32).astype(np.float64), lg.type, lg.bonds, lg.rotatable)
-        oracle.sample_ligand(cfg, op, pxyz, ptype, ol, l, w.poses, n_threads)
+        md = None if mdn is None else oracle.mdn(res, mdn[offs[l]:offs[l + 1]].astype(np.float64))
+        oracle.sample_ligand(cfg, op, pxyz, ptype, ol, l, w.poses, n_threads, md=md)
         n += 1
         units += w.poses * w.steps
         if time.perf_counter() - t0 >= budget_s:
@@ -171,6 +204,9 @@ def main():
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--n-lig", type=int, default=0, help="first N ligands only (small profiling case)")
     ap.add_argument("--cell", type=float, default=0.0, help="candidate-grid cell edge in A (0 = library default)")
+    ap.add_argument("--terms", default="vina5", choices=sorted(TERMS),
+                    help="term set: vina5 (default), trids (atom-pair E_MDN), trids_res (residue-level E_MDN)")
+    ap.add_argument("--optimizer", default="adam", choices=["adam", "adamw", "rmsprop", "adagrad", "sgd"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -187,15 +223,23 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     w = synth.workload(2, n_lig=args.n_lig or None)
-    sp = api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, w.cutoff)
+    sp, res = score_setup(args.terms, w)
     arrays = synth.concat_ligands(w.ligands)
     tuned = None
+    if sp.term_set != 0:
+        args.cell, args.warps = args.cell or 0.5, args.warps or 16
     if not args.cell and not args.warps:
         from paper_2510_24186_b300 import autotune
         tuned = autotune.autotune(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, arrays, w.poses)
         args.cell, args.warps = tuned.cell, tuned.warps_per_block
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, cell=args.cell)
+    mdn = None
+    if res is not None:
+        pk.set_residues(res)
+        mdn = torch.from_numpy(mdn_kernels(w, int(arrays[0].sum()), res)).cuda()
     b = api.Batch(pk, *arrays)
+    if mdn is not None:
+        b.set_mdn(mdn)
     P, S, Lm = w.poses, w.steps, w.mc_loops
     n_lig = b.n_lig
     units = n_lig * P * S
@@ -208,7 +252,7 @@ def main():
 
     def one_step(seed, **kw):
         o = api.sample(pk, b, P, S, mc_loops=Lm, seed=seed, lig_base=lig_base, dof=dof, state=state, energy=energy,
-                       warps_per_block=args.warps, stream=stream, **kw)
+                       warps_per_block=args.warps, stream=stream, optimizer=args.optimizer, **kw)
         return o
 
     with torch.cuda.stream(stream):
@@ -273,9 +317,11 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         bb = api.Batch(pk, *arrays)
+        if mdn is not None:
+            bb.set_mdn(mdn, stream=stream)
         with torch.cuda.stream(stream):
             o = api.sample(pk, bb, P, S, mc_loops=Lm, seed=5000 + k, lig_base=lig_base, dof=dof, state=state,
-                           energy=energy, stream=stream, warps_per_block=args.warps)
+                           energy=energy, stream=stream, warps_per_block=args.warps, optimizer=args.optimizer)
             idx, etop = api.topk(bb, energy, dof, w.topk, 1.0, stream=stream)
             idx_h, e_h = idx.cpu(), etop.cpu()
         stream.synchronize()
@@ -295,12 +341,13 @@ def main():
     mhz, mhz_src = sm_max_mhz()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     peak = n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-    flops = [p * F_PAIR_VINA for p in pairs]
+    f_pair = F_PAIR_VINA if sp.term_set == 0 else F_PAIR_TRIDS
+    flops = [p * f_pair for p in pairs]
     achieved = sum(flops) / (sum(t_sample) / 1000.0) / 1e12
     clocks = clk.summary()
     traffic = None
     prof = os.path.join(ROOT, "profiles", "sample_persistent_vina5_batched_screening.json")
-    if os.path.exists(prof):
+    if os.path.exists(prof) and sp.term_set == 0 and args.optimizer == "adam":
         pj = json.load(open(prof))
         if pj.get("source_hash") == kernel_source_hash():
             traffic = pj.get("dram_bytes_per_launch")
@@ -309,7 +356,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "n_lig": n_lig, "poses": P, "steps": S, "mc_loops": Lm,
-                   "pocket_atoms": len(w.pocket.type), "top_k": w.topk, "term_set": "vina5",
+                   "pocket_atoms": len(w.pocket.type), "top_k": w.topk, "term_set": args.terms,
+                   "optimizer": args.optimizer,
                    "graph": True, "l2": "flushed between steps (256 MB write)", "cell": args.cell or 0.5,
                    "warps_per_block": args.warps or 8,
                    "autotuned": None if tuned is None else {"table_ms": tuned.table, "probe": "256 ligands x 6 "
@@ -317,8 +365,10 @@ def main():
                    "parallelism": f"ligand shards x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "note": f"in-cutoff pairs x {F_PAIR_VINA} FP32 FLOP / persistent-sampler time; peak = "
-                             f"{n_sm} SM x 128 lanes x 2 x {mhz:.0f} MHz ({mhz_src})"},
+                     "note": f"in-cutoff atom pairs x {f_pair} FP32 FLOP / persistent-sampler time; peak = "
+                             f"{n_sm} SM x 128 lanes x 2 x {mhz:.0f} MHz ({mhz_src})"
+                             + ("" if sp.term_set == 0 else "; extra Gaussian kernels and the residue phase are "
+                                "not counted (a lower bound)")},
         "kernel": {"sample_ms": statistics.mean(t_sample), "topk_ms": statistics.mean(
             [t_step[k] - t_sample[k] for k in range(args.steps)]), "pairs_per_step": statistics.mean(pairs),
             "pairs_per_pose_step": statistics.mean(pairs) / units, "count_run_bit_identical": identical,
@@ -335,7 +385,7 @@ def main():
     if clocks["sm_mhz"]:
         line["roofline"]["frac_at_load_clock"] = achieved / (peak * clocks["sm_mhz"] / mhz)
     if not args.no_cpu and world == 1:
-        r, cores, n, dt = oracle_sample_rate(w, budget_s=12.0)
+        r, cores, n, dt = oracle_sample_rate(w, budget_s=12.0, terms=args.terms)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"first {n} ligands x {P} poses x {S} evaluations, FP64 all-pairs "
                                           f"oracle, {dt:.1f} s"}

@@ -55,6 +55,23 @@ extern "C" {
 #define TRIDS_MAX_MDN_K 16    /* Gaussian kernels per (ligand atom, residue) pair */
 #define TRIDS_MAX_RESIDUES 8191
 
+/* Update rules of the refinement steps (Sec. 2 samples with Adam; Table S5 compares
+ * the others).  Each is PyTorch's definition on g = (dE/dt, torque, dE/dtheta):
+ *   ADAM     m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ *            step = -(lr / (1 - b1^k)) m / (sqrt(v) / sqrt(1 - b2^k) + eps), k = step in loop
+ *   ADAMW    the Adam step - lr weight_decay p
+ *   RMSPROP  v = alpha v + (1-alpha) g^2; step = -lr g / (sqrt(v) + eps)
+ *   ADAGRAD  v = v + g^2; step = -lr g / (sqrt(v) + eps)
+ *   SGD      m = momentum m + g; step = -lr m
+ * m and v restart at every Monte-Carlo loop.  The values p a decay acts on: t minus the
+ * centre of the pose's box, 0 for the rotation vector (the tangent is re-centred at the
+ * current orientation every step), theta. */
+#define TRIDS_OPT_ADAM 0
+#define TRIDS_OPT_ADAMW 1
+#define TRIDS_OPT_RMSPROP 2
+#define TRIDS_OPT_ADAGRAD 3
+#define TRIDS_OPT_SGD 4
+
 #define TRIDS_MODE_PERSISTENT 0 /* one persistent fused launch (optionally a CUDA graph) */
 #define TRIDS_MODE_PER_LIGAND 1 /* plain form: one launch per (ligand, step) */
 
@@ -126,7 +143,7 @@ typedef struct trids_sample_cfg {
     int32_t step_begin;      /* run evaluations [step_begin, step_end) of the schedule; */
     int32_t step_end;        /*   step_begin > 0 resumes from dof + state */
     int32_t mc_loops;        /* Monte-Carlo loops (8 in the paper) */
-    float lr, beta1, beta2, eps; /* Adam (lr 0.1 in the paper; torch defaults otherwise) */
+    float lr, beta1, beta2, eps; /* update rule (Adam: lr 0.1 in the paper; torch defaults otherwise) */
     float beta;              /* Metropolis beta (0.069 in the paper) */
     uint64_t seed;           /* Philox4x32-10 key */
     int32_t lig_base;        /* random-stream id of ligand 0 of this batch */
@@ -137,6 +154,10 @@ typedef struct trids_sample_cfg {
     const int32_t* trace_slot; /* device [n_lig*poses]: trace slot of each pose or -1 */
     int32_t n_trace;         /* number of trace slots */
     unsigned long long* pair_count; /* nullable device counter: adds in-cutoff pairs evaluated */
+    int32_t optimizer;       /* TRIDS_OPT_*; 0 = Adam, the paper's */
+    float weight_decay;      /* AdamW decay (torch default 0.01), >= 0 */
+    float momentum;          /* SGD momentum in [0, 1) (torch default 0) */
+    float alpha;             /* RMSprop smoothing in [0, 1) (torch default 0.99) */
 } trids_sample_cfg;
 
 /* Message of the calling thread's last failure ("" if none). */

@@ -37,7 +37,11 @@ class SampleCfg(C.Structure):
                 ("eps", C.c_float), ("beta", C.c_float), ("seed", C.c_uint64), ("lig_base", C.c_int32),
                 ("mode", C.c_int32), ("warps_per_block", C.c_int32), ("use_graph", C.c_int32),
                 ("trace", C.c_void_p), ("trace_slot", C.c_void_p), ("n_trace", C.c_int32),
-                ("pair_count", C.c_void_p)]
+                ("pair_count", C.c_void_p), ("optimizer", C.c_int32), ("weight_decay", C.c_float),
+                ("momentum", C.c_float), ("alpha", C.c_float)]
+
+
+OPTIMIZERS = {"adam": 0, "adamw": 1, "rmsprop": 2, "adagrad": 3, "sgd": 4}
 
 
 class TridsError(RuntimeError):

@@ -233,8 +233,11 @@ def sample(pocket: Pocket, batch: Batch, poses: int, steps: int, mc_loops: int =
            trace_poses: Optional[Sequence[int]] = None, count_pairs: bool = False,
            dof: Optional[torch.Tensor] = None, state: Optional[torch.Tensor] = None,
            energy: Optional[torch.Tensor] = None, step_begin: int = 0, step_end: Optional[int] = None,
-           stream=None) -> dict:
-    """Monte-Carlo + Adam sampling of every ligand's poses (trids_sample)."""
+           stream=None, optimizer: str = "adam", weight_decay: float = 0.01, momentum: float = 0.0,
+           alpha: float = 0.99) -> dict:
+    """Monte-Carlo + gradient sampling of every ligand's poses (trids_sample).  optimizer:
+    adam (the paper's), adamw, rmsprop, adagrad or sgd; eps is passed as given (torch's
+    defaults are 1e-8, except Adagrad's 1e-10)."""
     _require_cuda()
     dev = torch.device("cuda", torch.cuda.current_device())
     n_lig, D = batch.n_lig, batch.dof_stride
@@ -252,6 +255,8 @@ def sample(pocket: Pocket, batch: Batch, poses: int, steps: int, mc_loops: int =
     cfg.lr, cfg.beta1, cfg.beta2, cfg.eps, cfg.beta = lr, beta1, beta2, eps, beta
     cfg.seed, cfg.lig_base, cfg.mode = seed, lig_base, mode
     cfg.warps_per_block, cfg.use_graph = warps_per_block, int(use_graph)
+    cfg.optimizer = _lib.OPTIMIZERS[optimizer]
+    cfg.weight_decay, cfg.momentum, cfg.alpha = weight_decay, momentum, alpha
     out = {"dof": dof, "state": state, "energy": energy}
     if trace_poses is not None:
         tp = np.asarray(trace_poses, dtype=np.int64)

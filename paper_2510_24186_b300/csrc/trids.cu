@@ -777,6 +777,8 @@ struct SampleArgs {
     DevBatch B;
     int P, S, step_begin, step_end, Lmc;
     float lr, b1, b2, eps, beta;
+    int opt;
+    float wd, momentum, alpha;
     uint64_t seed;
     int lig_base;
     float* dof;
@@ -886,11 +888,28 @@ __device__ void store_pose(const SampleArgs& A, const LigHdr& h, int lane, int l
     }
 }
 
-__device__ __forceinline__ float adam_delta(const SampleArgs& A, float g, float& m, float& v, float bc1, float sbc2) {
-    m = fmaf(A.b1, m, (1.f - A.b1) * g);
-    v = fmaf(A.b2, v, (1.f - A.b2) * g * g);
-    const float denom = sqrtf(v) / sbc2 + A.eps;
-    return -(A.lr / bc1) * m / denom;
+// Step of one variable under the configured update rule (trids.h, TRIDS_OPT_*); pv is
+// the value a weight decay acts on.  bc1 = 1 - b1^k and sbc2 = sqrt(1 - b2^k) for Adam(W).
+__device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float pv, float& m, float& v, float bc1,
+                                           float sbc2) {
+    switch (A.opt) {
+    case TRIDS_OPT_RMSPROP:
+        v = fmaf(A.alpha, v, (1.f - A.alpha) * g * g);
+        return -A.lr * g / (sqrtf(v) + A.eps);
+    case TRIDS_OPT_ADAGRAD:
+        v = fmaf(g, g, v);
+        return -A.lr * g / (sqrtf(v) + A.eps);
+    case TRIDS_OPT_SGD:
+        m = fmaf(A.momentum, m, g);
+        return -A.lr * m;
+    default: {
+        m = fmaf(A.b1, m, (1.f - A.b1) * g);
+        v = fmaf(A.b2, v, (1.f - A.b2) * g * g);
+        const float denom = sqrtf(v) / sbc2 + A.eps;
+        const float d = -(A.lr / bc1) * m / denom;
+        return A.opt == TRIDS_OPT_ADAMW ? fmaf(-A.lr * A.wd, pv, d) : d;
+    }
+    }
 }
 
 // One evaluation (and its update or acceptance test) of the warp's pose; s is the
@@ -965,13 +984,14 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
         const int ta = sc.j + 1;
         const float bc1 = 1.f - powf(A.b1, (float)ta);
         const float sbc2 = sqrtf(1.f - powf(A.b2, (float)ta));
-        if (own) st.th = wrap_pi(st.th + adam_delta(A, gth, st.mth, st.vth, bc1, sbc2));
+        if (own) st.th = wrap_pi(st.th + opt_delta(A, gth, st.th, st.mth, st.vth, bc1, sbc2));
         for (int d = 0; d < 3; ++d) {
-            const float dlt = adam_delta(A, gt[d], st.m[d], st.v[d], bc1, sbc2);
-            st.t[d] = fminf(fmaxf(st.t[d] + dlt, A.pk.box_lo[bx][d]), A.pk.box_hi[bx][d]);
+            const float lo = A.pk.box_lo[bx][d], hi = A.pk.box_hi[bx][d];
+            const float dlt = opt_delta(A, gt[d], st.t[d] - 0.5f * (lo + hi), st.m[d], st.v[d], bc1, sbc2);
+            st.t[d] = fminf(fmaxf(st.t[d] + dlt, lo), hi);
         }
         float dw[3];
-        for (int d = 0; d < 3; ++d) dw[d] = adam_delta(A, tau[d], st.m[3 + d], st.v[3 + d], bc1, sbc2);
+        for (int d = 0; d < 3; ++d) dw[d] = opt_delta(A, tau[d], 0.f, st.m[3 + d], st.v[3 + d], bc1, sbc2);
         const float phi = sqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
         if (phi > 0.f) {
             float sh, ch;
@@ -2065,6 +2085,11 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     if (!(c.lr > 0.f) || !std::isfinite(c.lr) || !(c.beta1 >= 0.f && c.beta1 < 1.f) ||
         !(c.beta2 >= 0.f && c.beta2 < 1.f) || !(c.eps > 0.f) || !std::isfinite(c.beta))
         return fail(TRIDS_EINVAL, "invalid Adam or Metropolis parameters");
+    if (c.optimizer < TRIDS_OPT_ADAM || c.optimizer > TRIDS_OPT_SGD)
+        return fail(TRIDS_EINVAL, "unknown optimizer %d", c.optimizer);
+    if (!(c.weight_decay >= 0.f) || !std::isfinite(c.weight_decay) || !(c.momentum >= 0.f && c.momentum < 1.f) ||
+        !(c.alpha >= 0.f && c.alpha < 1.f))
+        return fail(TRIDS_EINVAL, "need weight_decay >= 0, 0 <= momentum < 1, 0 <= alpha < 1");
     if (c.mode != TRIDS_MODE_PERSISTENT && c.mode != TRIDS_MODE_PER_LIGAND)
         return fail(TRIDS_EINVAL, "unknown mode %d", c.mode);
     if (c.trace && (!c.trace_slot || c.n_trace < 1))
@@ -2084,7 +2109,8 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     std::memset(&A, 0, sizeof A);  // the bytes form the graph-cache key
     A.pk = pk->view(); A.B = b->view(); A.P = c.poses; A.S = c.steps; A.step_begin = c.step_begin;
     A.step_end = c.step_end; A.Lmc = c.mc_loops; A.lr = c.lr; A.b1 = c.beta1; A.b2 = c.beta2; A.eps = c.eps;
-    A.beta = c.beta; A.seed = c.seed; A.lig_base = c.lig_base; A.dof = dof; A.state = state; A.energy = energy;
+    A.beta = c.beta; A.opt = c.optimizer; A.wd = c.weight_decay; A.momentum = c.momentum; A.alpha = c.alpha;
+    A.seed = c.seed; A.lig_base = c.lig_base; A.dof = dof; A.state = state; A.energy = energy;
     A.trace = c.trace; A.trace_slot = c.trace_slot; A.n_trace = c.n_trace; A.pair_count = c.pair_count;
     A.lig_order = b->d_lig_order; A.n_items = b->dims.n_lig * c.poses; A.counter = b->d_counter; A.err = b->d_err;
     A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.ptype_off = L.ptype_off;

@@ -1,0 +1,75 @@
+"""GPU parity of the update rules other than Adam (Table S5): per-evaluation trace of
+config 1 against the oracle, which applies its FP64 rule to the GPU's state and gradient."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_24186_b300 import synth
+
+from parity_util import check_trace, oracle_ligands, oracle_params, pocket_arrays, score_params
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+f32 = lambda x: float(np.float32(x))
+
+RULES = [
+    ("adamw", dict(lr=0.1, weight_decay=0.01)),
+    ("rmsprop", dict(lr=0.02, alpha=0.99)),
+    ("adagrad", dict(lr=0.1, eps=1e-10)),
+    ("sgd", dict(lr=0.005, momentum=0.9)),
+    ("sgd", dict(lr=0.002, momentum=0.0)),
+]
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2510_24186_b300 import api as a
+    return a
+
+
+@pytest.mark.parametrize("name,hp", RULES, ids=[f"{n}-{i}" for i, (n, _) in enumerate(RULES)])
+def test_update_rule_per_step_parity(api, name, hp):
+    w = synth.workload(1)
+    sp = score_params(0, cutoff=w.cutoff)
+    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
+    b = api.Batch.from_ligands(pk, w.ligands)
+    seed, P, S = 1301, 32, w.steps
+    kw = dict(lr=0.1, eps=1e-8, weight_decay=0.01, momentum=0.0, alpha=0.99)
+    kw.update(hp)
+    out = api.sample(pk, b, P, S, mc_loops=w.mc_loops, seed=seed, trace_poses=list(range(P)), optimizer=name, **kw)
+    assert api.sync(b, P, out["state"], timeout_ms=60000) == 0
+    lo = (w.box_center - w.box_size / 2).astype(np.float32).astype(np.float64)
+    hi = (w.box_center + w.box_size / 2).astype(np.float32).astype(np.float64)
+    cfg = oracle.sample_cfg(steps=S, mc_loops=w.mc_loops, lr=f32(kw["lr"]), b1=f32(0.9), b2=f32(0.999),
+                            eps=f32(kw["eps"]), beta=f32(0.069), seed=seed, box_lo=lo, box_hi=hi, optimizer=name,
+                            weight_decay=f32(kw["weight_decay"]), momentum=f32(kw["momentum"]),
+                            alpha=f32(kw["alpha"]))
+    st = check_trace(out["trace"].cpu().numpy(), list(range(P)), P, oracle_ligands(w.ligands),
+                     *pocket_arrays(w.pocket), oracle_params(sp), cfg, S, w.mc_loops, seed,
+                     out["dof"].cpu().numpy(), out["energy"].cpu().numpy())
+    print(f"\n[{name} {hp}] n={st.n} max|dE|={st.e_abs:.3e} max grad rel={st.g_rel:.3e} "
+          f"max state err={st.s_err:.3e} near ties={st.near_ties}")
+    assert not st.fails, "\n".join(st.fails)
+    # the persistent launch and the plain per-ligand form agree bit for bit
+    o2 = api.sample(pk, b, P, S, mc_loops=w.mc_loops, seed=seed, mode=1, optimizer=name, **kw)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(o2["dof"].cpu().numpy(), out["dof"].cpu().numpy())
+
+
+def test_unknown_update_rule_is_rejected(api):
+    from paper_2510_24186_b300 import _lib
+    w = synth.workload(1)
+    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, score_params(0))
+    b = api.Batch.from_ligands(pk, w.ligands)
+    _lib.OPTIMIZERS["bogus"] = 9
+    try:
+        with pytest.raises(_lib.TridsError, match="optimizer"):
+            api.sample(pk, b, 4, 3, optimizer="bogus")
+    finally:
+        del _lib.OPTIMIZERS["bogus"]
+    with pytest.raises(_lib.TridsError, match="momentum"):
+        api.sample(pk, b, 4, 3, optimizer="sgd", momentum=1.0)
