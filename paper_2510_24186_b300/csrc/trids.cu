@@ -890,32 +890,37 @@ __device__ void store_pose(const SampleArgs& A, const LigHdr& h, int lane, int l
 
 // Step of one variable under the configured update rule (trids.h, TRIDS_OPT_*); pv is
 // the value a weight decay acts on.  bc1 = 1 - b1^k and sbc2 = sqrt(1 - b2^k) for Adam(W).
+// GOPT = false compiles Adam alone: the other rules' code would otherwise enlarge the
+// sampler kernel, which costs the pair loop instruction-cache hits.
+template <bool GOPT>
 __device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float pv, float& m, float& v, float bc1,
                                            float sbc2) {
-    switch (A.opt) {
-    case TRIDS_OPT_RMSPROP:
-        v = fmaf(A.alpha, v, (1.f - A.alpha) * g * g);
-        return -A.lr * g / (sqrtf(v) + A.eps);
-    case TRIDS_OPT_ADAGRAD:
-        v = fmaf(g, g, v);
-        return -A.lr * g / (sqrtf(v) + A.eps);
-    case TRIDS_OPT_SGD:
-        m = fmaf(A.momentum, m, g);
-        return -A.lr * m;
-    default: {
-        m = fmaf(A.b1, m, (1.f - A.b1) * g);
-        v = fmaf(A.b2, v, (1.f - A.b2) * g * g);
-        const float denom = sqrtf(v) / sbc2 + A.eps;
-        const float d = -(A.lr / bc1) * m / denom;
-        return A.opt == TRIDS_OPT_ADAMW ? fmaf(-A.lr * A.wd, pv, d) : d;
+    if (GOPT) {
+        switch (A.opt) {
+        case TRIDS_OPT_RMSPROP:
+            v = fmaf(A.alpha, v, (1.f - A.alpha) * g * g);
+            return -A.lr * g / (sqrtf(v) + A.eps);
+        case TRIDS_OPT_ADAGRAD:
+            v = fmaf(g, g, v);
+            return -A.lr * g / (sqrtf(v) + A.eps);
+        case TRIDS_OPT_SGD:
+            m = fmaf(A.momentum, m, g);
+            return -A.lr * m;
+        default:
+            break;
+        }
     }
-    }
+    m = fmaf(A.b1, m, (1.f - A.b1) * g);
+    v = fmaf(A.b2, v, (1.f - A.b2) * g * g);
+    const float denom = sqrtf(v) / sbc2 + A.eps;
+    const float d = -(A.lr / bc1) * m / denom;
+    return GOPT && A.opt == TRIDS_OPT_ADAMW ? fmaf(-A.lr * A.wd, pv, d) : d;
 }
 
 // One evaluation (and its update or acceptance test) of the warp's pose; s is the
 // global evaluation index of the schedule.  Every branch below is uniform across the
 // warp except the per-torsion lanes.
-template <int TS, bool COUNT>
+template <int TS, bool COUNT, bool GOPT>
 __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h, const PW& W, int l, int p, int s,
                             PoseState& st, uint32_t& npairs) {
     if (st.status & 1) return;  // frozen after a non-finite energy
@@ -984,14 +989,14 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
         const int ta = sc.j + 1;
         const float bc1 = 1.f - powf(A.b1, (float)ta);
         const float sbc2 = sqrtf(1.f - powf(A.b2, (float)ta));
-        if (own) st.th = wrap_pi(st.th + opt_delta(A, gth, st.th, st.mth, st.vth, bc1, sbc2));
+        if (own) st.th = wrap_pi(st.th + opt_delta<GOPT>(A, gth, st.th, st.mth, st.vth, bc1, sbc2));
         for (int d = 0; d < 3; ++d) {
             const float lo = A.pk.box_lo[bx][d], hi = A.pk.box_hi[bx][d];
-            const float dlt = opt_delta(A, gt[d], st.t[d] - 0.5f * (lo + hi), st.m[d], st.v[d], bc1, sbc2);
+            const float dlt = opt_delta<GOPT>(A, gt[d], st.t[d] - 0.5f * (lo + hi), st.m[d], st.v[d], bc1, sbc2);
             st.t[d] = fminf(fmaxf(st.t[d] + dlt, lo), hi);
         }
         float dw[3];
-        for (int d = 0; d < 3; ++d) dw[d] = opt_delta(A, tau[d], 0.f, st.m[3 + d], st.v[3 + d], bc1, sbc2);
+        for (int d = 0; d < 3; ++d) dw[d] = opt_delta<GOPT>(A, tau[d], 0.f, st.m[3 + d], st.v[3 + d], bc1, sbc2);
         const float phi = sqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
         if (phi > 0.f) {
             float sh, ch;
@@ -1026,7 +1031,7 @@ __device__ __forceinline__ void flush_count(unsigned long long* cnt, uint32_t n)
 
 // Persistent fused sampler: each warp pops poses from a global counter (ligands in
 // decreasing-cost order) and runs every evaluation of the pose with its state on chip.
-template <int TS, bool COUNT>
+template <int TS, bool COUNT, bool GOPT>
 __global__ void __launch_bounds__(512, 1) k_sample_persistent(SampleArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
@@ -1045,7 +1050,7 @@ __global__ void __launch_bounds__(512, 1) k_sample_persistent(SampleArgs A) {
         PoseState st;
         if (A.step_begin == 0) init_pose(A, h, W.lane, l, p, st);
         else load_pose(A, h, W.lane, l, p, st);
-        for (int s = A.step_begin; s < A.step_end; ++s) sample_step<TS, COUNT>(A, S, h, W, l, p, s, st, npairs);
+        for (int s = A.step_begin; s < A.step_end; ++s) sample_step<TS, COUNT, GOPT>(A, S, h, W, l, p, s, st, npairs);
         store_pose(A, h, W.lane, l, p, st);
         __syncwarp();
     }
@@ -1054,7 +1059,7 @@ __global__ void __launch_bounds__(512, 1) k_sample_persistent(SampleArgs A) {
 
 // Plain form: one launch per (ligand, evaluation), one warp per pose, the state in
 // global memory between launches; the same device code as the persistent sampler.
-template <int TS, bool COUNT>
+template <int TS, bool COUNT, bool GOPT>
 __global__ void __launch_bounds__(512, 1) k_sample_step(SampleArgs A, int l, int s) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
@@ -1068,7 +1073,7 @@ __global__ void __launch_bounds__(512, 1) k_sample_step(SampleArgs A, int l, int
     PoseState st;
     if (s == 0) init_pose(A, h, W.lane, l, p, st);
     else load_pose(A, h, W.lane, l, p, st);
-    sample_step<TS, COUNT>(A, S, h, W, l, p, s, st, npairs);
+    sample_step<TS, COUNT, GOPT>(A, S, h, W, l, p, s, st, npairs);
     store_pose(A, h, W.lane, l, p, st);
     if (COUNT) flush_count(A.pair_count, npairs);
 }
@@ -1603,21 +1608,27 @@ using StepKernel = void (*)(SampleArgs, int, int);
 using ScoreKernel = void (*)(ScoreArgs);
 
 template <int TS>
-PersistentKernel persistent_for(bool cnt) { return cnt ? k_sample_persistent<TS, true> : k_sample_persistent<TS, false>; }
+PersistentKernel persistent_for(bool cnt, bool gopt) {
+    return gopt ? (cnt ? k_sample_persistent<TS, true, true> : k_sample_persistent<TS, false, true>)
+                : (cnt ? k_sample_persistent<TS, true, false> : k_sample_persistent<TS, false, false>);
+}
 template <int TS>
-StepKernel step_for(bool cnt) { return cnt ? k_sample_step<TS, true> : k_sample_step<TS, false>; }
+StepKernel step_for(bool cnt, bool gopt) {
+    return gopt ? (cnt ? k_sample_step<TS, true, true> : k_sample_step<TS, false, true>)
+                : (cnt ? k_sample_step<TS, true, false> : k_sample_step<TS, false, false>);
+}
 template <int TS>
 ScoreKernel score_for(bool params) { return params ? k_score<TS, true> : k_score<TS, false>; }
 
-PersistentKernel persistent_kernel(int ts, bool cnt) {
-    return ts == TRIDS_TERMS_TRIDS ? persistent_for<TRIDS_TERMS_TRIDS>(cnt)
-         : ts == TRIDS_TERMS_TRIDS_RES ? persistent_for<TRIDS_TERMS_TRIDS_RES>(cnt)
-                                       : persistent_for<TRIDS_TERMS_VINA5>(cnt);
+PersistentKernel persistent_kernel(int ts, bool cnt, bool gopt) {
+    return ts == TRIDS_TERMS_TRIDS ? persistent_for<TRIDS_TERMS_TRIDS>(cnt, gopt)
+         : ts == TRIDS_TERMS_TRIDS_RES ? persistent_for<TRIDS_TERMS_TRIDS_RES>(cnt, gopt)
+                                       : persistent_for<TRIDS_TERMS_VINA5>(cnt, gopt);
 }
-StepKernel step_kernel(int ts, bool cnt) {
-    return ts == TRIDS_TERMS_TRIDS ? step_for<TRIDS_TERMS_TRIDS>(cnt)
-         : ts == TRIDS_TERMS_TRIDS_RES ? step_for<TRIDS_TERMS_TRIDS_RES>(cnt)
-                                       : step_for<TRIDS_TERMS_VINA5>(cnt);
+StepKernel step_kernel(int ts, bool cnt, bool gopt) {
+    return ts == TRIDS_TERMS_TRIDS ? step_for<TRIDS_TERMS_TRIDS>(cnt, gopt)
+         : ts == TRIDS_TERMS_TRIDS_RES ? step_for<TRIDS_TERMS_TRIDS_RES>(cnt, gopt)
+                                       : step_for<TRIDS_TERMS_VINA5>(cnt, gopt);
 }
 ScoreKernel score_kernel(int ts, bool params) {
     return ts == TRIDS_TERMS_TRIDS ? score_for<TRIDS_TERMS_TRIDS>(params)
@@ -2119,8 +2130,9 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     cudaStream_t st = (cudaStream_t)stream;
     const int ts = pk->prm.term_set;
     const bool cnt = c.pair_count != nullptr;
+    const bool gopt = c.optimizer != TRIDS_OPT_ADAM;
     if (c.mode == TRIDS_MODE_PER_LIGAND) {
-        const StepKernel kern = step_kernel(ts, cnt);
+        const StepKernel kern = step_kernel(ts, cnt, gopt);
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
         const int blocks = (c.poses + warps - 1) / warps;
         for (int s = c.step_begin; s < c.step_end; ++s)
@@ -2128,7 +2140,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         CK(cudaGetLastError());
         return TRIDS_OK;
     }
-    const PersistentKernel kern = persistent_kernel(ts, cnt);
+    const PersistentKernel kern = persistent_kernel(ts, cnt, gopt);
     int grid = 0;
     if ((rc = grid_for(kern, warps, L.total, pk->device, A.n_items, &grid))) return rc;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -2145,7 +2157,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     // against the caller's by events.
     std::vector<unsigned char> key(sizeof(SampleArgs) + 4 * sizeof(int));
     std::memcpy(key.data(), &A, sizeof(SampleArgs));
-    const int extra[4] = {grid, warps, ts, cnt ? 1 : 0};
+    const int extra[4] = {grid, warps, ts, (cnt ? 1 : 0) | (gopt ? 2 : 0)};
     std::memcpy(key.data() + sizeof(SampleArgs), extra, sizeof extra);
     const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
     if (legacy && !b->side) {
