@@ -42,7 +42,7 @@ class Eval(C.Structure):
                 ("g_w", C.c_double * 5), ("g_R", C.c_double * NT),
                 ("n_inter", C.c_int64), ("n_intra", C.c_int64), ("n_straddle", C.c_int32),
                 ("e_slack", C.c_double), ("g_slack", C.c_double), ("e_mag", C.c_double),
-                ("g_mag", C.c_double * (7 + TMAX)), ("n_res_pairs", C.c_int64)]
+                ("g_mag", C.c_double * (7 + TMAX)), ("n_res_pairs", C.c_int64), ("n_map_atoms", C.c_int64)]
 
 
 class Mdn(C.Structure):
@@ -60,6 +60,20 @@ def mdn(res, prm):
     m.res = res.ctypes.data_as(C.POINTER(C.c_int32))
     m.prm = prm.ctypes.data_as(C.POINTER(C.c_double))
     m._keep = (res, prm)
+    return m
+
+
+class Maps(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("h", C.c_double), ("n", C.c_int32 * 3)]
+
+
+def maps(lo, h, n):
+    """Grid-map domain: points lo + h * (a, b, c), 0 <= (a, b, c) < n."""
+    m = Maps()
+    for d in range(3):
+        m.lo[d] = float(lo[d])
+        m.n[d] = int(n[d])
+    m.h = float(h)
     return m
 
 
@@ -110,6 +124,8 @@ def lib():
                                P(C.c_double), P(Eval)]
         L.or_score_mdn.argtypes = [P(Params), C.c_int, P(C.c_double), P(C.c_int32), P(Mdn), P(Ligand),
                                    P(C.c_double), P(Eval)]
+        L.or_score_full.argtypes = [P(Params), C.c_int, P(C.c_double), P(C.c_int32), P(Mdn), P(Maps), P(Ligand),
+                                    P(C.c_double), P(Eval)]
         L.or_loop_steps.argtypes = [C.c_int, C.c_int, C.c_int]
         L.or_init_pose.argtypes = [P(SampleCfg), C.c_int, C.c_uint32, C.c_uint32, P(C.c_double)]
         L.or_perturb.argtypes = [P(SampleCfg), C.c_int, C.c_uint32, C.c_uint32, C.c_uint32, P(C.c_double)]
@@ -119,10 +135,11 @@ def lib():
         L.or_opt_step.argtypes = [P(SampleCfg), C.c_int, C.c_int, C.c_uint32, P(C.c_double), P(C.c_double),
                                   P(C.c_double), P(C.c_double)]
         L.or_sample_pose.argtypes = [P(SampleCfg), P(Params), C.c_int, P(C.c_double), P(C.c_int32),
-                                     P(Mdn), P(Ligand), C.c_uint32, C.c_uint32, P(C.c_double), P(C.c_int64)]
+                                     P(Mdn), P(Maps), P(Ligand), C.c_uint32, C.c_uint32, P(C.c_double),
+                                     P(C.c_int64)]
         L.or_sample_pose.restype = C.c_double
         L.or_sample_ligand.argtypes = [P(SampleCfg), P(Params), C.c_int, P(C.c_double), P(C.c_int32),
-                                       P(Mdn), P(Ligand), C.c_uint32, C.c_int, C.c_int, P(C.c_double),
+                                       P(Mdn), P(Maps), P(Ligand), C.c_uint32, C.c_int, C.c_int, P(C.c_double),
                                        P(C.c_double), C.c_int]
         L.or_sample_ligand.restype = C.c_int64
         L.or_topk.argtypes = [C.c_int, P(C.c_double), P(C.c_double), C.c_int, C.c_int, C.c_double,
@@ -193,14 +210,15 @@ def fk(lg, dof, brute=False):
     return x
 
 
-def score(p, pxyz, ptype, lg, dof, md=None):
-    """Returns (status, Eval) in FP64.  md: residue-level E_MDN inputs (term_set 2), see mdn()."""
+def score(p, pxyz, ptype, lg, dof, md=None, mp=None):
+    """Returns (status, Eval) in FP64.  md: residue-level E_MDN inputs (term_set 2), see mdn();
+    mp: grid-map domain (the map form of the ligand-pocket atom-pair terms), see maps()."""
     ev = Eval()
     pxyz = np.ascontiguousarray(pxyz, dtype=np.float64)
     ptype = np.ascontiguousarray(ptype, dtype=np.int32)
     dof = np.ascontiguousarray(dof, dtype=np.float64)
-    st = lib().or_score_mdn(C.byref(p), len(ptype), _dp(pxyz), _ip(ptype), None if md is None else C.byref(md),
-                            C.byref(lg), _dp(dof), C.byref(ev))
+    st = lib().or_score_full(C.byref(p), len(ptype), _dp(pxyz), _ip(ptype), None if md is None else C.byref(md),
+                             None if mp is None else C.byref(mp), C.byref(lg), _dp(dof), C.byref(ev))
     return st, ev
 
 
@@ -285,7 +303,7 @@ def loop_steps(S, Lmc, l):
     return lib().or_loop_steps(S, Lmc, l)
 
 
-def sample_ligand(cfg, p, pxyz, ptype, lg, lig, P, n_threads=1, md=None):
+def sample_ligand(cfg, p, pxyz, ptype, lg, lig, P, n_threads=1, md=None, mp=None):
     """FP64 trajectories of P poses; returns (dof [P, 7+T], energy [P], in-cutoff pair count)."""
     T = lg.n_tor
     dof = np.zeros((P, 7 + T))
@@ -293,7 +311,8 @@ def sample_ligand(cfg, p, pxyz, ptype, lg, lig, P, n_threads=1, md=None):
     pxyz = np.ascontiguousarray(pxyz, dtype=np.float64)
     ptype = np.ascontiguousarray(ptype, dtype=np.int32)
     pairs = lib().or_sample_ligand(C.byref(cfg), C.byref(p), len(ptype), _dp(pxyz), _ip(ptype),
-                                   None if md is None else C.byref(md), C.byref(lg), lig, P, 7 + T, _dp(dof), _dp(e), n_threads)
+                                   None if md is None else C.byref(md), None if mp is None else C.byref(mp),
+                                   C.byref(lg), lig, P, 7 + T, _dp(dof), _dp(e), n_threads)
     return dof, e, pairs
 
 

@@ -19,6 +19,9 @@
  *   or_pair                pinned: hand-computed closed forms (tests/golden/terms.txt)
  *   or_fk                  pinned: or_fk_brute (independent algorithm) + invariants
  *   or_score               pinned: rigid-motion invariance, FD of energy, 1+1 atom closed form
+ *   grid maps              pinned: trilinear reproduces linear fields exactly, grid-point values
+ *                          equal the direct one-atom energy, FD of the interpolated energy,
+ *                          convergence to the direct sum as the spacing shrinks
  *   residue E_MDN          pinned: closed forms (tests/golden/terms.txt), a numpy brute force of
  *                          the residue minimum, FD, rigid-motion invariance, argmin tie rule
  *   or_opt_step            pinned: torch.optim.Adam / AdamW / RMSprop / Adagrad / SGD
@@ -82,6 +85,7 @@ typedef struct {
     double e_mag;
     double g_mag[7 + OR_TMAX];
     int64_t n_res_pairs;         /* (ligand atom, residue) pairs inside the E_MDN cutoff */
+    int64_t n_map_atoms;         /* ligand atoms scored from the grid maps */
 } or_eval;
 
 /* Residue-level E_MDN inputs (term_set 2).  res[j] = residue of pocket atom j;
@@ -92,6 +96,14 @@ typedef struct {
     const int32_t* res;
     const double* prm;
 } or_mdn;
+
+/* Grid-map domain (the map form of the ligand-pocket terms): points lo + h (a, b, c),
+ * 0 <= a < n[0], 0 <= b < n[1], 0 <= c < n[2]. */
+typedef struct {
+    double lo[3];
+    double h;
+    int32_t n[3];
+} or_maps;
 
 #define OR_MAX_BOXES 8
 typedef struct {
@@ -686,15 +698,176 @@ static void residue_mdn(const or_params* p, int M, const double* pxyz, const or_
     free(arg);
 }
 
+/*
+ * Grid-map form of the ligand-pocket atom-pair terms (the DSDP / Vina practice; the paper
+ * itself scores pairs directly, Sec. 4 item 4).  The map of ligand type ti holds at each
+ * grid point g the ligand-pocket energy an atom of that type would have there: the sum of
+ * the weighted pair terms over pocket atoms with |g - p_j| < cutoff.  An atom whose cell
+ * (all 8 corners) lies inside the domain takes the trilinear interpolation of its cell's
+ * corner values and the analytic derivative of that interpolation; any other atom keeps
+ * the direct sum.  The residue-level E_MDN (term set 2) is never mapped.
+ * Slack (counted as straddles): corner pairs on the cutoff or a value jump; an atom within
+ * OR_STRADDLE (A) of a cell face (the gradient differs between the two cells) or of the
+ * domain boundary (interpolated vs direct).
+ */
+static double map_value(const or_params* p, int M, const double* pxyz, const int32_t* ptype, int ti,
+                        const double g[3], double* jump)
+{
+    double E = 0;
+    for (int j = 0; j < M; ++j) {
+        double dx = g[0] - pxyz[3 * j], dy = g[1] - pxyz[3 * j + 1], dz = g[2] - pxyz[3 * j + 2];
+        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        double e[5], dr[5], dR[5], vj, gj;
+        if (!(r < p->cutoff) && !(fabs(r - p->cutoff) < OR_STRADDLE)) continue;
+        or_pair(p, ti, ptype[j], r, 1, e, dr, dR, &vj, &gj);
+        double es = 0;
+        for (int t = 0; t < 5; ++t) es += p->w[t] * e[t];
+        *jump += vj;
+        if (r < p->cutoff) E += es;
+    }
+    return E;
+}
+
+/* Interpolated energy and gradient in cell c (corner values V[a][b][k] at c + (a, b, k)). */
+static void trilinear(const double V[2][2][2], const double f[3], double h, double* E, double g[3])
+{
+    double e = 0, gx = 0, gy = 0, gz = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int k = 0; k < 2; ++k) {
+                double wx = a ? f[0] : 1 - f[0], wy = b ? f[1] : 1 - f[1], wz = k ? f[2] : 1 - f[2];
+                double sx = a ? 1 : -1, sy = b ? 1 : -1, sz = k ? 1 : -1;
+                e += wx * wy * wz * V[a][b][k];
+                gx += sx * wy * wz * V[a][b][k];
+                gy += wx * sy * wz * V[a][b][k];
+                gz += wx * wy * sz * V[a][b][k];
+            }
+    *E = e;
+    g[0] = gx / h; g[1] = gy / h; g[2] = gz / h;
+}
+
+static void cell_corners(const or_params* p, int M, const double* pxyz, const int32_t* ptype, const or_maps* mp,
+                         int ti, const int c[3], double V[2][2][2], double* jump)
+{
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int k = 0; k < 2; ++k) {
+                double g[3] = {mp->lo[0] + mp->h * (c[0] + a), mp->lo[1] + mp->h * (c[1] + b),
+                               mp->lo[2] + mp->h * (c[2] + k)};
+                V[a][b][k] = map_value(p, M, pxyz, ptype, ti, g, jump);
+            }
+}
+
+static int cell_inside(const or_maps* mp, const int c[3])
+{
+    for (int d = 0; d < 3; ++d)
+        if (c[d] < 0 || c[d] + 1 >= mp->n[d]) return 0;
+    return 1;
+}
+
+/* Map energy of atom i (returns 0 when the atom is left to the direct sum). */
+static int map_atom(const or_params* p, int M, const double* pxyz, const int32_t* ptype, const or_maps* mp,
+                    int ti, const double* x, double* E, double g[3], or_eval* ev, double* mag)
+{
+    double u[3], f[3];
+    int c[3];
+    for (int d = 0; d < 3; ++d) {
+        u[d] = (x[d] - mp->lo[d]) / mp->h;
+        c[d] = (int)floor(u[d]);
+        f[d] = u[d] - c[d];
+    }
+    const double tol = OR_STRADDLE / mp->h;
+    int inside = cell_inside(mp, c);
+    int near_edge = 0;
+    for (int d = 0; d < 3; ++d)
+        if (fabs(u[d]) < tol || fabs(u[d] - (mp->n[d] - 1)) < tol) near_edge = 1;
+    if (!inside && !near_edge) return 0;
+    double V[2][2][2], jump = 0, Em = 0, gm3[3] = {0, 0, 0};
+    if (inside) {
+        cell_corners(p, M, pxyz, ptype, mp, ti, c, V, &jump);
+        trilinear(V, f, mp->h, &Em, gm3);
+        double sv = 0;
+        for (int a = 0; a < 8; ++a) sv += fabs(((double*)V)[a]);
+        *mag += 2.0 * sv / mp->h;
+        ev->e_mag += sv;
+        ev->e_slack += jump;
+        if (jump > 0) ev->n_straddle++;
+        /* near a face: the neighbouring cell's gradient */
+        for (int d = 0; d < 3; ++d) {
+            int side = f[d] < tol ? -1 : (f[d] > 1 - tol ? 1 : 0);
+            if (!side) continue;
+            int c2[3] = {c[0], c[1], c[2]};
+            c2[d] += side;
+            if (!cell_inside(mp, c2)) continue;   /* the domain-boundary case below covers it */
+            double V2[2][2][2], j2 = 0, E2, g2[3], f2[3] = {f[0], f[1], f[2]};
+            f2[d] = side < 0 ? f[d] + 1.0 : f[d] - 1.0;
+            cell_corners(p, M, pxyz, ptype, mp, ti, c2, V2, &j2);
+            trilinear(V2, f2, mp->h, &E2, g2);
+            ev->n_straddle++;
+            ev->g_slack += sqrt((g2[0] - gm3[0]) * (g2[0] - gm3[0]) + (g2[1] - gm3[1]) * (g2[1] - gm3[1]) +
+                                (g2[2] - gm3[2]) * (g2[2] - gm3[2]));
+        }
+    }
+    if (near_edge) {
+        /* the GPU may take the other side of the domain boundary: interpolated vs direct */
+        double Ed = 0, gd[3] = {0, 0, 0};
+        for (int j = 0; j < M; ++j) {
+            double dx = x[0] - pxyz[3 * j], dy = x[1] - pxyz[3 * j + 1], dz = x[2] - pxyz[3 * j + 2];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            if (!(r < p->cutoff)) continue;
+            double e[5], dr[5], dR[5], vj, gj;
+            or_pair(p, ti, ptype[j], r, 1, e, dr, dR, &vj, &gj);
+            double es = 0, de = 0;
+            for (int t = 0; t < 5; ++t) { es += p->w[t] * e[t]; de += p->w[t] * dr[t]; }
+            Ed += es;
+            if (r > 0) { gd[0] += de * dx / r; gd[1] += de * dy / r; gd[2] += de * dz / r; }
+        }
+        ev->n_straddle++;
+        if (inside) {
+            ev->e_slack += fabs(Em - Ed);
+            ev->g_slack += sqrt((gd[0] - gm3[0]) * (gd[0] - gm3[0]) + (gd[1] - gm3[1]) * (gd[1] - gm3[1]) +
+                                (gd[2] - gm3[2]) * (gd[2] - gm3[2]));
+        } else {
+            /* outside by a hair: the direct sum stays, with the map's cell as the alternative */
+            int c2[3];
+            double f2[3];
+            for (int d = 0; d < 3; ++d) {
+                c2[d] = c[d] < 0 ? 0 : (c[d] > mp->n[d] - 2 ? mp->n[d] - 2 : c[d]);
+                f2[d] = u[d] - c2[d];
+            }
+            double V2[2][2][2], j2 = 0, E2, g2[3];
+            cell_corners(p, M, pxyz, ptype, mp, ti, c2, V2, &j2);
+            trilinear(V2, f2, mp->h, &E2, g2);
+            ev->e_slack += fabs(E2 - Ed);
+            ev->g_slack += sqrt((gd[0] - g2[0]) * (gd[0] - g2[0]) + (gd[1] - g2[1]) * (gd[1] - g2[1]) +
+                                (gd[2] - g2[2]) * (gd[2] - g2[2]));
+            return 0;
+        }
+    }
+    *E = Em;
+    g[0] = gm3[0]; g[1] = gm3[1]; g[2] = gm3[2];
+    return 1;
+}
+
+int or_score_full(const or_params* p, int M, const double* pxyz, const int32_t* ptype, const or_mdn* md,
+                  const or_maps* mp, const or_ligand* lg, const double* dof, or_eval* ev);
+
 int or_score(const or_params* p, int M, const double* pxyz, const int32_t* ptype,
              const or_ligand* lg, const double* dof, or_eval* ev)
 {
-    return or_score_mdn(p, M, pxyz, ptype, NULL, lg, dof, ev);
+    return or_score_full(p, M, pxyz, ptype, NULL, NULL, lg, dof, ev);
 }
 
-/* term_set 2 needs md (residues and per-pair kernels); other term sets ignore it. */
 int or_score_mdn(const or_params* p, int M, const double* pxyz, const int32_t* ptype, const or_mdn* md,
                  const or_ligand* lg, const double* dof, or_eval* ev)
+{
+    return or_score_full(p, M, pxyz, ptype, md, NULL, lg, dof, ev);
+}
+
+/* term_set 2 needs md (residues and per-pair kernels); other term sets ignore it.
+ * mp (nullable): grid-map form of the ligand-pocket atom-pair terms. */
+int or_score_full(const or_params* p, int M, const double* pxyz, const int32_t* ptype, const or_mdn* md,
+                  const or_maps* mp, const or_ligand* lg, const double* dof, or_eval* ev)
 {
     memset(ev, 0, sizeof *ev);
     if (p->term_set == 2 && !md) return OR_EINVAL;
@@ -705,10 +878,18 @@ int or_score_mdn(const or_params* p, int M, const double* pxyz, const int32_t* p
     or_fk(lg, dof, &ev->x[0][0]);
     double gm[OR_LMAX];
     for (int i = 0; i < L; ++i) gm[i] = 0;
-    for (int i = 0; i < L; ++i)
+    for (int i = 0; i < L; ++i) {
+        double Em, gmap[3];
+        if (mp && map_atom(p, M, pxyz, ptype, mp, lg->type[i], ev->x[i], &Em, gmap, ev, &gm[i])) {
+            ev->e_inter += Em;
+            for (int d = 0; d < 3; ++d) ev->g_x[i][d] += gmap[d];
+            ev->n_map_atoms++;
+            continue;
+        }
         for (int j = 0; j < M; ++j)
             accumulate_pair(p, lg->type[i], ptype[j], ev->x[i], pxyz + 3 * j, 1,
                             &ev->e_inter, ev->g_x[i], NULL, ev, 1.0, &gm[i], NULL);
+    }
     for (int k = 0; k < lg->n_pairs; ++k) {
         int i = lg->pi[k], j = lg->pj[k];
         accumulate_pair(p, lg->type[i], lg->type[j], ev->x[i], ev->x[j], 0,
@@ -905,8 +1086,8 @@ void or_opt_step(const or_sample_cfg* cfg, int T, int ta, uint32_t pose, const d
  * non-finite energy froze the pose).  pairs (nullable) accumulates the number
  * of pairs inside the cutoff over all evaluations. */
 double or_sample_pose(const or_sample_cfg* cfg, const or_params* p, int M, const double* pxyz,
-                      const int32_t* ptype, const or_mdn* md, const or_ligand* lg, uint32_t lig, uint32_t pose,
-                      double* dof, int64_t* pairs)
+                      const int32_t* ptype, const or_mdn* md, const or_maps* mp, const or_ligand* lg, uint32_t lig,
+                      uint32_t pose, double* dof, int64_t* pairs)
 {
     int T = lg->n_tor;
     double m[6 + OR_TMAX], v[6 + OR_TMAX], saved[7 + OR_TMAX], g[6 + OR_TMAX];
@@ -924,7 +1105,7 @@ double or_sample_pose(const or_sample_cfg* cfg, const or_params* p, int M, const
         memset(m, 0, sizeof m);
         memset(v, 0, sizeof v);
         for (int j = 0; j < n; ++j) {
-            int st = or_score_mdn(p, M, pxyz, ptype, md, lg, dof, ev);
+            int st = or_score_full(p, M, pxyz, ptype, md, mp, lg, dof, ev);
             if (pairs) *pairs += ev->n_inter + ev->n_intra;
             if (st != OR_OK) { free(ev); return NAN; }
             if (j < n - 1) {
@@ -949,14 +1130,14 @@ double or_sample_pose(const or_sample_cfg* cfg, const or_params* p, int M, const
 
 typedef struct {
     const or_sample_cfg* cfg; const or_params* p; int M; const double* pxyz; const int32_t* ptype;
-    const or_mdn* md; const or_ligand* lg; uint32_t lig; int pose0, pose1, dstride; double* dof; double* e; int64_t pairs;
+    const or_mdn* md; const or_maps* mp; const or_ligand* lg; uint32_t lig; int pose0, pose1, dstride; double* dof; double* e; int64_t pairs;
 } or_job;
 
 static void* or_worker(void* arg)
 {
     or_job* j = (or_job*)arg;
     for (int ps = j->pose0; ps < j->pose1; ++ps)
-        j->e[ps] = or_sample_pose(j->cfg, j->p, j->M, j->pxyz, j->ptype, j->md, j->lg, j->lig, (uint32_t)ps,
+        j->e[ps] = or_sample_pose(j->cfg, j->p, j->M, j->pxyz, j->ptype, j->md, j->mp, j->lg, j->lig, (uint32_t)ps,
                                   j->dof + (size_t)ps * j->dstride, &j->pairs);
     return NULL;
 }
@@ -964,7 +1145,8 @@ static void* or_worker(void* arg)
 /* Poses [0, P) of one ligand on n_threads POSIX threads (contiguous chunks).
  * dof: [P][dstride], e: [P].  Returns the number of in-cutoff pairs evaluated. */
 int64_t or_sample_ligand(const or_sample_cfg* cfg, const or_params* p, int M, const double* pxyz,
-                         const int32_t* ptype, const or_mdn* md, const or_ligand* lg, uint32_t lig, int P, int dstride,
+                         const int32_t* ptype, const or_mdn* md, const or_maps* mp, const or_ligand* lg, uint32_t lig,
+                         int P, int dstride,
                          double* dof, double* e, int n_threads)
 {
     if (n_threads < 1) n_threads = 1;
@@ -973,7 +1155,7 @@ int64_t or_sample_ligand(const or_sample_cfg* cfg, const or_params* p, int M, co
     pthread_t th[256];
     if (n_threads > 256) n_threads = 256;
     for (int t = 0; t < n_threads; ++t) {
-        or_job j = {cfg, p, M, pxyz, ptype, md, lg, lig, (int)((int64_t)P * t / n_threads),
+        or_job j = {cfg, p, M, pxyz, ptype, md, mp, lg, lig, (int)((int64_t)P * t / n_threads),
                     (int)((int64_t)P * (t + 1) / n_threads), dstride, dof, e, 0};
         jobs[t] = j;
         pthread_create(&th[t], NULL, or_worker, &jobs[t]);
