@@ -211,6 +211,27 @@ int trids_free_pocket(trids_pocket* pk);
 int trids_set_residues(trids_pocket* pk, int32_t n_res, const int32_t* residue);
 
 /*
+ * Grid maps of the ligand-pocket atom-pair terms (the DSDP / Vina practice; the paper
+ * itself sums pairs directly, Sec. 4 item 4): for every ligand type, the energy an atom
+ * of that type would have at each point lo + spacing * (x, y, z) of a regular grid,
+ * summed over the pocket atoms within the cutoff.  While maps are present, a ligand atom
+ * whose cell (all 8 corners) lies inside the grid takes the trilinear interpolation of
+ * its type's map and the analytic gradient of that interpolation; any other atom keeps
+ * the direct pair sum.  Intra-ligand pairs and the residue-level E_MDN stay direct.
+ *   spacing  grid spacing (A) in [0.05, 4] (Vina uses 0.375); 0 frees the maps.
+ *   margin   the grid spans the union of the docking boxes grown by margin (A) per side,
+ *            in [0, 64].
+ * Memory: n_types * (points per axis)^3 floats.  The maps hold the parameters of the
+ * build: after trids_set_params, scoring and sampling fail with TRIDS_EINVAL until the
+ * maps are rebuilt; parameter gradients (g_w, g_radius) are refused while maps are
+ * present.  Launches on `stream`; later launches on that stream see the maps.
+ */
+int trids_build_maps(trids_pocket* pk, float spacing, float margin, void* stream);
+
+/* Map grid in use: origin lo (A), spacing (A) and points per axis (all 0 without maps). */
+int trids_maps_info(const trids_pocket* pk, float lo[3], float* spacing, int32_t dims[3]);
+
+/*
  * trids_pack_ligands -- validate ligands, build their torsion trees and upload them.
  * Inputs are host arrays, concatenated over ligands: n_atoms[n_lig]; xyz[sum L][3]
  * float32 input geometry (theta = 0); type[sum L]; n_bonds[n_lig];

@@ -13,7 +13,7 @@ MAX_MDN_K, MAX_RESIDUES = 16, 8191
 MODE_PERSISTENT, MODE_PER_LIGAND = 0, 1
 
 EXPORTS = ("trids_last_error", "trids_version", "trids_make_pocket", "trids_set_params", "trids_set_boxes",
-           "trids_free_pocket", "trids_set_residues",
+           "trids_free_pocket", "trids_set_residues", "trids_build_maps", "trids_maps_info",
            "trids_pack_ligands", "trids_free_batch", "trids_set_mdn", "trids_batch_info", "trids_batch_query",
            "trids_pack_topology", "trids_score_grad", "trids_score_grad_noalloc", "trids_state_floats",
            "trids_sample", "trids_topk", "trids_sync")
@@ -74,6 +74,8 @@ def lib(build_if_missing: bool = True):
     L.trids_pack_ligands.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, P(vp)]
     L.trids_free_batch.argtypes = [vp]
     L.trids_set_residues.argtypes = [vp, i32, vp]
+    L.trids_build_maps.argtypes = [vp, fp, fp, vp]
+    L.trids_maps_info.argtypes = [vp, P(C.c_float * 3), P(C.c_float), P(C.c_int32 * 3)]
     L.trids_set_mdn.argtypes = [vp, i32, i32, vp, vp]
     L.trids_batch_info.argtypes = [vp, P(BatchDims)]
     L.trids_batch_query.argtypes = [vp, vp, vp, i32, vp, i32]

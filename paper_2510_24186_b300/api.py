@@ -103,6 +103,18 @@ class Pocket:
         self.n_res = int(r.max()) + 1
         check(_lib.lib().trids_set_residues(self.handle, self.n_res, r.ctypes.data))
 
+    def build_maps(self, spacing: float = 0.375, margin: float = 8.0, stream=None):
+        """Grid maps of the ligand-pocket terms (trids_build_maps); spacing 0 frees them."""
+        check(_lib.lib().trids_build_maps(self.handle, float(spacing), float(margin), _stream(stream)))
+
+    def maps_info(self):
+        """(origin [3], spacing, points per axis [3]) of the maps in use (zeros without maps)."""
+        lo = (C.c_float * 3)()
+        h = C.c_float()
+        n = (C.c_int32 * 3)()
+        check(_lib.lib().trids_maps_info(self.handle, C.byref(lo), C.byref(h), C.byref(n)))
+        return np.array(lo[:], dtype=np.float32), float(h.value), tuple(n[:])
+
     def close(self):
         if getattr(self, "handle", None):
             _lib.lib().trids_free_pocket(self.handle)

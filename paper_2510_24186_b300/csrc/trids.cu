@@ -431,6 +431,18 @@ __device__ __forceinline__ void cell_range(const DevPocket& pk, const uint32_t* 
     }
 }
 
+// Grid-map cell of a point: true (and the cell + fractions in c / f) when maps are in use
+// and all 8 corners of the point's cell lie inside the map domain.
+__device__ __forceinline__ bool map_cell(const DevPocket& pk, float x, float y, float z, float4* cf) {
+    if (!pk.use_maps) return false;
+    const float ux = (x - pk.mlo[0]) * pk.inv_mh, uy = (y - pk.mlo[1]) * pk.inv_mh, uz = (z - pk.mlo[2]) * pk.inv_mh;
+    if (!(ux >= 0.f && uy >= 0.f && uz >= 0.f && ux < (float)(pk.mx - 1) && uy < (float)(pk.my - 1) &&
+          uz < (float)(pk.mz - 1)))
+        return false;
+    if (cf) *cf = make_float4(ux, uy, uz, 0.f);
+    return true;
+}
+
 // Forward kinematics of the warp's pose.  Lane k < T builds torsion k's rotation
 // (Rodrigues, angle th held by lane k) into W.rk; then each lane places its atoms:
 // torsions deepest first (reverse BFS order) about their input-geometry axes -- the
@@ -484,7 +496,7 @@ __device__ void fk_warp(const DevBatch& B, const LigHdr& h, const PW& W, const f
 // atom are added in lane order (bit-reproducible).  The Vina-form block is branch-free:
 // all candidates are evaluated and masked by r^2 < cutoff^2.  Writes the forces to W.gs;
 // returns the lane's ligand-pocket energy and, in *e_in2, twice its intra energy.
-template <int TS, bool PARAMS, bool COUNT>
+template <int TS, bool PARAMS, bool COUNT, bool MAPS>
 __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
                            const float w[5], float ebar, ParamAcc& acc, uint32_t& npairs, float* e_in2) {
     const DevParams& P = *S.P;
@@ -503,7 +515,7 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             uint32_t beg, end;
             cell_range(pk, pk.cell_start, x.x, x.y, x.z, beg, end);
             const int i0 = __ldg(&B.ipre[h.ipre_off + i]), i1 = __ldg(&B.ipre[h.ipre_off + i + 1]);
-            const int cbk = (int)((end - beg) >> 3);
+            const int cbk = (MAPS && map_cell(pk, x.x, x.y, x.z, nullptr)) ? 0 : (int)((end - beg) >> 3);
             W.cs[i] = beg;
             W.cb[i] = cbk;
             W.ip[i] = i0;
@@ -655,6 +667,44 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
     return e_lp;
 }
 
+// Grid-map energy of the warp's pose: each lane takes its atoms whose cell lies inside
+// the map domain (the pair loop skipped their pocket candidates): trilinear interpolation
+// of the atom type's map at the 8 corners and its analytic gradient, added to W.gs.
+// Out of line: the direct-sum sampler keeps its instruction footprint.
+__device__ __noinline__ float map_warp(const DevBatch& B, const DevPocket& pk, const LigHdr& h, const PW& W) {
+    float e = 0.f;
+    for (int i = W.lane; i < h.n_atoms; i += 32) {
+        const float4 x = W.xs[i];
+        float4 u;
+        if (!map_cell(pk, x.x, x.y, x.z, &u)) continue;
+        const int cx = (int)u.x, cy = (int)u.y, cz = (int)u.z;
+        const float fx = u.x - (float)cx, fy = u.y - (float)cy, fz = u.z - (float)cz;
+        const int t = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
+        const size_t sx = 1, sy = (size_t)pk.mx, sz = (size_t)pk.mx * pk.my;
+        const float* __restrict__ m = pk.maps + (size_t)t * sz * pk.mz + cz * sz + cy * sy + cx;
+        const float v000 = __ldg(m), v100 = __ldg(m + sx), v010 = __ldg(m + sy), v110 = __ldg(m + sy + sx);
+        const float v001 = __ldg(m + sz), v101 = __ldg(m + sz + sx), v011 = __ldg(m + sz + sy),
+                    v111 = __ldg(m + sz + sy + sx);
+        // along x, then y, then z
+        const float a00 = fmaf(fx, v100 - v000, v000), a10 = fmaf(fx, v110 - v010, v010);
+        const float a01 = fmaf(fx, v101 - v001, v001), a11 = fmaf(fx, v111 - v011, v011);
+        const float b0 = fmaf(fy, a10 - a00, a00), b1 = fmaf(fy, a11 - a01, a01);
+        e += fmaf(fz, b1 - b0, b0);
+        const float dz = b1 - b0;
+        const float dy = fmaf(fz, (a11 - a01) - (a10 - a00), a10 - a00);
+        const float d00 = v100 - v000, d10 = v110 - v010, d01 = v101 - v001, d11 = v111 - v011;
+        const float c0 = fmaf(fy, d10 - d00, d00), c1 = fmaf(fy, d11 - d01, d01);
+        const float dx = fmaf(fz, c1 - c0, c0);
+        float4 g = W.gs[i];
+        g.x = fmaf(dx, pk.inv_mh, g.x);
+        g.y = fmaf(dy, pk.inv_mh, g.y);
+        g.z = fmaf(dz, pk.inv_mh, g.z);
+        W.gs[i] = g;
+    }
+    __syncwarp();
+    return e;
+}
+
 // Residue-level E_MDN of the warp's pose (term set 2; Sec. 2, Eqs. P(d) and E_MDN): for
 // each ligand atom (one lane per atom) and each residue listed for its cell, the
 // minimum distance d over the residue's atoms; d < 5 A adds
@@ -710,14 +760,15 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
 }
 
 // E_total of the warp's pose (same value on every lane); forces in W.gs.
-template <int TS, bool PARAMS, bool COUNT>
+template <int TS, bool PARAMS, bool COUNT, bool MAPS>
 __device__ float score_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
                             float ebar, ParamAcc& acc, float* e_inter, uint32_t& npairs) {
     float w[5];
 #pragma unroll
     for (int t = 0; t < 5; ++t) w[t] = S.P->w[t];
     float ein2;
-    float el = pairs_warp<TS, PARAMS, COUNT>(B, pk, S, h, W, w, ebar, acc, npairs, &ein2);
+    float el = pairs_warp<TS, PARAMS, COUNT, MAPS>(B, pk, S, h, W, w, ebar, acc, npairs, &ein2);
+    if (MAPS && pk.use_maps) el += map_warp(B, pk, h, W);
     if constexpr (TS == TRIDS_TERMS_TRIDS_RES) el += residue_warp<PARAMS>(B, pk, S, h, W, w[0], ebar, acc);
     const float e_lp = warp_sum(el);
     *e_inter = e_lp;
@@ -890,12 +941,12 @@ __device__ void store_pose(const SampleArgs& A, const LigHdr& h, int lane, int l
 
 // Step of one variable under the configured update rule (trids.h, TRIDS_OPT_*); pv is
 // the value a weight decay acts on.  bc1 = 1 - b1^k and sbc2 = sqrt(1 - b2^k) for Adam(W).
-// GOPT = false compiles Adam alone: the other rules' code would otherwise enlarge the
+// GEN = false compiles Adam alone: the other rules' code would otherwise enlarge the
 // sampler kernel, which costs the pair loop instruction-cache hits.
-template <bool GOPT>
+template <bool GEN>
 __device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float pv, float& m, float& v, float bc1,
                                            float sbc2) {
-    if (GOPT) {
+    if (GEN) {
         switch (A.opt) {
         case TRIDS_OPT_RMSPROP:
             v = fmaf(A.alpha, v, (1.f - A.alpha) * g * g);
@@ -914,13 +965,13 @@ __device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float p
     v = fmaf(A.b2, v, (1.f - A.b2) * g * g);
     const float denom = sqrtf(v) / sbc2 + A.eps;
     const float d = -(A.lr / bc1) * m / denom;
-    return GOPT && A.opt == TRIDS_OPT_ADAMW ? fmaf(-A.lr * A.wd, pv, d) : d;
+    return GEN && A.opt == TRIDS_OPT_ADAMW ? fmaf(-A.lr * A.wd, pv, d) : d;
 }
 
 // One evaluation (and its update or acceptance test) of the warp's pose; s is the
 // global evaluation index of the schedule.  Every branch below is uniform across the
 // warp except the per-torsion lanes.
-template <int TS, bool COUNT, bool GOPT>
+template <int TS, bool COUNT, bool GEN>
 __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h, const PW& W, int l, int p, int s,
                             PoseState& st, uint32_t& npairs) {
     if (st.status & 1) return;  // frozen after a non-finite energy
@@ -960,7 +1011,7 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
     fk_warp(A.B, h, W, st.t, st.q, st.th, S.P->radius);
     ParamAcc acc;
     float e_inter;
-    const float E = score_warp<TS, false, COUNT>(A.B, A.pk, S, h, W, 1.f, acc, &e_inter, npairs);
+    const float E = score_warp<TS, false, COUNT, GEN>(A.B, A.pk, S, h, W, 1.f, acc, &e_inter, npairs);
     float gt[3], tau[3];
     const float gth = adjoint_warp(A.B, h, W, st.t, gt, tau);
     if (A.trace) {
@@ -989,14 +1040,14 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
         const int ta = sc.j + 1;
         const float bc1 = 1.f - powf(A.b1, (float)ta);
         const float sbc2 = sqrtf(1.f - powf(A.b2, (float)ta));
-        if (own) st.th = wrap_pi(st.th + opt_delta<GOPT>(A, gth, st.th, st.mth, st.vth, bc1, sbc2));
+        if (own) st.th = wrap_pi(st.th + opt_delta<GEN>(A, gth, st.th, st.mth, st.vth, bc1, sbc2));
         for (int d = 0; d < 3; ++d) {
             const float lo = A.pk.box_lo[bx][d], hi = A.pk.box_hi[bx][d];
-            const float dlt = opt_delta<GOPT>(A, gt[d], st.t[d] - 0.5f * (lo + hi), st.m[d], st.v[d], bc1, sbc2);
+            const float dlt = opt_delta<GEN>(A, gt[d], st.t[d] - 0.5f * (lo + hi), st.m[d], st.v[d], bc1, sbc2);
             st.t[d] = fminf(fmaxf(st.t[d] + dlt, lo), hi);
         }
         float dw[3];
-        for (int d = 0; d < 3; ++d) dw[d] = opt_delta<GOPT>(A, tau[d], 0.f, st.m[3 + d], st.v[3 + d], bc1, sbc2);
+        for (int d = 0; d < 3; ++d) dw[d] = opt_delta<GEN>(A, tau[d], 0.f, st.m[3 + d], st.v[3 + d], bc1, sbc2);
         const float phi = sqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
         if (phi > 0.f) {
             float sh, ch;
@@ -1031,7 +1082,7 @@ __device__ __forceinline__ void flush_count(unsigned long long* cnt, uint32_t n)
 
 // Persistent fused sampler: each warp pops poses from a global counter (ligands in
 // decreasing-cost order) and runs every evaluation of the pose with its state on chip.
-template <int TS, bool COUNT, bool GOPT>
+template <int TS, bool COUNT, bool GEN>
 __global__ void __launch_bounds__(512, 1) k_sample_persistent(SampleArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
@@ -1050,7 +1101,7 @@ __global__ void __launch_bounds__(512, 1) k_sample_persistent(SampleArgs A) {
         PoseState st;
         if (A.step_begin == 0) init_pose(A, h, W.lane, l, p, st);
         else load_pose(A, h, W.lane, l, p, st);
-        for (int s = A.step_begin; s < A.step_end; ++s) sample_step<TS, COUNT, GOPT>(A, S, h, W, l, p, s, st, npairs);
+        for (int s = A.step_begin; s < A.step_end; ++s) sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, st, npairs);
         store_pose(A, h, W.lane, l, p, st);
         __syncwarp();
     }
@@ -1059,7 +1110,7 @@ __global__ void __launch_bounds__(512, 1) k_sample_persistent(SampleArgs A) {
 
 // Plain form: one launch per (ligand, evaluation), one warp per pose, the state in
 // global memory between launches; the same device code as the persistent sampler.
-template <int TS, bool COUNT, bool GOPT>
+template <int TS, bool COUNT, bool GEN>
 __global__ void __launch_bounds__(512, 1) k_sample_step(SampleArgs A, int l, int s) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
@@ -1073,7 +1124,7 @@ __global__ void __launch_bounds__(512, 1) k_sample_step(SampleArgs A, int l, int
     PoseState st;
     if (s == 0) init_pose(A, h, W.lane, l, p, st);
     else load_pose(A, h, W.lane, l, p, st);
-    sample_step<TS, COUNT, GOPT>(A, S, h, W, l, p, s, st, npairs);
+    sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, st, npairs);
     store_pose(A, h, W.lane, l, p, st);
     if (COUNT) flush_count(A.pair_count, npairs);
 }
@@ -1130,7 +1181,7 @@ __global__ void __launch_bounds__(512, 1) k_score(ScoreArgs A) {
             fk_warp(A.B, h, W, t, q, th, S.P->radius);
             float e_inter;
             uint32_t np = 0;
-            const float E = score_warp<TS, PARAMS, false>(A.B, A.pk, S, h, W, ebar, acc, &e_inter, np);
+            const float E = score_warp<TS, PARAMS, false, !PARAMS>(A.B, A.pk, S, h, W, ebar, acc, &e_inter, np);
             if (lane == 0) {
                 A.energy[gp] = E;
                 if (A.e_inter) A.e_inter[gp] = e_inter;
@@ -1289,6 +1340,60 @@ __global__ void __launch_bounds__(128) k_topk(DevBatch B, int P, const float* en
     }
 }
 
+// Grid maps: one thread per map point; the ligand-pocket atom-pair energy an atom of each
+// ligand type would have there, summed over the pocket atoms of the point's candidate-grid
+// cell within the cutoff (residue-level E_MDN is not mapped).
+template <int TS>
+__global__ void __launch_bounds__(256) k_build_maps(DevPocket pk, const DevParams* __restrict__ prm, float* maps) {
+    __shared__ DevParams P;
+    for (int k = threadIdx.x; k < (int)(sizeof(DevParams) / 4); k += blockDim.x)
+        reinterpret_cast<uint32_t*>(&P)[k] = reinterpret_cast<const uint32_t*>(prm)[k];
+    __syncthreads();
+    const int nt = P.n_types;
+    const int64_t npts = (int64_t)pk.mx * pk.my * pk.mz;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < npts;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(idx % pk.mx), iy = (int)((idx / pk.mx) % pk.my), iz = (int)(idx / ((int64_t)pk.mx * pk.my));
+        const float gx = fmaf(pk.mh, (float)ix, pk.mlo[0]), gy = fmaf(pk.mh, (float)iy, pk.mlo[1]),
+                    gz = fmaf(pk.mh, (float)iz, pk.mlo[2]);
+        uint32_t beg, end;
+        cell_range(pk, pk.cell_start, gx, gy, gz, beg, end);
+        float acc[kNT];
+#pragma unroll
+        for (int t = 0; t < kNT; ++t) acc[t] = 0.f;
+        for (uint32_t q = beg; q < end; ++q) {
+            const int j = __ldg(&pk.cand[q]) & 0x1fff;
+            const float4 a = __ldg(&pk.atoms[j]);
+            const float dx = gx - a.x, dy = gy - a.y, dz = gz - a.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (!(r2 < P.cut2)) continue;
+            const int tj = pk.ptype[j];
+            const uint32_t fj = P.tflags[tj];
+#pragma unroll
+            for (int t = 0; t < kNT; ++t) {
+                if (t >= nt) break;
+                const uint32_t fi = P.tflags[t];
+                const bool hb = ((fi & 2u) && (fj & 4u)) || ((fi & 4u) && (fj & 2u));
+                float e;
+                if (TS == TRIDS_TERMS_VINA5) {
+                    float dd, rinv;
+                    e = vina_eval<false>(r2, P.radius[t] + a.w, (fi & fj & 1u) ? 1.f : 0.f, hb ? 1.f : 0.f, P.w, dd,
+                                         rinv, nullptr);
+                } else {
+                    float fr, dRs;
+                    const bool mdn = TS == TRIDS_TERMS_TRIDS;
+                    e = pair_trids<false>(fmaxf(r2, 1e-12f), P.radius[t] + a.w, hb ? 2 : 0,
+                                          mdn ? &P.gmm[t][tj][0] : nullptr, P.gmm_k, mdn, P.w, fr, nullptr, dRs);
+                }
+                acc[t] += e;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kNT; ++t)
+            if (t < nt) maps[t * npts + idx] = acc[t];
+    }
+}
+
 __global__ void k_status(const float* state, int n_lig, int P, int n_fields, int* out) {
     const size_t n = (size_t)n_lig * P;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -1332,6 +1437,10 @@ struct trids_pocket {
     uint32_t* d_cell = nullptr;
     uint16_t* d_cand = nullptr;
     DevParams* d_params = nullptr;
+    float* d_maps = nullptr;             // grid maps [type][z][y][x]
+    int mdims[3] = {0, 0, 0};
+    float mlo[3] = {0.f, 0.f, 0.f}, mh = 0.f;
+    bool maps_stale = false;             // parameters changed since the maps were built
     ResidueGrid rgrid;                   // residue-level E_MDN (term set 2)
     int32_t* d_res_start = nullptr;
     uint16_t* d_res_atoms = nullptr;
@@ -1342,6 +1451,11 @@ struct trids_pocket {
         v.atoms = d_atoms; v.ptype = d_ptype; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
         v.n_res = rgrid.n_res; v.res_start = d_res_start; v.res_atoms = d_res_atoms; v.rcell_start = d_rcell;
         v.rlist = d_rlist;
+        v.use_maps = d_maps != nullptr;
+        v.mx = mdims[0]; v.my = mdims[1]; v.mz = mdims[2];
+        for (int d = 0; d < 3; ++d) v.mlo[d] = mlo[d];
+        v.mh = mh; v.inv_mh = mh > 0.f ? 1.f / mh : 0.f;
+        v.maps = d_maps;
         v.nx = grid.dims[0]; v.ny = grid.dims[1]; v.nz = grid.dims[2];
         v.gx = grid.lo[0]; v.gy = grid.lo[1]; v.gz = grid.lo[2]; v.inv_h = 1.f / grid.h;
         v.n_boxes = n_boxes;
@@ -1595,6 +1709,8 @@ int check_device_ptr(const void* p, const char* name, bool nullable) {
 
 // Inputs a term set needs beyond the pocket and the batch.
 int check_terms(const trids_pocket* pk, const trids_batch* b) {
+    if (pk->d_maps && pk->maps_stale)
+        return fail(TRIDS_EINVAL, "the grid maps predate trids_set_params: call trids_build_maps again");
     if (pk->prm.term_set != TRIDS_TERMS_TRIDS_RES) return TRIDS_OK;
     if (pk->rgrid.n_res < 1) return fail(TRIDS_EINVAL, "term set 2 needs trids_set_residues on the pocket");
     if (!b->d_mdn) return fail(TRIDS_EINVAL, "term set 2 needs trids_set_mdn on the batch");
@@ -1608,27 +1724,27 @@ using StepKernel = void (*)(SampleArgs, int, int);
 using ScoreKernel = void (*)(ScoreArgs);
 
 template <int TS>
-PersistentKernel persistent_for(bool cnt, bool gopt) {
-    return gopt ? (cnt ? k_sample_persistent<TS, true, true> : k_sample_persistent<TS, false, true>)
+PersistentKernel persistent_for(bool cnt, bool gen) {
+    return gen ? (cnt ? k_sample_persistent<TS, true, true> : k_sample_persistent<TS, false, true>)
                 : (cnt ? k_sample_persistent<TS, true, false> : k_sample_persistent<TS, false, false>);
 }
 template <int TS>
-StepKernel step_for(bool cnt, bool gopt) {
-    return gopt ? (cnt ? k_sample_step<TS, true, true> : k_sample_step<TS, false, true>)
+StepKernel step_for(bool cnt, bool gen) {
+    return gen ? (cnt ? k_sample_step<TS, true, true> : k_sample_step<TS, false, true>)
                 : (cnt ? k_sample_step<TS, true, false> : k_sample_step<TS, false, false>);
 }
 template <int TS>
 ScoreKernel score_for(bool params) { return params ? k_score<TS, true> : k_score<TS, false>; }
 
-PersistentKernel persistent_kernel(int ts, bool cnt, bool gopt) {
-    return ts == TRIDS_TERMS_TRIDS ? persistent_for<TRIDS_TERMS_TRIDS>(cnt, gopt)
-         : ts == TRIDS_TERMS_TRIDS_RES ? persistent_for<TRIDS_TERMS_TRIDS_RES>(cnt, gopt)
-                                       : persistent_for<TRIDS_TERMS_VINA5>(cnt, gopt);
+PersistentKernel persistent_kernel(int ts, bool cnt, bool gen) {
+    return ts == TRIDS_TERMS_TRIDS ? persistent_for<TRIDS_TERMS_TRIDS>(cnt, gen)
+         : ts == TRIDS_TERMS_TRIDS_RES ? persistent_for<TRIDS_TERMS_TRIDS_RES>(cnt, gen)
+                                       : persistent_for<TRIDS_TERMS_VINA5>(cnt, gen);
 }
-StepKernel step_kernel(int ts, bool cnt, bool gopt) {
-    return ts == TRIDS_TERMS_TRIDS ? step_for<TRIDS_TERMS_TRIDS>(cnt, gopt)
-         : ts == TRIDS_TERMS_TRIDS_RES ? step_for<TRIDS_TERMS_TRIDS_RES>(cnt, gopt)
-                                       : step_for<TRIDS_TERMS_VINA5>(cnt, gopt);
+StepKernel step_kernel(int ts, bool cnt, bool gen) {
+    return ts == TRIDS_TERMS_TRIDS ? step_for<TRIDS_TERMS_TRIDS>(cnt, gen)
+         : ts == TRIDS_TERMS_TRIDS_RES ? step_for<TRIDS_TERMS_TRIDS_RES>(cnt, gen)
+                                       : step_for<TRIDS_TERMS_VINA5>(cnt, gen);
 }
 ScoreKernel score_kernel(int ts, bool params) {
     return ts == TRIDS_TERMS_TRIDS ? score_for<TRIDS_TERMS_TRIDS>(params)
@@ -1721,6 +1837,7 @@ int trids_set_params(trids_pocket* pk, const trids_params* prm, void* stream) {
     if ((rc = device_guard(pk->device))) return rc;
     const bool flags_changed = std::memcmp(pk->prm.flags, prm->flags, sizeof prm->flags) != 0;
     pk->prm = *prm;
+    if (pk->d_maps) pk->maps_stale = true;
     if ((rc = upload_pocket_arrays(pk, (cudaStream_t)stream))) return rc;
     if (flags_changed)
         for (trids_batch* b : pk->batches)
@@ -1755,6 +1872,7 @@ int trids_free_pocket(trids_pocket* pk) {
     cudaFree(pk->d_cell);
     cudaFree(pk->d_cand);
     cudaFree(pk->d_params);
+    cudaFree(pk->d_maps);
     cudaFree(pk->d_res_start);
     cudaFree(pk->d_res_atoms);
     cudaFree(pk->d_rcell);
@@ -1789,6 +1907,77 @@ int trids_set_residues(trids_pocket* pk, int32_t n_res, const int32_t* residue) 
     cudaFree(pk->d_res_start); cudaFree(pk->d_res_atoms); cudaFree(pk->d_rcell); cudaFree(pk->d_rlist);
     pk->d_res_start = d_start; pk->d_res_atoms = d_atoms; pk->d_rcell = d_cell; pk->d_rlist = d_list;
     pk->rgrid = std::move(rg);
+    return TRIDS_OK;
+}
+
+int trids_build_maps(trids_pocket* pk, float spacing, float margin, void* stream) {
+    g_err.clear();
+    if (!pk) return fail(TRIDS_EINVAL, "pocket is NULL");
+    int rc = device_guard(pk->device);
+    if (rc) return rc;
+    if (spacing == 0.f) {
+        if (pk->d_maps) {
+            CK(cudaDeviceSynchronize());   // no launch may still read the maps
+            cudaFree(pk->d_maps);
+        }
+        pk->d_maps = nullptr;
+        pk->mdims[0] = pk->mdims[1] = pk->mdims[2] = 0;
+        pk->maps_stale = false;
+        return TRIDS_OK;
+    }
+    if (!(spacing >= 0.05f && spacing <= 4.f)) return fail(TRIDS_EINVAL, "spacing must be 0 or in [0.05, 4] A");
+    if (!(margin >= 0.f && margin <= 64.f)) return fail(TRIDS_EINVAL, "margin must be in [0, 64] A");
+    float lo[3], hi[3];
+    int n[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = pk->box_lo[0][d];
+        hi[d] = pk->box_hi[0][d];
+        for (int b = 1; b < pk->n_boxes; ++b) {
+            lo[d] = std::min(lo[d], pk->box_lo[b][d]);
+            hi[d] = std::max(hi[d], pk->box_hi[b][d]);
+        }
+        lo[d] -= margin;
+        hi[d] += margin;
+        n[d] = (int)std::ceil((double)(hi[d] - lo[d]) / spacing) + 1;
+        if (n[d] < 2) n[d] = 2;
+    }
+    const size_t pts = (size_t)n[0] * n[1] * n[2];
+    const size_t bytes = pts * pk->prm.n_types * sizeof(float);
+    if (pts > (size_t)1 << 31) return fail(TRIDS_EINVAL, "map grid of %zu points is too large", pts);
+    float* d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) return fail(TRIDS_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+    DevPocket v = pk->view();
+    v.mx = n[0]; v.my = n[1]; v.mz = n[2];
+    for (int k = 0; k < 3; ++k) v.mlo[k] = lo[k];
+    v.mh = spacing;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int blocks = (int)std::min<size_t>((pts + 255) / 256, (size_t)n_sms(pk->device) * 16);
+    switch (pk->prm.term_set) {
+    case TRIDS_TERMS_TRIDS: k_build_maps<TRIDS_TERMS_TRIDS><<<blocks, 256, 0, st>>>(v, pk->d_params, d); break;
+    case TRIDS_TERMS_TRIDS_RES: k_build_maps<TRIDS_TERMS_TRIDS_RES><<<blocks, 256, 0, st>>>(v, pk->d_params, d); break;
+    default: k_build_maps<TRIDS_TERMS_VINA5><<<blocks, 256, 0, st>>>(v, pk->d_params, d); break;
+    }
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) {
+        cudaFree(d);
+        return fail(TRIDS_ECUDA, "map build launch: %s", cudaGetErrorString(le));
+    }
+    if (pk->d_maps) {
+        CK(cudaDeviceSynchronize());
+        cudaFree(pk->d_maps);
+    }
+    pk->d_maps = d;
+    for (int k = 0; k < 3; ++k) { pk->mdims[k] = n[k]; pk->mlo[k] = lo[k]; }
+    pk->mh = spacing;
+    pk->maps_stale = false;
+    return TRIDS_OK;
+}
+
+int trids_maps_info(const trids_pocket* pk, float lo[3], float* spacing, int32_t dims[3]) {
+    g_err.clear();
+    if (!pk || !lo || !spacing || !dims) return fail(TRIDS_EINVAL, "NULL argument");
+    for (int d = 0; d < 3; ++d) { lo[d] = pk->mlo[d]; dims[d] = pk->mdims[d]; }
+    *spacing = pk->mh;
     return TRIDS_OK;
 }
 
@@ -2045,6 +2234,8 @@ int trids_score_grad(const trids_pocket* pk, const trids_batch* bc, int32_t pose
         return rc;
     if ((rc = ensure_items(b, poses))) return rc;
     const bool params = g_w || g_radius;
+    if (params && pk->d_maps)
+        return fail(TRIDS_EINVAL, "parameter gradients need direct scoring: free the grid maps first");
     if (params) {
         const size_t need = (size_t)b->n_items * (5 + kNT);
         if (need > b->partials_cap) {
@@ -2130,9 +2321,11 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     cudaStream_t st = (cudaStream_t)stream;
     const int ts = pk->prm.term_set;
     const bool cnt = c.pair_count != nullptr;
-    const bool gopt = c.optimizer != TRIDS_OPT_ADAM;
+    // the general kernels carry the other update rules and the grid maps; the plain ones
+    // (Adam, direct pair sums: the paper's configuration) leave that code out
+    const bool gen = c.optimizer != TRIDS_OPT_ADAM || pk->d_maps != nullptr;
     if (c.mode == TRIDS_MODE_PER_LIGAND) {
-        const StepKernel kern = step_kernel(ts, cnt, gopt);
+        const StepKernel kern = step_kernel(ts, cnt, gen);
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
         const int blocks = (c.poses + warps - 1) / warps;
         for (int s = c.step_begin; s < c.step_end; ++s)
@@ -2140,7 +2333,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         CK(cudaGetLastError());
         return TRIDS_OK;
     }
-    const PersistentKernel kern = persistent_kernel(ts, cnt, gopt);
+    const PersistentKernel kern = persistent_kernel(ts, cnt, gen);
     int grid = 0;
     if ((rc = grid_for(kern, warps, L.total, pk->device, A.n_items, &grid))) return rc;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -2157,7 +2350,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     // against the caller's by events.
     std::vector<unsigned char> key(sizeof(SampleArgs) + 4 * sizeof(int));
     std::memcpy(key.data(), &A, sizeof(SampleArgs));
-    const int extra[4] = {grid, warps, ts, (cnt ? 1 : 0) | (gopt ? 2 : 0)};
+    const int extra[4] = {grid, warps, ts, (cnt ? 1 : 0) | (gen ? 2 : 0)};
     std::memcpy(key.data() + sizeof(SampleArgs), extra, sizeof extra);
     const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
     if (legacy && !b->side) {
@@ -2275,6 +2468,8 @@ int trids_score_grad_noalloc(const trids_pocket* pk, const trids_batch* b, int32
         (rc = check_terms(pk, b)))
         return rc;
     const bool params = g_w || g_radius;
+    if (params && pk->d_maps)
+        return fail(TRIDS_EINVAL, "parameter gradients need direct scoring: free the grid maps first");
     const int tiles = (poses + 31) / 32;
     const size_t n_items = (size_t)b->dims.n_lig * tiles;
     const size_t items_off = 256;

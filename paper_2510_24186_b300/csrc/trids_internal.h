@@ -93,6 +93,12 @@ struct DevPocket {
     float gx, gy, gz, inv_h;
     int n_boxes;                   // pose p samples in box p mod n_boxes
     float box_lo[kMaxBoxes][3], box_hi[kMaxBoxes][3];
+    // grid maps of the ligand-pocket atom-pair terms: maps[type][z][y][x] at points
+    // mlo + mh * (x, y, z); an atom whose cell lies inside takes the trilinear value
+    int use_maps;
+    int mx, my, mz;
+    float mlo[3], mh, inv_mh;
+    const float* maps;
     // residue-level E_MDN (term set 2)
     int n_res;
     const int32_t* res_start;      // [n_res + 1]

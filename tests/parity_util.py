@@ -130,7 +130,7 @@ def state_err(d_gpu, d_ref, T):
 
 
 def check_trace(trace, poses_g, P, ligs_or, pxyz, ptype, op, cfg_or, S, Lmc, seed, dof_final, e_final,
-                lig_base=0, st: Stats | None = None, mds=None) -> Stats:
+                lig_base=0, st: Stats | None = None, mds=None, mp=None) -> Stats:
     """Per-evaluation parity of a sampler trace.
 
     trace [S, n_trace, rec] (GPU float32), poses_g = global pose ids (l * P + p) of the slots.
@@ -138,7 +138,8 @@ def check_trace(trace, poses_g, P, ligs_or, pxyz, ptype, op, cfg_or, S, Lmc, see
     compares energy and gradient; it then applies the method's next action (Adam update,
     or Metropolis decision + perturbation at a loop boundary) in FP64 to the GPU's state
     and gradient and compares with the GPU's next state; finally the returned state and
-    energy are checked.  mds: per-ligand residue-level E_MDN inputs (term set 2).
+    energy are checked.  mds: per-ligand residue-level E_MDN inputs (term set 2); mp: the
+    grid-map domain when the GPU scored with maps.
     """
     st = st or Stats()
     trace = np.asarray(trace, dtype=np.float64)
@@ -165,7 +166,7 @@ def check_trace(trace, poses_g, P, ligs_or, pxyz, ptype, op, cfg_or, S, Lmc, see
             dof = rec[:7 + T]
             E = rec[D]
             gt, tau, gth = rec[D + 1:D + 4], rec[D + 4:D + 7], rec[D + 7:D + 7 + T]
-            stt, ev = oracle.score(op, pxyz, ptype, lg, dof, None if mds is None else mds[l])
+            stt, ev = oracle.score(op, pxyz, ptype, lg, dof, None if mds is None else mds[l], mp)
             st.n += 1
             energy_ok(E, ev, st, f"pose {g} step {s}")
             sl = grad_slack(ev)
