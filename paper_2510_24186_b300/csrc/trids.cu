@@ -445,9 +445,9 @@ __device__ __forceinline__ bool map_cell(const DevPocket& pk, float x, float y, 
 
 // Forward kinematics of the warp's pose.  Lane k < T builds torsion k's rotation
 // (Rodrigues, angle th held by lane k) into W.rk; then each lane places its atoms:
-// torsions deepest first (reverse BFS order) about their input-geometry axes -- the
-// axis atoms of a torsion are never moved by the torsions below it -- then
-// x = t + R(q) z.
+// the torsions that move an atom (its fragment's torsion and that torsion's ancestors),
+// deepest first, about their input-geometry axes -- the axis atoms of a torsion are never
+// moved by the torsions below it -- then x = t + R(q) z.
 __device__ void fk_warp(const DevBatch& B, const LigHdr& h, const PW& W, const float t[3], const float q[4], float th,
                         const float* __restrict__ rad) {
     const int T = h.n_tor, L = h.n_atoms;
@@ -463,19 +463,19 @@ __device__ void fk_warp(const DevBatch& B, const LigHdr& h, const PW& W, const f
     __syncwarp();
     float R[9];
     quat_to_mat(q, R);
+    const int8_t* __restrict__ tpar = B.tor_par + h.tor_off;
     for (int i = W.lane; i < L; i += 32) {
         const float4 y = __ldg(&B.atom_y[h.atom_off + i]);
         float x0 = y.x, x1 = y.y, x2 = y.z;
-        for (int k = T - 1; k >= 0; --k) {
-            const int4 ti = __ldg(&B.tor_idx[h.tor_off + k]);
-            if (i >= ti.z && i < ti.w) {
-                const float4 p = __ldg(&B.tor_p[h.tor_off + k]);
-                const float4 r0 = W.rk[3 * k], r1 = W.rk[3 * k + 1], r2 = W.rk[3 * k + 2];
-                const float vx = x0 - p.x, vy = x1 - p.y, vz = x2 - p.z;
-                x0 = p.x + (r0.x * vx + r0.y * vy + r0.z * vz);
-                x1 = p.y + (r1.x * vx + r1.y * vy + r1.z * vz);
-                x2 = p.z + (r2.x * vx + r2.y * vy + r2.z * vz);
-            }
+        // the torsions that move atom i are its fragment's torsion and that torsion's
+        // ancestors; walking up the tree visits them deepest first
+        for (int k = __ldg(&B.atom_tor[h.atom_off + i]); k >= 0; k = __ldg(&tpar[k])) {
+            const float4 p = __ldg(&B.tor_p[h.tor_off + k]);
+            const float4 r0 = W.rk[3 * k], r1 = W.rk[3 * k + 1], r2 = W.rk[3 * k + 2];
+            const float vx = x0 - p.x, vy = x1 - p.y, vz = x2 - p.z;
+            x0 = p.x + (r0.x * vx + r0.y * vy + r0.z * vz);
+            x1 = p.y + (r1.x * vx + r1.y * vy + r1.z * vz);
+            x2 = p.z + (r2.x * vx + r2.y * vy + r2.z * vz);
         }
         W.xs[i] = make_float4(t[0] + (R[0] * x0 + R[1] * x1 + R[2] * x2), t[1] + (R[3] * x0 + R[4] * x1 + R[5] * x2),
                               t[2] + (R[6] * x0 + R[7] * x1 + R[8] * x2), rad[__float_as_int(y.w)]);
@@ -777,7 +777,8 @@ __device__ float score_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
 
 // dE/dt = sum g_i and world torque tau = sum (x_i - t) x g_i (every lane), and
 // dE/dtheta_k = a_k . sum over the moving subtree of (x_i - p_k) x g_i with a_k the world
-// axis (parent atom -> child atom) and p_k the world parent atom (lane k).
+// axis (parent atom -> child atom) and p_k the world parent atom (lane k, which sums its
+// subtree serially: no shuffles, and the subtree is one contiguous range).
 __device__ float adjoint_warp(const DevBatch& B, const LigHdr& h, const PW& W, const float t[3], float gt[3],
                               float tau[3]) {
     const int L = h.n_atoms, T = h.n_tor;
@@ -792,23 +793,22 @@ __device__ float adjoint_warp(const DevBatch& B, const LigHdr& h, const PW& W, c
     }
     gt[0] = warp_sum(a0); gt[1] = warp_sum(a1); gt[2] = warp_sum(a2);
     tau[0] = warp_sum(a3); tau[1] = warp_sum(a4); tau[2] = warp_sum(a5);
+    // torsion k on lane k: its moving subtree is the contiguous atom range [ti.z, ti.w)
     float mine = 0.f;
-    for (int k = 0; k < T; ++k) {
-        const int4 ti = __ldg(&B.tor_idx[h.tor_off + k]);
+    if (W.lane < T) {
+        const int4 ti = __ldg(&B.tor_idx[h.tor_off + W.lane]);
         const float4 p = W.xs[ti.x], c = W.xs[ti.y];
-        float ax = c.x - p.x, ay = c.y - p.y, az = c.z - p.z;
-        const float n = rsqrtf(ax * ax + ay * ay + az * az);
-        ax *= n; ay *= n; az *= n;
-        float s = 0.f;
-        for (int i = W.lane; i < L; i += 32) {
-            if (i >= ti.z && i < ti.w) {
-                const float4 x = W.xs[i], g = W.gs[i];
-                const float rx = x.x - p.x, ry = x.y - p.y, rz = x.z - p.z;
-                s += ax * (ry * g.z - rz * g.y) + ay * (rz * g.x - rx * g.z) + az * (rx * g.y - ry * g.x);
-            }
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int i = ti.z; i < ti.w; ++i) {
+            const float4 x = W.xs[i], g = W.gs[i];
+            const float rx = x.x - p.x, ry = x.y - p.y, rz = x.z - p.z;
+            sx += ry * g.z - rz * g.y;
+            sy += rz * g.x - rx * g.z;
+            sz += rx * g.y - ry * g.x;
         }
-        s = warp_sum(s);
-        if (W.lane == k) mine = s;
+        const float ax = c.x - p.x, ay = c.y - p.y, az = c.z - p.z;
+        const float n = rsqrtf(ax * ax + ay * ay + az * az);
+        mine = (ax * sx + ay * sy + az * sz) * n;
     }
     return mine;
 }
@@ -939,13 +939,25 @@ __device__ void store_pose(const SampleArgs& A, const LigHdr& h, int lane, int l
     }
 }
 
+// b^n, n >= 0, by repeated squaring: the same float operations in every form of the sampler.
+__device__ __forceinline__ float ipowf(float b, int n) {
+    float r = 1.f;
+    while (n) {
+        if (n & 1) r *= b;
+        b *= b;
+        n >>= 1;
+    }
+    return r;
+}
+
 // Step of one variable under the configured update rule (trids.h, TRIDS_OPT_*); pv is
-// the value a weight decay acts on.  bc1 = 1 - b1^k and sbc2 = sqrt(1 - b2^k) for Adam(W).
+// the value a weight decay acts on.  For Adam(W) lr_bc1 = lr / (1 - b1^k) and
+// rsbc2 = 1 / sqrt(1 - b2^k), k = the step within the Monte-Carlo loop.
 // GEN = false compiles Adam alone: the other rules' code would otherwise enlarge the
 // sampler kernel, which costs the pair loop instruction-cache hits.
 template <bool GEN>
-__device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float pv, float& m, float& v, float bc1,
-                                           float sbc2) {
+__device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float pv, float& m, float& v, float lr_bc1,
+                                           float rsbc2) {
     if (GEN) {
         switch (A.opt) {
         case TRIDS_OPT_RMSPROP:
@@ -963,8 +975,8 @@ __device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float p
     }
     m = fmaf(A.b1, m, (1.f - A.b1) * g);
     v = fmaf(A.b2, v, (1.f - A.b2) * g * g);
-    const float denom = sqrtf(v) / sbc2 + A.eps;
-    const float d = -(A.lr / bc1) * m / denom;
+    const float denom = fmaf(sqrtf(v), rsbc2, A.eps);
+    const float d = -lr_bc1 * __fdividef(m, denom);
     return GEN && A.opt == TRIDS_OPT_ADAMW ? fmaf(-A.lr * A.wd, pv, d) : d;
 }
 
@@ -973,9 +985,8 @@ __device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float p
 // warp except the per-torsion lanes.
 template <int TS, bool COUNT, bool GEN>
 __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h, const PW& W, int l, int p, int s,
-                            PoseState& st, uint32_t& npairs) {
+                            const Sched& sc, PoseState& st, uint32_t& npairs) {
     if (st.status & 1) return;  // frozen after a non-finite energy
-    const Sched sc = schedule(A.S, A.Lmc, s);
     const int T = h.n_tor, lane = W.lane;
     const int bx = A.pk.n_boxes > 1 ? p % A.pk.n_boxes : 0;   // the pose's docking box
     const bool own = lane < T;
@@ -1038,16 +1049,16 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
     }
     if (sc.j < sc.n - 1) {
         const int ta = sc.j + 1;
-        const float bc1 = 1.f - powf(A.b1, (float)ta);
-        const float sbc2 = sqrtf(1.f - powf(A.b2, (float)ta));
-        if (own) st.th = wrap_pi(st.th + opt_delta<GEN>(A, gth, st.th, st.mth, st.vth, bc1, sbc2));
+        const float lr_bc1 = __fdividef(A.lr, 1.f - ipowf(A.b1, ta));
+        const float rsbc2 = rsqrtf(1.f - ipowf(A.b2, ta));
+        if (own) st.th = wrap_pi(st.th + opt_delta<GEN>(A, gth, st.th, st.mth, st.vth, lr_bc1, rsbc2));
         for (int d = 0; d < 3; ++d) {
             const float lo = A.pk.box_lo[bx][d], hi = A.pk.box_hi[bx][d];
-            const float dlt = opt_delta<GEN>(A, gt[d], st.t[d] - 0.5f * (lo + hi), st.m[d], st.v[d], bc1, sbc2);
+            const float dlt = opt_delta<GEN>(A, gt[d], st.t[d] - 0.5f * (lo + hi), st.m[d], st.v[d], lr_bc1, rsbc2);
             st.t[d] = fminf(fmaxf(st.t[d] + dlt, lo), hi);
         }
         float dw[3];
-        for (int d = 0; d < 3; ++d) dw[d] = opt_delta<GEN>(A, tau[d], 0.f, st.m[3 + d], st.v[3 + d], bc1, sbc2);
+        for (int d = 0; d < 3; ++d) dw[d] = opt_delta<GEN>(A, tau[d], 0.f, st.m[3 + d], st.v[3 + d], lr_bc1, rsbc2);
         const float phi = sqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
         if (phi > 0.f) {
             float sh, ch;
@@ -1101,7 +1112,15 @@ __global__ void __launch_bounds__(512, 1) k_sample_persistent(SampleArgs A) {
         PoseState st;
         if (A.step_begin == 0) init_pose(A, h, W.lane, l, p, st);
         else load_pose(A, h, W.lane, l, p, st);
-        for (int s = A.step_begin; s < A.step_end; ++s) sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, st, npairs);
+        Sched sc = schedule(A.S, A.Lmc, A.step_begin);
+        for (int s = A.step_begin; s < A.step_end; ++s) {
+            sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, sc, st, npairs);
+            if (++sc.j == sc.n) {   // next Monte-Carlo loop: the schedule of evaluation s + 1
+                ++sc.loop;
+                sc.j = 0;
+                sc.n = A.S / A.Lmc + (sc.loop < A.S % A.Lmc ? 1 : 0);
+            }
+        }
         store_pose(A, h, W.lane, l, p, st);
         __syncwarp();
     }
@@ -1124,7 +1143,7 @@ __global__ void __launch_bounds__(512, 1) k_sample_step(SampleArgs A, int l, int
     PoseState st;
     if (s == 0) init_pose(A, h, W.lane, l, p, st);
     else load_pose(A, h, W.lane, l, p, st);
-    sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, st, npairs);
+    sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, schedule(A.S, A.Lmc, s), st, npairs);
     store_pose(A, h, W.lane, l, p, st);
     if (COUNT) flush_count(A.pair_count, npairs);
 }
@@ -1484,6 +1503,8 @@ struct trids_batch {
     float4* d_tor_p = nullptr;
     int* d_ipre = nullptr;
     uint16_t* d_ient = nullptr;
+    int8_t* d_atom_tor = nullptr;
+    int8_t* d_tor_par = nullptr;
     std::vector<uint16_t> ient_j;     // intra partner lists: target index (pad = max_atoms)
     std::vector<uint8_t> ient_type;   // target type (for re-encoding flags)
     trids_pocket* owner = nullptr;    // pocket whose flags are encoded in d_ient
@@ -1507,6 +1528,7 @@ struct trids_batch {
         v.dof_stride = dims.dof_stride; v.n_fields = dims.state_fields;
         v.lig = d_lig; v.atom_y = d_atom_y; v.atom_orig = d_atom_orig; v.tor_idx = d_tor_idx;
         v.tor_u = d_tor_u; v.tor_p = d_tor_p; v.ipre = d_ipre; v.ient = d_ient;
+        v.atom_tor = d_atom_tor; v.tor_par = d_tor_par;
         v.mdn = d_mdn; v.mdn_res = mdn_res; v.mdn_k = mdn_k;
         return v;
     }
@@ -2041,6 +2063,7 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
     std::vector<int4> tidx;
     std::vector<float4> tu, tp;
     std::vector<int> ipre;
+    std::vector<int8_t> atom_tor, tor_par;
     ao = 0;
     for (int l = 0; l < n_lig; ++l) {
         const PackedLigand& lg = b->ligs[l];
@@ -2062,6 +2085,7 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
             ay.push_back(make_float4((float)((double)X[3 * a] - lg.c[0]), (float)((double)X[3 * a + 1] - lg.c[1]),
                                      (float)((double)X[3 * a + 2] - lg.c[2]), tb));
             aorig.push_back(a);
+            atom_tor.push_back((int8_t)(lg.frag[i] - 1));
         }
         for (int k = 0; k < lg.n_tor; ++k) {
             const int pa = lg.perm[lg.tp[k]], ha = lg.perm[lg.th[k]];
@@ -2073,6 +2097,7 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
             nn = std::sqrt(nn);
             if (!(nn > 1e-6)) return fail(TRIDS_EINVAL, "ligand %d: rotatable bond %d has zero length", l, k);
             tidx.push_back(make_int4(lg.tp[k], lg.th[k], lg.sb[k], lg.se[k]));
+            tor_par.push_back((int8_t)lg.tpar[k]);
             tu.push_back(make_float4((float)(u[0] / nn), (float)(u[1] / nn), (float)(u[2] / nn), 0.f));
             tp.push_back(make_float4((float)((double)X[3 * pa] - lg.c[0]), (float)((double)X[3 * pa + 1] - lg.c[1]),
                                      (float)((double)X[3 * pa + 2] - lg.c[2]), 0.f));
@@ -2107,7 +2132,8 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
     }
     if ((rc = upload(&b->d_lig, b->hdr)) || (rc = upload(&b->d_atom_y, ay)) || (rc = upload(&b->d_atom_orig, aorig)) ||
         (rc = upload(&b->d_tor_idx, tidx)) || (rc = upload(&b->d_tor_u, tu)) || (rc = upload(&b->d_tor_p, tp)) ||
-        (rc = upload(&b->d_ipre, ipre)) || (rc = encode_intra(pk, b.get(), true))) {
+        (rc = upload(&b->d_ipre, ipre)) || (rc = upload(&b->d_atom_tor, atom_tor)) ||
+        (rc = upload(&b->d_tor_par, tor_par)) || (rc = encode_intra(pk, b.get(), true))) {
         trids_free_batch(b.release());
         return rc;
     }
@@ -2136,6 +2162,7 @@ int trids_free_batch(trids_batch* b) {
     cudaFree(b->d_lig); cudaFree(b->d_atom_y); cudaFree(b->d_atom_orig); cudaFree(b->d_tor_idx);
     cudaFree(b->d_tor_u); cudaFree(b->d_tor_p); cudaFree(b->d_ipre); cudaFree(b->d_ient); cudaFree(b->d_items); cudaFree(b->d_lig_order);
     cudaFree(b->d_counter); cudaFree(b->d_err); cudaFree(b->d_partials); cudaFree(b->d_mdn);
+    cudaFree(b->d_atom_tor); cudaFree(b->d_tor_par);
     delete b;
     return TRIDS_OK;
 }

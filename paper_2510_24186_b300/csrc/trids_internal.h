@@ -121,6 +121,8 @@ struct DevBatch {
     const int4* tor_idx;           // (parent atom, child atom, subtree begin, subtree end)
     const float4* tor_u;           // unit axis, input geometry
     const float4* tor_p;           // parent atom, local coords
+    const int8_t* atom_tor;        // per packed atom: torsion whose moving fragment holds it (-1: root)
+    const int8_t* tor_par;         // per torsion: parent torsion (-1: child of the root fragment)
     const int* ipre;               // per atom: first block of its intra partner list
     const uint16_t* ient;          // partner index | partner flags << 13; each intra pair appears
                                    // once from each side; padding = max_atoms (far sentinel)
