@@ -134,6 +134,7 @@ typedef struct trids_batch_dims {
     int32_t dof_stride;   /* 7 + max_tor: floats per pose row of a DOF array */
     int32_t state_fields; /* floats per pose of the sampler state buffer */
     int64_t n_intra;      /* intra-ligand pairs over the batch */
+    int64_t upload_bytes; /* host-to-device bytes trids_pack_ligands copied for the batch */
 } trids_batch_dims;
 
 /* Sampler configuration (Sec. 2 "Conformation sampling", Fig. 2). */

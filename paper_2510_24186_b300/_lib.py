@@ -28,7 +28,8 @@ class Params(C.Structure):
 
 class BatchDims(C.Structure):
     _fields_ = [("n_lig", C.c_int32), ("max_atoms", C.c_int32), ("max_tor", C.c_int32),
-                ("dof_stride", C.c_int32), ("state_fields", C.c_int32), ("n_intra", C.c_int64)]
+                ("dof_stride", C.c_int32), ("state_fields", C.c_int32), ("n_intra", C.c_int64),
+                ("upload_bytes", C.c_int64)]
 
 
 class SampleCfg(C.Structure):

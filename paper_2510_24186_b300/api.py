@@ -149,6 +149,7 @@ class Batch:
         check(L.trids_batch_info(h, C.byref(d)))
         self.n_lig, self.max_atoms, self.max_tor = d.n_lig, d.max_atoms, d.max_tor
         self.dof_stride, self.state_fields, self.n_intra = d.dof_stride, d.state_fields, d.n_intra
+        self.upload_bytes = d.upload_bytes
         self.n_tor = np.zeros(self.n_lig, dtype=np.int32)
         self.n_atoms = np.zeros(self.n_lig, dtype=np.int32)
         check(L.trids_batch_query(h, self.n_tor.ctypes.data, self.n_atoms.ctypes.data, 0, None, 0))
@@ -307,12 +308,16 @@ def sync(batch: Batch, poses: int, state: Optional[torch.Tensor] = None, timeout
 
 
 def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd: float = 1.0, seed: int = 0,
-                  mc_loops: int = 8, warps_per_block: int = 0, stream=None):
+                  mc_loops: int = 8, warps_per_block: int = 0, stream=None, stats: Optional[dict] = None,
+                  prepare=None, **sample_kw):
     """Screen an iterable of ligand batches (each a tuple of arrays as for Batch) through one
     pocket.  The next batch is packed on a host thread while the current one samples; the
     DOF, state and energy buffers stay on the device and are reused.  Yields
     (first ligand id, top-k indices [n, k], top-k energies [n, k]) per batch as numpy arrays.
-    Ligand ids (the random-stream ids) run on across batches."""
+    Ligand ids (the random-stream ids) run on across batches.  stats (optional dict) receives
+    the host-to-device and device-to-host bytes of the last batch; prepare(batch), if given,
+    runs on each packed batch before it samples (e.g. Batch.set_mdn); sample_kw go to sample()."""
+    stats = {} if stats is None else stats
     import concurrent.futures as cf
     _require_cuda()
     st = stream or torch.cuda.current_stream()
@@ -327,11 +332,14 @@ def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd:
 
     it = iter(batches)
     base = 0
+    pinned = None
     with cf.ThreadPoolExecutor(max_workers=1) as ex:
         nxt = next(it, None)
         fut = ex.submit(Batch, pocket, *nxt) if nxt is not None else None
         while fut is not None:
             b = fut.result()
+            if prepare is not None:
+                prepare(b)
             nxt = next(it, None)
             fut = ex.submit(Batch, pocket, *nxt) if nxt is not None else None
             D = b.dof_stride
@@ -340,13 +348,17 @@ def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd:
             energy = view("energy", b.n_lig * poses).view(b.n_lig, poses)
             with torch.cuda.stream(st):
                 sample(pocket, b, poses, steps, mc_loops=mc_loops, seed=seed, lig_base=base, dof=dof, state=state,
-                       energy=energy, warps_per_block=warps_per_block, stream=st)
+                       energy=energy, warps_per_block=warps_per_block, stream=st, **sample_kw)
                 idx, e = topk(b, energy, dof, k, rmsd, stream=st)
-                idx_h = torch.empty(idx.shape, dtype=idx.dtype, pin_memory=True)
-                e_h = torch.empty(e.shape, dtype=e.dtype, pin_memory=True)
+                if pinned is None or pinned[0].shape != idx.shape:
+                    pinned = (torch.empty(idx.shape, dtype=idx.dtype, pin_memory=True),
+                              torch.empty(e.shape, dtype=e.dtype, pin_memory=True))
+                idx_h, e_h = pinned
                 idx_h.copy_(idx, non_blocking=True)
                 e_h.copy_(e, non_blocking=True)
             st.synchronize()
+            stats["h2d_bytes"] = b.upload_bytes
+            stats["d2h_bytes"] = idx_h.numel() * idx_h.element_size() + e_h.numel() * e_h.element_size()
             yield base, idx_h.numpy().copy(), e_h.numpy().copy()
             base += b.n_lig
             b.close()

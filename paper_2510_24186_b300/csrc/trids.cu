@@ -2036,22 +2036,40 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
     b->device = pk->device;
     b->n_types = pk->prm.n_types;
     b->ligs.resize(n_lig);
-    size_t ao = 0, bo = 0;
-    int Lmax = 1, Tmax = 0;
-    int64_t npairs = 0;
+    // per-ligand input offsets, then the ligands packed on host threads (each ligand is
+    // independent; the first failing ligand in index order is reported)
+    std::vector<size_t> aoff(n_lig + 1, 0), boff(n_lig + 1, 0);
     for (int l = 0; l < n_lig; ++l) {
         if (n_bonds[l] < 0) return fail(TRIDS_EINVAL, "ligand %d: negative bond count", l);
         if (n_bonds[l] > 0 && (!bonds || !rotatable)) return fail(TRIDS_EINVAL, "bonds is NULL");
-        std::string m = pack_ligand(n_atoms[l], xyz + 3 * ao, type + ao, pk->prm.n_types, n_bonds[l],
-                                    bonds ? bonds + 2 * bo : nullptr, rotatable ? rotatable + bo : nullptr,
-                                    &b->ligs[l]);
-        if (!m.empty()) return fail(TRIDS_EINVAL, "ligand %d: %s", l, m.c_str());
+        if (n_atoms[l] < 0) return fail(TRIDS_EINVAL, "ligand %d: negative atom count", l);
+        aoff[l + 1] = aoff[l] + (size_t)n_atoms[l];
+        boff[l + 1] = boff[l] + (size_t)n_bonds[l];
+    }
+    std::vector<std::string> msg(n_lig);
+    {
+        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+        const int nt = std::max(1, std::min({hw, 32, n_lig / 16}));
+        auto work = [&](int t) {
+            for (int l = t; l < n_lig; l += nt)
+                msg[l] = pack_ligand(n_atoms[l], xyz + 3 * aoff[l], type + aoff[l], pk->prm.n_types, n_bonds[l],
+                                     bonds ? bonds + 2 * boff[l] : nullptr, rotatable ? rotatable + boff[l] : nullptr,
+                                     &b->ligs[l]);
+        };
+        std::vector<std::thread> th;
+        for (int t = 1; t < nt; ++t) th.emplace_back(work, t);
+        work(0);
+        for (auto& x : th) x.join();
+    }
+    int Lmax = 1, Tmax = 0;
+    int64_t npairs = 0;
+    for (int l = 0; l < n_lig; ++l) {
+        if (!msg[l].empty()) return fail(TRIDS_EINVAL, "ligand %d: %s", l, msg[l].c_str());
         Lmax = std::max(Lmax, n_atoms[l]);
         Tmax = std::max(Tmax, b->ligs[l].n_tor);
         npairs += (int64_t)b->ligs[l].pairs.size();
-        ao += n_atoms[l];
-        bo += n_bonds[l];
     }
+    size_t ao = 0;
     b->dims.n_lig = n_lig;
     b->dims.max_atoms = Lmax;
     b->dims.max_tor = Tmax;
@@ -2143,6 +2161,11 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
         trids_free_batch(b.release());
         return rc;
     }
+    b->dims.upload_bytes = (int64_t)(b->hdr.size() * sizeof(LigHdr) + ay.size() * sizeof(float4) +
+                                     aorig.size() * sizeof(int) + atom_tor.size() + tor_par.size() +
+                                     tidx.size() * sizeof(int4) + (tu.size() + tp.size()) * sizeof(float4) +
+                                     ipre.size() * sizeof(int) + b->ient_j.size() * sizeof(uint16_t) +
+                                     zeros.size() * sizeof(unsigned int) + zi.size() * sizeof(int));
     b->owner = const_cast<trids_pocket*>(pk);
     b->owner->batches.push_back(b.get());
     *out = b.release();
