@@ -149,7 +149,7 @@ typedef struct trids_sample_cfg {
     uint64_t seed;           /* Philox4x32-10 key */
     int32_t lig_base;        /* random-stream id of ligand 0 of this batch */
     int32_t mode;            /* TRIDS_MODE_* */
-    int32_t warps_per_block; /* 0 = library default; each warp owns 32 poses of one ligand */
+    int32_t warps_per_block; /* poses (warps) per block, 1..20; 0 = 20, or fewer if the pocket needs the shared memory */
     int32_t use_graph;       /* persistent mode: capture the launch in a CUDA graph and replay it */
     float* trace;            /* nullable device buffer, see trids_sample */
     const int32_t* trace_slot; /* device [n_lig*poses]: trace slot of each pose or -1 */

@@ -26,7 +26,7 @@ import torch
 from . import api
 
 CELLS = (0.5, 0.75, 1.0)
-WARPS = (4, 8, 16)
+WARPS = (8, 16, 20)
 
 
 @dataclasses.dataclass

@@ -170,8 +170,14 @@ __host__ __device__ inline size_t pose_warp_core_bytes(int Lm, int Tm) {
            12 * (size_t)Lm + 4 * (size_t)(Lm + 1);
 }
 
+constexpr size_t kPoseStateBytes = 132;   // sizeof(PoseState), checked below
+// per-warp region: [core][pose state, 32 lanes][per-lane dE/dR (parameter-gradient kernels)]
+__host__ __device__ inline size_t pose_state_off(int Lm, int Tm) { return align_up(pose_warp_core_bytes(Lm, Tm), 16); }
+__host__ __device__ inline size_t pose_grs_off(int Lm, int Tm) {
+    return align_up(pose_state_off(Lm, Tm) + 32 * kPoseStateBytes, 16);
+}
 __host__ __device__ inline size_t pose_warp_bytes(int Lm, int Tm, bool params) {
-    size_t b = align_up(pose_warp_core_bytes(Lm, Tm), 16);
+    size_t b = pose_grs_off(Lm, Tm);
     if (params) b += 4 * (size_t)kNT * 32;
     return align_up(b, 128);
 }
@@ -248,8 +254,13 @@ __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t par
 //   rec float4[Lm + 32] partial ligand-pocket forces, slot (atom + lane)
 //   cs  uint32[Lm]      candidate-list offset of each atom's cell
 //   pre int[Lm + 1]     exclusive prefix of each atom's candidate blocks
+//   pst PoseState[32]   the pose's sampler state, one copy per lane: kept in shared memory
+//                       so that it holds no registers across the pair loop (the sampler then
+//                       fits 96 registers per thread, 20 warps per SM)
 //   grs float[kNT][32]  per-lane dE/dR_a (parameter-gradient kernels only)
+struct PoseState;
 struct PW {
+    PoseState* pst; // [32] the pose's sampler state, one copy per lane (sampler kernels)
     float4* xs;     // [Lm + 1] (x, y, z, radius); xs[Lm] is a far sentinel
     float4* gs;
     float4* rk;
@@ -273,7 +284,8 @@ __device__ __forceinline__ PW make_pw(unsigned char* smem, size_t warp_off, size
     W.cb = reinterpret_cast<int*>(W.cs + Lm);
     W.ip = W.cb + Lm;
     W.pre = W.ip + Lm;
-    W.grs = reinterpret_cast<float*>(base + align_up(pose_warp_core_bytes(Lm, Tm), 16));
+    W.pst = reinterpret_cast<PoseState*>(base + pose_state_off(Lm, Tm));
+    W.grs = reinterpret_cast<float*>(base + pose_grs_off(Lm, Tm));
     W.lane = threadIdx.x & 31;
     return W;
 }
@@ -822,6 +834,7 @@ struct PoseState {
     int status;
     float th, mth, vth, sth;
 };
+static_assert(sizeof(PoseState) == kPoseStateBytes, "PoseState size");
 
 struct SampleArgs {
     DevPocket pk;
@@ -1094,7 +1107,7 @@ __device__ __forceinline__ void flush_count(unsigned long long* cnt, uint32_t n)
 // Persistent fused sampler: each warp pops poses from a global counter (ligands in
 // decreasing-cost order) and runs every evaluation of the pose with its state on chip.
 template <int TS, bool COUNT, bool GEN>
-__global__ void __launch_bounds__(512, 1) k_sample_persistent(SampleArgs A) {
+__global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
     Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
@@ -1109,7 +1122,7 @@ __global__ void __launch_bounds__(512, 1) k_sample_persistent(SampleArgs A) {
         const int l = A.lig_order[it / A.P];
         const int p = it % A.P;
         const LigHdr h = A.B.lig[l];
-        PoseState st;
+        PoseState& st = W.pst[W.lane];   // in shared memory: not held in registers across the pair loop
         if (A.step_begin == 0) init_pose(A, h, W.lane, l, p, st);
         else load_pose(A, h, W.lane, l, p, st);
         Sched sc = schedule(A.S, A.Lmc, A.step_begin);
@@ -1130,7 +1143,7 @@ __global__ void __launch_bounds__(512, 1) k_sample_persistent(SampleArgs A) {
 // Plain form: one launch per (ligand, evaluation), one warp per pose, the state in
 // global memory between launches; the same device code as the persistent sampler.
 template <int TS, bool COUNT, bool GEN>
-__global__ void __launch_bounds__(512, 1) k_sample_step(SampleArgs A, int l, int s) {
+__global__ void __launch_bounds__(640, 1) k_sample_step(SampleArgs A, int l, int s) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
     Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
@@ -1140,7 +1153,7 @@ __global__ void __launch_bounds__(512, 1) k_sample_step(SampleArgs A, int l, int
     if (p >= A.P) return;
     const LigHdr h = A.B.lig[l];
     uint32_t npairs = 0;
-    PoseState st;
+    PoseState& st = W.pst[W.lane];
     if (s == 0) init_pose(A, h, W.lane, l, p, st);
     else load_pose(A, h, W.lane, l, p, st);
     sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, schedule(A.S, A.Lmc, s), st, npairs);
@@ -1698,7 +1711,7 @@ size_t max_smem(int dev) {
 // Pick warps per block: the requested count, capped so the block fits in shared memory.
 int pick_warps(int requested, const trids_pocket* pk, const trids_batch* b, bool params, Layout* L) {
     const size_t cap = max_smem(pk->device);
-    int w = requested > 0 ? std::min(requested, 16) : 8;
+    int w = requested > 0 ? std::min(requested, 20) : 8;
     for (; w >= 1; --w) {
         *L = make_layout(pk->prm.term_set, pk->M, b->dims.max_atoms, b->dims.max_tor, w, params);
         if (L->total <= cap) return w;
@@ -2355,7 +2368,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         return rc;
     if ((rc = ensure_items(b, c.poses))) return rc;
     Layout L;
-    const int warps = pick_warps(c.warps_per_block, pk, b, false, &L);
+    const int warps = pick_warps(c.warps_per_block > 0 ? c.warps_per_block : 20, pk, b, false, &L);
     if (!warps) return fail(TRIDS_EINVAL, "pocket of %d atoms does not fit in shared memory", pk->M);
     SampleArgs A;
     std::memset(&A, 0, sizeof A);  // the bytes form the graph-cache key
