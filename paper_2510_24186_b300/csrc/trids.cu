@@ -429,6 +429,90 @@ __device__ __forceinline__ void vina_x2(uint32_t wd, const float4* __restrict__ 
     if (COUNT) cnt += ((r2.x < cut2) + (r2.y < cut2)) * cw;
 }
 
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The TRIDS atom-pair terms (pair_trids) for the two candidates of one candidate-list
+// word, branch-free on the packed FP32 pipe: every term is evaluated and masked (cutoff,
+// r < 10 for E_long, r < d_clash, donor-acceptor pair with r < 3.4, r < 5 for the
+// atom-pair E_MDN) by
+// multiplying with 0/1, exact for the finite values every candidate gives.  exp and log
+// go through ex2 / lg2.  mb selects the candidate's donor/acceptor flag bits (low entry;
+// shifted by 16 for the high entry).  gmm (term set 1, ligand-pocket pairs only; else
+// null): the ligand atom type's row of (pi, mu, -1/(2 sigma^2), 1/sigma^2) by pocket type.
+template <bool COUNT>
+__device__ __forceinline__ void trids_x2(uint32_t wd, const float4* __restrict__ src, float2 nxy, float2 nzr,
+                                         float cut2, const float w[5], uint32_t mb, const float4* __restrict__ gmm,
+                                         const uint8_t* __restrict__ ptype, int K, float2& eb, float& ax, float& ay,
+                                         float& az, uint32_t& cnt, uint32_t cw) {
+    constexpr float kL2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
+    const uint32_t ja = wd & 0x1fffu, jb = (wd >> 16) & 0x1fffu;
+    const float4 a = src[ja], c = src[jb];
+    const float2 pm = make_float2(1.f, -1.f);
+    const float2 pa = __fadd2_rn(make_float2(a.x, a.y), nxy);
+    const float2 qa = __ffma2_rn(make_float2(a.z, a.w), pm, nzr);      // (z_j - z_i, -(R_i + R_j))
+    const float2 pc = __fadd2_rn(make_float2(c.x, c.y), nxy);
+    const float2 qc = __ffma2_rn(make_float2(c.z, c.w), pm, nzr);
+    const float2 sa = __fmul2_rn(pa, pa), sc = __fmul2_rn(pc, pc);
+    const float2 r2 = make_float2(fmaf(qa.x, qa.x, sa.x) + sa.y, fmaf(qc.x, qc.x, sc.x) + sc.y);
+    const float2 in = make_float2(r2.x < cut2 ? 1.f : 0.f, r2.y < cut2 ? 1.f : 0.f);
+    const float2 rr = __fadd2_rn(r2, make_float2(1e-12f, 1e-12f));
+    const float2 ri = make_float2(rsqrtf(rr.x), rsqrtf(rr.y));
+    const float2 r = __fmul2_rn(rr, ri);
+    const float2 rs = make_float2(-qa.y, -qc.y);                            // R_i + R_j
+    const float2 hb = make_float2((wd & mb) ? 1.f : 0.f, (wd & (mb << 16)) ? 1.f : 0.f);
+    // E_long: -exp(-(r - R_i - R_j - 3)^2 / 4); dE/dr = 0.5 gl z
+    const float2 z = __fadd2_rn(r, make_float2(qa.y - 3.f, qc.y - 3.f));
+    const float2 al = __fmul2_rn(__fmul2_rn(z, z), make_float2(-0.25f * kL2e, -0.25f * kL2e));
+    const float2 gl = make_float2(r.x < 10.f ? ex2_approx(al.x) : 0.f, r.y < 10.f ? ex2_approx(al.y) : 0.f);
+    float2 e = __fmul2_rn(make_float2(-w[1], -w[1]), gl);
+    float2 d = __fmul2_rn(__fmul2_rn(make_float2(0.5f * w[1], 0.5f * w[1]), gl), z);
+    // E_clash: -ln(max(r, 0.5) / d_clash) for r < d_clash (2.6 for a donor-acceptor pair,
+    // else R_i + R_j); dE/dr = -1/r above 0.5
+    const float2 dcl = make_float2(hb.x != 0.f ? 2.6f : rs.x, hb.y != 0.f ? 2.6f : rs.y);
+    const float2 mcl = make_float2(r.x < dcl.x ? 1.f : 0.f, r.y < dcl.y ? 1.f : 0.f);
+    const float2 lr = make_float2(lg2_approx(fmaxf(r.x, 0.5f)) - lg2_approx(dcl.x),
+                                  lg2_approx(fmaxf(r.y, 0.5f)) - lg2_approx(dcl.y));
+    e = __ffma2_rn(__fmul2_rn(mcl, make_float2(-w[2] * kLn2, -w[2] * kLn2)), lr, e);
+    const float2 m05 = make_float2(r.x < 0.5f ? 0.f : mcl.x, r.y < 0.5f ? 0.f : mcl.y);
+    d = __ffma2_rn(__fmul2_rn(m05, make_float2(-w[2], -w[2])), ri, d);
+    // E_Hbond: -exp(-(r - 2.88)^2 / (2 0.3^2)) for donor-acceptor pairs with r < 3.4
+    const float2 mh = make_float2(r.x < 3.4f ? hb.x : 0.f, r.y < 3.4f ? hb.y : 0.f);
+    const float2 zh = __fadd2_rn(r, make_float2(-2.88f, -2.88f));
+    const float2 ah = __fmul2_rn(__fmul2_rn(zh, zh), make_float2(-kL2e / 0.18f, -kL2e / 0.18f));
+    const float2 gh = __fmul2_rn(mh, make_float2(ex2_approx(ah.x), ex2_approx(ah.y)));
+    e = __ffma2_rn(make_float2(-w[3], -w[3]), gh, e);
+    d = __ffma2_rn(__fmul2_rn(make_float2(w[3] / 0.09f, w[3] / 0.09f), gh), zh, d);
+    // E_MDN over atom pairs (term set 1, ligand-pocket): -sum_k pi_k exp(-(r - mu_k)^2 / (2 sigma_k^2))
+    if (gmm) {
+        const float2 m5 = make_float2(r.x < 5.f ? 1.f : 0.f, r.y < 5.f ? 1.f : 0.f);
+        const float4* __restrict__ ga = gmm + ptype[ja] * kK;
+        const float4* __restrict__ gc = gmm + ptype[jb] * kK;
+        float2 e0 = make_float2(0.f, 0.f), d0 = make_float2(0.f, 0.f);
+        for (int k = 0; k < K; ++k) {
+            const float4 u = ga[k], v = gc[k];
+            const float2 zz = __fadd2_rn(r, make_float2(-u.y, -v.y));
+            const float2 ar = __fmul2_rn(__fmul2_rn(zz, zz), make_float2(u.z * kL2e, v.z * kL2e));
+            const float2 ex = __fmul2_rn(make_float2(u.x, v.x), make_float2(ex2_approx(ar.x), ex2_approx(ar.y)));
+            e0 = __fadd2_rn(e0, ex);
+            d0 = __ffma2_rn(__fmul2_rn(ex, zz), make_float2(u.w, v.w), d0);
+        }
+        e = __ffma2_rn(__fmul2_rn(m5, make_float2(-w[0], -w[0])), e0, e);
+        d = __ffma2_rn(__fmul2_rn(m5, make_float2(w[0], w[0])), d0, d);
+    }
+    eb = __ffma2_rn(e, in, eb);
+    // force on i: dE/dr / r * (x_i - x_j) = -dE/dr / r * p
+    const float2 f = __fmul2_rn(__fmul2_rn(d, in), make_float2(-ri.x, -ri.y));
+    float2 axy = make_float2(ax, ay);
+    axy = __ffma2_rn(make_float2(f.x, f.x), pa, axy); az = fmaf(f.x, qa.x, az);
+    axy = __ffma2_rn(make_float2(f.y, f.y), pc, axy); az = fmaf(f.y, qc.x, az);
+    ax = axy.x; ay = axy.y;
+    if (COUNT) cnt += ((r2.x < cut2) + (r2.y < cut2)) * cw;
+}
+
 // Candidate-grid cell range (entries [beg, end) of pk.cand) of a point; empty outside
 // the grid, where no pocket atom lies within the cutoff.
 __device__ __forceinline__ void cell_range(const DevPocket& pk, const uint32_t* __restrict__ starts, float x, float y,
@@ -609,6 +693,12 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                     for (int u = 0; u < 2; ++u)
                         vina_x2<COUNT>(wv[u], src, nxy, nzr, cut2, K, mh, mb, eb2, ax, ay, az, npairs,
                                        intra ? 1u : 2u);   // doubled: intra pairs come twice
+                } else if constexpr (!PARAMS) {
+                    const float4* gm = (TS == TRIDS_TERMS_TRIDS && !intra) ? &P.gmm[ti][0][0] : nullptr;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+                        trids_x2<COUNT>(wv[u], src, nxy, nzr, cut2, w, mb, gm, S.ptype, P.gmm_k, eb2, ax, ay, az,
+                                        npairs, intra ? 1u : 2u);
                 } else {
 #pragma unroll
                     for (int s = 0; s < 4; ++s) {
@@ -655,7 +745,7 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                     }
                 }
             }
-            if (TS == TRIDS_TERMS_VINA5 && !PARAMS) eb = eb2.x + eb2.y;
+            if (!PARAMS) eb = eb2.x + eb2.y;
             if (intra) e_in += eb; else e_lp += eb;
         }
         W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
