@@ -808,29 +808,78 @@ __device__ __noinline__ float map_warp(const DevBatch& B, const DevPocket& pk, c
 }
 
 // Residue-level E_MDN of the warp's pose (term set 2; Sec. 2, Eqs. P(d) and E_MDN): for
-// each ligand atom (one lane per atom) and each residue listed for its cell, the
-// minimum distance d over the residue's atoms; d < 5 A adds
-// -w0 sum_k pi_k exp(-(d - mu_k)^2 / (2 sigma_k^2)), with the force along the nearest
-// atom (strict < over ascending atom indices keeps the lowest index on ties).  Adds the
-// forces to W.gs (each lane owns its atoms' rows) and returns the lane's energy.
+// each ligand atom and each residue listed for its cell, the minimum distance d over the
+// residue's atoms (one contiguous range of the staged pocket, ascending input index, so a
+// strict < keeps the lowest index on ties); d < 5 A adds
+// -w0 sum_k pi_k exp(-(d - mu_k)^2 / (2 sigma_k^2)) with the force along the nearest atom.
+// The (atom, residue) items are numbered atom by atom and split into 32 equal contiguous
+// segments, one per lane, as in the pair loop; per-atom partial forces go to slot
+// (atom + lane) of W.rec and are added to W.gs in lane order.  Returns the lane's energy.
 template <bool PARAMS>
 __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
                               float w0, float ebar, ParamAcc& acc) {
     constexpr float kCut2 = kMdnCut * kMdnCut;
-    const int K = B.mdn_k, R = B.mdn_res;
+    constexpr float kL2e = 1.4426950408889634f;
+    const int K = B.mdn_k, R = B.mdn_res, L = h.n_atoms, lane = W.lane;
+    int carry = 0;
+    for (int base = 0; base < L; base += 32) {
+        const int i = base + lane;
+        int n = 0;
+        if (i < L) {
+            const float4 x = W.xs[i];
+            uint32_t beg, end;
+            cell_range(pk, pk.rcell_start, x.x, x.y, x.z, beg, end);
+            W.cs[i] = beg;
+            n = (int)(end - beg);
+        }
+        int v = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += t;
+        }
+        if (i < L) W.pre[i + 1] = carry + v;
+        carry += __shfl_sync(kFull, v, 31);
+    }
+    if (lane == 0) W.pre[0] = 0;
+    for (int r = lane; r < L + 32; r += 32) W.rec[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    const int N = carry;
+    const int lo = (int)(((long long)N * lane) >> 5), hi = (int)(((long long)N * (lane + 1)) >> 5);
     float e = 0.f;
-    for (int i = W.lane; i < h.n_atoms; i += 32) {
-        const float4 x = W.xs[i];
-        uint32_t beg, end;
-        cell_range(pk, pk.rcell_start, x.x, x.y, x.z, beg, end);
+    if (lo < hi) {
+        int i = 0;
+        {
+            int a = 0, b = L - 1;
+            while (a < b) {
+                const int m = (a + b + 1) >> 1;
+                if (W.pre[m] <= lo) a = m; else b = m - 1;
+            }
+            i = a;
+        }
+        int first = W.pre[i], nxt = W.pre[i + 1];
+        uint32_t cs = W.cs[i];
+        float4 x = W.xs[i];
         const float4* __restrict__ kern = B.mdn + (size_t)(h.atom_off + i) * R * K;
         float gx = 0.f, gy = 0.f, gz = 0.f, ei = 0.f;
-        for (uint32_t q = beg; q < end; ++q) {
-            const int r = __ldg(&pk.rlist[q]);
+        for (int it = lo; it < hi; ++it) {
+            if (it == nxt) {                       // move to the atom owning item it
+                W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
+                e = fmaf(w0, ei, e);
+                if (PARAMS) acc.gw[0] = fmaf(ebar, ei, acc.gw[0]);
+                gx = gy = gz = ei = 0.f;
+                do { ++i; } while (W.pre[i + 1] == it);
+                first = W.pre[i];
+                nxt = W.pre[i + 1];
+                cs = W.cs[i];
+                x = W.xs[i];
+                kern = B.mdn + (size_t)(h.atom_off + i) * R * K;
+            }
+            const int r = __ldg(&pk.rlist[cs + (uint32_t)(it - first)]);
             const int a1 = __ldg(&pk.res_start[r + 1]);
             float best = 3.0e38f, bx = 0.f, by = 0.f, bz = 0.f;
             for (int a = __ldg(&pk.res_start[r]); a < a1; ++a) {
-                const float4 p = S.pocket[__ldg(&pk.res_atoms[a])];
+                const float4 p = S.pocket[a];
                 const float dx = x.x - p.x, dy = x.y - p.y, dz = x.z - p.z;
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                 if (r2 < best) { best = r2; bx = dx; by = dy; bz = dz; }
@@ -842,7 +891,7 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
                 for (int k = 0; k < K; ++k) {
                     const float4 g = __ldg(&kern[r * K + k]);   // (pi, mu, -1/(2 sigma^2), 1/sigma^2)
                     const float z = d - g.y;
-                    const float ex = g.x * __expf(g.z * z * z);
+                    const float ex = g.x * ex2_approx(g.z * kL2e * z * z);
                     P += ex;
                     dP = fmaf(-ex * z, g.w, dP);                // dP/dd
                 }
@@ -851,11 +900,24 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
                 gx = fmaf(f, bx, gx); gy = fmaf(f, by, gy); gz = fmaf(f, bz, gz);
             }
         }
-        float4 g = W.gs[i];
-        g.x += gx; g.y += gy; g.z += gz;
-        W.gs[i] = g;
+        W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
         e = fmaf(w0, ei, e);
         if (PARAMS) acc.gw[0] = fmaf(ebar, ei, acc.gw[0]);
+    }
+    __syncwarp();
+    for (int i = lane; i < L; i += 32) {
+        const int b0 = W.pre[i], b1 = W.pre[i + 1];
+        if (b0 < b1) {
+            float gx = 0.f, gy = 0.f, gz = 0.f;
+            const int l0 = min(31, (32 * (b0 + 1) - 1) / N), l1 = min(31, (32 * b1 - 1) / N);
+            for (int l = l0; l <= l1; ++l) {
+                const float4 q = W.rec[i + l];
+                gx += q.x; gy += q.y; gz += q.z;
+            }
+            float4 g = W.gs[i];
+            g.x += gx; g.y += gy; g.z += gz;
+            W.gs[i] = g;
+        }
     }
     __syncwarp();
     return e;
@@ -1544,8 +1606,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 struct trids_pocket {
     int device = 0;
     int M = 0;
-    std::vector<float> xyz;
+    std::vector<float> xyz;            // storage order (grouped by residue after trids_set_residues)
     std::vector<int> type;
+    std::vector<int> orig;             // storage index -> input index
     uint8_t* d_ptype = nullptr;
     std::vector<trids_batch*> batches;   // batches whose intra entries carry this pocket's flags
     float cutoff_built = 0.f;
@@ -1565,13 +1628,12 @@ struct trids_pocket {
     bool maps_stale = false;             // parameters changed since the maps were built
     ResidueGrid rgrid;                   // residue-level E_MDN (term set 2)
     int32_t* d_res_start = nullptr;
-    uint16_t* d_res_atoms = nullptr;
     uint32_t* d_rcell = nullptr;
     uint16_t* d_rlist = nullptr;
     DevPocket view() const {
         DevPocket v;
         v.atoms = d_atoms; v.ptype = d_ptype; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
-        v.n_res = rgrid.n_res; v.res_start = d_res_start; v.res_atoms = d_res_atoms; v.rcell_start = d_rcell;
+        v.n_res = rgrid.n_res; v.res_start = d_res_start; v.rcell_start = d_rcell;
         v.rlist = d_rlist;
         v.use_maps = d_maps != nullptr;
         v.mx = mdims[0]; v.my = mdims[1]; v.mz = mdims[2];
@@ -1928,6 +1990,8 @@ int trids_make_pocket(const float* xyz, const int32_t* type, int32_t n_atoms, co
     pk->cell = cell > 0.f ? cell : 0.5f;
     pk->xyz.assign(xyz, xyz + 3 * (size_t)n_atoms);
     pk->type.assign(type, type + n_atoms);
+    pk->orig.resize(n_atoms);
+    for (int j = 0; j < n_atoms; ++j) pk->orig[j] = j;
     for (int d = 0; d < 3; ++d) {
         for (int b = 0; b < kMaxBoxes; ++b) {
             pk->box_lo[b][d] = box_center[d] - 0.5f * box_size[d];
@@ -1999,7 +2063,6 @@ int trids_free_pocket(trids_pocket* pk) {
     cudaFree(pk->d_params);
     cudaFree(pk->d_maps);
     cudaFree(pk->d_res_start);
-    cudaFree(pk->d_res_atoms);
     cudaFree(pk->d_rcell);
     cudaFree(pk->d_rlist);
     delete pk;
@@ -2018,19 +2081,49 @@ int trids_set_residues(trids_pocket* pk, int32_t n_res, const int32_t* residue) 
         if (residue[j] < 0 || residue[j] >= n_res) return fail(TRIDS_EINVAL, "atom %d: residue out of range", j);
     int rc = device_guard(pk->device);
     if (rc) return rc;
+    // Store the pocket atoms grouped by residue (ascending input index inside a residue), so
+    // that a residue is one contiguous range of the staged pocket.  residue[] is indexed by
+    // input atom; pk->orig maps the current storage order to input indices.
+    const int M = pk->M;
+    std::vector<int> order(M);
+    for (int c = 0; c < M; ++c) order[c] = c;
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        const int ra = residue[pk->orig[a]], rb = residue[pk->orig[b]];
+        return ra != rb ? ra < rb : pk->orig[a] < pk->orig[b];
+    });
+    std::vector<float> xyz(3 * (size_t)M);
+    std::vector<int> type(M), orig(M), res_sorted(M);
+    for (int c = 0; c < M; ++c) {
+        for (int d = 0; d < 3; ++d) xyz[3 * c + d] = pk->xyz[3 * order[c] + d];
+        type[c] = pk->type[order[c]];
+        orig[c] = pk->orig[order[c]];
+        res_sorted[c] = residue[orig[c]];
+    }
+    CandidateGrid grid;
+    build_grid(M, xyz.data(), pk->cutoff_built, pk->cell, &grid);
+    if (grid.cand.size() != pk->grid.cand.size() || grid.start.size() != pk->grid.start.size())
+        return fail(TRIDS_ECUDA, "internal: the reordered candidate grid changed size");
     ResidueGrid rg;
-    build_residue_grid(pk->M, pk->xyz.data(), residue, n_res, pk->grid, &rg);
+    build_residue_grid(M, xyz.data(), res_sorted.data(), n_res, grid, &rg);
     int32_t* d_start = nullptr;
-    uint16_t *d_atoms = nullptr, *d_list = nullptr;
+    uint16_t* d_list = nullptr;
     uint32_t* d_cell = nullptr;
-    if ((rc = upload(&d_start, rg.start)) || (rc = upload(&d_atoms, rg.atoms)) || (rc = upload(&d_cell, rg.cell_start)) ||
-        (rc = upload(&d_list, rg.list))) {
-        cudaFree(d_start); cudaFree(d_atoms); cudaFree(d_cell); cudaFree(d_list);
+    if ((rc = upload(&d_start, rg.start)) || (rc = upload(&d_cell, rg.cell_start)) || (rc = upload(&d_list, rg.list))) {
+        cudaFree(d_start); cudaFree(d_cell); cudaFree(d_list);
         return rc;
     }
     CK(cudaDeviceSynchronize());   // no launch may still read the arrays being replaced
-    cudaFree(pk->d_res_start); cudaFree(pk->d_res_atoms); cudaFree(pk->d_rcell); cudaFree(pk->d_rlist);
-    pk->d_res_start = d_start; pk->d_res_atoms = d_atoms; pk->d_rcell = d_cell; pk->d_rlist = d_list;
+    std::vector<uint8_t> ptype(align_up((size_t)M + 1, 16), 0);
+    for (int j = 0; j < M; ++j) ptype[j] = (uint8_t)type[j];
+    CK(cudaMemcpy(pk->d_ptype, ptype.data(), ptype.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pk->d_cell, grid.start.data(), grid.start.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    pk->xyz.swap(xyz);
+    pk->type.swap(type);
+    pk->orig.swap(orig);
+    pk->grid = std::move(grid);
+    if ((rc = upload_pocket_arrays(pk, nullptr))) return rc;   // atoms + candidate entries with flags
+    cudaFree(pk->d_res_start); cudaFree(pk->d_rcell); cudaFree(pk->d_rlist);
+    pk->d_res_start = d_start; pk->d_rcell = d_cell; pk->d_rlist = d_list;
     pk->rgrid = std::move(rg);
     return TRIDS_OK;
 }

@@ -55,9 +55,10 @@ struct CandidateGrid {
 void build_grid(int M, const float* xyz, float cutoff, float h, CandidateGrid* g);
 
 // Residue lists of the residue-level E_MDN.  Atoms are grouped by residue (ascending
-// atom index inside a residue, so the first minimum met is the lowest index).  On the
-// candidate grid's cells, each cell lists (ascending) every residue with an atom within
-// kMdnCut + half the cell diagonal (+ a small margin) of the cell centre.
+// atom index inside a residue, so the first minimum met is the lowest index; the library
+// stores the pocket in that order once residues are set).  On the candidate grid's cells,
+// each cell lists (ascending) every residue with an atom within kMdnCut + half the cell
+// diagonal (+ a small margin) of the cell centre.
 constexpr float kMdnCut = 5.0f;   // Sec. 2: node pairs closer than d_cutoff = 5 A
 struct ResidueGrid {
     int n_res = 0;
@@ -101,8 +102,7 @@ struct DevPocket {
     const float* maps;
     // residue-level E_MDN (term set 2)
     int n_res;
-    const int32_t* res_start;      // [n_res + 1]
-    const uint16_t* res_atoms;     // atoms grouped by residue
+    const int32_t* res_start;      // [n_res + 1]: residue r = staged pocket atoms [start[r], start[r+1])
     const uint32_t* rcell_start;   // [ncell + 1], same cells as cell_start
     const uint16_t* rlist;         // residues near each cell
 };
