@@ -323,7 +323,11 @@ void build_residue_grid(int M, const float* xyz, const int32_t* res, int n_res, 
     out->list.assign(total, 0);
     std::fill(mark.begin(), mark.end(), -1);
     std::vector<uint32_t> fill(out->cell_start.begin(), out->cell_start.end() - 1);
-    for (int r = 0; r < n_res; ++r) visit_residue(r, [&](size_t cell) { out->list[fill[cell]++] = (uint16_t)r; });
+    for (int r = 0; r < n_res; ++r) {
+        const uint32_t ent = (uint32_t)r | ((uint32_t)out->start[r] << 13) |
+                             ((uint32_t)(out->start[r + 1] - out->start[r]) << 26);
+        visit_residue(r, [&](size_t cell) { out->list[fill[cell]++] = ent; });
+    }
 }
 
 }  // namespace trids

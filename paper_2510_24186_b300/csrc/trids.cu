@@ -862,6 +862,7 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
         float4 x = W.xs[i];
         const float4* __restrict__ kern = B.mdn + (size_t)(h.atom_off + i) * R * K;
         float gx = 0.f, gy = 0.f, gz = 0.f, ei = 0.f;
+        uint32_t ent = __ldg(&pk.rlist[cs + (uint32_t)(lo - first)]);
         for (int it = lo; it < hi; ++it) {
             if (it == nxt) {                       // move to the atom owning item it
                 W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
@@ -874,11 +875,14 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
                 cs = W.cs[i];
                 x = W.xs[i];
                 kern = B.mdn + (size_t)(h.atom_off + i) * R * K;
+                ent = __ldg(&pk.rlist[cs + (uint32_t)(it - first)]);
             }
-            const int r = __ldg(&pk.rlist[cs + (uint32_t)(it - first)]);
-            const int a1 = __ldg(&pk.res_start[r + 1]);
+            const uint32_t cur = ent;
+            if (it + 1 < hi && it + 1 < nxt) ent = __ldg(&pk.rlist[cs + (uint32_t)(it + 1 - first)]);   // prefetch
+            const int r = (int)(cur & 0x1fffu);
+            const int a0 = (int)((cur >> 13) & 0x1fffu), a1 = a0 + (int)(cur >> 26);
             float best = 3.0e38f, bx = 0.f, by = 0.f, bz = 0.f;
-            for (int a = __ldg(&pk.res_start[r]); a < a1; ++a) {
+            for (int a = a0; a < a1; ++a) {
                 const float4 p = S.pocket[a];
                 const float dx = x.x - p.x, dy = x.y - p.y, dz = x.z - p.z;
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -1629,7 +1633,7 @@ struct trids_pocket {
     ResidueGrid rgrid;                   // residue-level E_MDN (term set 2)
     int32_t* d_res_start = nullptr;
     uint32_t* d_rcell = nullptr;
-    uint16_t* d_rlist = nullptr;
+    uint32_t* d_rlist = nullptr;
     DevPocket view() const {
         DevPocket v;
         v.atoms = d_atoms; v.ptype = d_ptype; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
@@ -2077,8 +2081,14 @@ int trids_set_residues(trids_pocket* pk, int32_t n_res, const int32_t* residue) 
     if (pk->cutoff_built < kMdnCut)
         return fail(TRIDS_EINVAL, "the pocket grid was built for cutoff %.3f; residue terms need >= 5",
                     pk->cutoff_built);
-    for (int j = 0; j < pk->M; ++j)
-        if (residue[j] < 0 || residue[j] >= n_res) return fail(TRIDS_EINVAL, "atom %d: residue out of range", j);
+    {
+        std::vector<int> count(n_res, 0);
+        for (int j = 0; j < pk->M; ++j) {
+            if (residue[j] < 0 || residue[j] >= n_res) return fail(TRIDS_EINVAL, "atom %d: residue out of range", j);
+            if (++count[residue[j]] > kMaxResidueAtoms)
+                return fail(TRIDS_EINVAL, "residue %d has more than %d atoms", residue[j], kMaxResidueAtoms);
+        }
+    }
     int rc = device_guard(pk->device);
     if (rc) return rc;
     // Store the pocket atoms grouped by residue (ascending input index inside a residue), so
@@ -2106,7 +2116,7 @@ int trids_set_residues(trids_pocket* pk, int32_t n_res, const int32_t* residue) 
     ResidueGrid rg;
     build_residue_grid(M, xyz.data(), res_sorted.data(), n_res, grid, &rg);
     int32_t* d_start = nullptr;
-    uint16_t* d_list = nullptr;
+    uint32_t* d_list = nullptr;
     uint32_t* d_cell = nullptr;
     if ((rc = upload(&d_start, rg.start)) || (rc = upload(&d_cell, rg.cell_start)) || (rc = upload(&d_list, rg.list))) {
         cudaFree(d_start); cudaFree(d_cell); cudaFree(d_list);

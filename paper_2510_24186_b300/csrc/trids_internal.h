@@ -60,12 +60,13 @@ void build_grid(int M, const float* xyz, float cutoff, float h, CandidateGrid* g
 // each cell lists (ascending) every residue with an atom within kMdnCut + half the cell
 // diagonal (+ a small margin) of the cell centre.
 constexpr float kMdnCut = 5.0f;   // Sec. 2: node pairs closer than d_cutoff = 5 A
+constexpr int kMaxResidueAtoms = 63;
 struct ResidueGrid {
     int n_res = 0;
     std::vector<int32_t> start;        // [n_res + 1] offsets into atoms
     std::vector<uint16_t> atoms;       // pocket atom indices grouped by residue
     std::vector<uint32_t> cell_start;  // [ncell + 1]
-    std::vector<uint16_t> list;        // residue indices
+    std::vector<uint32_t> list;        // residue r | first atom << 13 | atom count << 26
 };
 void build_residue_grid(int M, const float* xyz, const int32_t* res, int n_res, const CandidateGrid& g,
                         ResidueGrid* out);
@@ -104,7 +105,7 @@ struct DevPocket {
     int n_res;
     const int32_t* res_start;      // [n_res + 1]: residue r = staged pocket atoms [start[r], start[r+1])
     const uint32_t* rcell_start;   // [ncell + 1], same cells as cell_start
-    const uint16_t* rlist;         // residues near each cell
+    const uint32_t* rlist;         // residues near each cell: r | first atom << 13 | atom count << 26
 };
 
 struct LigHdr {

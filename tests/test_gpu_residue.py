@@ -170,6 +170,10 @@ def test_residue_inputs_are_checked(api):
         api.score_grad(pk, b, dof)
     with pytest.raises(TridsError):
         pk.set_residues(np.full(len(res), -1))
+    big = np.arange(len(res)) % 200
+    big[:64] = 0                                  # one residue of 64 atoms: above the 63-atom limit
+    with pytest.raises(TridsError, match="more than 63"):
+        pk.set_residues(big)
     small = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size,
                        api.ScoreParams(2, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.TRIDS_WEIGHTS, 4.0))
     with pytest.raises(TridsError, match="cutoff"):
