@@ -229,7 +229,7 @@ def main():
     arrays = synth.concat_ligands(w.ligands)
     tuned = None
     if sp.term_set != 0:
-        args.cell, args.warps = args.cell or 0.5, args.warps or 16
+        args.cell, args.warps = args.cell or 0.5, args.warps or 20
     if not args.cell and not args.warps:
         from paper_2510_24186_b300 import autotune
         tuned = autotune.autotune(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, arrays, w.poses)
