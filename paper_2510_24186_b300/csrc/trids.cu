@@ -170,11 +170,13 @@ __host__ __device__ inline size_t pose_warp_core_bytes(int Lm, int Tm) {
            12 * (size_t)Lm + 4 * (size_t)(Lm + 1);
 }
 
-constexpr size_t kPoseStateBytes = 132;   // sizeof(PoseState), checked below
-// per-warp region: [core][pose state, 32 lanes][per-lane dE/dR (parameter-gradient kernels)]
+constexpr size_t kRigidStateBytes = 128;   // sizeof(RigidState), checked below
+constexpr size_t kTorStateBytes = 16;      // sizeof(TorState)
+// per-warp region: [core][rigid pose state][torsion state, 32 lanes][per-lane dE/dR
+// (parameter-gradient kernels)]
 __host__ __device__ inline size_t pose_state_off(int Lm, int Tm) { return align_up(pose_warp_core_bytes(Lm, Tm), 16); }
 __host__ __device__ inline size_t pose_grs_off(int Lm, int Tm) {
-    return align_up(pose_state_off(Lm, Tm) + 32 * kPoseStateBytes, 16);
+    return align_up(pose_state_off(Lm, Tm) + kRigidStateBytes + 32 * kTorStateBytes, 16);
 }
 __host__ __device__ inline size_t pose_warp_bytes(int Lm, int Tm, bool params) {
     size_t b = pose_grs_off(Lm, Tm);
@@ -254,13 +256,18 @@ __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t par
 //   rec float4[Lm + 32] partial ligand-pocket forces, slot (atom + lane)
 //   cs  uint32[Lm]      candidate-list offset of each atom's cell
 //   pre int[Lm + 1]     exclusive prefix of each atom's candidate blocks
-//   pst PoseState[32]   the pose's sampler state, one copy per lane: kept in shared memory
-//                       so that it holds no registers across the pair loop (the sampler then
-//                       fits 96 registers per thread, 20 warps per SM)
+//   rig RigidState      the pose's rigid sampler state (t, q, Adam moments, saved state,
+//                       loop energies, status), one copy per warp: every lane computes the
+//                       same values
+//   tor TorState[32]    lane k's torsion angle, moments and saved angle
+//                       (kept in shared memory, the state holds no registers across the pair
+//                       loop: the sampler fits 96 registers per thread, 20 warps per SM)
 //   grs float[kNT][32]  per-lane dE/dR_a (parameter-gradient kernels only)
-struct PoseState;
+struct RigidState;
+struct TorState;
 struct PW {
-    PoseState* pst; // [32] the pose's sampler state, one copy per lane (sampler kernels)
+    RigidState* rig;  // the pose's rigid sampler state (sampler kernels)
+    TorState* tor;    // [32] per-lane torsion state (sampler kernels)
     float4* xs;     // [Lm + 1] (x, y, z, radius); xs[Lm] is a far sentinel
     float4* gs;
     float4* rk;
@@ -284,7 +291,8 @@ __device__ __forceinline__ PW make_pw(unsigned char* smem, size_t warp_off, size
     W.cb = reinterpret_cast<int*>(W.cs + Lm);
     W.ip = W.cb + Lm;
     W.pre = W.ip + Lm;
-    W.pst = reinterpret_cast<PoseState*>(base + pose_state_off(Lm, Tm));
+    W.rig = reinterpret_cast<RigidState*>(base + pose_state_off(Lm, Tm));
+    W.tor = reinterpret_cast<TorState*>(base + pose_state_off(Lm, Tm) + kRigidStateBytes);
     W.grs = reinterpret_cast<float*>(base + pose_grs_off(Lm, Tm));
     W.lane = threadIdx.x & 31;
     return W;
@@ -982,15 +990,38 @@ __device__ float adjoint_warp(const DevBatch& B, const LigHdr& h, const PW& W, c
 }
 
 // ------------------------------------------------------------------ sampler state
-// Rigid state is held by every lane; lane k < T holds torsion k's angle, Adam moments
-// and saved angle.
-struct PoseState {
+// The rigid state is the same on every lane (every lane computes it); lane k < T holds
+// torsion k's angle, Adam moments and saved angle.  PoseState is a handle on the warp's
+// shared-memory copy.
+struct RigidState {
     float t[3], q[4], m[6], v[6], st[3], sq[4];
     float ecur, esaved;
     int status;
+    float pad[3];
+};
+struct TorState {
     float th, mth, vth, sth;
 };
-static_assert(sizeof(PoseState) == kPoseStateBytes, "PoseState size");
+static_assert(sizeof(RigidState) == kRigidStateBytes && sizeof(TorState) == kTorStateBytes, "pose state size");
+
+struct PoseState {
+    float (&t)[3];
+    float (&q)[4];
+    float (&m)[6];
+    float (&v)[6];
+    float (&st)[3];
+    float (&sq)[4];
+    float& ecur;
+    float& esaved;
+    int& status;
+    float& th;
+    float& mth;
+    float& vth;
+    float& sth;
+    __device__ PoseState(RigidState& r, TorState& k)
+        : t(r.t), q(r.q), m(r.m), v(r.v), st(r.st), sq(r.sq), ecur(r.ecur), esaved(r.esaved), status(r.status),
+          th(k.th), mth(k.mth), vth(k.vth), sth(k.sth) {}
+};
 
 struct SampleArgs {
     DevPocket pk;
@@ -1155,6 +1186,7 @@ __device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float p
 template <int TS, bool COUNT, bool GEN>
 __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h, const PW& W, int l, int p, int s,
                             const Sched& sc, PoseState& st, uint32_t& npairs) {
+    __syncwarp();               // the rigid state is one shared copy written by every lane
     if (st.status & 1) return;  // frozen after a non-finite energy
     const int T = h.n_tor, lane = W.lane;
     const int bx = A.pk.n_boxes > 1 ? p % A.pk.n_boxes : 0;   // the pose's docking box
@@ -1278,9 +1310,10 @@ __global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
         const int l = A.lig_order[it / A.P];
         const int p = it % A.P;
         const LigHdr h = A.B.lig[l];
-        PoseState& st = W.pst[W.lane];   // in shared memory: not held in registers across the pair loop
+        PoseState st(*W.rig, W.tor[W.lane]);   // in shared memory: no registers across the pair loop
         if (A.step_begin == 0) init_pose(A, h, W.lane, l, p, st);
         else load_pose(A, h, W.lane, l, p, st);
+        __syncwarp();
         Sched sc = schedule(A.S, A.Lmc, A.step_begin);
         for (int s = A.step_begin; s < A.step_end; ++s) {
             sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, sc, st, npairs);
@@ -1290,6 +1323,7 @@ __global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
                 sc.n = A.S / A.Lmc + (sc.loop < A.S % A.Lmc ? 1 : 0);
             }
         }
+        __syncwarp();
         store_pose(A, h, W.lane, l, p, st);
         __syncwarp();
     }
@@ -1309,10 +1343,12 @@ __global__ void __launch_bounds__(640, 1) k_sample_step(SampleArgs A, int l, int
     if (p >= A.P) return;
     const LigHdr h = A.B.lig[l];
     uint32_t npairs = 0;
-    PoseState& st = W.pst[W.lane];
+    PoseState st(*W.rig, W.tor[W.lane]);
     if (s == 0) init_pose(A, h, W.lane, l, p, st);
     else load_pose(A, h, W.lane, l, p, st);
+    __syncwarp();
     sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, schedule(A.S, A.Lmc, s), st, npairs);
+    __syncwarp();
     store_pose(A, h, W.lane, l, p, st);
     if (COUNT) flush_count(A.pair_count, npairs);
 }
