@@ -119,3 +119,44 @@ def test_map_rules(api):
     assert torch.allclose(e_map, e_direct, rtol=0.05, atol=0.5)
     with pytest.raises(TridsError):
         pk.build_maps(0.01, 8.0)
+
+
+def test_maps_with_residue_terms(api):
+    """Term set 2 with grid maps: the maps hold the atom-pair physics terms, the residue-level
+    E_MDN stays direct; every pose checked against the oracle's map form with residues."""
+    w = synth.workload(1)
+    sp = api.ScoreParams(2, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.TRIDS_WEIGHTS, 10.0)
+    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
+    rng = np.random.default_rng(61)
+    res = synth.gen_residues(rng, w.pocket.xyz)
+    pk.set_residues(res)
+    pk.build_maps(0.375, 6.0)
+    b = api.Batch.from_ligands(pk, w.ligands)
+    mdn = synth.gen_mdn(rng, int(b.n_atoms.sum()), int(res.max()) + 1, 3)
+    b.set_mdn(torch.from_numpy(mdn).cuda())
+    P = 48
+    dof = synth.random_dofs(rng, b.n_tor, P, w.box_center - w.box_size / 2, w.box_center + w.box_size / 2,
+                            b.dof_stride)
+    out = api.score_grad(pk, b, torch.from_numpy(dof).cuda(), grad=True)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in out.items()}
+    op = oracle_params(sp)
+    mp = oracle_maps(pk)
+    md = oracle.mdn(res, mdn.astype(np.float64))
+    pxyz, ptype = pocket_arrays(w.pocket)
+    lg = oracle_ligands(w.ligands)[0]
+    T = lg.n_tor
+    st = Stats()
+    mapped = res_pairs = 0
+    for p in range(P):
+        _, ev = oracle.score(op, pxyz, ptype, lg, dof[0, p, :7 + T], md, mp)
+        mapped += ev.n_map_atoms
+        res_pairs += ev.n_res_pairs
+        st.n += 1
+        energy_ok(out["energy"][0, p], ev, st, f"pose {p}")
+        sl = grad_slack(ev)
+        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], sl + round_slack(ev, 0, 3), st, f"pose {p} t")
+        block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"pose {p} q")
+        block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"pose {p} th")
+    assert mapped > 0 and res_pairs > 0
+    report(st, "maps + residue E_MDN")
