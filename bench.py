@@ -131,6 +131,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(mhz)}
 
 
+def gemm_load_mhz():
+    """Median SM clock a seconds-long dense bf16 GEMM settled at on this pool (measured peaks)."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["clocks_under_load"]["sm_mhz_median"])
+    except Exception:
+        return None
+
+
 def cpu_threads():
     try:
         return len(os.sched_getaffinity(0))
@@ -389,11 +397,23 @@ def main():
     }
     if clocks["sm_mhz"]:
         line["roofline"]["frac_at_load_clock"] = achieved / (peak * clocks["sm_mhz"] / mhz)
+    gemm_mhz = gemm_load_mhz()
+    if gemm_mhz:
+        # the same fraction against the clock a power-capped dense GEMM settles at on this part
+        line["roofline"]["frac_at_gemm_load_clock"] = achieved / (peak * gemm_mhz / mhz)
+        line["roofline"]["gemm_load_mhz"] = gemm_mhz
     if not args.no_cpu and world == 1:
         r, cores, n, dt = oracle_sample_rate(w, budget_s=12.0, terms=args.terms)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"first {n} ligands x {P} poses x {S} evaluations, FP64 all-pairs "
                                           f"oracle, {dt:.1f} s"}
+        if args.terms == "vina5":
+            w1 = synth.workload(1)
+            r1, c1, n1, dt1 = oracle_sample_rate(w1, budget_s=0.0, max_ligs=1, n_threads=1)
+            line["cpu_baseline_config1"] = {"value": r1, "unit": UNIT, "cores": c1, "kind": "oracle",
+                                            "sample": f"the single-ligand workload in full ({w1.poses} poses x "
+                                                      f"{w1.steps} evaluations, 300-atom pocket), one thread, "
+                                                      f"{dt1:.2f} s"}
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
