@@ -330,4 +330,43 @@ void build_residue_grid(int M, const float* xyz, const int32_t* res, int n_res, 
     }
 }
 
+void build_near_lists(int M, const float* xyz, float cutoff, const CandidateGrid& g, std::vector<uint32_t>* start,
+                      std::vector<uint16_t>* list) {
+    const int nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
+    const double h = g.h;
+    const size_t ncell = (size_t)nx * ny * nz;
+    const double reach = cutoff + 0.5 * std::sqrt(3.0) * h + 1e-3 * h + 1e-4;
+    const double reach2 = reach * reach;
+    const int span = (int)std::ceil(reach / h) + 1;
+    auto visit = [&](int j, auto&& fn) {
+        const double p[3] = {xyz[3 * j], xyz[3 * j + 1], xyz[3 * j + 2]};
+        int c[3];
+        for (int d = 0; d < 3; ++d) c[d] = (int)std::floor((p[d] - g.lo[d]) / h);
+        for (int iz = std::max(0, c[2] - span); iz <= std::min(nz - 1, c[2] + span); ++iz) {
+            const double cz = g.lo[2] + (iz + 0.5) * h - p[2];
+            for (int iy = std::max(0, c[1] - span); iy <= std::min(ny - 1, c[1] + span); ++iy) {
+                const double cy = g.lo[1] + (iy + 0.5) * h - p[1];
+                const double r2yz = cy * cy + cz * cz;
+                if (r2yz > reach2) continue;
+                for (int ix = std::max(0, c[0] - span); ix <= std::min(nx - 1, c[0] + span); ++ix) {
+                    const double cx = g.lo[0] + (ix + 0.5) * h - p[0];
+                    if (cx * cx + r2yz <= reach2) fn(((size_t)iz * ny + iy) * nx + ix);
+                }
+            }
+        }
+    };
+    std::vector<uint32_t> count(ncell, 0);
+    for (int j = 0; j < M; ++j) visit(j, [&](size_t cell) { ++count[cell]; });
+    start->assign(ncell + 1, 0);
+    size_t total = 0;
+    for (size_t c = 0; c < ncell; ++c) {
+        (*start)[c] = (uint32_t)total;
+        total += count[c];
+    }
+    (*start)[ncell] = (uint32_t)total;
+    list->assign(total, 0);
+    std::vector<uint32_t> fill(start->begin(), start->end() - 1);
+    for (int j = 0; j < M; ++j) visit(j, [&](size_t cell) { (*list)[fill[cell]++] = (uint16_t)j; });
+}
+
 }  // namespace trids

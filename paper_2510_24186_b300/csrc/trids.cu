@@ -702,7 +702,7 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                         vina_x2<COUNT>(wv[u], src, nxy, nzr, cut2, K, mh, mb, eb2, ax, ay, az, npairs,
                                        intra ? 1u : 2u);   // doubled: intra pairs come twice
                 } else if constexpr (!PARAMS) {
-                    const float4* gm = (TS == TRIDS_TERMS_TRIDS && !intra) ? &P.gmm[ti][0][0] : nullptr;
+                    const float4* gm = nullptr;   // term set 1: the atom-pair E_MDN runs in gmm_warp
 #pragma unroll
                     for (int u = 0; u < 2; ++u)
                         trids_x2<COUNT>(wv[u], src, nxy, nzr, cut2, w, mb, gm, S.ptype, P.gmm_k, eb2, ax, ay, az,
@@ -810,6 +810,117 @@ __device__ __noinline__ float map_warp(const DevBatch& B, const DevPocket& pk, c
         g.y = fmaf(dy, pk.inv_mh, g.y);
         g.z = fmaf(dz, pk.inv_mh, g.z);
         W.gs[i] = g;
+    }
+    __syncwarp();
+    return e;
+}
+
+// Atom-pair E_MDN of the warp's pose (term set 1; Sec. 2, Eqs. P(d) and E_MDN on atom
+// pairs): each ligand atom against the pocket atoms of its cell's near list (within 5 A
+// plus half the cell diagonal); a pair with r < min(5 A, cutoff) adds
+// -w0 sum_k pi_k exp(-(r - mu_k)^2 / (2 sigma_k^2)) with (pi, mu, sigma) by the atom-type
+// pair.  A separate pass over these short lists keeps the K Gaussians off the 10 A pair
+// loop (about 1 in 8 of its candidates is within 5 A).  Items (atom, near-list entry) are
+// split into 32 equal contiguous lane segments; per-atom partials go to slot (atom + lane)
+// of W.rec and are added to W.gs in lane order.  Atoms that the grid maps cover are
+// skipped (their maps hold this term).  Returns the lane's energy.
+template <bool MAPS>
+__device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
+                          float w0) {
+    constexpr float kL2e = 1.4426950408889634f;
+    const DevParams& P = *S.P;
+    const int K = P.gmm_k, L = h.n_atoms, lane = W.lane;
+    const float nc2 = pk.near_cut2;
+    int carry = 0;
+    for (int base = 0; base < L; base += 32) {
+        const int i = base + lane;
+        int n = 0;
+        if (i < L) {
+            const float4 x = W.xs[i];
+            uint32_t beg = 0, end = 0;
+            if (!(MAPS && map_cell(pk, x.x, x.y, x.z, nullptr))) cell_range(pk, pk.ncell_start, x.x, x.y, x.z, beg, end);
+            W.cs[i] = beg;
+            n = (int)(end - beg);
+        }
+        int v = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += t;
+        }
+        if (i < L) W.pre[i + 1] = carry + v;
+        carry += __shfl_sync(kFull, v, 31);
+    }
+    if (lane == 0) W.pre[0] = 0;
+    for (int r = lane; r < L + 32; r += 32) W.rec[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    const int N = carry;
+    const int lo = (int)(((long long)N * lane) >> 5), hi = (int)(((long long)N * (lane + 1)) >> 5);
+    float e = 0.f;
+    if (lo < hi) {
+        int i = 0;
+        {
+            int a = 0, b = L - 1;
+            while (a < b) {
+                const int m = (a + b + 1) >> 1;
+                if (W.pre[m] <= lo) a = m; else b = m - 1;
+            }
+            i = a;
+        }
+        int first = W.pre[i], nxt = W.pre[i + 1];
+        uint32_t cs = W.cs[i];
+        float4 x = W.xs[i];
+        const float4* g = &P.gmm[__float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w)][0][0];
+        float gx = 0.f, gy = 0.f, gz = 0.f, ei = 0.f;
+        for (int it = lo; it < hi; ++it) {
+            if (it == nxt) {
+                W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
+                e = fmaf(w0, ei, e);
+                gx = gy = gz = ei = 0.f;
+                do { ++i; } while (W.pre[i + 1] == it);
+                first = W.pre[i];
+                nxt = W.pre[i + 1];
+                cs = W.cs[i];
+                x = W.xs[i];
+                g = &P.gmm[__float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w)][0][0];
+            }
+            const int j = __ldg(&pk.nlist[cs + (uint32_t)(it - first)]);
+            const float4 p = S.pocket[j];
+            const float dx = x.x - p.x, dy = x.y - p.y, dz = x.z - p.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float in = r2 < nc2 ? 1.f : 0.f;
+            const float rinv = rsqrtf(fmaxf(r2, 1e-12f));
+            const float r = r2 * rinv;
+            const float4* gk = g + S.ptype[j] * kK;
+            float e0 = 0.f, d0 = 0.f;
+            for (int k = 0; k < K; ++k) {
+                const float4 u = gk[k];                          // (pi, mu, -1/(2 sigma^2), 1/sigma^2)
+                const float z = r - u.y;
+                const float ex = u.x * ex2_approx(u.z * kL2e * z * z);
+                e0 += ex;
+                d0 = fmaf(ex * z, u.w, d0);
+            }
+            ei = fmaf(-in, e0, ei);
+            const float f = in * w0 * d0 * rinv;                 // (dE/dr) / r
+            gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
+        }
+        W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
+        e = fmaf(w0, ei, e);
+    }
+    __syncwarp();
+    for (int i = lane; i < L; i += 32) {
+        const int b0 = W.pre[i], b1 = W.pre[i + 1];
+        if (b0 < b1) {
+            float gx = 0.f, gy = 0.f, gz = 0.f;
+            const int l0 = min(31, (32 * (b0 + 1) - 1) / N), l1 = min(31, (32 * b1 - 1) / N);
+            for (int l = l0; l <= l1; ++l) {
+                const float4 q = W.rec[i + l];
+                gx += q.x; gy += q.y; gz += q.z;
+            }
+            float4 gg = W.gs[i];
+            gg.x += gx; gg.y += gy; gg.z += gz;
+            W.gs[i] = gg;
+        }
     }
     __syncwarp();
     return e;
@@ -945,6 +1056,7 @@ __device__ float score_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
     float ein2;
     float el = pairs_warp<TS, PARAMS, COUNT, MAPS>(B, pk, S, h, W, w, ebar, acc, npairs, &ein2);
     if (MAPS && pk.use_maps) el += map_warp(B, pk, h, W);
+    if constexpr (TS == TRIDS_TERMS_TRIDS && !PARAMS) el += gmm_warp<MAPS>(B, pk, S, h, W, w[0]);
     if constexpr (TS == TRIDS_TERMS_TRIDS_RES) el += residue_warp<PARAMS>(B, pk, S, h, W, w[0], ebar, acc);
     const float e_lp = warp_sum(el);
     *e_inter = e_lp;
@@ -1662,6 +1774,8 @@ struct trids_pocket {
     uint32_t* d_cell = nullptr;
     uint16_t* d_cand = nullptr;
     DevParams* d_params = nullptr;
+    uint32_t* d_ncell = nullptr;         // near lists of the atom-pair E_MDN (term set 1)
+    uint16_t* d_nlist = nullptr;
     float* d_maps = nullptr;             // grid maps [type][z][y][x]
     int mdims[3] = {0, 0, 0};
     float mlo[3] = {0.f, 0.f, 0.f}, mh = 0.f;
@@ -1675,6 +1789,11 @@ struct trids_pocket {
         v.atoms = d_atoms; v.ptype = d_ptype; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
         v.n_res = rgrid.n_res; v.res_start = d_res_start; v.rcell_start = d_rcell;
         v.rlist = d_rlist;
+        v.ncell_start = d_ncell; v.nlist = d_nlist;
+        {
+            const float nc = std::min(kMdnCut, prm.cutoff);
+            v.near_cut2 = nc * nc;
+        }
         v.use_maps = d_maps != nullptr;
         v.mx = mdims[0]; v.my = mdims[1]; v.mz = mdims[2];
         for (int d = 0; d < 3; ++d) v.mlo[d] = mlo[d];
@@ -1934,6 +2053,26 @@ int check_device_ptr(const void* p, const char* name, bool nullable) {
     return TRIDS_OK;
 }
 
+// Near lists of the atom-pair E_MDN on the pocket's current grid (storage order).
+int upload_near_lists(trids_pocket* pk) {
+    std::vector<uint32_t> start;
+    std::vector<uint16_t> list;
+    build_near_lists(pk->M, pk->xyz.data(), std::min(kMdnCut, pk->cutoff_built), pk->grid, &start, &list);
+    uint32_t* d_start = nullptr;
+    uint16_t* d_list = nullptr;
+    int rc;
+    if ((rc = upload(&d_start, start)) || (rc = upload(&d_list, list))) {
+        cudaFree(d_start);
+        cudaFree(d_list);
+        return rc;
+    }
+    cudaFree(pk->d_ncell);
+    cudaFree(pk->d_nlist);
+    pk->d_ncell = d_start;
+    pk->d_nlist = d_list;
+    return TRIDS_OK;
+}
+
 // Inputs a term set needs beyond the pocket and the batch.
 int check_terms(const trids_pocket* pk, const trids_batch* b) {
     if (pk->d_maps && pk->maps_stale)
@@ -2047,7 +2186,8 @@ int trids_make_pocket(const float* xyz, const int32_t* type, int32_t n_atoms, co
     std::vector<DevParams> hp(1, pk->hp);
     if ((rc = upload(&pk->d_atoms, atoms)) || (rc = upload(&pk->d_ptype, ptype)) ||
         (rc = upload(&pk->d_cell, pk->grid.start)) || (rc = upload(&pk->d_cand, pk->grid.cand)) ||
-        (rc = upload(&pk->d_params, hp)) || (rc = upload_pocket_arrays(pk.get(), nullptr))) {
+        (rc = upload(&pk->d_params, hp)) || (rc = upload_pocket_arrays(pk.get(), nullptr)) ||
+        (rc = upload_near_lists(pk.get()))) {
         trids_free_pocket(pk.release());
         return rc;
     }
@@ -2102,6 +2242,8 @@ int trids_free_pocket(trids_pocket* pk) {
     cudaFree(pk->d_cand);
     cudaFree(pk->d_params);
     cudaFree(pk->d_maps);
+    cudaFree(pk->d_ncell);
+    cudaFree(pk->d_nlist);
     cudaFree(pk->d_res_start);
     cudaFree(pk->d_rcell);
     cudaFree(pk->d_rlist);
@@ -2168,6 +2310,7 @@ int trids_set_residues(trids_pocket* pk, int32_t n_res, const int32_t* residue) 
     pk->orig.swap(orig);
     pk->grid = std::move(grid);
     if ((rc = upload_pocket_arrays(pk, nullptr))) return rc;   // atoms + candidate entries with flags
+    if ((rc = upload_near_lists(pk))) return rc;
     cudaFree(pk->d_res_start); cudaFree(pk->d_rcell); cudaFree(pk->d_rlist);
     pk->d_res_start = d_start; pk->d_rcell = d_cell; pk->d_rlist = d_list;
     pk->rgrid = std::move(rg);

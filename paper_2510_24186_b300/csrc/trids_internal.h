@@ -71,6 +71,12 @@ struct ResidueGrid {
 void build_residue_grid(int M, const float* xyz, const int32_t* res, int n_res, const CandidateGrid& g,
                         ResidueGrid* out);
 
+// Near lists of the atom-pair E_MDN (term set 1, r < 5 A): on the candidate grid's cells,
+// each cell lists (ascending) the pocket atoms within `cutoff` + half the cell diagonal
+// (+ a small margin) of the cell centre.  No padding.
+void build_near_lists(int M, const float* xyz, float cutoff, const CandidateGrid& g, std::vector<uint32_t>* start,
+                      std::vector<uint16_t>* list);
+
 // ---------------------------------------------------------------- device views
 // Staged into shared memory by every block: the Vina-form path copies the prefix up
 // to `gmm`, the TRIDS path the whole struct.
@@ -101,6 +107,10 @@ struct DevPocket {
     int mx, my, mz;
     float mlo[3], mh, inv_mh;
     const float* maps;
+    // near lists of the atom-pair E_MDN (term set 1), same cells as cell_start
+    const uint32_t* ncell_start;
+    const uint16_t* nlist;
+    float near_cut2;               // min(5 A, cutoff)^2
     // residue-level E_MDN (term set 2)
     int n_res;
     const int32_t* res_start;      // [n_res + 1]: residue r = staged pocket atoms [start[r], start[r+1])
