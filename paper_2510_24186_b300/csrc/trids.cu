@@ -1000,13 +1000,30 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
             if (it + 1 < hi && it + 1 < nxt) ent = __ldg(&pk.rlist[cs + (uint32_t)(it + 1 - first)]);   // prefetch
             const int r = (int)(cur & 0x1fffu);
             const int a0 = (int)((cur >> 13) & 0x1fffu), a1 = a0 + (int)(cur >> 26);
-            float best = 3.0e38f, bx = 0.f, by = 0.f, bz = 0.f;
-            for (int a = a0; a < a1; ++a) {
-                const float4 p = S.pocket[a];
-                const float dx = x.x - p.x, dy = x.y - p.y, dz = x.z - p.z;
-                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                if (r2 < best) { best = r2; bx = dx; by = dy; bz = dz; }
+            // two interleaved streams (even / odd offsets), each keeping its first minimum;
+            // the merge takes the smaller distance, on a tie the lower atom index: the same
+            // atom a single ascending scan with a strict < would keep
+            float b0 = 3.0e38f, b1 = 3.0e38f;
+            int i0 = a0, i1 = a0;
+            int a = a0;
+            for (; a + 1 < a1; a += 2) {
+                const float4 p = S.pocket[a], q = S.pocket[a + 1];
+                const float px = x.x - p.x, py = x.y - p.y, pz = x.z - p.z;
+                const float qx = x.x - q.x, qy = x.y - q.y, qz = x.z - q.z;
+                const float rp = fmaf(pz, pz, fmaf(py, py, px * px)), rq = fmaf(qz, qz, fmaf(qy, qy, qx * qx));
+                if (rp < b0) { b0 = rp; i0 = a; }
+                if (rq < b1) { b1 = rq; i1 = a + 1; }
             }
+            if (a < a1) {
+                const float4 p = S.pocket[a];
+                const float px = x.x - p.x, py = x.y - p.y, pz = x.z - p.z;
+                const float rp = fmaf(pz, pz, fmaf(py, py, px * px));
+                if (rp < b0) { b0 = rp; i0 = a; }
+            }
+            const bool take1 = b1 < b0 || (b1 == b0 && i1 < i0);
+            const float best = take1 ? b1 : b0;
+            const float4 pb = S.pocket[take1 ? i1 : i0];
+            const float bx = x.x - pb.x, by = x.y - pb.y, bz = x.z - pb.z;
             if (best < kCut2) {
                 const float rinv = rsqrtf(fmaxf(best, 1e-12f));
                 const float d = best * rinv;
