@@ -588,6 +588,74 @@ __device__ void fk_warp(const DevBatch& B, const LigHdr& h, const PW& W, const f
     __syncwarp();
 }
 
+// ------------------------------------------------------------------ balanced item loops
+// The pair loop and the E_MDN passes number a pose's work items atom by atom and give
+// lane k the k-th of 32 equal contiguous segments.  A lane accumulates its current atom's
+// force in registers and leaves a partial in slot (atom + lane) of W.rec: slots are unique
+// because atoms never decrease along the lanes.  The partials of an atom are then added in
+// lane order, so the result does not depend on timing.
+
+// Per-atom item counts -> exclusive prefix W.pre[0..L], 32 atoms per call: atom i =
+// base + lane has n items (0 for i >= L); carry runs over the calls.  seg_finish then sets
+// W.pre[0], clears W.rec and returns the total.
+__device__ __forceinline__ void seg_scan(const PW& W, int L, int i, int n, int& carry) {
+    const int lane = W.lane;
+    int v = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    if (i < L) W.pre[i + 1] = carry + v;
+    carry += __shfl_sync(kFull, v, 31);
+}
+
+__device__ __forceinline__ int seg_finish(const PW& W, int L, int carry) {
+    if (W.lane == 0) W.pre[0] = 0;
+    for (int r = W.lane; r < L + 32; r += 32) W.rec[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    return carry;
+}
+
+// The lane's item range [lo, hi) of N items and the atom holding item lo (when lo < hi).
+__device__ __forceinline__ int seg_range(const PW& W, int L, int N, int& lo, int& hi) {
+    lo = (int)(((long long)N * W.lane) >> 5);
+    hi = (int)(((long long)N * (W.lane + 1)) >> 5);
+    int a = 0, b = L - 1;
+    while (a < b) {
+        const int m = (a + b + 1) >> 1;
+        if (W.pre[m] <= lo) a = m; else b = m - 1;
+    }
+    return a;
+}
+
+// Each atom's partials in lane order: W.gs[i] = sum (ADD: W.gs[i] += sum).
+template <bool ADD>
+__device__ __forceinline__ void seg_combine(const PW& W, int L, int N) {
+    __syncwarp();
+    for (int i = W.lane; i < L; i += 32) {
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        const int b0 = W.pre[i], b1 = W.pre[i + 1];
+        if (b0 < b1) {
+            const int l0 = min(31, (32 * (b0 + 1) - 1) / N), l1 = min(31, (32 * b1 - 1) / N);
+            for (int l = l0; l <= l1; ++l) {
+                const float4 r = W.rec[i + l];
+                gx += r.x; gy += r.y; gz += r.z;
+            }
+        }
+        if (ADD) {
+            if (b0 < b1) {
+                float4 g = W.gs[i];
+                g.x += gx; g.y += gy; g.z += gz;
+                W.gs[i] = g;
+            }
+        } else {
+            W.gs[i] = make_float4(gx, gy, gz, 0.f);
+        }
+    }
+    __syncwarp();
+}
+
 // All pairs of the warp's pose.  Atom i's work list is its cell's candidate pocket atoms
 // followed by its intra-ligand partners (every intra pair appears once from each side),
 // both in blocks of 8 uint16 entries (target index, 13 bits | target's flags << 13;
@@ -625,31 +693,13 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             W.ip[i] = i0;
             nblk = cbk + (i1 - i0);
         }
-        int v = nblk;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int n = __shfl_up_sync(kFull, v, o);
-            if (lane >= o) v += n;
-        }
-        if (i < L) W.pre[i + 1] = carry + v;
-        carry += __shfl_sync(kFull, v, 31);
+        seg_scan(W, L, i, nblk, carry);
     }
-    if (lane == 0) W.pre[0] = 0;
-    for (int r = lane; r < L + 32; r += 32) W.rec[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncwarp();
-    const int N = carry;
-    const int lo = (int)(((long long)N * lane) >> 5), hi = (int)(((long long)N * (lane + 1)) >> 5);
+    const int N = seg_finish(W, L, carry);
+    int lo, hi;
+    int i = seg_range(W, L, N, lo, hi);
     float e_lp = 0.f, e_in = 0.f;
     if (lo < hi) {
-        int i = 0;
-        {
-            int a = 0, b = L - 1;
-            while (a < b) {
-                const int m = (a + b + 1) >> 1;
-                if (W.pre[m] <= lo) a = m; else b = m - 1;
-            }
-            i = a;
-        }
         int first = W.pre[i], nxt = W.pre[i + 1], cbk = W.cb[i], ipb = W.ip[i];
         uint32_t csb = W.cs[i];
         float4 xa = W.xs[i];
@@ -758,21 +808,8 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
         }
         W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
     }
-    __syncwarp();
     // 2. add each atom's partials in lane order
-    for (int i = lane; i < L; i += 32) {
-        float gx = 0.f, gy = 0.f, gz = 0.f;
-        const int b0 = W.pre[i], b1 = W.pre[i + 1];
-        if (b0 < b1) {
-            const int l0 = min(31, (32 * (b0 + 1) - 1) / N), l1 = min(31, (32 * b1 - 1) / N);
-            for (int l = l0; l <= l1; ++l) {
-                const float4 r = W.rec[i + l];
-                gx += r.x; gy += r.y; gz += r.z;
-            }
-        }
-        W.gs[i] = make_float4(gx, gy, gz, 0.f);
-    }
-    __syncwarp();
+    seg_combine<false>(W, L, N);
     *e_in2 = e_in;
     return e_lp;
 }
@@ -842,31 +879,13 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
             W.cs[i] = beg;
             n = (int)(end - beg);
         }
-        int v = n;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, v, o);
-            if (lane >= o) v += t;
-        }
-        if (i < L) W.pre[i + 1] = carry + v;
-        carry += __shfl_sync(kFull, v, 31);
+        seg_scan(W, L, i, n, carry);
     }
-    if (lane == 0) W.pre[0] = 0;
-    for (int r = lane; r < L + 32; r += 32) W.rec[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncwarp();
-    const int N = carry;
-    const int lo = (int)(((long long)N * lane) >> 5), hi = (int)(((long long)N * (lane + 1)) >> 5);
+    const int N = seg_finish(W, L, carry);
+    int lo, hi;
+    int i = seg_range(W, L, N, lo, hi);
     float e = 0.f;
     if (lo < hi) {
-        int i = 0;
-        {
-            int a = 0, b = L - 1;
-            while (a < b) {
-                const int m = (a + b + 1) >> 1;
-                if (W.pre[m] <= lo) a = m; else b = m - 1;
-            }
-            i = a;
-        }
         int first = W.pre[i], nxt = W.pre[i + 1];
         uint32_t cs = W.cs[i];
         float4 x = W.xs[i];
@@ -907,22 +926,7 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
         W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
         e = fmaf(w0, ei, e);
     }
-    __syncwarp();
-    for (int i = lane; i < L; i += 32) {
-        const int b0 = W.pre[i], b1 = W.pre[i + 1];
-        if (b0 < b1) {
-            float gx = 0.f, gy = 0.f, gz = 0.f;
-            const int l0 = min(31, (32 * (b0 + 1) - 1) / N), l1 = min(31, (32 * b1 - 1) / N);
-            for (int l = l0; l <= l1; ++l) {
-                const float4 q = W.rec[i + l];
-                gx += q.x; gy += q.y; gz += q.z;
-            }
-            float4 gg = W.gs[i];
-            gg.x += gx; gg.y += gy; gg.z += gz;
-            W.gs[i] = gg;
-        }
-    }
-    __syncwarp();
+    seg_combine<true>(W, L, N);
     return e;
 }
 
@@ -951,31 +955,13 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
             W.cs[i] = beg;
             n = (int)(end - beg);
         }
-        int v = n;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, v, o);
-            if (lane >= o) v += t;
-        }
-        if (i < L) W.pre[i + 1] = carry + v;
-        carry += __shfl_sync(kFull, v, 31);
+        seg_scan(W, L, i, n, carry);
     }
-    if (lane == 0) W.pre[0] = 0;
-    for (int r = lane; r < L + 32; r += 32) W.rec[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncwarp();
-    const int N = carry;
-    const int lo = (int)(((long long)N * lane) >> 5), hi = (int)(((long long)N * (lane + 1)) >> 5);
+    const int N = seg_finish(W, L, carry);
+    int lo, hi;
+    int i = seg_range(W, L, N, lo, hi);
     float e = 0.f;
     if (lo < hi) {
-        int i = 0;
-        {
-            int a = 0, b = L - 1;
-            while (a < b) {
-                const int m = (a + b + 1) >> 1;
-                if (W.pre[m] <= lo) a = m; else b = m - 1;
-            }
-            i = a;
-        }
         int first = W.pre[i], nxt = W.pre[i + 1];
         uint32_t cs = W.cs[i];
         float4 x = W.xs[i];
@@ -1044,22 +1030,7 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
         e = fmaf(w0, ei, e);
         if (PARAMS) acc.gw[0] = fmaf(ebar, ei, acc.gw[0]);
     }
-    __syncwarp();
-    for (int i = lane; i < L; i += 32) {
-        const int b0 = W.pre[i], b1 = W.pre[i + 1];
-        if (b0 < b1) {
-            float gx = 0.f, gy = 0.f, gz = 0.f;
-            const int l0 = min(31, (32 * (b0 + 1) - 1) / N), l1 = min(31, (32 * b1 - 1) / N);
-            for (int l = l0; l <= l1; ++l) {
-                const float4 q = W.rec[i + l];
-                gx += q.x; gy += q.y; gz += q.z;
-            }
-            float4 g = W.gs[i];
-            g.x += gx; g.y += gy; g.z += gz;
-            W.gs[i] = g;
-        }
-    }
-    __syncwarp();
+    seg_combine<true>(W, L, N);
     return e;
 }
 
