@@ -66,7 +66,9 @@ def mdn_kernels(w, n_atoms_total, res):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("paper_2510_24186_b300/csrc/trids.cu", "paper_2510_24186_b300/csrc/trids_internal.h"):
+    for f in ("trids.cu", "trids_internal.h", "device_core.cuh", "device_passes.cuh", "device_kernels.cuh",
+              "host_objects.cuh"):
+        f = os.path.join("paper_2510_24186_b300", "csrc", f)
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 

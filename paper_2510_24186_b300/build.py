@@ -9,7 +9,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libtrids.so")
 SOURCES = [os.path.join(CSRC, f) for f in ("trids.cu", "pack.cpp")]
-HEADERS = [os.path.join(CSRC, "trids_internal.h"), os.path.join(ROOT, "include", "trids.h")]
+HEADERS = [os.path.join(CSRC, f) for f in ("trids_internal.h", "device_core.cuh", "device_passes.cuh",
+                                            "device_kernels.cuh", "host_objects.cuh")] + \
+    [os.path.join(ROOT, "include", "trids.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-shared", "-I" + os.path.join(ROOT, "include")]

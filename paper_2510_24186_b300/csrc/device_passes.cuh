@@ -1,0 +1,510 @@
+// libtrids device code, part 2: the per-pose passes of one evaluation -- the balanced pair
+// loop, the grid-map, atom-pair E_MDN and residue E_MDN passes, the score and the adjoint.
+// Included by trids.cu only.
+#pragma once
+
+namespace {
+
+// ------------------------------------------------------------------ balanced item loops
+// The pair loop and the E_MDN passes number a pose's work items atom by atom and give
+// lane k the k-th of 32 equal contiguous segments.  A lane accumulates its current atom's
+// force in registers and leaves a partial in slot (atom + lane) of W.rec: slots are unique
+// because atoms never decrease along the lanes.  The partials of an atom are then added in
+// lane order, so the result does not depend on timing.
+
+// Per-atom item counts -> exclusive prefix W.pre[0..L], 32 atoms per call: atom i =
+// base + lane has n items (0 for i >= L); carry runs over the calls.  seg_finish then sets
+// W.pre[0], clears W.rec and returns the total.
+__device__ __forceinline__ void seg_scan(const PW& W, int L, int i, int n, int& carry) {
+    const int lane = W.lane;
+    int v = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    if (i < L) W.pre[i + 1] = carry + v;
+    carry += __shfl_sync(kFull, v, 31);
+}
+
+__device__ __forceinline__ int seg_finish(const PW& W, int L, int carry) {
+    if (W.lane == 0) W.pre[0] = 0;
+    for (int r = W.lane; r < L + 32; r += 32) W.rec[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+    return carry;
+}
+
+// The lane's item range [lo, hi) of N items and the atom holding item lo (when lo < hi).
+__device__ __forceinline__ int seg_range(const PW& W, int L, int N, int& lo, int& hi) {
+    lo = (int)(((long long)N * W.lane) >> 5);
+    hi = (int)(((long long)N * (W.lane + 1)) >> 5);
+    int a = 0, b = L - 1;
+    while (a < b) {
+        const int m = (a + b + 1) >> 1;
+        if (W.pre[m] <= lo) a = m; else b = m - 1;
+    }
+    return a;
+}
+
+// Each atom's partials in lane order: W.gs[i] = sum (ADD: W.gs[i] += sum).
+template <bool ADD>
+__device__ __forceinline__ void seg_combine(const PW& W, int L, int N) {
+    __syncwarp();
+    for (int i = W.lane; i < L; i += 32) {
+        float gx = 0.f, gy = 0.f, gz = 0.f;
+        const int b0 = W.pre[i], b1 = W.pre[i + 1];
+        if (b0 < b1) {
+            const int l0 = min(31, (32 * (b0 + 1) - 1) / N), l1 = min(31, (32 * b1 - 1) / N);
+            for (int l = l0; l <= l1; ++l) {
+                const float4 r = W.rec[i + l];
+                gx += r.x; gy += r.y; gz += r.z;
+            }
+        }
+        if (ADD) {
+            if (b0 < b1) {
+                float4 g = W.gs[i];
+                g.x += gx; g.y += gy; g.z += gz;
+                W.gs[i] = g;
+            }
+        } else {
+            W.gs[i] = make_float4(gx, gy, gz, 0.f);
+        }
+    }
+    __syncwarp();
+}
+
+// All pairs of the warp's pose.  Atom i's work list is its cell's candidate pocket atoms
+// followed by its intra-ligand partners (every intra pair appears once from each side),
+// both in blocks of 8 uint16 entries (target index, 13 bits | target's flags << 13;
+// padding points at a far sentinel).  Pocket targets are read from the block's staged
+// pocket, ligand targets from the pose's own coordinates (W.xs); both float4 carry
+// (x, y, z, radius).  The pose's blocks are numbered atom by atom (prefix in W.pre) and
+// split into 32 equal contiguous segments, one per lane, so the lanes stay balanced
+// whatever the atoms' list lengths.  A lane accumulates the force on its current atom
+// in registers and leaves a partial in slot (atom + lane) of W.rec; the partials of an
+// atom are added in lane order (bit-reproducible).  The Vina-form block is branch-free:
+// all candidates are evaluated and masked by r^2 < cutoff^2.  Writes the forces to W.gs;
+// returns the lane's ligand-pocket energy and, in *e_in2, twice its intra energy.
+template <int TS, bool PARAMS, bool COUNT, bool MAPS>
+__device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
+                           const float w[5], float ebar, ParamAcc& acc, uint32_t& npairs, float* e_in2) {
+    const DevParams& P = *S.P;
+    const float cut2 = P.cut2;
+    const VinaX2 K = make_vina_x2(w);
+    const int L = h.n_atoms, lane = W.lane;
+    const uint16_t* __restrict__ cand = pk.cand;
+    const uint16_t* __restrict__ ient = B.ient + h.ient_off;
+    // 1. per-atom work: candidate blocks of the cell + intra-partner blocks; prefix
+    int carry = 0;
+    for (int base = 0; base < L; base += 32) {
+        const int i = base + lane;
+        int nblk = 0;
+        if (i < L) {
+            const float4 x = W.xs[i];
+            uint32_t beg, end;
+            cell_range(pk, pk.cell_start, x.x, x.y, x.z, beg, end);
+            const int i0 = __ldg(&B.ipre[h.ipre_off + i]), i1 = __ldg(&B.ipre[h.ipre_off + i + 1]);
+            const int cbk = (MAPS && map_cell(pk, x.x, x.y, x.z, nullptr)) ? 0 : (int)((end - beg) >> 3);
+            W.cs[i] = beg;
+            W.cb[i] = cbk;
+            W.ip[i] = i0;
+            nblk = cbk + (i1 - i0);
+        }
+        seg_scan(W, L, i, nblk, carry);
+    }
+    const int N = seg_finish(W, L, carry);
+    int lo, hi;
+    int i = seg_range(W, L, N, lo, hi);
+    float e_lp = 0.f, e_in = 0.f;
+    if (lo < hi) {
+        int first = W.pre[i], nxt = W.pre[i + 1], cbk = W.cb[i], ipb = W.ip[i];
+        uint32_t csb = W.cs[i];
+        float4 xa = W.xs[i];
+        int ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
+        float ri = xa.w;
+        uint32_t fi = P.tflags[ti];
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        auto block_ptr = [&](int blk) -> const uint4* {
+            const int loc = blk - first;
+            return loc < cbk ? reinterpret_cast<const uint4*>(cand + csb + 8u * (uint32_t)loc)
+                             : reinterpret_cast<const uint4*>(ient + 8 * (ipb + loc - cbk));
+        };
+        uint4 v = __ldg(block_ptr(lo));
+        for (int blk = lo; blk < hi; ++blk) {
+            if (blk == nxt) {                      // move to the atom owning block blk
+                W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
+                ax = ay = az = 0.f;
+                do { ++i; } while (W.pre[i + 1] == blk);
+                first = W.pre[i];
+                nxt = W.pre[i + 1];
+                cbk = W.cb[i];
+                ipb = W.ip[i];
+                csb = W.cs[i];
+                xa = W.xs[i];
+                ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
+                ri = xa.w;
+                fi = P.tflags[ti];
+                v = __ldg(block_ptr(blk));
+            }
+            const uint4 vc = v;
+            const bool intra = blk - first >= cbk;
+            if (blk + 1 < hi && blk + 1 < nxt) v = __ldg(block_ptr(blk + 1));
+            const float4* __restrict__ src = intra ? W.xs : S.pocket;
+            // pair-flag selectors: hydrophobic needs both bit0; donor-acceptor needs
+            // (donor_i & acceptor_j) | (acceptor_i & donor_j)
+            const uint32_t f_hyd = fi & 1u;
+            const uint32_t f_hb = ((fi & 2u) << 1) | ((fi & 4u) >> 1);
+            float eb = 0.f;
+            float2 eb2 = make_float2(0.f, 0.f);
+            const float2 nxy = make_float2(-xa.x, -xa.y), nzr = make_float2(-xa.z, -ri);
+            const uint32_t mh = f_hyd << 13, mb = f_hb << 13;
+            // two halves of four candidates: the loop body stays small for the
+            // instruction cache, which the 16 resident warps share across all phases
+#pragma unroll 1
+            for (int hv = 0; hv < 2; ++hv) {
+                const uint32_t wv[2] = {hv ? vc.z : vc.x, hv ? vc.w : vc.y};
+                if constexpr (TS == TRIDS_TERMS_VINA5 && !PARAMS) {
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+                        vina_x2<COUNT>(wv[u], src, nxy, nzr, cut2, K, mh, mb, eb2, ax, ay, az, npairs,
+                                       intra ? 1u : 2u);   // doubled: intra pairs come twice
+                } else if constexpr (!PARAMS) {
+                    const float4* gm = nullptr;   // term set 1: the atom-pair E_MDN runs in gmm_warp
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+                        trids_x2<COUNT>(wv[u], src, nxy, nzr, cut2, w, mb, gm, S.ptype, P.gmm_k, eb2, ax, ay, az,
+                                        npairs, intra ? 1u : 2u);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        const uint32_t ent = (s & 1) ? (wv[s >> 1] >> 16) : (wv[s >> 1] & 0xffffu);
+                        const int j = (int)(ent & 0x1fffu);
+                        const uint32_t fj = ent >> 13;
+                        const float4 a = src[j];
+                        const float dx = xa.x - a.x, dy = xa.y - a.y, dz = xa.z - a.z;
+                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                        const bool in = r2 < cut2;
+                        if (TS == TRIDS_TERMS_VINA5) {
+                            float dd, rinv, et[5];
+                            const float e = vina_eval<PARAMS>(r2, ri + a.w, (f_hyd & fj) ? 1.f : 0.f,
+                                                              (f_hb & fj) ? 1.f : 0.f, w, dd, rinv, et);
+                            const float fr = in ? dd * rinv : 0.f;
+                            eb += in ? e : 0.f;
+                            ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
+                            if (PARAMS && in) {
+                                const float sc = intra ? 0.5f * ebar : ebar;
+#pragma unroll
+                                for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(sc, et[t], acc.gw[t]);
+                                W.grs[ti * 32 + lane] -= ebar * dd;
+                                if (!intra) W.grs[S.ptype[j] * 32 + lane] -= ebar * dd;
+                            }
+                        } else if (in) {
+                            const int tj = intra ? 0 : S.ptype[j];
+                            const bool mdn = TS == TRIDS_TERMS_TRIDS && !intra;   // atom-pair E_MDN
+                            float fr, dRs;
+                            float et[5];
+                            const float e = pair_trids<PARAMS>(fmaxf(r2, 1e-12f), ri + a.w, (f_hb & fj) ? 2 : 0,
+                                                               mdn ? &P.gmm[ti][tj][0] : nullptr, P.gmm_k, mdn, w, fr,
+                                                               et, dRs);
+                            eb += e;
+                            ax = fmaf(fr, dx, ax); ay = fmaf(fr, dy, ay); az = fmaf(fr, dz, az);
+                            if (PARAMS) {
+                                const float sc = intra ? 0.5f * ebar : ebar;
+#pragma unroll
+                                for (int t = 0; t < 5; ++t) acc.gw[t] = fmaf(sc, et[t], acc.gw[t]);
+                                W.grs[ti * 32 + lane] += ebar * dRs;
+                                if (!intra) W.grs[tj * 32 + lane] += ebar * dRs;
+                            }
+                        }
+                        if (COUNT) npairs += in ? (intra ? 1u : 2u) : 0u;   // doubled: intra pairs come twice
+                    }
+                }
+            }
+            if (!PARAMS) eb = eb2.x + eb2.y;
+            if (intra) e_in += eb; else e_lp += eb;
+        }
+        W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
+    }
+    // 2. add each atom's partials in lane order
+    seg_combine<false>(W, L, N);
+    *e_in2 = e_in;
+    return e_lp;
+}
+
+// Grid-map energy of the warp's pose: each lane takes its atoms whose cell lies inside
+// the map domain (the pair loop skipped their pocket candidates): trilinear interpolation
+// of the atom type's map at the 8 corners and its analytic gradient, added to W.gs.
+// Out of line: the direct-sum sampler keeps its instruction footprint.
+__device__ __noinline__ float map_warp(const DevBatch& B, const DevPocket& pk, const LigHdr& h, const PW& W) {
+    float e = 0.f;
+    for (int i = W.lane; i < h.n_atoms; i += 32) {
+        const float4 x = W.xs[i];
+        float4 u;
+        if (!map_cell(pk, x.x, x.y, x.z, &u)) continue;
+        const int cx = (int)u.x, cy = (int)u.y, cz = (int)u.z;
+        const float fx = u.x - (float)cx, fy = u.y - (float)cy, fz = u.z - (float)cz;
+        const int t = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
+        const size_t sx = 1, sy = (size_t)pk.mx, sz = (size_t)pk.mx * pk.my;
+        const float* __restrict__ m = pk.maps + (size_t)t * sz * pk.mz + cz * sz + cy * sy + cx;
+        const float v000 = __ldg(m), v100 = __ldg(m + sx), v010 = __ldg(m + sy), v110 = __ldg(m + sy + sx);
+        const float v001 = __ldg(m + sz), v101 = __ldg(m + sz + sx), v011 = __ldg(m + sz + sy),
+                    v111 = __ldg(m + sz + sy + sx);
+        // along x, then y, then z
+        const float a00 = fmaf(fx, v100 - v000, v000), a10 = fmaf(fx, v110 - v010, v010);
+        const float a01 = fmaf(fx, v101 - v001, v001), a11 = fmaf(fx, v111 - v011, v011);
+        const float b0 = fmaf(fy, a10 - a00, a00), b1 = fmaf(fy, a11 - a01, a01);
+        e += fmaf(fz, b1 - b0, b0);
+        const float dz = b1 - b0;
+        const float dy = fmaf(fz, (a11 - a01) - (a10 - a00), a10 - a00);
+        const float d00 = v100 - v000, d10 = v110 - v010, d01 = v101 - v001, d11 = v111 - v011;
+        const float c0 = fmaf(fy, d10 - d00, d00), c1 = fmaf(fy, d11 - d01, d01);
+        const float dx = fmaf(fz, c1 - c0, c0);
+        float4 g = W.gs[i];
+        g.x = fmaf(dx, pk.inv_mh, g.x);
+        g.y = fmaf(dy, pk.inv_mh, g.y);
+        g.z = fmaf(dz, pk.inv_mh, g.z);
+        W.gs[i] = g;
+    }
+    __syncwarp();
+    return e;
+}
+
+// Atom-pair E_MDN of the warp's pose (term set 1; Sec. 2, Eqs. P(d) and E_MDN on atom
+// pairs): each ligand atom against the pocket atoms of its cell's near list (within 5 A
+// plus half the cell diagonal); a pair with r < min(5 A, cutoff) adds
+// -w0 sum_k pi_k exp(-(r - mu_k)^2 / (2 sigma_k^2)) with (pi, mu, sigma) by the atom-type
+// pair.  A separate pass over these short lists keeps the K Gaussians off the 10 A pair
+// loop (about 1 in 8 of its candidates is within 5 A).  Items (atom, near-list entry) are
+// split into 32 equal contiguous lane segments; per-atom partials go to slot (atom + lane)
+// of W.rec and are added to W.gs in lane order.  Atoms that the grid maps cover are
+// skipped (their maps hold this term).  Returns the lane's energy.
+template <bool MAPS>
+__device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
+                          float w0) {
+    constexpr float kL2e = 1.4426950408889634f;
+    const DevParams& P = *S.P;
+    const int K = P.gmm_k, L = h.n_atoms, lane = W.lane;
+    const float nc2 = pk.near_cut2;
+    int carry = 0;
+    for (int base = 0; base < L; base += 32) {
+        const int i = base + lane;
+        int n = 0;
+        if (i < L) {
+            const float4 x = W.xs[i];
+            uint32_t beg = 0, end = 0;
+            if (!(MAPS && map_cell(pk, x.x, x.y, x.z, nullptr))) cell_range(pk, pk.ncell_start, x.x, x.y, x.z, beg, end);
+            W.cs[i] = beg;
+            n = (int)(end - beg);
+        }
+        seg_scan(W, L, i, n, carry);
+    }
+    const int N = seg_finish(W, L, carry);
+    int lo, hi;
+    int i = seg_range(W, L, N, lo, hi);
+    float e = 0.f;
+    if (lo < hi) {
+        int first = W.pre[i], nxt = W.pre[i + 1];
+        uint32_t cs = W.cs[i];
+        float4 x = W.xs[i];
+        const float4* g = &P.gmm[__float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w)][0][0];
+        float gx = 0.f, gy = 0.f, gz = 0.f, ei = 0.f;
+        for (int it = lo; it < hi; ++it) {
+            if (it == nxt) {
+                W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
+                e = fmaf(w0, ei, e);
+                gx = gy = gz = ei = 0.f;
+                do { ++i; } while (W.pre[i + 1] == it);
+                first = W.pre[i];
+                nxt = W.pre[i + 1];
+                cs = W.cs[i];
+                x = W.xs[i];
+                g = &P.gmm[__float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w)][0][0];
+            }
+            const int j = __ldg(&pk.nlist[cs + (uint32_t)(it - first)]);
+            const float4 p = S.pocket[j];
+            const float dx = x.x - p.x, dy = x.y - p.y, dz = x.z - p.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float in = r2 < nc2 ? 1.f : 0.f;
+            const float rinv = rsqrtf(fmaxf(r2, 1e-12f));
+            const float r = r2 * rinv;
+            const float4* gk = g + S.ptype[j] * kK;
+            float e0 = 0.f, d0 = 0.f;
+            for (int k = 0; k < K; ++k) {
+                const float4 u = gk[k];                          // (pi, mu, -1/(2 sigma^2), 1/sigma^2)
+                const float z = r - u.y;
+                const float ex = u.x * ex2_approx(u.z * kL2e * z * z);
+                e0 += ex;
+                d0 = fmaf(ex * z, u.w, d0);
+            }
+            ei = fmaf(-in, e0, ei);
+            const float f = in * w0 * d0 * rinv;                 // (dE/dr) / r
+            gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
+        }
+        W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
+        e = fmaf(w0, ei, e);
+    }
+    seg_combine<true>(W, L, N);
+    return e;
+}
+
+// Residue-level E_MDN of the warp's pose (term set 2; Sec. 2, Eqs. P(d) and E_MDN): for
+// each ligand atom and each residue listed for its cell, the minimum distance d over the
+// residue's atoms (one contiguous range of the staged pocket, ascending input index, so a
+// strict < keeps the lowest index on ties); d < 5 A adds
+// -w0 sum_k pi_k exp(-(d - mu_k)^2 / (2 sigma_k^2)) with the force along the nearest atom.
+// The (atom, residue) items are numbered atom by atom and split into 32 equal contiguous
+// segments, one per lane, as in the pair loop; per-atom partial forces go to slot
+// (atom + lane) of W.rec and are added to W.gs in lane order.  Returns the lane's energy.
+template <bool PARAMS>
+__device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
+                              float w0, float ebar, ParamAcc& acc) {
+    constexpr float kCut2 = kMdnCut * kMdnCut;
+    constexpr float kL2e = 1.4426950408889634f;
+    const int K = B.mdn_k, R = B.mdn_res, L = h.n_atoms, lane = W.lane;
+    int carry = 0;
+    for (int base = 0; base < L; base += 32) {
+        const int i = base + lane;
+        int n = 0;
+        if (i < L) {
+            const float4 x = W.xs[i];
+            uint32_t beg, end;
+            cell_range(pk, pk.rcell_start, x.x, x.y, x.z, beg, end);
+            W.cs[i] = beg;
+            n = (int)(end - beg);
+        }
+        seg_scan(W, L, i, n, carry);
+    }
+    const int N = seg_finish(W, L, carry);
+    int lo, hi;
+    int i = seg_range(W, L, N, lo, hi);
+    float e = 0.f;
+    if (lo < hi) {
+        int first = W.pre[i], nxt = W.pre[i + 1];
+        uint32_t cs = W.cs[i];
+        float4 x = W.xs[i];
+        const float4* __restrict__ kern = B.mdn + (size_t)(h.atom_off + i) * R * K;
+        float gx = 0.f, gy = 0.f, gz = 0.f, ei = 0.f;
+        uint32_t ent = __ldg(&pk.rlist[cs + (uint32_t)(lo - first)]);
+        for (int it = lo; it < hi; ++it) {
+            if (it == nxt) {                       // move to the atom owning item it
+                W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
+                e = fmaf(w0, ei, e);
+                if (PARAMS) acc.gw[0] = fmaf(ebar, ei, acc.gw[0]);
+                gx = gy = gz = ei = 0.f;
+                do { ++i; } while (W.pre[i + 1] == it);
+                first = W.pre[i];
+                nxt = W.pre[i + 1];
+                cs = W.cs[i];
+                x = W.xs[i];
+                kern = B.mdn + (size_t)(h.atom_off + i) * R * K;
+                ent = __ldg(&pk.rlist[cs + (uint32_t)(it - first)]);
+            }
+            const uint32_t cur = ent;
+            if (it + 1 < hi && it + 1 < nxt) ent = __ldg(&pk.rlist[cs + (uint32_t)(it + 1 - first)]);   // prefetch
+            const int r = (int)(cur & 0x1fffu);
+            const int a0 = (int)((cur >> 13) & 0x1fffu), a1 = a0 + (int)(cur >> 26);
+            // two interleaved streams (even / odd offsets), each keeping its first minimum;
+            // the merge takes the smaller distance, on a tie the lower atom index: the same
+            // atom a single ascending scan with a strict < would keep
+            float b0 = 3.0e38f, b1 = 3.0e38f;
+            int i0 = a0, i1 = a0;
+            int a = a0;
+            for (; a + 1 < a1; a += 2) {
+                const float4 p = S.pocket[a], q = S.pocket[a + 1];
+                const float px = x.x - p.x, py = x.y - p.y, pz = x.z - p.z;
+                const float qx = x.x - q.x, qy = x.y - q.y, qz = x.z - q.z;
+                const float rp = fmaf(pz, pz, fmaf(py, py, px * px)), rq = fmaf(qz, qz, fmaf(qy, qy, qx * qx));
+                if (rp < b0) { b0 = rp; i0 = a; }
+                if (rq < b1) { b1 = rq; i1 = a + 1; }
+            }
+            if (a < a1) {
+                const float4 p = S.pocket[a];
+                const float px = x.x - p.x, py = x.y - p.y, pz = x.z - p.z;
+                const float rp = fmaf(pz, pz, fmaf(py, py, px * px));
+                if (rp < b0) { b0 = rp; i0 = a; }
+            }
+            const bool take1 = b1 < b0 || (b1 == b0 && i1 < i0);
+            const float best = take1 ? b1 : b0;
+            const float4 pb = S.pocket[take1 ? i1 : i0];
+            const float bx = x.x - pb.x, by = x.y - pb.y, bz = x.z - pb.z;
+            if (best < kCut2) {
+                const float rinv = rsqrtf(fmaxf(best, 1e-12f));
+                const float d = best * rinv;
+                float P = 0.f, dP = 0.f;
+                for (int k = 0; k < K; ++k) {
+                    const float4 g = __ldg(&kern[r * K + k]);   // (pi, mu, -1/(2 sigma^2), 1/sigma^2)
+                    const float z = d - g.y;
+                    const float ex = g.x * ex2_approx(g.z * kL2e * z * z);
+                    P += ex;
+                    dP = fmaf(-ex * z, g.w, dP);                // dP/dd
+                }
+                ei -= P;
+                const float f = -w0 * dP * rinv;                // (dE/dd) / d
+                gx = fmaf(f, bx, gx); gy = fmaf(f, by, gy); gz = fmaf(f, bz, gz);
+            }
+        }
+        W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
+        e = fmaf(w0, ei, e);
+        if (PARAMS) acc.gw[0] = fmaf(ebar, ei, acc.gw[0]);
+    }
+    seg_combine<true>(W, L, N);
+    return e;
+}
+
+// E_total of the warp's pose (same value on every lane); forces in W.gs.
+template <int TS, bool PARAMS, bool COUNT, bool MAPS>
+__device__ float score_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
+                            float ebar, ParamAcc& acc, float* e_inter, uint32_t& npairs) {
+    float w[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) w[t] = S.P->w[t];
+    float ein2;
+    float el = pairs_warp<TS, PARAMS, COUNT, MAPS>(B, pk, S, h, W, w, ebar, acc, npairs, &ein2);
+    if (MAPS && pk.use_maps) el += map_warp(B, pk, h, W);
+    if constexpr (TS == TRIDS_TERMS_TRIDS && !PARAMS) el += gmm_warp<MAPS>(B, pk, S, h, W, w[0]);
+    if constexpr (TS == TRIDS_TERMS_TRIDS_RES) el += residue_warp<PARAMS>(B, pk, S, h, W, w[0], ebar, acc);
+    const float e_lp = warp_sum(el);
+    *e_inter = e_lp;
+    return e_lp + 0.5f * warp_sum(ein2);
+}
+
+// dE/dt = sum g_i and world torque tau = sum (x_i - t) x g_i (every lane), and
+// dE/dtheta_k = a_k . sum over the moving subtree of (x_i - p_k) x g_i with a_k the world
+// axis (parent atom -> child atom) and p_k the world parent atom (lane k, which sums its
+// subtree serially: no shuffles, and the subtree is one contiguous range).
+__device__ float adjoint_warp(const DevBatch& B, const LigHdr& h, const PW& W, const float t[3], float gt[3],
+                              float tau[3]) {
+    const int L = h.n_atoms, T = h.n_tor;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
+    for (int i = W.lane; i < L; i += 32) {
+        const float4 g = W.gs[i], x = W.xs[i];
+        const float rx = x.x - t[0], ry = x.y - t[1], rz = x.z - t[2];
+        a0 += g.x; a1 += g.y; a2 += g.z;
+        a3 += ry * g.z - rz * g.y;
+        a4 += rz * g.x - rx * g.z;
+        a5 += rx * g.y - ry * g.x;
+    }
+    gt[0] = warp_sum(a0); gt[1] = warp_sum(a1); gt[2] = warp_sum(a2);
+    tau[0] = warp_sum(a3); tau[1] = warp_sum(a4); tau[2] = warp_sum(a5);
+    // torsion k on lane k: its moving subtree is the contiguous atom range [ti.z, ti.w)
+    float mine = 0.f;
+    if (W.lane < T) {
+        const int4 ti = __ldg(&B.tor_idx[h.tor_off + W.lane]);
+        const float4 p = W.xs[ti.x], c = W.xs[ti.y];
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int i = ti.z; i < ti.w; ++i) {
+            const float4 x = W.xs[i], g = W.gs[i];
+            const float rx = x.x - p.x, ry = x.y - p.y, rz = x.z - p.z;
+            sx += ry * g.z - rz * g.y;
+            sy += rz * g.x - rx * g.z;
+            sz += rx * g.y - ry * g.x;
+        }
+        const float ax = c.x - p.x, ay = c.y - p.y, az = c.z - p.z;
+        const float n = rsqrtf(ax * ax + ay * ay + az * az);
+        mine = (ax * sx + ay * sy + az * sz) * n;
+    }
+    return mine;
+}
+
+
+}  // namespace
