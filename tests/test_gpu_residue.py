@@ -178,3 +178,25 @@ def test_residue_inputs_are_checked(api):
                        api.ScoreParams(2, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.TRIDS_WEIGHTS, 4.0))
     with pytest.raises(TridsError, match="cutoff"):
         small.set_residues(res)
+
+
+def test_residue_full_size_sampled(api):
+    """The batched-screening workload with the paper's residue-level E_MDN (1,024 ligands x
+    128 poses x 50 evaluations, about 220 residues, K = 4, persistent launch in a CUDA
+    graph): 96 seeded poses traced and checked per evaluation against the oracle."""
+    w = synth.workload(2)
+    sp, pk, b, mds = res_setup(api, w, w.ligands, K=4, seed=2202)
+    P, S, seed = w.poses, w.steps, 2203
+    rng = np.random.default_rng(22)
+    poses_g = np.sort(rng.choice(b.n_lig * P, 96, replace=False))
+    out = api.sample(pk, b, P, S, mc_loops=w.mc_loops, seed=seed, trace_poses=poses_g.tolist())
+    assert api.sync(b, P, out["state"], timeout_ms=120000) == 0
+    lo = (w.box_center - w.box_size / 2).astype(np.float32).astype(np.float64)
+    hi = (w.box_center + w.box_size / 2).astype(np.float32).astype(np.float64)
+    cfg = oracle.sample_cfg(steps=S, mc_loops=w.mc_loops, lr=float(np.float32(0.1)), b1=float(np.float32(0.9)),
+                            b2=float(np.float32(0.999)), eps=float(np.float32(1e-8)),
+                            beta=float(np.float32(0.069)), seed=seed, box_lo=lo, box_hi=hi)
+    st = check_trace(out["trace"].cpu().numpy(), poses_g, P, oracle_ligands(w.ligands), *pocket_arrays(w.pocket),
+                     oracle_params(sp), cfg, S, w.mc_loops, seed, out["dof"].cpu().numpy(),
+                     out["energy"].cpu().numpy(), mds=mds)
+    report(st, "residue E_MDN, batched screening, sampled")
