@@ -69,3 +69,27 @@ def test_null_arguments_are_rejected_without_a_gpu():
     out = C.c_void_p()
     assert L.trids_pack_ligands(None, 1, None, None, None, None, None, None, C.byref(out)) == _lib.EINVAL
     assert out.value is None
+
+
+def test_new_entry_points_reject_null_handles_without_a_gpu():
+    L = _lib.lib()
+    assert L.trids_set_residues(None, 4, None) == _lib.EINVAL
+    assert L.trids_set_mdn(None, 4, 2, None, None) == _lib.EINVAL
+    assert L.trids_build_maps(None, 0.375, 8.0, None) == _lib.EINVAL
+    lo = (C.c_float * 3)()
+    h = C.c_float()
+    n = (C.c_int32 * 3)()
+    assert L.trids_maps_info(None, C.byref(lo), C.byref(h), C.byref(n)) == _lib.EINVAL
+    assert L.trids_set_boxes(None, 1, None, None) == _lib.EINVAL
+
+
+def test_python_api_fails_loudly_without_cuda():
+    """There is no CPU fallback: the product path raises when no CUDA device is present."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2510_24186_b300 import api, synth
+    w = synth.workload(1)
+    sp = api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, 8.0)
+    with pytest.raises(RuntimeError, match="CUDA"):
+        api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
