@@ -74,6 +74,7 @@ struct trids_batch {
     trids_batch_dims dims{};
     std::vector<PackedLigand> ligs;
     std::vector<LigHdr> hdr;
+    unsigned char* d_block = nullptr;   // one allocation holding the arrays below up to d_err
     LigHdr* d_lig = nullptr;
     float4* d_atom_y = nullptr;
     int* d_atom_orig = nullptr;
@@ -213,14 +214,52 @@ int upload_pocket_arrays(trids_pocket* pk, cudaStream_t st) {
     return TRIDS_OK;
 }
 
+// Runs fn(l) for every ligand l in [0, n) on up to 32 host threads (ligands are independent).
+template <class F>
+void for_ligands(int n, F&& fn) {
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::max(1, std::min({hw, 32, n / 16}));
+    auto work = [&](int t) {
+        for (int l = t; l < n; l += nt) fn(l);
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(work, t);
+    work(0);
+    for (auto& x : th) x.join();
+}
+
+// Intra partner lists of one packed ligand: per atom, every partner (both directions,
+// ascending) in blocks of 8 padded with the far sentinel index pad; pre[i] is atom i's
+// first block (n_atoms + 1 entries).
+void partner_lists(const PackedLigand& lg, int pad, std::vector<int>* pre, std::vector<uint16_t>* ent) {
+    const int n = lg.n_atoms;
+    std::vector<int> deg(n + 1, 0);
+    for (const auto& pr : lg.pairs) {
+        ++deg[pr.first + 1];
+        ++deg[pr.second + 1];
+    }
+    for (int i = 0; i < n; ++i) deg[i + 1] += deg[i];
+    std::vector<int> adj(deg[n]), fill(deg.begin(), deg.end() - 1);
+    for (const auto& pr : lg.pairs) {
+        adj[fill[pr.first]++] = pr.second;
+        adj[fill[pr.second]++] = pr.first;
+    }
+    pre->assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) (*pre)[i + 1] = (*pre)[i] + (deg[i + 1] - deg[i] + 7) / 8;
+    ent->assign(8 * (size_t)(*pre)[n], (uint16_t)pad);
+    for (int i = 0; i < n; ++i) {
+        std::sort(adj.begin() + deg[i], adj.begin() + deg[i + 1]);
+        for (int k = deg[i]; k < deg[i + 1]; ++k) (*ent)[8 * (size_t)(*pre)[i] + (k - deg[i])] = (uint16_t)adj[k];
+    }
+}
+
 // (Re-)encode a batch's intra partner entries with the pocket's current type flags.
-int encode_intra(const trids_pocket* pk, trids_batch* b, bool allocate) {
+int encode_intra(const trids_pocket* pk, trids_batch* b) {
     std::vector<uint16_t> ent(b->ient_j.size());
     for (size_t k = 0; k < ent.size(); ++k) {
         const uint32_t f = b->ient_type[k] == 0xff ? 0u : (uint32_t)(pk->prm.flags[b->ient_type[k]] & 7);
         ent[k] = (uint16_t)((uint32_t)b->ient_j[k] | (f << 13));
     }
-    if (allocate) return upload(&b->d_ient, ent);
     if (!ent.empty()) CK(cudaMemcpy(b->d_ient, ent.data(), ent.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
     return TRIDS_OK;
 }

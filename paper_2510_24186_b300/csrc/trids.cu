@@ -134,7 +134,7 @@ int trids_set_params(trids_pocket* pk, const trids_params* prm, void* stream) {
     if ((rc = upload_pocket_arrays(pk, (cudaStream_t)stream))) return rc;
     if (flags_changed)
         for (trids_batch* b : pk->batches)
-            if ((rc = encode_intra(pk, b, false))) return rc;
+            if ((rc = encode_intra(pk, b))) return rc;
     return TRIDS_OK;
 }
 
@@ -330,6 +330,9 @@ int trids_pack_topology(int32_t n_atoms, const float* xyz, const int32_t* type, 
     return TRIDS_OK;
 }
 
+// Packs every ligand on host threads (torsion tree, intra pairs and partner lists), lays
+// the batch's device arrays out in one host staging buffer (each ligand fills its own
+// slices, again on host threads) and uploads it with one allocation and one copy.
 int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_atoms, const float* xyz,
                        const int32_t* type, const int32_t* n_bonds, const int32_t* bonds,
                        const uint8_t* rotatable, trids_batch** out) {
@@ -345,75 +348,94 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
     b->device = pk->device;
     b->n_types = pk->prm.n_types;
     b->ligs.resize(n_lig);
-    // per-ligand input offsets, then the ligands packed on host threads (each ligand is
-    // independent; the first failing ligand in index order is reported)
     std::vector<size_t> aoff(n_lig + 1, 0), boff(n_lig + 1, 0);
+    int Lmax = 1;
     for (int l = 0; l < n_lig; ++l) {
         if (n_bonds[l] < 0) return fail(TRIDS_EINVAL, "ligand %d: negative bond count", l);
         if (n_bonds[l] > 0 && (!bonds || !rotatable)) return fail(TRIDS_EINVAL, "bonds is NULL");
         if (n_atoms[l] < 0) return fail(TRIDS_EINVAL, "ligand %d: negative atom count", l);
         aoff[l + 1] = aoff[l] + (size_t)n_atoms[l];
         boff[l + 1] = boff[l] + (size_t)n_bonds[l];
+        Lmax = std::max(Lmax, (int)n_atoms[l]);
     }
+    // 1. torsion trees and partner lists (the first failing ligand in index order is reported)
     std::vector<std::string> msg(n_lig);
-    {
-        const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-        const int nt = std::max(1, std::min({hw, 32, n_lig / 16}));
-        auto work = [&](int t) {
-            for (int l = t; l < n_lig; l += nt)
-                msg[l] = pack_ligand(n_atoms[l], xyz + 3 * aoff[l], type + aoff[l], pk->prm.n_types, n_bonds[l],
-                                     bonds ? bonds + 2 * boff[l] : nullptr, rotatable ? rotatable + boff[l] : nullptr,
-                                     &b->ligs[l]);
-        };
-        std::vector<std::thread> th;
-        for (int t = 1; t < nt; ++t) th.emplace_back(work, t);
-        work(0);
-        for (auto& x : th) x.join();
-    }
-    int Lmax = 1, Tmax = 0;
+    std::vector<std::vector<int>> lpre(n_lig);
+    std::vector<std::vector<uint16_t>> lent(n_lig);
+    for_ligands(n_lig, [&](int l) {
+        msg[l] = pack_ligand(n_atoms[l], xyz + 3 * aoff[l], type + aoff[l], pk->prm.n_types, n_bonds[l],
+                             bonds ? bonds + 2 * boff[l] : nullptr, rotatable ? rotatable + boff[l] : nullptr,
+                             &b->ligs[l]);
+        if (msg[l].empty()) partner_lists(b->ligs[l], Lmax, &lpre[l], &lent[l]);
+    });
+    int Tmax = 0;
     int64_t npairs = 0;
+    std::vector<int64_t> toff(n_lig + 1, 0), poff(n_lig + 1, 0), eoff(n_lig + 1, 0);
     for (int l = 0; l < n_lig; ++l) {
         if (!msg[l].empty()) return fail(TRIDS_EINVAL, "ligand %d: %s", l, msg[l].c_str());
-        Lmax = std::max(Lmax, n_atoms[l]);
         Tmax = std::max(Tmax, b->ligs[l].n_tor);
         npairs += (int64_t)b->ligs[l].pairs.size();
+        toff[l + 1] = toff[l] + b->ligs[l].n_tor;
+        poff[l + 1] = poff[l] + n_atoms[l] + 1;
+        eoff[l + 1] = eoff[l] + (int64_t)lent[l].size();
     }
-    size_t ao = 0;
+    if ((int64_t)aoff[n_lig] > INT32_MAX || poff[n_lig] > INT32_MAX || eoff[n_lig] > INT32_MAX)
+        return fail(TRIDS_EINVAL, "batch too large: split it (more than 2^31 atoms or partner entries)");
     b->dims.n_lig = n_lig;
     b->dims.max_atoms = Lmax;
     b->dims.max_tor = Tmax;
     b->dims.dof_stride = 7 + Tmax;
     b->dims.state_fields = state_fields(Tmax);
     b->dims.n_intra = npairs;
-    std::vector<float4> ay;
-    std::vector<int> aorig;
-    std::vector<int4> tidx;
-    std::vector<float4> tu, tp;
-    std::vector<int> ipre;
-    std::vector<int8_t> atom_tor, tor_par;
-    ao = 0;
-    for (int l = 0; l < n_lig; ++l) {
+    // 2. device layout: one buffer of 256-byte aligned sections
+    const size_t A = aoff[n_lig], T = (size_t)toff[n_lig], P = (size_t)poff[n_lig], E = (size_t)eoff[n_lig];
+    size_t total = 0;
+    auto section = [&](size_t bytes) {
+        const size_t o = total;
+        total = align_up(o + bytes, 256);
+        return o;
+    };
+    const size_t o_hdr = section(sizeof(LigHdr) * n_lig), o_ay = section(sizeof(float4) * A),
+                 o_orig = section(sizeof(int) * A), o_tidx = section(sizeof(int4) * T),
+                 o_tu = section(sizeof(float4) * T), o_tp = section(sizeof(float4) * T), o_ipre = section(sizeof(int) * P),
+                 o_ient = section(sizeof(uint16_t) * E), o_ator = section(A), o_tpar = section(T),
+                 o_cnt = section(4 * sizeof(unsigned int)), o_err = section(2 * sizeof(int));
+    std::vector<unsigned char> stage(total, 0);
+    unsigned char* hs = stage.data();
+    b->hdr.resize(n_lig);
+    b->ient_j.resize(E);
+    b->ient_type.resize(E);
+    // 3. each ligand's slices (atoms about the root centroid, torsions, partner lists)
+    for_ligands(n_lig, [&](int l) {
         const PackedLigand& lg = b->ligs[l];
         LigHdr h{};
         h.n_atoms = lg.n_atoms;
         h.n_tor = lg.n_tor;
-        h.atom_off = (int)ay.size();
-        h.tor_off = (int)tidx.size();
-        h.ipre_off = (int)ipre.size();
-        h.ient_off = (int)b->ient_j.size();
+        h.atom_off = (int)aoff[l];
+        h.tor_off = (int)toff[l];
+        h.ipre_off = (int)poff[l];
+        h.ient_off = (int)eoff[l];
         h.n_pairs = (int)lg.pairs.size();
-        const float* X = xyz + 3 * ao;
-        const int32_t* Ty = type + ao;
+        b->hdr[l] = h;
+        const float* X = xyz + 3 * aoff[l];
+        const int32_t* Ty = type + aoff[l];
+        float4* ay = reinterpret_cast<float4*>(hs + o_ay) + aoff[l];
+        int* orig = reinterpret_cast<int*>(hs + o_orig) + aoff[l];
+        int8_t* atom_tor = reinterpret_cast<int8_t*>(hs + o_ator) + aoff[l];
         for (int i = 0; i < lg.n_atoms; ++i) {
             const int a = lg.perm[i];
             float tb;
-            int t = Ty[a];
+            const int t = Ty[a];
             std::memcpy(&tb, &t, 4);
-            ay.push_back(make_float4((float)((double)X[3 * a] - lg.c[0]), (float)((double)X[3 * a + 1] - lg.c[1]),
-                                     (float)((double)X[3 * a + 2] - lg.c[2]), tb));
-            aorig.push_back(a);
-            atom_tor.push_back((int8_t)(lg.frag[i] - 1));
+            ay[i] = make_float4((float)((double)X[3 * a] - lg.c[0]), (float)((double)X[3 * a + 1] - lg.c[1]),
+                                (float)((double)X[3 * a + 2] - lg.c[2]), tb);
+            orig[i] = a;
+            atom_tor[i] = (int8_t)(lg.frag[i] - 1);
         }
+        int4* tidx = reinterpret_cast<int4*>(hs + o_tidx) + toff[l];
+        float4* tu = reinterpret_cast<float4*>(hs + o_tu) + toff[l];
+        float4* tp = reinterpret_cast<float4*>(hs + o_tp) + toff[l];
+        int8_t* tor_par = reinterpret_cast<int8_t*>(hs + o_tpar) + toff[l];
         for (int k = 0; k < lg.n_tor; ++k) {
             const int pa = lg.perm[lg.tp[k]], ha = lg.perm[lg.th[k]];
             double u[3], nn = 0;
@@ -422,59 +444,66 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
                 nn += u[d] * u[d];
             }
             nn = std::sqrt(nn);
-            if (!(nn > 1e-6)) return fail(TRIDS_EINVAL, "ligand %d: rotatable bond %d has zero length", l, k);
-            tidx.push_back(make_int4(lg.tp[k], lg.th[k], lg.sb[k], lg.se[k]));
-            tor_par.push_back((int8_t)lg.tpar[k]);
-            tu.push_back(make_float4((float)(u[0] / nn), (float)(u[1] / nn), (float)(u[2] / nn), 0.f));
-            tp.push_back(make_float4((float)((double)X[3 * pa] - lg.c[0]), (float)((double)X[3 * pa + 1] - lg.c[1]),
-                                     (float)((double)X[3 * pa + 2] - lg.c[2]), 0.f));
-        }
-        // intra partner lists: per atom, every partner (both directions, ascending) in
-        // blocks of 8, padded with the far sentinel index max_atoms
-        {
-            std::vector<std::vector<int>> part(lg.n_atoms);
-            for (auto& pr : lg.pairs) {
-                part[pr.first].push_back(pr.second);
-                part[pr.second].push_back(pr.first);
+            if (!(nn > 1e-6)) {
+                char buf[96];
+                std::snprintf(buf, sizeof buf, "rotatable bond %d has zero length", k);
+                msg[l] = buf;
+                return;
             }
-            int blocks = 0;
-            for (int i = 0; i < lg.n_atoms; ++i) {
-                std::sort(part[i].begin(), part[i].end());
-                ipre.push_back(blocks);
-                for (int j : part[i]) {
-                    b->ient_j.push_back((uint16_t)j);
-                    b->ient_type.push_back((uint8_t)Ty[lg.perm[j]]);
-                }
-                const size_t pad = (8 - part[i].size() % 8) % 8;
-                for (size_t k = 0; k < pad; ++k) {
-                    b->ient_j.push_back((uint16_t)Lmax);
-                    b->ient_type.push_back(0xff);
-                }
-                blocks += (int)((part[i].size() + 7) / 8);
-            }
-            ipre.push_back(blocks);
+            tidx[k] = make_int4(lg.tp[k], lg.th[k], lg.sb[k], lg.se[k]);
+            tor_par[k] = (int8_t)lg.tpar[k];
+            tu[k] = make_float4((float)(u[0] / nn), (float)(u[1] / nn), (float)(u[2] / nn), 0.f);
+            tp[k] = make_float4((float)((double)X[3 * pa] - lg.c[0]), (float)((double)X[3 * pa + 1] - lg.c[1]),
+                                (float)((double)X[3 * pa + 2] - lg.c[2]), 0.f);
         }
-        b->hdr.push_back(h);
-        ao += n_atoms[l];
-    }
-    if ((rc = upload(&b->d_lig, b->hdr)) || (rc = upload(&b->d_atom_y, ay)) || (rc = upload(&b->d_atom_orig, aorig)) ||
-        (rc = upload(&b->d_tor_idx, tidx)) || (rc = upload(&b->d_tor_u, tu)) || (rc = upload(&b->d_tor_p, tp)) ||
-        (rc = upload(&b->d_ipre, ipre)) || (rc = upload(&b->d_atom_tor, atom_tor)) ||
-        (rc = upload(&b->d_tor_par, tor_par)) || (rc = encode_intra(pk, b.get(), true))) {
+        std::memcpy(reinterpret_cast<int*>(hs + o_ipre) + poff[l], lpre[l].data(), sizeof(int) * lpre[l].size());
+        uint16_t* ient = reinterpret_cast<uint16_t*>(hs + o_ient) + eoff[l];
+        for (size_t k = 0; k < lent[l].size(); ++k) {
+            const int j = lent[l][k];
+            const uint8_t ty = j == Lmax ? (uint8_t)0xff : (uint8_t)Ty[lg.perm[j]];
+            const uint32_t f = ty == 0xff ? 0u : (uint32_t)(pk->prm.flags[ty] & 7);
+            b->ient_j[eoff[l] + k] = (uint16_t)j;
+            b->ient_type[eoff[l] + k] = ty;
+            ient[k] = (uint16_t)((uint32_t)j | (f << 13));
+        }
+    });
+    for (int l = 0; l < n_lig; ++l)
+        if (!msg[l].empty()) return fail(TRIDS_EINVAL, "ligand %d: %s", l, msg[l].c_str());
+    std::memcpy(hs + o_hdr, b->hdr.data(), sizeof(LigHdr) * n_lig);
+    // 4. one allocation, one copy (a private non-blocking stream: the copy neither waits
+    // for nor stalls kernels on other streams)
+    if (cudaMalloc(&b->d_block, total) != cudaSuccess) {
         trids_free_batch(b.release());
-        return rc;
+        return fail(TRIDS_ENOMEM, "cudaMalloc of %zu bytes failed", total);
     }
-    std::vector<unsigned int> zeros(4, 0u);
-    std::vector<int> zi(2, 0);
-    if ((rc = upload(&b->d_counter, zeros)) || (rc = upload(&b->d_err, zi))) {
-        trids_free_batch(b.release());
-        return rc;
+    {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            trids_free_batch(b.release());
+            return fail(TRIDS_ECUDA, "cudaStreamCreateWithFlags failed");
+        }
+        cudaError_t e = cudaMemcpyAsync(b->d_block, hs, total, cudaMemcpyHostToDevice, s);
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            trids_free_batch(b.release());
+            return fail(TRIDS_ECUDA, "upload failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
     }
-    b->dims.upload_bytes = (int64_t)(b->hdr.size() * sizeof(LigHdr) + ay.size() * sizeof(float4) +
-                                     aorig.size() * sizeof(int) + atom_tor.size() + tor_par.size() +
-                                     tidx.size() * sizeof(int4) + (tu.size() + tp.size()) * sizeof(float4) +
-                                     ipre.size() * sizeof(int) + b->ient_j.size() * sizeof(uint16_t) +
-                                     zeros.size() * sizeof(unsigned int) + zi.size() * sizeof(int));
+    unsigned char* d = b->d_block;
+    b->d_lig = reinterpret_cast<LigHdr*>(d + o_hdr);
+    b->d_atom_y = reinterpret_cast<float4*>(d + o_ay);
+    b->d_atom_orig = reinterpret_cast<int*>(d + o_orig);
+    b->d_tor_idx = reinterpret_cast<int4*>(d + o_tidx);
+    b->d_tor_u = reinterpret_cast<float4*>(d + o_tu);
+    b->d_tor_p = reinterpret_cast<float4*>(d + o_tp);
+    b->d_ipre = reinterpret_cast<int*>(d + o_ipre);
+    b->d_ient = reinterpret_cast<uint16_t*>(d + o_ient);
+    b->d_atom_tor = reinterpret_cast<int8_t*>(d + o_ator);
+    b->d_tor_par = reinterpret_cast<int8_t*>(d + o_tpar);
+    b->d_counter = reinterpret_cast<unsigned int*>(d + o_cnt);
+    b->d_err = reinterpret_cast<int*>(d + o_err);
+    b->dims.upload_bytes = (int64_t)total;
     b->owner = const_cast<trids_pocket*>(pk);
     b->owner->batches.push_back(b.get());
     *out = b.release();
@@ -491,10 +520,8 @@ int trids_free_batch(trids_batch* b) {
     if (b->side) cudaStreamDestroy(b->side);
     if (b->ev_a) cudaEventDestroy(b->ev_a);
     if (b->ev_b) cudaEventDestroy(b->ev_b);
-    cudaFree(b->d_lig); cudaFree(b->d_atom_y); cudaFree(b->d_atom_orig); cudaFree(b->d_tor_idx);
-    cudaFree(b->d_tor_u); cudaFree(b->d_tor_p); cudaFree(b->d_ipre); cudaFree(b->d_ient); cudaFree(b->d_items); cudaFree(b->d_lig_order);
-    cudaFree(b->d_counter); cudaFree(b->d_err); cudaFree(b->d_partials); cudaFree(b->d_mdn);
-    cudaFree(b->d_atom_tor); cudaFree(b->d_tor_par);
+    cudaFree(b->d_block);   // every packed array, the pop counter and the error words
+    cudaFree(b->d_items); cudaFree(b->d_lig_order); cudaFree(b->d_partials); cudaFree(b->d_mdn);
     delete b;
     return TRIDS_OK;
 }
