@@ -65,9 +65,9 @@ def mdn_kernels(w, n_atoms_total, res):
 
 
 def kernel_source_hash():
+    """Hash of the files that define the sampler kernels' code (not the host code around them)."""
     h = hashlib.sha256()
-    for f in ("trids.cu", "trids_internal.h", "device_core.cuh", "device_passes.cuh", "device_kernels.cuh",
-              "host_objects.cuh"):
+    for f in ("trids_internal.h", "device_core.cuh", "device_passes.cuh", "device_kernels.cuh"):
         f = os.path.join("paper_2510_24186_b300", "csrc", f)
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
@@ -361,7 +361,7 @@ def main():
     prof = os.path.join(ROOT, "profiles", "sample_persistent_vina5_batched_screening.json")
     if os.path.exists(prof) and sp.term_set == 0 and args.optimizer == "adam" and maps is None:
         pj = json.load(open(prof))
-        if pj.get("source_hash") == kernel_source_hash():
+        if pj.get("source_hash") == kernel_source_hash() and (pj.get("cell"), pj.get("warps")) == (args.cell, args.warps):
             traffic = pj.get("dram_bytes_per_launch")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
