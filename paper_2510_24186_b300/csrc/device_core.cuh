@@ -485,6 +485,26 @@ __device__ __forceinline__ void cell_range(const DevPocket& pk, const uint32_t* 
     }
 }
 
+// Candidate blocks a point needs (pairs within the cutoff): the first entry of its cell's
+// list in beg and, in nblk, the blocks of the reach level that covers the point's distance
+// from the cell centre (delta <= (k + 1) / kReachLevels of the half diagonal, k =
+// floor(delta / half diagonal * kReachLevels)); nblk = 0 outside the grid.
+__device__ __forceinline__ void cell_blocks(const DevPocket& pk, float x, float y, float z, uint32_t& beg, int& nblk) {
+    const float fx = (x - pk.gx) * pk.inv_h, fy = (y - pk.gy) * pk.inv_h, fz = (z - pk.gz) * pk.inv_h;
+    beg = 0;
+    nblk = 0;
+    if (fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)pk.nx && fy < (float)pk.ny && fz < (float)pk.nz) {
+        const int cx = min((int)fx, pk.nx - 1), cy = min((int)fy, pk.ny - 1), cz = min((int)fz, pk.nz - 1);
+        const size_t cell = ((size_t)cz * pk.ny + cy) * pk.nx + cx;
+        const float ux = fx - ((float)cx + 0.5f), uy = fy - ((float)cy + 0.5f), uz = fz - ((float)cz + 0.5f);
+        // delta / half diagonal = |u| / (sqrt(3) / 2), in cell units
+        constexpr float kScale = (float)kReachLevels * 1.1547005383792515f;
+        const int k = min(kReachLevels - 1, (int)(sqrtf(fmaf(uz, uz, fmaf(uy, uy, ux * ux))) * kScale));
+        beg = __ldg(&pk.cell_start[cell]);
+        nblk = __ldg(&pk.cell_levels[cell * kReachLevels + k]);
+    }
+}
+
 // Grid-map cell of a point: true (and the cell + fractions in c / f) when maps are in use
 // and all 8 corners of the point's cell lie inside the map domain.
 __device__ __forceinline__ bool map_cell(const DevPocket& pk, float x, float y, float z, float4* cf) {

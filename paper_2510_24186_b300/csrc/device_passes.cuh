@@ -101,10 +101,11 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
         int nblk = 0;
         if (i < L) {
             const float4 x = W.xs[i];
-            uint32_t beg, end;
-            cell_range(pk, pk.cell_start, x.x, x.y, x.z, beg, end);
+            uint32_t beg;
+            int nb;
+            cell_blocks(pk, x.x, x.y, x.z, beg, nb);
             const int i0 = __ldg(&B.ipre[h.ipre_off + i]), i1 = __ldg(&B.ipre[h.ipre_off + i + 1]);
-            const int cbk = (MAPS && map_cell(pk, x.x, x.y, x.z, nullptr)) ? 0 : (int)((end - beg) >> 3);
+            const int cbk = (MAPS && map_cell(pk, x.x, x.y, x.z, nullptr)) ? 0 : nb;
             W.cs[i] = beg;
             W.cb[i] = cbk;
             W.ip[i] = i0;

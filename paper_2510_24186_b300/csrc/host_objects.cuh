@@ -28,6 +28,7 @@ struct trids_pocket {
     float4* d_atoms = nullptr;
     uint32_t* d_cell = nullptr;
     uint16_t* d_cand = nullptr;
+    uint16_t* d_levels = nullptr;        // candidate-grid reach levels [ncell][kReachLevels]
     DevParams* d_params = nullptr;
     uint32_t* d_ncell = nullptr;         // near lists of the atom-pair E_MDN (term set 1)
     uint16_t* d_nlist = nullptr;
@@ -42,6 +43,7 @@ struct trids_pocket {
     DevPocket view() const {
         DevPocket v;
         v.atoms = d_atoms; v.ptype = d_ptype; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
+        v.cell_levels = d_levels;
         v.n_res = rgrid.n_res; v.res_start = d_res_start; v.rcell_start = d_rcell;
         v.rlist = d_rlist;
         v.ncell_start = d_ncell; v.nlist = d_nlist;

@@ -266,6 +266,49 @@ void build_grid(int M, const float* xyz, float cutoff, float h, CandidateGrid* g
     g->cand.assign(total, (uint16_t)M);
     std::vector<uint32_t> fill(g->start.begin(), g->start.end() - 1);
     for (int j = 0; j < M; ++j) visit(j, [&](size_t cell) { g->cand[fill[cell]++] = (uint16_t)j; });
+    // Reach levels: a point at distance delta from its cell centre only needs the entries
+    // within cutoff + delta of the centre.  Level k covers delta <= (k + 1) / kReachLevels of
+    // the half diagonal; each cell's entries are ordered by level (ascending atom index
+    // inside a level) and level k's block count is stored.
+    g->levels.assign(ncell * kReachLevels, 0);
+    const double half = 0.5 * std::sqrt(3.0) * h, margin = 1e-3 * h + 1e-4;
+    double thr2[kReachLevels];
+    for (int k = 0; k < kReachLevels; ++k) {
+        const double t = cutoff + half * (k + 1) / kReachLevels + margin;
+        thr2[k] = t * t;
+    }
+    std::vector<uint16_t> tmp;
+    std::vector<int> lvl;
+    for (int iz = 0; iz < nz; ++iz)
+        for (int iy = 0; iy < ny; ++iy)
+            for (int ix = 0; ix < nx; ++ix) {
+                const size_t cell = ((size_t)iz * ny + iy) * nx + ix;
+                const uint32_t b = g->start[cell], n = count[cell];
+                if (n == 0) continue;
+                const double c[3] = {g->lo[0] + (ix + 0.5) * h, g->lo[1] + (iy + 0.5) * h, g->lo[2] + (iz + 0.5) * h};
+                int cnt[kReachLevels] = {0};
+                lvl.resize(n);
+                for (uint32_t q = 0; q < n; ++q) {
+                    const int j = g->cand[b + q];
+                    double r2 = 0;
+                    for (int d = 0; d < 3; ++d) {
+                        const double u = (double)xyz[3 * j + d] - c[d];
+                        r2 += u * u;
+                    }
+                    int k = 0;
+                    while (k < kReachLevels - 1 && r2 > thr2[k]) ++k;
+                    lvl[q] = k;
+                    ++cnt[k];
+                }
+                int at[kReachLevels];
+                for (int k = 0, acc = 0; k < kReachLevels; ++k) {
+                    at[k] = acc;
+                    acc += cnt[k];
+                    g->levels[cell * kReachLevels + k] = (uint16_t)((acc + 7) / 8);
+                }
+                tmp.assign(g->cand.begin() + b, g->cand.begin() + b + n);
+                for (uint32_t q = 0; q < n; ++q) g->cand[b + at[lvl[q]]++] = tmp[q];
+            }
 }
 
 void build_residue_grid(int M, const float* xyz, const int32_t* res, int n_res, const CandidateGrid& g,

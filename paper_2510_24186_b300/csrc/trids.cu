@@ -110,6 +110,7 @@ int trids_make_pocket(const float* xyz, const int32_t* type, int32_t n_atoms, co
     std::vector<DevParams> hp(1, pk->hp);
     if ((rc = upload(&pk->d_atoms, atoms)) || (rc = upload(&pk->d_ptype, ptype)) ||
         (rc = upload(&pk->d_cell, pk->grid.start)) || (rc = upload(&pk->d_cand, pk->grid.cand)) ||
+        (rc = upload(&pk->d_levels, pk->grid.levels)) ||
         (rc = upload(&pk->d_params, hp)) || (rc = upload_pocket_arrays(pk.get(), nullptr)) ||
         (rc = upload_near_lists(pk.get()))) {
         trids_free_pocket(pk.release());
@@ -164,6 +165,7 @@ int trids_free_pocket(trids_pocket* pk) {
     cudaFree(pk->d_ptype);
     cudaFree(pk->d_cell);
     cudaFree(pk->d_cand);
+    cudaFree(pk->d_levels);
     cudaFree(pk->d_params);
     cudaFree(pk->d_maps);
     cudaFree(pk->d_ncell);
@@ -229,6 +231,7 @@ int trids_set_residues(trids_pocket* pk, int32_t n_res, const int32_t* residue) 
     for (int j = 0; j < M; ++j) ptype[j] = (uint8_t)type[j];
     CK(cudaMemcpy(pk->d_ptype, ptype.data(), ptype.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(pk->d_cell, grid.start.data(), grid.start.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(pk->d_levels, grid.levels.data(), grid.levels.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
     pk->xyz.swap(xyz);
     pk->type.swap(type);
     pk->orig.swap(orig);

@@ -42,15 +42,22 @@ void topology_ints(const PackedLigand& lg, std::vector<int32_t>* out);
 // ---------------------------------------------------------------- candidate grid
 // Uniform grid over the pocket's bounding box grown by the cutoff.  Each cell lists
 // every pocket atom within cutoff + half the cell diagonal (+ a small margin) of the
-// cell centre, ascending, padded to a multiple of 8 with the sentinel index M.  A
-// ligand atom outside the grid has no pocket atom within the cutoff.  The device copy
-// carries each atom's flags in the top 3 bits of its entry (so M < 8192).
+// cell centre, padded to a multiple of 8 with the sentinel index M.  A ligand atom
+// outside the grid has no pocket atom within the cutoff.  The entries of a cell are
+// ordered by reach level: level k holds the atoms within cutoff + (k + 1) / kReachLevels
+// of the half diagonal (+ the margin) of the centre and not in a lower level (ascending
+// atom index inside a level); levels[cell][k] is the number of 8-entry blocks that
+// covers levels 0..k, so a point at distance delta <= (k + 1) / kReachLevels of the half
+// diagonal from its cell centre needs only those blocks.  The device copy carries each
+// atom's flags in the top 3 bits of its entry (so M < 8192).
+constexpr int kReachLevels = 8;
 struct CandidateGrid {
     float lo[3];
     float h;
     int dims[3];
     std::vector<uint32_t> start;    // [ncell + 1], offsets in entries (multiples of 8)
     std::vector<uint16_t> cand;
+    std::vector<uint16_t> levels;   // [ncell][kReachLevels] block counts
 };
 void build_grid(int M, const float* xyz, float cutoff, float h, CandidateGrid* g);
 
@@ -95,6 +102,7 @@ struct DevPocket {
     const uint8_t* ptype;          // [M + 1] (padded to 16 bytes): atom types
     const uint32_t* cell_start;
     const uint16_t* cand;          // pocket index (13 bits) | flags of that atom << 13
+    const uint16_t* cell_levels;   // [ncell][kReachLevels]: blocks needed per reach level
     const DevParams* params;
     int M;
     int nx, ny, nz;
