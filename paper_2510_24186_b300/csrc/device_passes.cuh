@@ -124,6 +124,9 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
         int ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
         float ri = xa.w;
         uint32_t fi = P.tflags[ti];
+        // per-atom operands of the packed evaluation, set when the lane changes atom
+        float2 nxy = make_float2(-xa.x, -xa.y), nzr = make_float2(-xa.z, -ri);
+        uint32_t mh = (fi & 1u) << 13, mb = (((fi & 2u) << 1) | ((fi & 4u) >> 1)) << 13;
         float ax = 0.f, ay = 0.f, az = 0.f;
         auto block_ptr = [&](int blk) -> const uint4* {
             const int loc = blk - first;
@@ -145,6 +148,10 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                 ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
                 ri = xa.w;
                 fi = P.tflags[ti];
+                nxy = make_float2(-xa.x, -xa.y);
+                nzr = make_float2(-xa.z, -ri);
+                mh = (fi & 1u) << 13;
+                mb = (((fi & 2u) << 1) | ((fi & 4u) >> 1)) << 13;
                 v = __ldg(block_ptr(blk));
             }
             const uint4 vc = v;
@@ -157,8 +164,6 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             const uint32_t f_hb = ((fi & 2u) << 1) | ((fi & 4u) >> 1);
             float eb = 0.f;
             float2 eb2 = make_float2(0.f, 0.f);
-            const float2 nxy = make_float2(-xa.x, -xa.y), nzr = make_float2(-xa.z, -ri);
-            const uint32_t mh = f_hyd << 13, mb = f_hb << 13;
             // two halves of four candidates: the loop body stays small for the
             // instruction cache, which the 16 resident warps share across all phases
 #pragma unroll 1
