@@ -476,36 +476,62 @@ __device__ float score_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
 
 // dE/dt = sum g_i and world torque tau = sum (x_i - t) x g_i (every lane), and
 // dE/dtheta_k = a_k . sum over the moving subtree of (x_i - p_k) x g_i with a_k the world
-// axis (parent atom -> child atom) and p_k the world parent atom (lane k, which sums its
-// subtree serially: no shuffles, and the subtree is one contiguous range).
+// axis (parent atom -> child atom) and p_k the world parent atom.  A torsion's moving
+// subtree is one contiguous atom range [z_k, w_k), so one warp scan gives inclusive
+// prefixes G(i) = sum_{i' <= i} g_i' and U(i) = sum_{i' <= i} (x_i' - t) x g_i' (kept in
+// W.rec and the per-atom list arrays, free at this point); lane k then takes
+// sum_[z,w) (x_i - p_k) x g_i = dU - (p_k - t) x dG with dU, dG the range differences.
 __device__ float adjoint_warp(const DevBatch& B, const LigHdr& h, const PW& W, const float t[3], float gt[3],
                               float tau[3]) {
-    const int L = h.n_atoms, T = h.n_tor;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f, a5 = 0.f;
-    for (int i = W.lane; i < L; i += 32) {
-        const float4 g = W.gs[i], x = W.xs[i];
-        const float rx = x.x - t[0], ry = x.y - t[1], rz = x.z - t[2];
-        a0 += g.x; a1 += g.y; a2 += g.z;
-        a3 += ry * g.z - rz * g.y;
-        a4 += rz * g.x - rx * g.z;
-        a5 += rx * g.y - ry * g.x;
+    const int L = h.n_atoms, T = h.n_tor, lane = W.lane;
+    float4* __restrict__ pu = W.rec;                                  // U prefix, [L]
+    float4* __restrict__ pg = reinterpret_cast<float4*>(W.cs);       // G prefix, [L]
+    float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};                      // totals of the rounds so far
+    for (int base = 0; base < L; base += 32) {
+        const int i = base + lane;
+        float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (i < L) {
+            const float4 g = W.gs[i], x = W.xs[i];
+            const float rx = x.x - t[0], ry = x.y - t[1], rz = x.z - t[2];
+            v[0] = g.x; v[1] = g.y; v[2] = g.z;
+            v[3] = ry * g.z - rz * g.y;
+            v[4] = rz * g.x - rx * g.z;
+            v[5] = rx * g.y - ry * g.x;
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float u = __shfl_up_sync(kFull, v[k], o);
+                if (lane >= o) v[k] += u;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] += c[k];
+        if (i < L) {
+            pg[i] = make_float4(v[0], v[1], v[2], 0.f);
+            pu[i] = make_float4(v[3], v[4], v[5], 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) c[k] = __shfl_sync(kFull, v[k], 31);
     }
-    gt[0] = warp_sum(a0); gt[1] = warp_sum(a1); gt[2] = warp_sum(a2);
-    tau[0] = warp_sum(a3); tau[1] = warp_sum(a4); tau[2] = warp_sum(a5);
+    gt[0] = c[0]; gt[1] = c[1]; gt[2] = c[2];
+    tau[0] = c[3]; tau[1] = c[4]; tau[2] = c[5];
+    __syncwarp();
     // torsion k on lane k: its moving subtree is the contiguous atom range [ti.z, ti.w)
     float mine = 0.f;
-    if (W.lane < T) {
-        const int4 ti = __ldg(&B.tor_idx[h.tor_off + W.lane]);
-        const float4 p = W.xs[ti.x], c = W.xs[ti.y];
-        float sx = 0.f, sy = 0.f, sz = 0.f;
-        for (int i = ti.z; i < ti.w; ++i) {
-            const float4 x = W.xs[i], g = W.gs[i];
-            const float rx = x.x - p.x, ry = x.y - p.y, rz = x.z - p.z;
-            sx += ry * g.z - rz * g.y;
-            sy += rz * g.x - rx * g.z;
-            sz += rx * g.y - ry * g.x;
-        }
-        const float ax = c.x - p.x, ay = c.y - p.y, az = c.z - p.z;
+    if (lane < T) {
+        const int4 ti = __ldg(&B.tor_idx[h.tor_off + lane]);
+        const float4 p = W.xs[ti.x], cc = W.xs[ti.y];
+        const float4 gw = pg[ti.w - 1], uw = pu[ti.w - 1];
+        const float4 gz = ti.z > 0 ? pg[ti.z - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 uz = ti.z > 0 ? pu[ti.z - 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float dgx = gw.x - gz.x, dgy = gw.y - gz.y, dgz = gw.z - gz.z;
+        const float px = p.x - t[0], py = p.y - t[1], pz = p.z - t[2];
+        const float sx = (uw.x - uz.x) - (py * dgz - pz * dgy);
+        const float sy = (uw.y - uz.y) - (pz * dgx - px * dgz);
+        const float sz = (uw.z - uz.z) - (px * dgy - py * dgx);
+        const float ax = cc.x - p.x, ay = cc.y - p.y, az = cc.z - p.z;
         const float n = rsqrtf(ax * ax + ay * ay + az * az);
         mine = (ax * sx + ay * sy + az * sz) * n;
     }
