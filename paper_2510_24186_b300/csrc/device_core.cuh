@@ -202,7 +202,8 @@ __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t par
 // One warp owns one pose.  Per-warp shared memory (pose_warp_bytes):
 //   xs  float4[Lm]      world coordinates of the pose's atoms
 //   gs  float4[Lm]      dE/dx_i
-//   rk  float4[3 Tm]    rows of each torsion's rotation matrix
+//   rk  float4[3 Tm]    rows of each torsion's rotation matrix; .w of the three rows holds
+//                       the torsion's pivot (parent axis atom, local coordinates)
 //   rec float4[Lm + 32] partial ligand-pocket forces, slot (atom + lane)
 //   cs  uint32[Lm]      candidate-list offset of each atom's cell
 //   pre int[Lm + 1]     exclusive prefix of each atom's candidate blocks
@@ -518,10 +519,12 @@ __device__ __forceinline__ bool map_cell(const DevPocket& pk, float x, float y, 
 }
 
 // Forward kinematics of the warp's pose.  Lane k < T builds torsion k's rotation
-// (Rodrigues, angle th held by lane k) into W.rk; then each lane places its atoms:
-// the torsions that move an atom (its fragment's torsion and that torsion's ancestors),
-// deepest first, about their input-geometry axes -- the axis atoms of a torsion are never
-// moved by the torsions below it -- then x = t + R(q) z.
+// (Rodrigues, angle th held by lane k) and pivot into W.rk; then each lane places its
+// atoms: the torsions that move an atom (its fragment's torsion and that torsion's
+// ancestors, the set bits of its mask), deepest first, about their input-geometry axes --
+// the axis atoms of a torsion are never moved by the torsions below it -- then
+// x = t + R(q) z.  Torsions are numbered breadth-first from the root, so a parent's
+// number is below its children's and deepest first is descending bit order.
 __device__ void fk_warp(const DevBatch& B, const LigHdr& h, const PW& W, const float t[3], const float q[4], float th,
                         const float* __restrict__ rad) {
     const int T = h.n_tor, L = h.n_atoms;
@@ -530,26 +533,26 @@ __device__ void fk_warp(const DevBatch& B, const LigHdr& h, const PW& W, const f
         float s, c;
         sincosf(th, &s, &c);
         const float kc = 1.f - c;
-        W.rk[3 * W.lane + 0] = make_float4(c + kc * u.x * u.x, kc * u.x * u.y - s * u.z, kc * u.x * u.z + s * u.y, 0.f);
-        W.rk[3 * W.lane + 1] = make_float4(kc * u.y * u.x + s * u.z, c + kc * u.y * u.y, kc * u.y * u.z - s * u.x, 0.f);
-        W.rk[3 * W.lane + 2] = make_float4(kc * u.z * u.x - s * u.y, kc * u.z * u.y + s * u.x, c + kc * u.z * u.z, 0.f);
+        const float4 pv = __ldg(&B.tor_p[h.tor_off + W.lane]);
+        W.rk[3 * W.lane + 0] = make_float4(c + kc * u.x * u.x, kc * u.x * u.y - s * u.z, kc * u.x * u.z + s * u.y, pv.x);
+        W.rk[3 * W.lane + 1] = make_float4(kc * u.y * u.x + s * u.z, c + kc * u.y * u.y, kc * u.y * u.z - s * u.x, pv.y);
+        W.rk[3 * W.lane + 2] = make_float4(kc * u.z * u.x - s * u.y, kc * u.z * u.y + s * u.x, c + kc * u.z * u.z, pv.z);
     }
     __syncwarp();
     float R[9];
     quat_to_mat(q, R);
-    const int8_t* __restrict__ tpar = B.tor_par + h.tor_off;
     for (int i = W.lane; i < L; i += 32) {
         const float4 y = __ldg(&B.atom_y[h.atom_off + i]);
         float x0 = y.x, x1 = y.y, x2 = y.z;
-        // the torsions that move atom i are its fragment's torsion and that torsion's
-        // ancestors; walking up the tree visits them deepest first
-        for (int k = __ldg(&B.atom_tor[h.atom_off + i]); k >= 0; k = __ldg(&tpar[k])) {
-            const float4 p = __ldg(&B.tor_p[h.tor_off + k]);
+        // the torsions that move atom i, deepest (highest number) first
+        for (uint32_t m = __ldg(&B.atom_mask[h.atom_off + i]); m;) {
+            const int k = 31 - __clz(m);
+            m ^= 1u << k;
             const float4 r0 = W.rk[3 * k], r1 = W.rk[3 * k + 1], r2 = W.rk[3 * k + 2];
-            const float vx = x0 - p.x, vy = x1 - p.y, vz = x2 - p.z;
-            x0 = p.x + (r0.x * vx + r0.y * vy + r0.z * vz);
-            x1 = p.y + (r1.x * vx + r1.y * vy + r1.z * vz);
-            x2 = p.z + (r2.x * vx + r2.y * vy + r2.z * vz);
+            const float vx = x0 - r0.w, vy = x1 - r1.w, vz = x2 - r2.w;
+            x0 = r0.w + (r0.x * vx + r0.y * vy + r0.z * vz);
+            x1 = r1.w + (r1.x * vx + r1.y * vy + r1.z * vz);
+            x2 = r2.w + (r2.x * vx + r2.y * vy + r2.z * vz);
         }
         W.xs[i] = make_float4(t[0] + (R[0] * x0 + R[1] * x1 + R[2] * x2), t[1] + (R[3] * x0 + R[4] * x1 + R[5] * x2),
                               t[2] + (R[6] * x0 + R[7] * x1 + R[8] * x2), rad[__float_as_int(y.w)]);

@@ -85,8 +85,7 @@ struct trids_batch {
     float4* d_tor_p = nullptr;
     int* d_ipre = nullptr;
     uint16_t* d_ient = nullptr;
-    int8_t* d_atom_tor = nullptr;
-    int8_t* d_tor_par = nullptr;
+    uint32_t* d_atom_mask = nullptr;
     std::vector<uint16_t> ient_j;     // intra partner lists: target index (pad = max_atoms)
     std::vector<uint8_t> ient_type;   // target type (for re-encoding flags)
     trids_pocket* owner = nullptr;    // pocket whose flags are encoded in d_ient
@@ -110,7 +109,7 @@ struct trids_batch {
         v.dof_stride = dims.dof_stride; v.n_fields = dims.state_fields;
         v.lig = d_lig; v.atom_y = d_atom_y; v.atom_orig = d_atom_orig; v.tor_idx = d_tor_idx;
         v.tor_u = d_tor_u; v.tor_p = d_tor_p; v.ipre = d_ipre; v.ient = d_ient;
-        v.atom_tor = d_atom_tor; v.tor_par = d_tor_par;
+        v.atom_mask = d_atom_mask;
         v.mdn = d_mdn; v.mdn_res = mdn_res; v.mdn_k = mdn_k;
         return v;
     }

@@ -401,7 +401,7 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
     const size_t o_hdr = section(sizeof(LigHdr) * n_lig), o_ay = section(sizeof(float4) * A),
                  o_orig = section(sizeof(int) * A), o_tidx = section(sizeof(int4) * T),
                  o_tu = section(sizeof(float4) * T), o_tp = section(sizeof(float4) * T), o_ipre = section(sizeof(int) * P),
-                 o_ient = section(sizeof(uint16_t) * E), o_ator = section(A), o_tpar = section(T),
+                 o_ient = section(sizeof(uint16_t) * E), o_mask = section(sizeof(uint32_t) * A),
                  o_cnt = section(4 * sizeof(unsigned int)), o_err = section(2 * sizeof(int));
     std::vector<unsigned char> stage(total, 0);
     unsigned char* hs = stage.data();
@@ -424,7 +424,7 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
         const int32_t* Ty = type + aoff[l];
         float4* ay = reinterpret_cast<float4*>(hs + o_ay) + aoff[l];
         int* orig = reinterpret_cast<int*>(hs + o_orig) + aoff[l];
-        int8_t* atom_tor = reinterpret_cast<int8_t*>(hs + o_ator) + aoff[l];
+        uint32_t* amask = reinterpret_cast<uint32_t*>(hs + o_mask) + aoff[l];
         for (int i = 0; i < lg.n_atoms; ++i) {
             const int a = lg.perm[i];
             float tb;
@@ -433,12 +433,13 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
             ay[i] = make_float4((float)((double)X[3 * a] - lg.c[0]), (float)((double)X[3 * a + 1] - lg.c[1]),
                                 (float)((double)X[3 * a + 2] - lg.c[2]), tb);
             orig[i] = a;
-            atom_tor[i] = (int8_t)(lg.frag[i] - 1);
+            uint32_t m = 0;
+            for (int k = lg.frag[i] - 1; k >= 0; k = lg.tpar[k]) m |= 1u << k;
+            amask[i] = m;
         }
         int4* tidx = reinterpret_cast<int4*>(hs + o_tidx) + toff[l];
         float4* tu = reinterpret_cast<float4*>(hs + o_tu) + toff[l];
         float4* tp = reinterpret_cast<float4*>(hs + o_tp) + toff[l];
-        int8_t* tor_par = reinterpret_cast<int8_t*>(hs + o_tpar) + toff[l];
         for (int k = 0; k < lg.n_tor; ++k) {
             const int pa = lg.perm[lg.tp[k]], ha = lg.perm[lg.th[k]];
             double u[3], nn = 0;
@@ -454,7 +455,6 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
                 return;
             }
             tidx[k] = make_int4(lg.tp[k], lg.th[k], lg.sb[k], lg.se[k]);
-            tor_par[k] = (int8_t)lg.tpar[k];
             tu[k] = make_float4((float)(u[0] / nn), (float)(u[1] / nn), (float)(u[2] / nn), 0.f);
             tp[k] = make_float4((float)((double)X[3 * pa] - lg.c[0]), (float)((double)X[3 * pa + 1] - lg.c[1]),
                                 (float)((double)X[3 * pa + 2] - lg.c[2]), 0.f);
@@ -502,8 +502,7 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
     b->d_tor_p = reinterpret_cast<float4*>(d + o_tp);
     b->d_ipre = reinterpret_cast<int*>(d + o_ipre);
     b->d_ient = reinterpret_cast<uint16_t*>(d + o_ient);
-    b->d_atom_tor = reinterpret_cast<int8_t*>(d + o_ator);
-    b->d_tor_par = reinterpret_cast<int8_t*>(d + o_tpar);
+    b->d_atom_mask = reinterpret_cast<uint32_t*>(d + o_mask);
     b->d_counter = reinterpret_cast<unsigned int*>(d + o_cnt);
     b->d_err = reinterpret_cast<int*>(d + o_err);
     b->dims.upload_bytes = (int64_t)total;

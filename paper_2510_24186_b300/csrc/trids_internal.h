@@ -22,6 +22,7 @@ constexpr int kTmax = TRIDS_MAX_TOR;
 constexpr int kNT = TRIDS_MAX_TYPES;
 constexpr int kK = TRIDS_MAX_GMM;
 constexpr int kMaxBoxes = TRIDS_MAX_BOXES;
+static_assert(kTmax <= 32, "per-atom torsion masks are 32-bit");
 
 // ---------------------------------------------------------------- host-side pack
 // Packed torsion tree of one ligand (rules in trids.h, trids_pack_ligands).
@@ -140,8 +141,8 @@ struct DevBatch {
     const int4* tor_idx;           // (parent atom, child atom, subtree begin, subtree end)
     const float4* tor_u;           // unit axis, input geometry
     const float4* tor_p;           // parent atom, local coords
-    const int8_t* atom_tor;        // per packed atom: torsion whose moving fragment holds it (-1: root)
-    const int8_t* tor_par;         // per torsion: parent torsion (-1: child of the root fragment)
+    const uint32_t* atom_mask;     // per packed atom: bit k set when torsion k moves it (its fragment's
+                                   // torsion and that torsion's ancestors; 0 for the root fragment)
     const int* ipre;               // per atom: first block of its intra partner list
     const uint16_t* ient;          // partner index | partner flags << 13; each intra pair appears
                                    // once from each side; padding = max_atoms (far sentinel)
