@@ -486,14 +486,17 @@ __device__ __forceinline__ void cell_range(const DevPocket& pk, const uint32_t* 
     }
 }
 
-// Candidate blocks a point needs (pairs within the cutoff): the first entry of its cell's
-// list in beg and, in nblk, the blocks of the reach level that covers the point's distance
-// from the cell centre (delta <= (k + 1) / kReachLevels of the half diagonal, k =
-// floor(delta / half diagonal * kReachLevels)); nblk = 0 outside the grid.
-__device__ __forceinline__ void cell_blocks(const DevPocket& pk, float x, float y, float z, uint32_t& beg, int& nblk) {
+// The part of a point's cell list the point needs: the list's first entry in beg and, in
+// n, the count levels[cell][k] of the reach level that covers the point's distance from the
+// cell centre (delta <= (k + 1) / kReachLevels of the half diagonal, k =
+// floor(delta / half diagonal * kReachLevels)); n = 0 outside the grid.  For the candidate
+// lists the counts are 8-entry blocks, for the near and residue lists entries.
+__device__ __forceinline__ void cell_levels(const DevPocket& pk, const uint32_t* __restrict__ starts,
+                                            const uint16_t* __restrict__ levels, float x, float y, float z,
+                                            uint32_t& beg, int& n) {
     const float fx = (x - pk.gx) * pk.inv_h, fy = (y - pk.gy) * pk.inv_h, fz = (z - pk.gz) * pk.inv_h;
     beg = 0;
-    nblk = 0;
+    n = 0;
     if (fx >= 0.f && fy >= 0.f && fz >= 0.f && fx < (float)pk.nx && fy < (float)pk.ny && fz < (float)pk.nz) {
         const int cx = min((int)fx, pk.nx - 1), cy = min((int)fy, pk.ny - 1), cz = min((int)fz, pk.nz - 1);
         const size_t cell = ((size_t)cz * pk.ny + cy) * pk.nx + cx;
@@ -501,8 +504,8 @@ __device__ __forceinline__ void cell_blocks(const DevPocket& pk, float x, float 
         // delta / half diagonal = |u| / (sqrt(3) / 2), in cell units
         constexpr float kScale = (float)kReachLevels * 1.1547005383792515f;
         const int k = min(kReachLevels - 1, (int)(sqrtf(fmaf(uz, uz, fmaf(uy, uy, ux * ux))) * kScale));
-        beg = __ldg(&pk.cell_start[cell]);
-        nblk = __ldg(&pk.cell_levels[cell * kReachLevels + k]);
+        beg = __ldg(&starts[cell]);
+        n = __ldg(&levels[cell * kReachLevels + k]);
     }
 }
 

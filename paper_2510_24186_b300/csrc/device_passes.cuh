@@ -103,7 +103,7 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             const float4 x = W.xs[i];
             uint32_t beg;
             int nb;
-            cell_blocks(pk, x.x, x.y, x.z, beg, nb);
+            cell_levels(pk, pk.cell_start, pk.cell_levels, x.x, x.y, x.z, beg, nb);
             const int i0 = __ldg(&B.ipre[h.ipre_off + i]), i1 = __ldg(&B.ipre[h.ipre_off + i + 1]);
             const int cbk = (MAPS && map_cell(pk, x.x, x.y, x.z, nullptr)) ? 0 : nb;
             W.cs[i] = beg;
@@ -297,10 +297,10 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
         int n = 0;
         if (i < L) {
             const float4 x = W.xs[i];
-            uint32_t beg = 0, end = 0;
-            if (!(MAPS && map_cell(pk, x.x, x.y, x.z, nullptr))) cell_range(pk, pk.ncell_start, x.x, x.y, x.z, beg, end);
+            uint32_t beg = 0;
+            if (!(MAPS && map_cell(pk, x.x, x.y, x.z, nullptr)))
+                cell_levels(pk, pk.ncell_start, pk.nlevels, x.x, x.y, x.z, beg, n);
             W.cs[i] = beg;
-            n = (int)(end - beg);
         }
         seg_scan(W, L, i, n, carry);
     }
@@ -373,10 +373,9 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
         int n = 0;
         if (i < L) {
             const float4 x = W.xs[i];
-            uint32_t beg, end;
-            cell_range(pk, pk.rcell_start, x.x, x.y, x.z, beg, end);
+            uint32_t beg;
+            cell_levels(pk, pk.rcell_start, pk.rlevels, x.x, x.y, x.z, beg, n);
             W.cs[i] = beg;
-            n = (int)(end - beg);
         }
         seg_scan(W, L, i, n, carry);
     }

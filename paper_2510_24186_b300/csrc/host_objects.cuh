@@ -32,6 +32,7 @@ struct trids_pocket {
     DevParams* d_params = nullptr;
     uint32_t* d_ncell = nullptr;         // near lists of the atom-pair E_MDN (term set 1)
     uint16_t* d_nlist = nullptr;
+    uint16_t* d_nlevels = nullptr;
     float* d_maps = nullptr;             // grid maps [type][z][y][x]
     int mdims[3] = {0, 0, 0};
     float mlo[3] = {0.f, 0.f, 0.f}, mh = 0.f;
@@ -40,13 +41,14 @@ struct trids_pocket {
     int32_t* d_res_start = nullptr;
     uint32_t* d_rcell = nullptr;
     uint32_t* d_rlist = nullptr;
+    uint16_t* d_rlevels = nullptr;
     DevPocket view() const {
         DevPocket v;
         v.atoms = d_atoms; v.ptype = d_ptype; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
         v.cell_levels = d_levels;
         v.n_res = rgrid.n_res; v.res_start = d_res_start; v.rcell_start = d_rcell;
-        v.rlist = d_rlist;
-        v.ncell_start = d_ncell; v.nlist = d_nlist;
+        v.rlist = d_rlist; v.rlevels = d_rlevels;
+        v.ncell_start = d_ncell; v.nlist = d_nlist; v.nlevels = d_nlevels;
         {
             const float nc = std::min(kMdnCut, prm.cutoff);
             v.near_cut2 = nc * nc;
@@ -351,20 +353,24 @@ int check_device_ptr(const void* p, const char* name, bool nullable) {
 // Near lists of the atom-pair E_MDN on the pocket's current grid (storage order).
 int upload_near_lists(trids_pocket* pk) {
     std::vector<uint32_t> start;
-    std::vector<uint16_t> list;
-    build_near_lists(pk->M, pk->xyz.data(), std::min(kMdnCut, pk->cutoff_built), pk->grid, &start, &list);
+    std::vector<uint16_t> list, levels;
+    build_near_lists(pk->M, pk->xyz.data(), std::min(kMdnCut, pk->cutoff_built), pk->grid, &start, &list, &levels);
     uint32_t* d_start = nullptr;
     uint16_t* d_list = nullptr;
+    uint16_t* d_levels = nullptr;
     int rc;
-    if ((rc = upload(&d_start, start)) || (rc = upload(&d_list, list))) {
+    if ((rc = upload(&d_start, start)) || (rc = upload(&d_list, list)) || (rc = upload(&d_levels, levels))) {
         cudaFree(d_start);
         cudaFree(d_list);
+        cudaFree(d_levels);
         return rc;
     }
     cudaFree(pk->d_ncell);
     cudaFree(pk->d_nlist);
+    cudaFree(pk->d_nlevels);
     pk->d_ncell = d_start;
     pk->d_nlist = d_list;
+    pk->d_nlevels = d_levels;
     return TRIDS_OK;
 }
 

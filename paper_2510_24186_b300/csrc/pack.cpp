@@ -311,6 +311,50 @@ void build_grid(int M, const float* xyz, float cutoff, float h, CandidateGrid* g
             }
 }
 
+// Orders each cell's list [start[c], start[c+1]) by reach level and fills levels[c][k] with
+// the number of entries of levels 0..k (level k: distance from the cell centre within
+// base + (k + 1) / kReachLevels of the half diagonal, plus the rounding margin; the last level
+// takes the rest).  dist2(entry, centre) is an entry's squared distance from a cell centre.
+template <class E, class D>
+static void order_by_reach(const CandidateGrid& g, double base, const std::vector<uint32_t>& start, std::vector<E>* list,
+                           std::vector<uint16_t>* levels, D&& dist2) {
+    const int nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
+    const double h = g.h, half = 0.5 * std::sqrt(3.0) * h, margin = 1e-3 * h + 1e-4;
+    double thr2[kReachLevels];
+    for (int k = 0; k < kReachLevels; ++k) {
+        const double t = base + half * (k + 1) / kReachLevels + margin;
+        thr2[k] = t * t;
+    }
+    levels->assign((size_t)nx * ny * nz * kReachLevels, 0);
+    std::vector<E> tmp;
+    std::vector<int> lvl;
+    for (int iz = 0; iz < nz; ++iz)
+        for (int iy = 0; iy < ny; ++iy)
+            for (int ix = 0; ix < nx; ++ix) {
+                const size_t cell = ((size_t)iz * ny + iy) * nx + ix;
+                const uint32_t b = start[cell], n = start[cell + 1] - b;
+                if (n == 0) continue;
+                const double c[3] = {g.lo[0] + (ix + 0.5) * h, g.lo[1] + (iy + 0.5) * h, g.lo[2] + (iz + 0.5) * h};
+                int cnt[kReachLevels] = {0};
+                lvl.resize(n);
+                for (uint32_t q = 0; q < n; ++q) {
+                    const double r2 = dist2((*list)[b + q], c);
+                    int k = 0;
+                    while (k < kReachLevels - 1 && r2 > thr2[k]) ++k;
+                    lvl[q] = k;
+                    ++cnt[k];
+                }
+                int at[kReachLevels];
+                for (int k = 0, acc = 0; k < kReachLevels; ++k) {
+                    at[k] = acc;
+                    acc += cnt[k];
+                    (*levels)[cell * kReachLevels + k] = (uint16_t)acc;
+                }
+                tmp.assign(list->begin() + b, list->begin() + b + n);
+                for (uint32_t q = 0; q < n; ++q) (*list)[b + at[lvl[q]]++] = tmp[q];
+            }
+}
+
 void build_residue_grid(int M, const float* xyz, const int32_t* res, int n_res, const CandidateGrid& g,
                         ResidueGrid* out) {
     out->n_res = n_res;
@@ -371,10 +415,25 @@ void build_residue_grid(int M, const float* xyz, const int32_t* res, int n_res, 
                              ((uint32_t)(out->start[r + 1] - out->start[r]) << 26);
         visit_residue(r, [&](size_t cell) { out->list[fill[cell]++] = ent; });
     }
+    // reach levels by the residue's nearest atom to the cell centre
+    order_by_reach(g, kMdnCut, out->cell_start, &out->list, &out->levels, [&](uint32_t ent, const double* c) {
+        const int a0 = (int)((ent >> 13) & 0x1fffu), a1 = a0 + (int)(ent >> 26);
+        double best = 1e300;
+        for (int a = a0; a < a1; ++a) {
+            const int j = out->atoms[a];
+            double r2 = 0;
+            for (int d = 0; d < 3; ++d) {
+                const double u = (double)xyz[3 * j + d] - c[d];
+                r2 += u * u;
+            }
+            best = std::min(best, r2);
+        }
+        return best;
+    });
 }
 
 void build_near_lists(int M, const float* xyz, float cutoff, const CandidateGrid& g, std::vector<uint32_t>* start,
-                      std::vector<uint16_t>* list) {
+                      std::vector<uint16_t>* list, std::vector<uint16_t>* levels) {
     const int nx = g.dims[0], ny = g.dims[1], nz = g.dims[2];
     const double h = g.h;
     const size_t ncell = (size_t)nx * ny * nz;
@@ -410,6 +469,14 @@ void build_near_lists(int M, const float* xyz, float cutoff, const CandidateGrid
     list->assign(total, 0);
     std::vector<uint32_t> fill(start->begin(), start->end() - 1);
     for (int j = 0; j < M; ++j) visit(j, [&](size_t cell) { (*list)[fill[cell]++] = (uint16_t)j; });
+    order_by_reach(g, (double)cutoff, *start, list, levels, [&](uint16_t j, const double* c) {
+        double r2 = 0;
+        for (int d = 0; d < 3; ++d) {
+            const double u = (double)xyz[3 * j + d] - c[d];
+            r2 += u * u;
+        }
+        return r2;
+    });
 }
 
 }  // namespace trids

@@ -173,6 +173,8 @@ int trids_free_pocket(trids_pocket* pk) {
     cudaFree(pk->d_res_start);
     cudaFree(pk->d_rcell);
     cudaFree(pk->d_rlist);
+    cudaFree(pk->d_rlevels);
+    cudaFree(pk->d_nlevels);
     delete pk;
     return TRIDS_OK;
 }
@@ -222,8 +224,10 @@ int trids_set_residues(trids_pocket* pk, int32_t n_res, const int32_t* residue) 
     int32_t* d_start = nullptr;
     uint32_t* d_list = nullptr;
     uint32_t* d_cell = nullptr;
-    if ((rc = upload(&d_start, rg.start)) || (rc = upload(&d_cell, rg.cell_start)) || (rc = upload(&d_list, rg.list))) {
-        cudaFree(d_start); cudaFree(d_cell); cudaFree(d_list);
+    uint16_t* d_rlev = nullptr;
+    if ((rc = upload(&d_start, rg.start)) || (rc = upload(&d_cell, rg.cell_start)) || (rc = upload(&d_list, rg.list)) ||
+        (rc = upload(&d_rlev, rg.levels))) {
+        cudaFree(d_start); cudaFree(d_cell); cudaFree(d_list); cudaFree(d_rlev);
         return rc;
     }
     CK(cudaDeviceSynchronize());   // no launch may still read the arrays being replaced
@@ -238,8 +242,8 @@ int trids_set_residues(trids_pocket* pk, int32_t n_res, const int32_t* residue) 
     pk->grid = std::move(grid);
     if ((rc = upload_pocket_arrays(pk, nullptr))) return rc;   // atoms + candidate entries with flags
     if ((rc = upload_near_lists(pk))) return rc;
-    cudaFree(pk->d_res_start); cudaFree(pk->d_rcell); cudaFree(pk->d_rlist);
-    pk->d_res_start = d_start; pk->d_rcell = d_cell; pk->d_rlist = d_list;
+    cudaFree(pk->d_res_start); cudaFree(pk->d_rcell); cudaFree(pk->d_rlist); cudaFree(pk->d_rlevels);
+    pk->d_res_start = d_start; pk->d_rcell = d_cell; pk->d_rlist = d_list; pk->d_rlevels = d_rlev;
     pk->rgrid = std::move(rg);
     return TRIDS_OK;
 }

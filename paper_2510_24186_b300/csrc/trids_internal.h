@@ -65,8 +65,10 @@ void build_grid(int M, const float* xyz, float cutoff, float h, CandidateGrid* g
 // Residue lists of the residue-level E_MDN.  Atoms are grouped by residue (ascending
 // atom index inside a residue, so the first minimum met is the lowest index; the library
 // stores the pocket in that order once residues are set).  On the candidate grid's cells,
-// each cell lists (ascending) every residue with an atom within kMdnCut + half the cell
-// diagonal (+ a small margin) of the cell centre.
+// each cell lists every residue with an atom within kMdnCut + half the cell diagonal (+ a
+// small margin) of the cell centre, ordered by the reach level of the residue's nearest
+// atom (as for the candidate lists; ascending residue inside a level); levels[cell][k]
+// counts the residues of levels 0..k.
 constexpr float kMdnCut = 5.0f;   // Sec. 2: node pairs closer than d_cutoff = 5 A
 constexpr int kMaxResidueAtoms = 63;
 struct ResidueGrid {
@@ -75,15 +77,17 @@ struct ResidueGrid {
     std::vector<uint16_t> atoms;       // pocket atom indices grouped by residue
     std::vector<uint32_t> cell_start;  // [ncell + 1]
     std::vector<uint32_t> list;        // residue r | first atom << 13 | atom count << 26
+    std::vector<uint16_t> levels;      // [ncell][kReachLevels]
 };
 void build_residue_grid(int M, const float* xyz, const int32_t* res, int n_res, const CandidateGrid& g,
                         ResidueGrid* out);
 
 // Near lists of the atom-pair E_MDN (term set 1, r < 5 A): on the candidate grid's cells,
-// each cell lists (ascending) the pocket atoms within `cutoff` + half the cell diagonal
-// (+ a small margin) of the cell centre.  No padding.
+// each cell lists the pocket atoms within `cutoff` + half the cell diagonal (+ a small
+// margin) of the cell centre, ordered by reach level (ascending atom index inside a level);
+// levels[cell][k] counts the atoms of levels 0..k.  No padding.
 void build_near_lists(int M, const float* xyz, float cutoff, const CandidateGrid& g, std::vector<uint32_t>* start,
-                      std::vector<uint16_t>* list);
+                      std::vector<uint16_t>* list, std::vector<uint16_t>* levels);
 
 // ---------------------------------------------------------------- device views
 // Staged into shared memory by every block: the Vina-form path copies the prefix up
@@ -119,12 +123,14 @@ struct DevPocket {
     // near lists of the atom-pair E_MDN (term set 1), same cells as cell_start
     const uint32_t* ncell_start;
     const uint16_t* nlist;
+    const uint16_t* nlevels;       // [ncell][kReachLevels]: near-list entries per reach level
     float near_cut2;               // min(5 A, cutoff)^2
     // residue-level E_MDN (term set 2)
     int n_res;
     const int32_t* res_start;      // [n_res + 1]: residue r = staged pocket atoms [start[r], start[r+1])
     const uint32_t* rcell_start;   // [ncell + 1], same cells as cell_start
     const uint32_t* rlist;         // residues near each cell: r | first atom << 13 | atom count << 26
+    const uint16_t* rlevels;       // [ncell][kReachLevels]: residue-list entries per reach level
 };
 
 struct LigHdr {
