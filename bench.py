@@ -188,7 +188,7 @@ def oracle_sample_rate(w, budget_s=12.0, max_ligs=64, n_threads=None, first=0, t
 def run_reference(args, rank):
     if rank != 0:
         return
-    w = synth.workload(2)
+    w = synth.workload("batched_screening")
     rates = []
     for k in range(args.warmup + args.steps):
         r, cores, n, dt = oracle_sample_rate(w, budget_s=0.0, max_ligs=1, first=k % len(w.ligands))
@@ -214,13 +214,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="trids", choices=["trids", "reference"])
     ap.add_argument("--per-ligand-steps", type=int, default=None,
-                    help="timed steps of the plain per-ligand form (default 1 for workload 2, else 0)")
+                    help="timed steps of the plain per-ligand form (default 1 for batched_screening, else 0)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--n-lig", type=int, default=0, help="first N ligands only (small profiling case)")
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 4, 5],
-                    help="2: batched screening (the headline); 4: screening stream of 100,000 ligands "
-                         "(end to end over uneven batches); 5: blind-docking scale, three cavities")
+    ap.add_argument("--workload", default="batched_screening",
+                    choices=["batched_screening", "screening_stream", "blind_docking"],
+                    help="batched_screening (the headline); screening_stream: 100,000 ligands end to end "
+                         "over uneven batches; blind_docking: 6,000-atom region, three cavities")
     ap.add_argument("--cell", type=float, default=0.0, help="candidate-grid cell edge in A (0 = library default)")
     ap.add_argument("--terms", default="vina5", choices=sorted(TERMS),
                     help="term set: vina5 (default), trids (atom-pair E_MDN), trids_res (residue-level E_MDN)")
@@ -246,7 +247,7 @@ def main():
     if w.cell and not args.cell:
         args.cell = w.cell
     if args.per_ligand_steps is None:
-        args.per_ligand_steps = 1 if args.workload == 2 else 0
+        args.per_ligand_steps = 1 if args.workload == "batched_screening" else 0
     sp, res = score_setup(args.terms, w)
     arrays = synth.concat_ligands(w.ligands)
     tuned = None
@@ -348,13 +349,13 @@ def main():
     # end to end through the public API: the screening stream packs each batch's host arrays
     # (on a host thread, while the previous batch samples), uploads them, samples, ranks and
     # copies the top-k back to pinned host memory; every step is one whole batch
-    # (workload 4: one pass over the whole ligand set in seeded uneven batches of 500-5,000
+    # (screening_stream: one pass over the whole ligand set in seeded uneven batches of 500-5,000
     # ligands, the first batch untimed)
     stats = {}
     torch.cuda.synchronize()
     marks = []
     prep = (lambda bb: bb.set_mdn(mdn, stream=stream)) if mdn is not None else None
-    if args.workload == 4 and mdn is None:
+    if args.workload == "screening_stream" and mdn is None:
         rng4 = np.random.default_rng(w.seed + 4)
         cuts = [0]
         while cuts[-1] < len(w.ligands):
@@ -389,7 +390,7 @@ def main():
     clocks = clk.summary()
     traffic = None
     prof = os.path.join(ROOT, "profiles", "sample_persistent_vina5_batched_screening.json")
-    if os.path.exists(prof) and sp.term_set == 0 and args.optimizer == "adam" and maps is None and args.workload == 2:
+    if os.path.exists(prof) and sp.term_set == 0 and args.optimizer == "adam" and maps is None and args.workload == "batched_screening":
         pj = json.load(open(prof))
         if pj.get("source_hash") == kernel_source_hash() and (pj.get("cell"), pj.get("warps")) == (args.cell, args.warps):
             traffic = pj.get("dram_bytes_per_launch")
@@ -440,9 +441,9 @@ def main():
                                 "sample": f"first {n} ligands x {P} poses x {S} evaluations, FP64 all-pairs "
                                           f"oracle, {dt:.1f} s"}
         if args.terms == "vina5":
-            w1 = synth.workload(1)
+            w1 = synth.workload("single_ligand")
             r1, c1, n1, dt1 = oracle_sample_rate(w1, budget_s=0.0, max_ligs=1, n_threads=1)
-            line["cpu_baseline_config1"] = {"value": r1, "unit": UNIT, "cores": c1, "kind": "oracle",
+            line["cpu_baseline_single_ligand"] = {"value": r1, "unit": UNIT, "cores": c1, "kind": "oracle",
                                             "sample": f"the single-ligand workload in full ({w1.poses} poses x "
                                                       f"{w1.steps} evaluations, 300-atom pocket), one thread, "
                                                       f"{dt1:.2f} s"}

@@ -316,40 +316,52 @@ def _ligand_set(rng, n_lig, l_range, t_range, mix, center):
     return out
 
 
-def workload(k: int, n_lig: int | None = None) -> Workload:
-    """The five seeded workloads (seed 1000 + k).  `n_lig` truncates the ligand set.
+# Named seeded workloads and their seeds.
+WORKLOAD_SEEDS = {
+    "single_ligand": 1001,
+    "batched_screening": 1002,
+    "adjoint_check": 1003,
+    "screening_stream": 1004,
+    "blind_docking": 1005,
+}
 
-    1: 1 ligand, L=24, T=4, M=300, P=64, S=30.
-    2: 1,024 ligands, L~U{10..60}, T~U{0..15}, M=1,500, P=128, S=50, top-9.
-    3: 256 ligands, L~U{10..40}, T~U{0..10}, M=1,500, P=64 random poses.
-    4: 100,000 ligands, L~U{10..70}, T~U{0..20}, drug-like mix, M=2,000, P=64, S=40.
-    5: 6,000 atoms around 3 cavities, 4,096 ligands, L~U{20..60}, T<=15, P=512, S=100.
+
+def workload(name: str, n_lig: int | None = None) -> Workload:
+    """The five seeded workloads, by name.  `n_lig` truncates the ligand set.
+
+    single_ligand:     1 ligand, L=24, T=4, M=300, P=64, S=30.
+    batched_screening: 1,024 ligands, L~U{10..60}, T~U{0..15}, M=1,500, P=128, S=50, top-9.
+    adjoint_check:     256 ligands, L~U{10..40}, T~U{0..10}, M=1,500, P=64 random poses.
+    screening_stream:  100,000 ligands, L~U{10..70}, T~U{0..20}, drug-like mix, M=2,000, P=64, S=40.
+    blind_docking:     6,000 atoms around 3 cavities, 4,096 ligands, L~U{20..60}, T<=15, P=512, S=100.
     """
-    seed = 1000 + k
+    if name not in WORKLOAD_SEEDS:
+        raise ValueError(f"unknown workload {name!r}; one of {sorted(WORKLOAD_SEEDS)}")
+    seed = WORKLOAD_SEEDS[name]
     rng = np.random.default_rng(seed)
     c0 = np.zeros(3)
     box = np.full(3, 22.5)
-    if k == 1:
+    if name == "single_ligand":
         pk = gen_pocket(rng, 300, c0)
         ligs = [gen_ligand(rng, 24, 4, UNIFORM_MIX, c0)]
         return Workload("single ligand (L=24, T=4), 300-atom pocket, 64 poses x 30 steps",
                         pk, ligs, c0, box, 64, 30, 8, 8.0, 9, seed)
-    if k == 2:
+    if name == "batched_screening":
         pk = gen_pocket(rng, 1500, c0)
         ligs = _ligand_set(rng, n_lig or 1024, (10, 60), (0, 15), UNIFORM_MIX, c0)
         return Workload("batched screening: 1,024 ligands (L 10-60, T 0-15) x 128 poses x 50 steps, "
                         "1,500-atom pocket, top-9", pk, ligs, c0, box, 128, 50, 8, 8.0, 9, seed)
-    if k == 3:
+    if name == "adjoint_check":
         pk = gen_pocket(rng, 1500, c0)
         ligs = _ligand_set(rng, n_lig or 256, (10, 40), (0, 10), UNIFORM_MIX, c0)
         return Workload("adjoint check: 256 ligands (L 10-40, T 0-10) x 64 random poses",
                         pk, ligs, c0, box, 64, 0, 8, 8.0, 9, seed)
-    if k == 4:
+    if name == "screening_stream":
         pk = gen_pocket(rng, 2000, c0, type_probs=DRUGLIKE_MIX)
         ligs = _ligand_set(rng, n_lig or 100000, (10, 70), (0, 20), DRUGLIKE_MIX, c0)
         return Workload("screening stream: 100,000 ligands (L 10-70, T 0-20) x 64 poses x 40 steps, "
                         "2,000-atom pocket", pk, ligs, c0, box, 64, 40, 8, 8.0, 9, seed)
-    if k == 5:
+    if name == "blind_docking":
         side = 18.0
         cav = np.array([[0.0, 0.0, 0.0], [side, 0.0, 0.0], [side / 2, side * math.sqrt(3) / 2, 0.0]])
         cav -= cav.mean(axis=0)
@@ -358,4 +370,4 @@ def workload(k: int, n_lig: int | None = None) -> Workload:
         return Workload("blind-docking scale: 6,000-atom region, 3 cavities, 4,096 ligands x 512 poses "
                         "x 100 steps", pk, ligs, c0, np.full(3, 22.5), 512, 100, 8, 8.0, 9,
                         seed, cell=1.0, box_centers=cav, box_sizes=np.full((3, 3), 22.5))
-    raise ValueError(f"unknown workload {k}")
+    raise AssertionError(name)

@@ -23,7 +23,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_host_pack_matches_oracle_bit_exact(orc):
     rng = np.random.default_rng(21)
-    ligs = [synth.workload(1).ligands[0]]
+    ligs = [synth.workload("single_ligand").ligands[0]]
     ligs += [synth.gen_ligand(rng, int(rng.integers(1, 71)), int(rng.integers(0, 21))) for _ in range(60)]
     ligs += [synth.gen_ligand(rng, 70, 20), synth.gen_ligand(rng, 1, 0), synth.gen_ligand(rng, 2, 0)]
     for lg in ligs:
@@ -35,7 +35,7 @@ def test_host_pack_matches_oracle_bit_exact(orc):
 
 @pytest.mark.parametrize("case", ["ring_rot", "disconnected", "dup", "type", "nan", "big", "self"])
 def test_host_pack_rejects_bad_ligands(case):
-    lg = synth.workload(1).ligands[0]
+    lg = synth.workload("single_ligand").ligands[0]
     xyz, t, b, r = lg.xyz.copy(), lg.type.copy(), lg.bonds.copy(), lg.rotatable.copy()
     if case == "ring_rot":
         b = np.vstack([b, [[0, 9]]]) if not any((b == [0, 9]).all(1)) else b
@@ -89,7 +89,7 @@ def test_python_api_fails_loudly_without_cuda():
     if torch.cuda.is_available():
         pytest.skip("a CUDA device is present")
     from paper_2510_24186_b300 import api, synth
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     sp = api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, 8.0)
     with pytest.raises(RuntimeError, match="CUDA"):
         api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)

@@ -35,9 +35,9 @@ def report(st: Stats, what):
 
 @pytest.mark.parametrize("term_set", [0, 1])
 def test_map_score_parity(api, term_set):
-    """Config 1 shapes, 64 random poses, maps at 0.375 A over the box + 4 A (some atoms fall
+    """Single-ligand workload shapes, 64 random poses, maps at 0.375 A over the box + 4 A (some atoms fall
     outside and keep the direct sum)."""
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     sp = score_params(term_set, cutoff=w.cutoff if term_set == 0 else 10.0)
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
     pk.build_maps(0.375, 4.0)
@@ -69,8 +69,8 @@ def test_map_score_parity(api, term_set):
     report(st, f"map score term_set={term_set}")
 
 
-def test_map_sampler_per_step_parity_config1(api):
-    w = synth.workload(1)
+def test_map_sampler_per_step_parity_single_ligand(api):
+    w = synth.workload("single_ligand")
     sp = score_params(0, cutoff=w.cutoff)
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
     pk.build_maps(0.375, 8.0)
@@ -86,7 +86,7 @@ def test_map_sampler_per_step_parity_config1(api):
     st = check_trace(out["trace"].cpu().numpy(), list(range(P)), P, oracle_ligands(w.ligands),
                      *pocket_arrays(w.pocket), oracle_params(sp), cfg, S, w.mc_loops, seed,
                      out["dof"].cpu().numpy(), out["energy"].cpu().numpy(), mp=oracle_maps(pk))
-    report(st, "map sampler config 1")
+    report(st, "map sampler single ligand")
     o2 = api.sample(pk, b, P, S, mc_loops=w.mc_loops, seed=seed, mode=1)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(o2["dof"].cpu().numpy(), out["dof"].cpu().numpy())
@@ -94,7 +94,7 @@ def test_map_sampler_per_step_parity_config1(api):
 
 def test_map_rules(api):
     from paper_2510_24186_b300._lib import TridsError
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     sp = score_params(0, cutoff=w.cutoff)
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
     b = api.Batch.from_ligands(pk, w.ligands)
@@ -124,7 +124,7 @@ def test_map_rules(api):
 def test_maps_with_residue_terms(api):
     """Term set 2 with grid maps: the maps hold the atom-pair physics terms, the residue-level
     E_MDN stays direct; every pose checked against the oracle's map form with residues."""
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     sp = api.ScoreParams(2, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.TRIDS_WEIGHTS, 10.0)
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
     rng = np.random.default_rng(61)

@@ -1,5 +1,5 @@
 """GPU parity of the update rules other than Adam (Table S5): per-evaluation trace of
-config 1 against the oracle, which applies its FP64 rule to the GPU's state and gradient."""
+the single-ligand workload against the oracle, which applies its FP64 rule to the GPU's state and gradient."""
 import numpy as np
 import pytest
 
@@ -33,7 +33,7 @@ def api():
 
 @pytest.mark.parametrize("name,hp", RULES, ids=[f"{n}-{i}" for i, (n, _) in enumerate(RULES)])
 def test_update_rule_per_step_parity(api, name, hp):
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     sp = score_params(0, cutoff=w.cutoff)
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
     b = api.Batch.from_ligands(pk, w.ligands)
@@ -62,7 +62,7 @@ def test_update_rule_per_step_parity(api, name, hp):
 
 def test_unknown_update_rule_is_rejected(api):
     from paper_2510_24186_b300 import _lib
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, score_params(0))
     b = api.Batch.from_ligands(pk, w.ligands)
     _lib.OPTIMIZERS["bogus"] = 9

@@ -46,7 +46,7 @@ def report(st: Stats, what):
 
 # --------------------------------------------------------------------------- topology
 def test_batch_topology_matches_oracle(api):
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     rng = np.random.default_rng(5)
     ligs = w.ligands + [synth.gen_ligand(rng, int(rng.integers(1, 71)), int(rng.integers(0, 21))) for _ in range(40)]
     ligs.append(synth.gen_ligand(rng, 70, 20))
@@ -69,8 +69,8 @@ def _score_case(api, w, term_set, ligs, P, seed, xyz=False):
 
 @pytest.mark.parametrize("term_set", [0, 1])
 def test_score_grad_parity_single_ligand(api, term_set):
-    """Config 1 shapes: one 24-atom ligand, 300-atom pocket, 64 random poses; every pose checked."""
-    w = synth.workload(1)
+    """Single-ligand workload shapes: one 24-atom ligand, 300-atom pocket, 64 random poses; every pose checked."""
+    w = synth.workload("single_ligand")
     sp, b, dof, out = _score_case(api, w, term_set, w.ligands, 64, 11, xyz=True)
     op = oracle_params(sp)
     pxyz, ptype = pocket_arrays(w.pocket)
@@ -96,9 +96,9 @@ def test_score_grad_parity_single_ligand(api, term_set):
 
 @pytest.mark.parametrize("term_set", [0, 1])
 def test_score_grad_parity_batch_ragged(api, term_set):
-    """Config 3 shapes (ligands 10-40 atoms, 0-10 torsions, 1,500-atom pocket), 37 poses
+    """Adjoint-check workload shapes (ligands 10-40 atoms, 0-10 torsions, 1,500-atom pocket), 37 poses
     (a ragged 32-pose tile), a sample of ligands x poses checked one by one."""
-    w = synth.workload(3, n_lig=48)
+    w = synth.workload("adjoint_check", n_lig=48)
     sp, b, dof, out = _score_case(api, w, term_set, w.ligands, 37, 12)
     op = oracle_params(sp)
     pxyz, ptype = pocket_arrays(w.pocket)
@@ -123,7 +123,7 @@ def test_score_grad_parity_batch_ragged(api, term_set):
 def test_parameter_gradients_and_autograd(api, term_set):
     """dE/dw and dE/dR summed over poses with upstream weights, through TridsScore."""
     from paper_2510_24186_b300.autograd import score as tscore
-    w = synth.workload(3, n_lig=12)
+    w = synth.workload("adjoint_check", n_lig=12)
     sp, pk, b = make(api, w, term_set)
     rng = np.random.default_rng(4)
     P = 40
@@ -164,10 +164,10 @@ def _sample(api, pk, b, w, seed, P=None, S=None, **kw):
 
 
 @pytest.mark.parametrize("term_set", [0, 1])
-def test_sampler_per_step_parity_config1(api, term_set):
-    """Config 1: every pose, every evaluation: energy, gradient, Adam update, Metropolis
+def test_sampler_per_step_parity_single_ligand(api, term_set):
+    """Single-ligand workload: every pose, every evaluation: energy, gradient, Adam update, Metropolis
     decision, perturbation, initial and final state against the oracle."""
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     sp, pk, b = make(api, w, term_set)
     seed = 1001
     P, S = w.poses, w.steps
@@ -176,11 +176,11 @@ def test_sampler_per_step_parity_config1(api, term_set):
     st = check_trace(out["trace"].cpu().numpy(), list(range(P)), P, oracle_ligands(w.ligands),
                      *pocket_arrays(w.pocket), oracle_params(sp), cfg_for(w, seed), S, w.mc_loops, seed,
                      out["dof"].cpu().numpy(), out["energy"].cpu().numpy())
-    report(st, f"sampler config 1 term_set={term_set}")
+    report(st, f"sampler single ligand term_set={term_set}")
 
 
 def test_persistent_graph_and_per_ligand_forms_are_bit_identical(api):
-    w = synth.workload(3, n_lig=20)
+    w = synth.workload("adjoint_check", n_lig=20)
     sp, pk, b = make(api, w)
     P, S = 45, 13
     runs = []
@@ -199,7 +199,7 @@ def test_persistent_graph_and_per_ligand_forms_are_bit_identical(api):
 
 def test_resume_is_bit_exact(api):
     """S = S1 + S2 with the state buffer carried over equals one S-evaluation run."""
-    w = synth.workload(3, n_lig=10)
+    w = synth.workload("adjoint_check", n_lig=10)
     sp, pk, b = make(api, w)
     P, S = 33, 21
     full = api.sample(pk, b, P, S, mc_loops=5, seed=5)
@@ -213,7 +213,7 @@ def test_resume_is_bit_exact(api):
 
 def test_edge_ligands_and_tiny_schedules(api):
     """A 1-atom ligand, a 2-atom ligand, a 70-atom / 20-torsion ligand, 1 pose, S < loops."""
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     rng = np.random.default_rng(9)
     ligs = [synth.gen_ligand(rng, 1, 0), synth.gen_ligand(rng, 2, 0), synth.gen_ligand(rng, 70, 20)]
     sp, pk, b = make(api, w, ligs=ligs)
@@ -228,7 +228,7 @@ def test_edge_ligands_and_tiny_schedules(api):
 
 
 def test_topk_matches_oracle(api):
-    w = synth.workload(3, n_lig=16)
+    w = synth.workload("adjoint_check", n_lig=16)
     sp, pk, b = make(api, w)
     P = 64
     out = api.sample(pk, b, P, 16, mc_loops=4, seed=9)
@@ -250,7 +250,7 @@ def test_topk_matches_oracle(api):
 def test_nonfinite_pose_is_flagged_and_sync_times_out(api):
     """Host-observable failures: a huge radius overflows the repulsion term to inf in
     float32, the pose is frozen and trids_sync reports it; a zero wait limit times out."""
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     sp = score_params(0)
     rad = list(sp.radius)
     rad[0] = 1e30
@@ -261,7 +261,7 @@ def test_nonfinite_pose_is_flagged_and_sync_times_out(api):
     b = api.Batch.from_ligands(pk, [lig])
     out = api.sample(pk, b, 32, 8, mc_loops=2, seed=1)
     assert api.sync(b, 32, out["state"], timeout_ms=60000) == -5
-    w2 = synth.workload(3, n_lig=64)
+    w2 = synth.workload("adjoint_check", n_lig=64)
     sp2, pk2, b2 = make(api, w2)
     out = api.sample(pk2, b2, 128, 40, mc_loops=8, seed=2)
     rc = api.sync(b2, 128, out["state"], timeout_ms=1e-6)
@@ -269,11 +269,11 @@ def test_nonfinite_pose_is_flagged_and_sync_times_out(api):
     assert api.sync(b2, 128, out["state"], timeout_ms=120000) == 0
 
 
-def test_config2_full_size_sampled(api):
+def test_batched_screening_full_size_sampled(api):
     """The benchmark's workload and launch (1,024 ligands x 128 poses x 50 evaluations,
     persistent launch in a CUDA graph): 256 seeded poses traced and checked per
     evaluation, top-9 of the traced ligands checked against the oracle."""
-    w = synth.workload(2)
+    w = synth.workload("batched_screening")
     sp, pk, b = make(api, w)
     P, S, seed = w.poses, w.steps, 2002
     rng = np.random.default_rng(2)
@@ -284,7 +284,7 @@ def test_config2_full_size_sampled(api):
     ligs = oracle_ligands(w.ligands)
     st = check_trace(out["trace"].cpu().numpy(), poses_g, P, ligs, *pocket_arrays(w.pocket), oracle_params(sp),
                      cfg_for(w, seed), S, w.mc_loops, seed, out["dof"].cpu().numpy(), out["energy"].cpu().numpy())
-    report(st, "config 2 sampled")
+    report(st, "batched screening sampled")
     E = out["energy"].cpu().numpy().astype(np.float64)
     dof = out["dof"].cpu().numpy().astype(np.float64)
     idx = idx.cpu().numpy()
@@ -295,12 +295,12 @@ def test_config2_full_size_sampled(api):
             np.testing.assert_array_equal(idx[l], ref)
 
 
-def test_config3_full_size_score_sampled(api):
-    """Config 3 at full size (256 ligands x 64 random poses) through the autograd Function:
+def test_adjoint_check_full_size_score_sampled(api):
+    """Adjoint-check workload at full size (256 ligands x 64 random poses) through the autograd Function:
     energies, DOF gradients (t, q, theta) and parameter gradients against the oracle on a
     seeded sample of 192 poses, plus dE/dw, dE/dR summed over every pose."""
     from paper_2510_24186_b300.autograd import score as tscore
-    w = synth.workload(3)
+    w = synth.workload("adjoint_check")
     sp, pk, b = make(api, w)
     rng = np.random.default_rng(33)
     P = 64
@@ -338,14 +338,14 @@ def test_config3_full_size_score_sampled(api):
             gr += np.array(ev.g_R)
     block_ok(W.grad.numpy(), gw, 0.0, st, "dE/dw")
     block_ok(R.grad.numpy(), gr[:8], 0.0, st, "dE/dR")
-    report(st, "config 3 full size")
+    report(st, "adjoint check full size")
 
 
-def test_config5_three_cavities_sampled(api):
-    """Config 5 shapes: 6,000-atom region around three cavities, one docking box per
+def test_blind_docking_three_cavities_sampled(api):
+    """Blind-docking workload shapes: 6,000-atom region around three cavities, one docking box per
     cavity (pose p in box p mod 3), 512 poses; 48 ligands x 100 evaluations, 96 traced
     poses checked per evaluation against the oracle."""
-    w = synth.workload(5, n_lig=48)
+    w = synth.workload("blind_docking", n_lig=48)
     sp = score_params(0)
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, cell=1.0)
     pk.set_boxes(w.box_centers, w.box_sizes)
@@ -363,17 +363,17 @@ def test_config5_three_cavities_sampled(api):
     dof = out["dof"].cpu().numpy()
     st = check_trace(out["trace"].cpu().numpy(), poses_g, P, oracle_ligands(w.ligands), *pocket_arrays(w.pocket),
                      oracle_params(sp), cfg, S, w.mc_loops, seed, dof, out["energy"].cpu().numpy())
-    report(st, "config 5 sampled")
+    report(st, "blind docking sampled")
     # every final translation lies in its pose's box
     p_of = np.arange(P) % 3
     assert (dof[:, :, :3] >= lo[p_of][None] - 1e-4).all() and (dof[:, :, :3] <= hi[p_of][None] + 1e-4).all()
 
 
-def test_config4_stream_matches_separate_batches(api):
-    """Config 4 shapes (drug-like mix, 2,000-atom pocket, 64 poses x 40 evaluations) as a
+def test_screening_stream_matches_separate_batches(api):
+    """Screening-stream workload shapes (drug-like mix, 2,000-atom pocket, 64 poses x 40 evaluations) as a
     stream of uneven batches with device-resident buffers and host packing overlapped:
     identical to sampling each batch on its own with the same ligand ids."""
-    w = synth.workload(4, n_lig=300)
+    w = synth.workload("screening_stream", n_lig=300)
     sp = score_params(0)
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
     sizes = [70, 130, 100]

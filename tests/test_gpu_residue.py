@@ -52,8 +52,8 @@ def _check_pose(st, out, l, p, ev, T, what):
 
 
 def test_residue_score_parity_single_ligand(api):
-    """Config 1 shapes with residues: every one of 64 random poses, energy, DOF and atom gradients."""
-    w = synth.workload(1)
+    """Single-ligand workload shapes with residues: every one of 64 random poses, energy, DOF and atom gradients."""
+    w = synth.workload("single_ligand")
     sp, pk, b, mds = res_setup(api, w, w.ligands)
     rng = np.random.default_rng(31)
     P = 64
@@ -77,14 +77,14 @@ def test_residue_score_parity_single_ligand(api):
         gx[perm] = np.array(ev.g_x)[:lg.n_atoms]
         block_ok(out["g_xyz"][0, p].ravel(), gx.ravel(), 40 * grad_slack(ev), st, f"pose {p} xyz")
     assert n_res_pairs > 100 * P
-    report(st, "residue score config 1")
+    report(st, "residue score single ligand")
 
 
 def test_residue_score_parity_batch_and_param_grads(api):
-    """Config 3 shapes (1,500-atom pocket with ~220 residues), 24 ligands x 37 poses (a
+    """Adjoint-check workload shapes (1,500-atom pocket with ~220 residues), 24 ligands x 37 poses (a
     ragged tile), sampled poses; dE/dw summed with upstream weights through autograd."""
     from paper_2510_24186_b300.autograd import score as tscore
-    w = synth.workload(3, n_lig=24)
+    w = synth.workload("adjoint_check", n_lig=24)
     sp, pk, b, mds = res_setup(api, w, w.ligands, K=6)
     rng = np.random.default_rng(32)
     P = 37
@@ -120,11 +120,11 @@ def test_residue_score_parity_batch_and_param_grads(api):
     report(st, "residue score batch + param grads")
 
 
-def test_residue_sampler_per_step_parity_config1(api):
-    """Config 1 with residues: every pose and evaluation against the oracle (energy,
+def test_residue_sampler_per_step_parity_single_ligand(api):
+    """Single-ligand workload with residues: every pose and evaluation against the oracle (energy,
     gradient, Adam update, Metropolis, perturbation, final state); persistent and
     per-ligand forms bit-identical."""
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     sp, pk, b, mds = res_setup(api, w, w.ligands)
     seed = 1201
     P, S = w.poses, w.steps
@@ -138,7 +138,7 @@ def test_residue_sampler_per_step_parity_config1(api):
     st = check_trace(out["trace"].cpu().numpy(), list(range(P)), P, oracle_ligands(w.ligands),
                      *pocket_arrays(w.pocket), oracle_params(sp), cfg, S, w.mc_loops, seed,
                      out["dof"].cpu().numpy(), out["energy"].cpu().numpy(), mds=mds)
-    report(st, "residue sampler config 1")
+    report(st, "residue sampler single ligand")
     o2 = api.sample(pk, b, P, S, mc_loops=w.mc_loops, seed=seed, mode=1)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(o2["dof"].cpu().numpy(), out["dof"].cpu().numpy())
@@ -147,7 +147,7 @@ def test_residue_sampler_per_step_parity_config1(api):
 
 def test_residue_inputs_are_checked(api):
     from paper_2510_24186_b300._lib import TridsError
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     sp = api.ScoreParams(2, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.TRIDS_WEIGHTS, 10.0)
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
     b = api.Batch.from_ligands(pk, w.ligands)
@@ -184,7 +184,7 @@ def test_residue_full_size_sampled(api):
     """The batched-screening workload with the paper's residue-level E_MDN (1,024 ligands x
     128 poses x 50 evaluations, about 220 residues, K = 4, persistent launch in a CUDA
     graph): 96 seeded poses traced and checked per evaluation against the oracle."""
-    w = synth.workload(2)
+    w = synth.workload("batched_screening")
     sp, pk, b, mds = res_setup(api, w, w.ligands, K=4, seed=2202)
     P, S, seed = w.poses, w.steps, 2203
     rng = np.random.default_rng(22)

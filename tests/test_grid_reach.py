@@ -32,7 +32,7 @@ def checker(tmp_path_factory):
     subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
                            "-I", CUDA_INC, os.path.join(ROOT, "tests", "grid_reach_check.cpp"),
                            os.path.join(CSRC, "pack.cpp"), "-o", exe])
-    w = synth.workload(2)
+    w = synth.workload("batched_screening")
     xyz = w.pocket.xyz.astype(np.float32)
     res = np.asarray(synth.gen_residues(np.random.default_rng(7), w.pocket.xyz), dtype=np.int32)
     inp = str(d / "pocket.bin")

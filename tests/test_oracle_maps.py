@@ -36,7 +36,7 @@ def at(x):
 
 @pytest.fixture(scope="module")
 def pocket():
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     return w.pocket
 
 
@@ -92,7 +92,7 @@ def test_interpolation_matches_scipy_regular_grid(orc, pocket, mk):
 def test_interpolated_gradient_matches_central_differences(orc, pocket):
     p = vina(orc)
     mp = orc.maps((-9.0, -9.0, -9.0), 0.375, (50, 50, 50))
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     lig = w.ligands[0]
     st, lg = orc.pack(lig.xyz, lig.type, lig.bonds, lig.rotatable)
     rng = np.random.default_rng(5)

@@ -34,7 +34,7 @@ def trids_params(orc, rng=None, cutoff=10.0, K=2):
 
 def small_ligands(n=6, seed=3):
     rng = np.random.default_rng(seed)
-    out = [synth.workload(1).ligands[0]]
+    out = [synth.workload("single_ligand").ligands[0]]
     for _ in range(n):
         out.append(synth.gen_ligand(rng, int(rng.integers(6, 30)), int(rng.integers(0, 6))))
     return out
@@ -234,7 +234,7 @@ def test_pack_matches_networkx_brute_force(orc):
 
 
 def test_pack_rejects_bad_inputs(orc):
-    lig = synth.workload(1).ligands[0]
+    lig = synth.workload("single_ligand").ligands[0]
     # rotatable bond that closes a ring: add a ring bond and flag one ring edge
     bonds = np.vstack([lig.bonds, [[0, 5]]]) if not any((lig.bonds == [0, 5]).all(1)) else lig.bonds
     rot = np.concatenate([lig.rotatable, [1]])
@@ -295,7 +295,7 @@ def test_fk_identity_and_invariants(orc):
 # --------------------------------------------------------------------------- energy
 @pytest.mark.parametrize("ts", [0, 1])
 def test_rigid_motion_of_whole_complex(orc, ts):
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     p = vina_params(orc) if ts == 0 else trids_params(orc)
     lig = w.ligands[0]
     st, lg = orc.pack(lig.xyz, lig.type, lig.bonds, lig.rotatable)
@@ -359,7 +359,7 @@ def _fd_check(orc, p, pk, lg, dof, rng, h=1e-4):
 @pytest.mark.parametrize("ts", [0, 1])
 def test_dof_gradient_matches_central_differences(orc, ts):
     """FP64 central differences (h = 1e-4) of E w.r.t. t, q (through E(q/|q|)) and theta."""
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     p = vina_params(orc) if ts == 0 else trids_params(orc)
     rng = np.random.default_rng(9)
     for lig in small_ligands(3):
@@ -373,7 +373,7 @@ def test_dof_gradient_matches_central_differences(orc, ts):
 @pytest.mark.parametrize("ts", [0, 1])
 def test_parameter_gradients(orc, ts):
     """dE/dw_t equals the per-term sums (E is linear in w); dE/dR_a matches FD in R_a."""
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     rng = np.random.default_rng(10)
     lig = w.ligands[0]
     st, lg = orc.pack(lig.xyz, lig.type, lig.bonds, lig.rotatable)

@@ -38,7 +38,7 @@ def _worker(rank, world, port, out_path):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     rng = np.random.default_rng(3)
     ligs = [synth.gen_ligand(rng, int(rng.integers(6, 14)), int(rng.integers(0, 3))) for _ in range(7)]
     costs = parallel.ligand_cost([len(l.type) for l in ligs], [l.n_tor for l in ligs], [0] * len(ligs))
@@ -69,7 +69,7 @@ def test_two_rank_gloo_matches_single_process(tmp_path):
     mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
     r = np.load(out)
     assert r["tmax"] == 2.0
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     rng = np.random.default_rng(3)
     ligs = [synth.gen_ligand(rng, int(rng.integers(6, 14)), int(rng.integers(0, 3))) for _ in range(7)]
     tops, es = _run_shard(np.arange(7), ligs, w.pocket, 11, 6, 4)

@@ -24,7 +24,7 @@ def test_noalloc_matches_regular_entry_point_twice(term_set):
     if not torch.cuda.is_available():
         pytest.fail("CUDA device required for -m gpu tests")
     from paper_2510_24186_b300 import _lib, api, synth
-    w = synth.workload(3, n_lig=24)
+    w = synth.workload("adjoint_check", n_lig=24)
     rng = np.random.default_rng(17)
     if term_set == 0:
         sp = api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, 8.0)
@@ -65,7 +65,7 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     if not torch.cuda.is_available():
         pytest.fail("CUDA device required for -m gpu tests")
     from paper_2510_24186_b300 import _lib, api, synth
-    w = synth.workload(1)
+    w = synth.workload("single_ligand")
     sp = api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, 8.0)
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
     b = api.Batch.from_ligands(pk, w.ligands)
