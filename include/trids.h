@@ -318,9 +318,9 @@ int trids_score_grad(const trids_pocket* pk, const trids_batch* b, int32_t poses
  * the call allocates nothing: no cudaMalloc, no cudaFree, no allocating library routine.
  * The paper has no counterpart; this entry point exists for callers that cannot let a
  * library allocate device memory in the middle of their work: programs that hand out
- * all device memory from their own pool or a fixed arena reserved at start-up, code
- * recording work into a CUDA stream capture (where an allocation would break or
- * serialise the capture), and latency-sensitive loops that cannot afford the device-wide
+ * all device memory from their own pool or a fixed arena reserved at start-up (a
+ * library allocation would escape their accounting or fail once the arena holds the
+ * whole device), and latency-sensitive loops that cannot afford the device-wide
  * synchronisation an allocation can cause.  (trids_score_grad allocates its work list and
  * its parameter-gradient partials on first use of a pose count.)
  *   Arguments, layouts and results are those of trids_score_grad; the caller still owns
@@ -332,8 +332,9 @@ int trids_score_grad(const trids_pocket* pk, const trids_batch* b, int32_t poses
  *   (one item = one ligand x 32 poses) and, when g_w or g_radius is requested, 84 more
  *   bytes per item.  Larger requests fail with TRIDS_EINVAL and a message giving the
  *   bytes needed; split the batch or use trids_score_grad.
- *   The first call on a device looks up the array's device address; make that first call
- *   before any stream capture that includes this entry point.  Every call reuses the same
+ *   The first call on a device looks up the array's device address (set-up done once per
+ *   device, with that device current); make that first call before any stream capture
+ *   begins.  Every call reuses the same
  *   array (it keeps the previous call's contents; each call resets what must start at
  *   zero), so calls that can overlap on the GPU -- on two streams, or from two host
  *   threads -- race with each other and must be serialised by the caller.

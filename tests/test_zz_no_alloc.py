@@ -1,7 +1,7 @@
 """The allocation-free scoring entry point against the regular one, through the C-ABI.
 
 trids_score_grad_noalloc serves callers that cannot let a library allocate device
-memory during their work (own memory pools, stream capture, latency-bound loops); its
+memory during their work (own memory pools or fixed arenas, latency-bound loops); its
 scratch is a fixed array inside the library.  This file is collected last so that a
 stop-at-first-failure run has already run everything else; it also passes on its own.
 """
