@@ -388,6 +388,23 @@ int trids_topk(const trids_batch* b, int32_t poses, const float* energy, const f
                int32_t k, float rmsd, int32_t* idx, float* e_out, void* stream);
 
 /*
+ * trids_screen_energy -- the virtual-screening score of the kept poses (Sec. 2, the
+ * E_screen equation): E_screen = E_dock / (1 + w_tor * N_tor), with N_tor the ligand's
+ * realised number of torsions and w_tor the pocket's parameter (0.01 in the paper).
+ * Reading: E_dock is the ligand-pocket energy E_inter (the paper's score has no
+ * intra-ligand part), i.e. trids_score_grad's e_inter.  E_screen only rescales each
+ * ligand's energies, so it does not change the top-k order.
+ *   idx      device [n_lig][k] int32 in: pose indices as written by trids_topk (-1 = empty).
+ *   e_inter  device [n_lig][poses] float in.
+ *   e_screen device [n_lig][k] float out: one correctly rounded FP32 division per slot;
+ *            NaN where idx is -1 (or any index outside [0, poses)).
+ * Errors: TRIDS_EINVAL for NULL handles or pointers, poses < 1, k < 1, or a pocket and
+ * batch on different devices; asynchronous on `stream`.
+ */
+int trids_screen_energy(const trids_pocket* pk, const trids_batch* b, int32_t poses, int32_t k,
+                        const int32_t* idx, const float* e_inter, float* e_screen, void* stream);
+
+/*
  * Wait for `stream` (polling, at most timeout_ms; <= 0 waits without limit), then
  * check the per-pose status words of `state` (nullable): TRIDS_OK, TRIDS_ETIMEOUT,
  * TRIDS_ECUDA or TRIDS_ENONFINITE.

@@ -132,6 +132,8 @@ def lib():
         L.or_metropolis_u.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
         L.or_metropolis_u.restype = C.c_double
         L.or_metropolis_accept.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double]
+        L.or_screen_energy.argtypes = [C.c_double, C.c_double, C.c_int]
+        L.or_screen_energy.restype = C.c_double
         L.or_opt_step.argtypes = [P(SampleCfg), C.c_int, C.c_int, C.c_uint32, P(C.c_double), P(C.c_double),
                                   P(C.c_double), P(C.c_double)]
         L.or_sample_pose.argtypes = [P(SampleCfg), P(Params), C.c_int, P(C.c_double), P(C.c_int32),
@@ -314,6 +316,11 @@ def sample_ligand(cfg, p, pxyz, ptype, lg, lig, P, n_threads=1, md=None, mp=None
                                    None if md is None else C.byref(md), None if mp is None else C.byref(mp),
                                    C.byref(lg), lig, P, 7 + T, _dp(dof), _dp(e), n_threads)
     return dof, e, pairs
+
+
+def screen_energy(e_inter, w_tor, n_tor):
+    """E_screen = E_inter / (1 + w_tor N_tor) (FP64)."""
+    return lib().or_screen_energy(float(e_inter), float(w_tor), int(n_tor))
 
 
 def topk(E, X, k, rho):

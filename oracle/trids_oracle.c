@@ -29,6 +29,8 @@
  *   or_sample              pinned through its parts; end-to-end trajectories are chaotic,
  *                          so the whole trajectory is "parity unpinned" beyond per-step checks
  *   or_topk                pinned: brute-force enumeration on tiny inputs
+ *   or_screen_energy       pinned: hand-computed values (w_tor = 0.01), the w_tor = 0 and
+ *                          N_tor = 0 identities, the sign of the torsion penalty
  */
 #include <math.h>
 #include <pthread.h>
@@ -1209,6 +1211,16 @@ void or_topk(int P, const double* E, const double* X, int L, int k, double rho,
     }
     for (int m = nk; m < k; ++m) idx[m] = -1;
     free(ord);
+}
+
+/* E_screen (Sec. 2, virtual screening): the docking score divided by the torsion factor
+ * 1 + w_tor N_tor, N_tor = the ligand's number of rotatable bonds in the sampling.
+ * Reading: the docking score is the ligand-pocket energy E_inter (the paper's score has
+ * no intra-ligand part; the intra energy the sampler adds is left out), as in Vina's
+ * final rescaling of the intermolecular energy. */
+double or_screen_energy(double e_inter, double w_tor, int n_tor)
+{
+    return e_inter / (1.0 + w_tor * (double)n_tor);
 }
 
 size_t or_sizeof_ligand(void) { return sizeof(or_ligand); }

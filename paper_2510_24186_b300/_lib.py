@@ -16,7 +16,7 @@ EXPORTS = ("trids_last_error", "trids_version", "trids_make_pocket", "trids_set_
            "trids_free_pocket", "trids_set_residues", "trids_build_maps", "trids_maps_info",
            "trids_pack_ligands", "trids_free_batch", "trids_set_mdn", "trids_batch_info", "trids_batch_query",
            "trids_pack_topology", "trids_score_grad", "trids_score_grad_noalloc", "trids_state_floats",
-           "trids_sample", "trids_topk", "trids_sync")
+           "trids_sample", "trids_topk", "trids_screen_energy", "trids_sync")
 
 
 class Params(C.Structure):
@@ -87,6 +87,7 @@ def lib(build_if_missing: bool = True):
     L.trids_state_floats.restype = i64
     L.trids_sample.argtypes = [vp, vp, P(SampleCfg), vp, vp, vp, vp]
     L.trids_topk.argtypes = [vp, i32, vp, vp, i32, fp, vp, vp, vp]
+    L.trids_screen_energy.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
     L.trids_sync.argtypes = [vp, i32, vp, vp, C.c_double]
     for name in EXPORTS:
         if name not in ("trids_last_error", "trids_version", "trids_state_floats"):

@@ -302,6 +302,21 @@ def topk(batch: Batch, energy: torch.Tensor, dof: torch.Tensor, k: int, rmsd: fl
     return idx, e
 
 
+def screen_energy(pocket: Pocket, batch: Batch, idx: torch.Tensor, e_inter: torch.Tensor, stream=None):
+    """E_screen = E_inter / (1 + w_tor N_tor) of the kept poses (trids_screen_energy).
+    idx [n_lig, k] int32 from topk(); e_inter [n_lig, poses] from score_grad().  Returns
+    [n_lig, k] float32, NaN in empty slots."""
+    _require_cuda()
+    _check_dev(idx, "idx", torch.int32)
+    _check_dev(e_inter, "e_inter")
+    n_lig, k = idx.shape
+    P = e_inter.shape[1]
+    out = torch.empty(n_lig, k, device=idx.device)
+    check(_lib.lib().trids_screen_energy(pocket.handle, batch.handle, P, k, _ptr(idx), _ptr(e_inter), _ptr(out),
+                                         _stream(stream)))
+    return out
+
+
 def sync(batch: Batch, poses: int, state: Optional[torch.Tensor] = None, timeout_ms: float = 0.0, stream=None) -> int:
     """Wait for the stream (bounded) and check per-pose status words (trids_sync).  Returns the code."""
     return _lib.lib().trids_sync(batch.handle, poses, _ptr(state), _stream(stream), float(timeout_ms))

@@ -484,6 +484,18 @@ __global__ void k_reduce_params(const float* partials, int n_items, float* g_w, 
     else if (g_r) g_r[c - 5] = s;
 }
 
+// E_screen of the kept poses: e_inter of pose idx / (1 + w_tor * N_tor), one thread per
+// (ligand, slot); empty or out-of-range slots get NaN.
+__global__ void __launch_bounds__(256) k_screen(DevBatch B, int P, int k, const int* __restrict__ idx,
+                                               const float* __restrict__ e_inter, float w_tor, float* e_screen) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)B.n_lig * k) return;
+    const int l = (int)(t / k);
+    const int j = idx[t];
+    const float den = fmaf(w_tor, (float)B.lig[l].n_tor, 1.f);
+    e_screen[t] = (j >= 0 && j < P) ? __fdiv_rn(e_inter[(size_t)l * P + j], den) : __int_as_float(0x7fc00000);
+}
+
 // ------------------------------------------------------------------ top-k
 // One block per ligand: rank by (E, index) with non-finite energies last, then walk
 // the ranking and keep a pose unless its RMSD to a kept pose is below rho.

@@ -799,6 +799,26 @@ int trids_topk(const trids_batch* b, int32_t poses, const float* energy, const f
     return TRIDS_OK;
 }
 
+int trids_screen_energy(const trids_pocket* pk, const trids_batch* b, int32_t poses, int32_t k,
+                        const int32_t* idx, const float* e_inter, float* e_screen, void* stream) {
+    g_err.clear();
+    if (!pk || !b) return fail(TRIDS_EINVAL, "pocket or batch is NULL");
+    if (pk->device != b->device) return fail(TRIDS_EINVAL, "pocket and batch live on different devices");
+    if (poses < 1 || k < 1) return fail(TRIDS_EINVAL, "need poses >= 1 and k >= 1");
+    int rc = device_guard(b->device);
+    if (rc) return rc;
+    if ((rc = check_device_ptr(idx, "idx", false)) || (rc = check_device_ptr(e_inter, "e_inter", false)) ||
+        (rc = check_device_ptr(e_screen, "e_screen", false)))
+        return rc;
+    const long long n = (long long)b->dims.n_lig * k;
+    if (n > (long long)INT32_MAX * 256) return fail(TRIDS_EINVAL, "n_lig x k too large");
+    if (n == 0) return TRIDS_OK;
+    k_screen<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(b->view(), poses, k, idx, e_inter,
+                                                                            pk->prm.w_tor, e_screen);
+    CK(cudaGetLastError());
+    return TRIDS_OK;
+}
+
 int trids_sync(const trids_batch* b, int32_t poses, const float* state, void* stream, double timeout_ms) {
     g_err.clear();
     if (!b) return fail(TRIDS_EINVAL, "batch is NULL");

@@ -81,6 +81,8 @@ def test_new_entry_points_reject_null_handles_without_a_gpu():
     n = (C.c_int32 * 3)()
     assert L.trids_maps_info(None, C.byref(lo), C.byref(h), C.byref(n)) == _lib.EINVAL
     assert L.trids_set_boxes(None, 1, None, None) == _lib.EINVAL
+    assert L.trids_screen_energy(None, None, 1, 1, None, None, None, None) == _lib.EINVAL
+    assert b"NULL" in L.trids_last_error()
 
 
 def test_python_api_fails_loudly_without_cuda():

@@ -247,6 +247,51 @@ def test_topk_matches_oracle(api):
             np.testing.assert_array_equal(e.cpu().numpy()[l][idx[l] >= 0], E[l][idx[l][idx[l] >= 0]].astype(np.float32))
 
 
+def test_screen_energy_of_kept_poses_matches_oracle(api):
+    """E_screen = E_inter / (1 + w_tor N_tor) of the top-k poses: the GPU's e_inter of the
+    sampled poses (trids_score_grad) rescaled by trids_screen_energy, against the oracle's
+    FP64 E_inter of the same FP32 DOFs; empty slots (fewer distinct poses than k) are NaN."""
+    w = synth.workload("adjoint_check", n_lig=16)
+    sp, pk, b = make(api, w)
+    P, k = 64, 9
+    out = api.sample(pk, b, P, 16, mc_loops=4, seed=11)
+    idx, _ = api.topk(b, out["energy"], out["dof"], k, 1.0)
+    sc = api.score_grad(pk, b, out["dof"], grad=False)
+    es = api.screen_energy(pk, b, idx, sc["e_inter"])
+    # a slot past the end and a -1 slot must come out NaN, the rest as before
+    idx2 = idx.clone()
+    idx2[0, 0] = -1
+    idx2[1, 0] = P
+    es2 = api.screen_energy(pk, b, idx2, sc["e_inter"])
+    torch.cuda.synchronize()
+    idx, es, es2 = idx.cpu().numpy(), es.cpu().numpy(), es2.cpu().numpy()
+    dof = out["dof"].cpu().numpy().astype(np.float64)
+    op = oracle_params(sp)
+    pxyz, ptype = pocket_arrays(w.pocket)
+    ligs = oracle_ligands(w.ligands)
+    w_tor = float(np.float32(sp.w_tor))
+    st = Stats()
+    for l in range(b.n_lig):
+        T = ligs[l].n_tor
+        for s_ in range(k):
+            p = int(idx[l, s_])
+            if p < 0:
+                assert math.isnan(es[l, s_])
+                continue
+            _, ev = oracle.score(op, pxyz, ptype, ligs[l], dof[l, p, :7 + T])
+            ref = oracle.screen_energy(ev.e_inter, w_tor, T)
+            d = abs(float(es[l, s_]) - ref)
+            st.n += 1
+            st.e_abs = max(st.e_abs, d)
+            st.e_rel = max(st.e_rel, d / max(abs(ref), 1e-30))
+            if not d <= max(1e-3, 1e-5 * abs(ref)) + ev.e_slack:
+                st.fail(f"lig {l} slot {s_} pose {p}: E_screen gpu {es[l, s_]!r} oracle {ref!r}")
+    assert math.isnan(es2[0, 0]) and math.isnan(es2[1, 0])
+    np.testing.assert_array_equal(es2[2:], es[2:])
+    np.testing.assert_array_equal(es2[:2, 1:], es[:2, 1:])
+    report(st, "E_screen of the top-9 poses")
+
+
 def test_nonfinite_pose_is_flagged_and_sync_times_out(api):
     """Host-observable failures: a huge radius overflows the repulsion term to inf in
     float32, the pose is frozen and trids_sync reports it; a zero wait limit times out."""

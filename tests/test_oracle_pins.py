@@ -565,6 +565,19 @@ def test_topk_matches_brute_force(orc):
     assert orc.topk(E, X, 3, 0.0)[0].tolist() == [3, 1, 2]
 
 
+def test_screen_energy_values_and_identities(orc):
+    """E_screen (Sec. 2, virtual screening) divides the docking score by 1 + w_tor N_tor:
+    values worked by hand at the paper's w_tor = 0.01, the identities at w_tor = 0 and at
+    N_tor = 0, and the direction of the penalty (more torsions, less negative score)."""
+    assert orc.screen_energy(-10.5, 0.01, 5) == pytest.approx(-10.0, rel=1e-14)      # 1.05
+    assert orc.screen_energy(-12.0, 0.01, 20) == pytest.approx(-10.0, rel=1e-14)     # 1.20
+    assert orc.screen_energy(4.4, 0.01, 10) == pytest.approx(4.0, rel=1e-14)         # 1.10
+    assert orc.screen_energy(-7.25, 0.0, 13) == -7.25
+    assert orc.screen_energy(-7.25, 0.01, 0) == -7.25
+    vals = [orc.screen_energy(-9.0, 0.01, t) for t in range(21)]
+    assert all(a < b for a, b in zip(vals, vals[1:]))
+
+
 def test_multiple_boxes_assign_pose_p_to_box_p_mod_n(orc):
     """Several docking boxes: init, perturbation and the Adam clamp of pose p use box p mod n."""
     lo = np.array([[-30, -5, -5], [10, 10, 10], [-2, 20, -40]], dtype=float)
