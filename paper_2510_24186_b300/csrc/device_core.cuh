@@ -224,7 +224,8 @@ struct PW {
     float4* rk;
     float4* rec;
     uint32_t* cs;   // per atom: candidate-list offset of its cell
-    int* cb;        // per atom: candidate blocks of its cell
+    int* cb;        // per atom: candidate blocks of its cell | type flags << 24 | type << 27
+                    // (the pair loop); the atom type (the atom-pair E_MDN pass)
     int* ip;        // per atom: first intra-partner block
     int* pre;
     float* grs;

@@ -106,8 +106,9 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             cell_levels(pk, pk.cell_start, pk.cell_levels, x.x, x.y, x.z, beg, nb);
             const int i0 = __ldg(&B.ipre[h.ipre_off + i]), i1 = __ldg(&B.ipre[h.ipre_off + i + 1]);
             const int cbk = (MAPS && map_cell(pk, x.x, x.y, x.z, nullptr)) ? 0 : nb;
+            const int ty = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
             W.cs[i] = beg;
-            W.cb[i] = cbk;
+            W.cb[i] = cbk | (int)((P.tflags[ty] & 7u) << 24) | (ty << 27);   // blocks | flags | type
             W.ip[i] = i0;
             nblk = cbk + (i1 - i0);
         }
@@ -118,12 +119,12 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
     int i = seg_range(W, L, N, lo, hi);
     float e_lp = 0.f, e_in = 0.f;
     if (lo < hi) {
-        int first = W.pre[i], nxt = W.pre[i + 1], cbk = W.cb[i], ipb = W.ip[i];
+        int first = W.pre[i], nxt = W.pre[i + 1], cbw = W.cb[i], ipb = W.ip[i];
+        int cbk = cbw & 0xffffff, ti = cbw >> 27;
+        uint32_t fi = (uint32_t)(cbw >> 24) & 7u;
         uint32_t csb = W.cs[i];
         float4 xa = W.xs[i];
-        int ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
         float ri = xa.w;
-        uint32_t fi = P.tflags[ti];
         // per-atom operands of the packed evaluation, set when the lane changes atom
         float2 nxy = make_float2(-xa.x, -xa.y), nzr = make_float2(-xa.z, -ri);
         uint32_t mh = (fi & 1u) << 13, mb = (((fi & 2u) << 1) | ((fi & 4u) >> 1)) << 13;
@@ -141,13 +142,14 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                 do { ++i; } while (W.pre[i + 1] == blk);
                 first = W.pre[i];
                 nxt = W.pre[i + 1];
-                cbk = W.cb[i];
+                cbw = W.cb[i];
+                cbk = cbw & 0xffffff;
+                ti = cbw >> 27;
+                fi = (uint32_t)(cbw >> 24) & 7u;
                 ipb = W.ip[i];
                 csb = W.cs[i];
                 xa = W.xs[i];
-                ti = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
                 ri = xa.w;
-                fi = P.tflags[ti];
                 nxy = make_float2(-xa.x, -xa.y);
                 nzr = make_float2(-xa.z, -ri);
                 mh = (fi & 1u) << 13;
@@ -303,6 +305,7 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
             if (!(MAPS && map_cell(pk, x.x, x.y, x.z, nullptr)))
                 cell_levels(pk, pk.ncell_start, pk.nlevels, x.x, x.y, x.z, beg, n);
             W.cs[i] = beg;
+            W.cb[i] = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);   // the atom's type
         }
         seg_scan(W, L, i, n, carry);
     }
@@ -314,7 +317,7 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
         int first = W.pre[i], nxt = W.pre[i + 1];
         uint32_t cs = W.cs[i];
         float4 x = W.xs[i];
-        const float4* g = &P.gmm[__float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w)][0][0];
+        const float4* g = &P.gmm[W.cb[i]][0][0];
         float gx = 0.f, gy = 0.f, gz = 0.f, ei = 0.f;
         for (int it = lo; it < hi; ++it) {
             if (it == nxt) {
@@ -326,7 +329,7 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
                 nxt = W.pre[i + 1];
                 cs = W.cs[i];
                 x = W.xs[i];
-                g = &P.gmm[__float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w)][0][0];
+                g = &P.gmm[W.cb[i]][0][0];
             }
             const int j = __ldg(&pk.nlist[cs + (uint32_t)(it - first)]);
             const float4 p = S.pocket[j];
