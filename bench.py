@@ -255,7 +255,8 @@ def main():
         args.cell, args.warps = args.cell or 0.5, args.warps or 20
     if not args.cell and not args.warps:
         from paper_2510_24186_b300 import autotune
-        tuned = autotune.autotune(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, arrays, w.poses)
+        tuned = autotune.autotune(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, arrays, w.poses,
+                                  steps=w.steps, mc_loops=w.mc_loops)
         args.cell, args.warps = tuned.cell, tuned.warps_per_block
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, cell=args.cell)
     if w.box_centers is not None:
@@ -403,8 +404,8 @@ def main():
                    "optimizer": args.optimizer, "maps": maps,
                    "graph": True, "l2": "flushed between steps (256 MB write)", "cell": args.cell or 0.5,
                    "warps_per_block": args.warps or 20,
-                   "autotuned": None if tuned is None else {"table_ms": tuned.table, "probe": "256 ligands x 6 "
-                                                            "evaluations per shape"},
+                   "autotuned": None if tuned is None else {"table_ms": tuned.table, "probe": f"first 128 ligands x "
+                                                            f"{P} poses x {S} evaluations per shape"},
                    "parallelism": f"ligand shards x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,

@@ -6,9 +6,12 @@ Two shapes decide the sampler's speed on a given GPU, pocket and ligand mix:
     blocks fit on an SM;
   * the candidate-grid cell edge of the pocket (tile of the ligand-pocket culling):
     smaller cells test fewer pairs outside the cutoff but make longer lists.
-The tuner times a short sampling pass (a few evaluations over a subset of the ligands)
-for every combination, keeps the fastest, and caches the choice in a JSON file keyed by
-the GPU, the pocket size, the ligand-size profile and the pose count.  Results do not
+The tuner times a sampling pass over a subset of the ligands for every combination,
+keeps the fastest, and caches the choice in a JSON file keyed by the GPU, the pocket
+size, the ligand-size profile, the pose count and the schedule.  Given the workload's
+schedule (steps, mc_loops) the probe runs it in full: poses that start at random in the
+box and poses that have settled into the pocket meet different candidate-list lengths,
+so a few evaluations from random starts can favour another cell size than the whole run.  Results do not
 depend on the shapes (the kernels are bit-reproducible for any of them); only speed does.
 """
 from __future__ import annotations
@@ -37,17 +40,22 @@ class Choice:
     table: dict
 
 
-def _key(pocket_n, n_atoms, n_tor, poses, device_name):
+def _key(pocket_n, n_atoms, n_tor, poses, steps, mc_loops, device_name):
     la = np.asarray(n_atoms)
     lt = np.asarray(n_tor)
-    prof = (int(pocket_n), int(la.max()), int(round(la.mean())), int(lt.max()), int(round(lt.mean())), int(poses))
+    prof = (int(pocket_n), int(la.max()), int(round(la.mean())), int(lt.max()), int(round(lt.mean())), int(poses),
+            int(steps), int(mc_loops))
     return hashlib.sha1(f"{device_name}|{prof}".encode()).hexdigest()[:16]
 
 
 def autotune(pocket_xyz, pocket_type, box_center, box_size, params: api.ScoreParams, lig_arrays,
-             poses: int, probe_ligands: int = 256, probe_steps: int = 6, cells: Sequence[float] = CELLS,
-             warps: Sequence[int] = WARPS, cache_path: Optional[str] = None, repeats: int = 2) -> Choice:
-    """lig_arrays = (n_atoms, xyz, type, n_bonds, bonds, rotatable) as for api.Batch."""
+             poses: int, steps: Optional[int] = None, mc_loops: int = 8, probe_ligands: int = 128,
+             cells: Sequence[float] = CELLS, warps: Sequence[int] = WARPS, cache_path: Optional[str] = None,
+             repeats: int = 2) -> Choice:
+    """lig_arrays = (n_atoms, xyz, type, n_bonds, bonds, rotatable) as for api.Batch.  steps and
+    mc_loops: the workload's schedule, run in full by the probe (steps=None: 6 evaluations in
+    2 loops, a quick probe from random starts)."""
+    probe_steps, probe_loops = (steps, mc_loops) if steps else (6, 2)
     n_atoms, xyz, types, n_bonds, bonds, rot = lig_arrays
     dev = torch.cuda.get_device_name()
     # probe subset: the first ligands, whole
@@ -70,7 +78,7 @@ def autotune(pocket_xyz, pocket_type, box_center, box_size, params: api.ScorePar
         pk = api.Pocket(pocket_xyz, pocket_type, box_center, box_size, params, cell=cell)
         b = api.Batch(pk, *sub)
         if key is None:
-            key = _key(len(pocket_type), n_atoms, b.n_tor, poses, dev)
+            key = _key(len(pocket_type), n_atoms, b.n_tor, poses, probe_steps, probe_loops, dev)
             if key in cache:
                 c = cache[key]
                 return Choice(c["cell"], c["warps_per_block"], c["ms"], c.get("table", {}))
@@ -80,7 +88,7 @@ def autotune(pocket_xyz, pocket_type, box_center, box_size, params: api.ScorePar
                 for r in range(repeats + 1):
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    api.sample(pk, b, poses, probe_steps, mc_loops=2, seed=17 + r, warps_per_block=wpb,
+                    api.sample(pk, b, poses, probe_steps, mc_loops=probe_loops, seed=17 + r, warps_per_block=wpb,
                                stream=stream)
                     e1.record(stream)
                     stream.synchronize()
