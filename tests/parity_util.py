@@ -62,6 +62,7 @@ def pocket_arrays(pk):
 
 @dataclasses.dataclass
 class Stats:
+    """Worst and 99th-percentile errors of one parity check, plus its failures."""
     n: int = 0
     e_abs: float = 0.0
     e_rel: float = 0.0
@@ -70,16 +71,47 @@ class Stats:
     straddles: int = 0
     near_ties: int = 0
     fails: list = dataclasses.field(default_factory=list)
+    e_abs_all: list = dataclasses.field(default_factory=list)
+    g_rel_all: list = dataclasses.field(default_factory=list)
+    s_err_all: list = dataclasses.field(default_factory=list)
 
     def fail(self, msg):
         if len(self.fails) < 20:
             self.fails.append(msg)
 
+    def energy(self, d, ref):
+        self.e_abs = max(self.e_abs, d)
+        self.e_rel = max(self.e_rel, d / max(abs(ref), 1e-30))
+        self.e_abs_all.append(d)
+
+    def grad(self, r):
+        self.g_rel = max(self.g_rel, r)
+        self.g_rel_all.append(r)
+
+    def state(self, e):
+        self.s_err = max(self.s_err, e)
+        self.s_err_all.append(e)
+
+    @staticmethod
+    def _p99(v):
+        return float(np.percentile(v, 99)) if len(v) else 0.0
+
+    def summary(self, what):
+        return (f"[{what}] n={self.n} |dE| max {self.e_abs:.3e} p99 {self._p99(self.e_abs_all):.3e}, "
+                f"rel dE max {self.e_rel:.3e}; grad rel max {self.g_rel:.3e} p99 {self._p99(self.g_rel_all):.3e}; "
+                f"state err max {self.s_err:.3e} p99 {self._p99(self.s_err_all):.3e}; straddles={self.straddles} "
+                f"near ties={self.near_ties}")
+
+
+def report(st: Stats, what):
+    """Print the check's max and p99 errors (pytest -s shows them); fail on any recorded failure."""
+    print("\n" + st.summary(what))
+    assert not st.fails, "\n".join(st.fails)
+
 
 def energy_ok(e_gpu, ev, st: Stats, what=""):
     d = abs(e_gpu - ev.e_total)
-    st.e_abs = max(st.e_abs, d)
-    st.e_rel = max(st.e_rel, d / max(abs(ev.e_total), 1e-30))
+    st.energy(d, ev.e_total)
     st.straddles += ev.n_straddle
     tol = max(E_ABS, E_REL * abs(ev.e_total)) + ev.e_slack
     if not (d <= tol) or not math.isfinite(e_gpu):
@@ -93,7 +125,7 @@ def block_ok(g_gpu, g_ref, slack, st: Stats, what=""):
         return
     num = np.linalg.norm(g_gpu - g_ref)
     den = max(np.linalg.norm(g_ref), G_FLOOR)
-    st.g_rel = max(st.g_rel, num / den)
+    st.grad(num / den)
     if not (num <= G_REL * den + slack):
         st.fail(f"{what}: |dg| {num:.3e} |g| {np.linalg.norm(g_ref):.3e} slack {slack:.2e}")
 
@@ -155,7 +187,7 @@ def check_trace(trace, poses_g, P, ligs_or, pxyz, ptype, op, cfg_or, S, Lmc, see
         lig_id = lig_base + l
         init = oracle.init_pose(cfg_or, T, lig_id, p)
         e0 = state_err(trace[0, slot, :7 + T], init, T)
-        st.s_err = max(st.s_err, e0)
+        st.state(e0)
         if e0 > S_TOL:
             st.fail(f"pose {g}: initial state differs by {e0:.2e}")
         m = v = None
@@ -209,14 +241,14 @@ def check_trace(trace, poses_g, P, ligs_or, pxyz, ptype, op, cfg_or, S, Lmc, see
                         st.near_ties += 1
                         fin, e_cur = alt_base, alt_e
                     ef = state_err(dof_final[l, p, :7 + T], fin, T)
-                    st.s_err = max(st.s_err, ef)
+                    st.state(ef)
                     if ef > S_TOL:
                         st.fail(f"pose {g}: final state differs by {ef:.2e}")
                     if float(e_final[l, p]) != float(np.float32(e_cur)):
                         st.fail(f"pose {g}: final energy {float(e_final[l, p])} vs {e_cur}")
             if nxt is not None and s + 1 < S:
                 es = state_err(trace[s + 1, slot, :7 + T], nxt, T)
-                st.s_err = max(st.s_err, es)
+                st.state(es)
                 if es > S_TOL:
                     st.fail(f"pose {g} step {s}->{s + 1}: state differs by {es:.2e}")
     return st

@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_2510_24186_b300 import synth
 
-from parity_util import (Stats, block_ok, check_trace, energy_ok, grad_slack, oracle_ligands, oracle_params,
+from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, oracle_ligands, oracle_params,
                          pocket_arrays, round_slack, score_params)
 
 pytestmark = pytest.mark.gpu
@@ -60,8 +60,7 @@ def test_max_pocket_score_parity(api, big):
             block_ok(out["g_dof"][l, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"lig {l} pose {p} q")
             block_ok(out["g_dof"][l, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st,
                      f"lig {l} pose {p} theta")
-    print(f"\n[max pocket] n={st.n} max|dE|={st.e_abs:.3e} max grad rel={st.g_rel:.3e}")
-    assert not st.fails, "\n".join(st.fails)
+    report(st, "max pocket score")
 
 
 def test_max_pocket_sampler_trace(api, big):
@@ -77,8 +76,7 @@ def test_max_pocket_sampler_trace(api, big):
                             seed=seed, box_lo=lo, box_hi=hi)
     st = check_trace(out["trace"].cpu().numpy(), slots, P, oracle_ligands(ligs), *pocket_arrays(pocket),
                      oracle_params(sp), cfg, S, Lm, seed, out["dof"].cpu().numpy(), out["energy"].cpu().numpy())
-    print(f"\n[max pocket sampler] n={st.n} max|dE|={st.e_abs:.3e} max state err={st.s_err:.3e}")
-    assert not st.fails, "\n".join(st.fails)
+    report(st, "max pocket sampler")
 
 
 def test_pocket_size_limit_is_enforced(api):

@@ -6,7 +6,7 @@ import pytest
 import oracle
 from paper_2510_24186_b300 import synth
 
-from parity_util import (Stats, block_ok, check_trace, energy_ok, grad_slack, oracle_ligands, oracle_params,
+from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, oracle_ligands, oracle_params,
                          pocket_arrays, round_slack, score_params)
 
 pytestmark = pytest.mark.gpu
@@ -25,12 +25,6 @@ def api():
 def oracle_maps(pk):
     lo, h, n = pk.maps_info()
     return oracle.maps(lo.astype(np.float64), float(np.float32(h)), n)
-
-
-def report(st: Stats, what):
-    print(f"\n[{what}] n={st.n} max|dE|={st.e_abs:.3e} max rel dE={st.e_rel:.3e} max grad rel={st.g_rel:.3e} "
-          f"max state err={st.s_err:.3e} straddles={st.straddles} near ties={st.near_ties}")
-    assert not st.fails, "\n".join(st.fails)
 
 
 @pytest.mark.parametrize("term_set", [0, 1])

@@ -6,7 +6,7 @@ import pytest
 import oracle
 from paper_2510_24186_b300 import synth
 
-from parity_util import check_trace, oracle_ligands, oracle_params, pocket_arrays, score_params
+from parity_util import check_trace, report, oracle_ligands, oracle_params, pocket_arrays, score_params
 
 pytestmark = pytest.mark.gpu
 
@@ -51,9 +51,7 @@ def test_update_rule_per_step_parity(api, name, hp):
     st = check_trace(out["trace"].cpu().numpy(), list(range(P)), P, oracle_ligands(w.ligands),
                      *pocket_arrays(w.pocket), oracle_params(sp), cfg, S, w.mc_loops, seed,
                      out["dof"].cpu().numpy(), out["energy"].cpu().numpy())
-    print(f"\n[{name} {hp}] n={st.n} max|dE|={st.e_abs:.3e} max grad rel={st.g_rel:.3e} "
-          f"max state err={st.s_err:.3e} near ties={st.near_ties}")
-    assert not st.fails, "\n".join(st.fails)
+    report(st, f"{name} {hp}")
     # the persistent launch and the plain per-ligand form agree bit for bit
     o2 = api.sample(pk, b, P, S, mc_loops=w.mc_loops, seed=seed, mode=1, optimizer=name, **kw)
     torch.cuda.synchronize()

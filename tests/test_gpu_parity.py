@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_2510_24186_b300 import synth
 
-from parity_util import (Stats, block_ok, check_trace, energy_ok, grad_slack, oracle_ligands, oracle_params,
+from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, oracle_ligands, oracle_params,
                          pocket_arrays, round_slack, score_params, state_err)
 
 pytestmark = pytest.mark.gpu
@@ -36,12 +36,6 @@ def cfg_for(w, seed, S=None, Lmc=None):
     return oracle.sample_cfg(steps=S or w.steps, mc_loops=Lmc or w.mc_loops, lr=float(np.float32(0.1)),
                              b1=float(np.float32(0.9)), b2=float(np.float32(0.999)), eps=float(np.float32(1e-8)),
                              beta=float(np.float32(0.069)), seed=seed, box_lo=lo, box_hi=hi)
-
-
-def report(st: Stats, what):
-    print(f"\n[{what}] n={st.n} max|dE|={st.e_abs:.3e} max rel dE={st.e_rel:.3e} max grad rel={st.g_rel:.3e} "
-          f"max state err={st.s_err:.3e} straddles={st.straddles} near ties={st.near_ties}")
-    assert not st.fails, "\n".join(st.fails)
 
 
 # --------------------------------------------------------------------------- topology
@@ -282,8 +276,7 @@ def test_screen_energy_of_kept_poses_matches_oracle(api):
             ref = oracle.screen_energy(ev.e_inter, w_tor, T)
             d = abs(float(es[l, s_]) - ref)
             st.n += 1
-            st.e_abs = max(st.e_abs, d)
-            st.e_rel = max(st.e_rel, d / max(abs(ref), 1e-30))
+            st.energy(d, ref)
             if not d <= max(1e-3, 1e-5 * abs(ref)) + ev.e_slack:
                 st.fail(f"lig {l} slot {s_} pose {p}: E_screen gpu {es[l, s_]!r} oracle {ref!r}")
     assert math.isnan(es2[0, 0]) and math.isnan(es2[1, 0])

@@ -5,7 +5,7 @@ import pytest
 import oracle
 from paper_2510_24186_b300 import synth
 
-from parity_util import (Stats, block_ok, check_trace, energy_ok, grad_slack, oracle_ligands, oracle_params,
+from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, oracle_ligands, oracle_params,
                          pocket_arrays, round_slack)
 
 pytestmark = pytest.mark.gpu
@@ -35,12 +35,6 @@ def res_setup(api, w, ligs, K=4, seed=21, cell=0.0):
     offs = np.concatenate([[0], np.cumsum(b.n_atoms)])
     mds = [oracle.mdn(res, mdn[offs[l]:offs[l + 1]].astype(np.float64)) for l in range(len(ligs))]
     return sp, pk, b, mds
-
-
-def report(st: Stats, what):
-    print(f"\n[{what}] n={st.n} max|dE|={st.e_abs:.3e} max rel dE={st.e_rel:.3e} max grad rel={st.g_rel:.3e} "
-          f"max state err={st.s_err:.3e} straddles={st.straddles} near ties={st.near_ties}")
-    assert not st.fails, "\n".join(st.fails)
 
 
 def _check_pose(st, out, l, p, ev, T, what):
