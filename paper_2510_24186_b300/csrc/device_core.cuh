@@ -56,6 +56,12 @@ __device__ __forceinline__ void quat_premul(const float r[4], float q[4]) {
 
 __device__ __forceinline__ float wrap_pi(float a) { return a - kTwoPi * floorf((a + kPi) * (1.0f / kTwoPi)); }
 
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ------------------------------------------------------------------ pair terms
 // TRIDS E_dock terms on r (see trids.h).
 template <bool TERMS>
@@ -67,9 +73,9 @@ __device__ __forceinline__ float pair_trids(float r2, float rsum, int pf, const 
     float e0 = 0.f, d0 = 0.f, e1 = 0.f, d1 = 0.f, e2 = 0.f, d2 = 0.f, r2d = 0.f, e3 = 0.f, d3 = 0.f;
     if (inter && r < 5.f) {
         for (int k = 0; k < K; ++k) {
-            const float4 g = gmm[k];
+            const float4 g = gmm[k];                           // (pi, mu, -log2(e)/(2 sigma^2), 1/sigma^2)
             const float z = r - g.y;
-            const float ex = g.x * __expf(g.z * z * z);
+            const float ex = g.x * ex2_approx(g.z * z * z);
             e0 -= ex;
             d0 = fmaf(ex * z, g.w, d0);
         }
@@ -261,12 +267,6 @@ struct ParamAcc {
     float gw[5];
 };
 
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // Branch-free Vina-form pair on surface distance d = r - rsum.  hyd / hb are 1 for a
 // hydrophobic / donor-acceptor pair, else 0.  Returns the weighted energy and its
 // derivative dd = dE/dd (= dE/dr); rinv = 1/r.  With TERMS, et[] gets the unweighted
@@ -455,7 +455,7 @@ __device__ __forceinline__ void trids_x2(uint32_t wd, const float4* __restrict__
         for (int k = 0; k < K; ++k) {
             const float4 u = ga[k], v = gc[k];
             const float2 zz = __fadd2_rn(r, make_float2(-u.y, -v.y));
-            const float2 ar = __fmul2_rn(__fmul2_rn(zz, zz), make_float2(u.z * kL2e, v.z * kL2e));
+            const float2 ar = __fmul2_rn(__fmul2_rn(zz, zz), make_float2(u.z, v.z));
             const float2 ex = __fmul2_rn(make_float2(u.x, v.x), make_float2(ex2_approx(ar.x), ex2_approx(ar.y)));
             e0 = __fadd2_rn(e0, ex);
             d0 = __ffma2_rn(__fmul2_rn(ex, zz), make_float2(u.w, v.w), d0);

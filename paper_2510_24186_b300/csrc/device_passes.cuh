@@ -291,7 +291,6 @@ __device__ __noinline__ float map_warp(const DevBatch& B, const DevPocket& pk, c
 template <bool MAPS>
 __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
                           float w0) {
-    constexpr float kL2e = 1.4426950408889634f;
     const DevParams& P = *S.P;
     const int K = P.gmm_k, L = h.n_atoms, lane = W.lane;
     const float nc2 = pk.near_cut2;
@@ -319,6 +318,7 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
         float4 x = W.xs[i];
         const float4* g = &P.gmm[W.cb[i]][0][0];
         float gx = 0.f, gy = 0.f, gz = 0.f, ei = 0.f;
+        int jn = __ldg(&pk.nlist[cs + (uint32_t)(lo - first)]);
         for (int it = lo; it < hi; ++it) {
             if (it == nxt) {
                 W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
@@ -330,8 +330,10 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
                 cs = W.cs[i];
                 x = W.xs[i];
                 g = &P.gmm[W.cb[i]][0][0];
+                jn = __ldg(&pk.nlist[cs + (uint32_t)(it - first)]);
             }
-            const int j = __ldg(&pk.nlist[cs + (uint32_t)(it - first)]);
+            const int j = jn;
+            if (it + 1 < hi && it + 1 < nxt) jn = __ldg(&pk.nlist[cs + (uint32_t)(it + 1 - first)]);   // prefetch
             const float4 p = S.pocket[j];
             const float dx = x.x - p.x, dy = x.y - p.y, dz = x.z - p.z;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -341,9 +343,9 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
             const float4* gk = g + S.ptype[j] * kK;
             float e0 = 0.f, d0 = 0.f;
             for (int k = 0; k < K; ++k) {
-                const float4 u = gk[k];                          // (pi, mu, -1/(2 sigma^2), 1/sigma^2)
+                const float4 u = gk[k];                          // (pi, mu, -log2(e)/(2 sigma^2), 1/sigma^2)
                 const float z = r - u.y;
-                const float ex = u.x * ex2_approx(u.z * kL2e * z * z);
+                const float ex = u.x * ex2_approx(u.z * z * z);
                 e0 += ex;
                 d0 = fmaf(ex * z, u.w, d0);
             }
@@ -370,7 +372,6 @@ template <bool PARAMS>
 __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
                               float w0, float ebar, ParamAcc& acc) {
     constexpr float kCut2 = kMdnCut * kMdnCut;
-    constexpr float kL2e = 1.4426950408889634f;
     const int K = B.mdn_k, R = B.mdn_res, L = h.n_atoms, lane = W.lane;
     int carry = 0;
     for (int base = 0; base < L; base += 32) {
@@ -442,9 +443,9 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
                 const float d = best * rinv;
                 float P = 0.f, dP = 0.f;
                 for (int k = 0; k < K; ++k) {
-                    const float4 g = __ldg(&kern[r * K + k]);   // (pi, mu, -1/(2 sigma^2), 1/sigma^2)
+                    const float4 g = __ldg(&kern[r * K + k]);   // (pi, mu, -log2(e)/(2 sigma^2), 1/sigma^2)
                     const float z = d - g.y;
-                    const float ex = g.x * ex2_approx(g.z * kL2e * z * z);
+                    const float ex = g.x * ex2_approx(g.z * z * z);
                     P += ex;
                     dP = fmaf(-ex * z, g.w, dP);                // dP/dd
                 }

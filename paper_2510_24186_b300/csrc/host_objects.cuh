@@ -185,7 +185,7 @@ void fill_dev_params(const trids_params* p, DevParams* d) {
             for (int k = 0; k < kK; ++k) {
                 if (in && k < p->gmm_k) {
                     const float* g = p->gmm[a][b][k];
-                    d->gmm[a][b][k] = make_float4(g[0], g[1], -1.f / (2.f * g[2] * g[2]), 1.f / (g[2] * g[2]));
+                    d->gmm[a][b][k] = make_float4(g[0], g[1], -kLog2e / (2.f * g[2] * g[2]), 1.f / (g[2] * g[2]));
                 } else {
                     d->gmm[a][b][k] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
@@ -420,7 +420,8 @@ ScoreKernel score_kernel(int ts, bool params) {
 }
 
 // Residue-level E_MDN kernels: input rows (input atom order) -> packed rows as
-// (pi, mu, -1/(2 sigma^2), 1/sigma^2); flags entries with non-finite values or sigma <= 0.
+// (pi, mu, -log2(e)/(2 sigma^2), 1/sigma^2), the exponent scaled for ex2; flags entries with
+// non-finite values or sigma <= 0.
 __global__ void k_mdn_pack(const float* __restrict__ in, const int* __restrict__ in_row, int64_t rows, int RK,
                            float4* __restrict__ out, int* bad) {
     const int64_t n = rows * RK;
@@ -430,7 +431,7 @@ __global__ void k_mdn_pack(const float* __restrict__ in, const int* __restrict__
         const float pi = g[0], mu = g[1], sg = g[2];
         if (!isfinite(pi) || !isfinite(mu) || !isfinite(sg) || !(sg > 0.f)) atomicOr(bad, 1);
         const float is2 = 1.f / (sg * sg);
-        out[e] = make_float4(pi, mu, -0.5f * is2, is2);
+        out[e] = make_float4(pi, mu, -0.5f * kLog2e * is2, is2);
     }
 }
 

@@ -20,6 +20,7 @@ namespace trids {
 constexpr int kLmax = TRIDS_MAX_ATOMS;
 constexpr int kTmax = TRIDS_MAX_TOR;
 constexpr int kNT = TRIDS_MAX_TYPES;
+constexpr float kLog2e = 1.4426950408889634f;   // log2(e): exp(x) = 2^(x log2 e)
 constexpr int kK = TRIDS_MAX_GMM;
 constexpr int kMaxBoxes = TRIDS_MAX_BOXES;
 static_assert(kTmax <= 32, "per-atom torsion masks are 32-bit");
@@ -99,7 +100,8 @@ struct alignas(16) DevParams {
     float radius[kNT];
     uint32_t tflags[kNT];          // per type: bit0 hydrophobic, bit1 donor, bit2 acceptor
     float2 pairtab[kNT][kNT];      // (R_a + R_b, pair flags as int bits: 1 hydrophobic, 2 donor-acceptor)
-    float4 gmm[kNT][kNT][kK];      // (pi, mu, -1/(2 sigma^2), 1/sigma^2)
+    float4 gmm[kNT][kNT][kK];      // (pi, mu, -log2(e)/(2 sigma^2), 1/sigma^2): exp(-z^2/(2 sigma^2))
+                                   // = ex2(z^2 * .z)
 };
 
 struct DevPocket {
