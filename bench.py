@@ -258,6 +258,9 @@ def main():
         tuned = autotune.autotune(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, arrays, w.poses,
                                   steps=w.steps, mc_loops=w.mc_loops)
         args.cell, args.warps = tuned.cell, tuned.warps_per_block
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()               # so the job's tensors are not served from the tuner's cached blocks
+    free0 = torch.cuda.mem_get_info()[0]   # device memory of the job: pocket, batch, state, work lists, graph
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, cell=args.cell)
     if w.box_centers is not None:
         pk.set_boxes(w.box_centers, w.box_sizes)
@@ -297,6 +300,7 @@ def main():
             one_step(100 + k)
             api.topk(b, energy, dof, w.topk, 1.0, stream=stream)
     stream.synchronize()
+    job_mb = (free0 - torch.cuda.mem_get_info()[0] - flush.numel()) / 2 ** 20
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     seeds = [1000 + k for k in range(args.steps)]
@@ -427,6 +431,10 @@ def main():
                 "includes": "api.screen_stream: host pack (overlapped with the previous batch's sampling) + "
                             "upload, sample, top-k, D2H of top-k to pinned memory; " + e2e_note},
         "gpu_launches": 2 * args.steps,
+        "device_memory_mb": {"job": round(job_mb, 1),
+                             "what": "device memory taken from before the pocket is built to after the warm-up "
+                                     "(pocket grids, packed batch, DOF / sampler state / energies, work lists, "
+                                     "CUDA graph), less the L2-flush buffer"},
         "clocks": clocks,
     }
     if clocks["sm_mhz"]:
