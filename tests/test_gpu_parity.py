@@ -407,6 +407,23 @@ def test_blind_docking_three_cavities_sampled(api):
     assert (dof[:, :, :3] >= lo[p_of][None] - 1e-4).all() and (dof[:, :, :3] <= hi[p_of][None] + 1e-4).all()
 
 
+def test_screening_stream_shapes_sampled(api):
+    """Screening-stream workload shapes (drug-like type mix, 10-70 atoms, 0-20 torsions,
+    2,000-atom pocket, 64 poses x 40 evaluations): 256 seeded poses of 64 ligands traced and
+    checked against the oracle at every evaluation."""
+    w = synth.workload("screening_stream", n_lig=64)
+    sp, pk, b = make(api, w)
+    P, S, seed = w.poses, w.steps, 4004
+    rng = np.random.default_rng(4)
+    poses_g = np.sort(rng.choice(b.n_lig * P, 256, replace=False))
+    out = api.sample(pk, b, P, S, mc_loops=w.mc_loops, seed=seed, trace_poses=poses_g.tolist())
+    assert api.sync(b, P, out["state"], timeout_ms=120000) == 0
+    st = check_trace(out["trace"].cpu().numpy(), poses_g, P, oracle_ligands(w.ligands), *pocket_arrays(w.pocket),
+                     oracle_params(sp), cfg_for(w, seed), S, w.mc_loops, seed, out["dof"].cpu().numpy(),
+                     out["energy"].cpu().numpy())
+    report(st, "screening stream shapes sampled")
+
+
 def test_screening_stream_matches_separate_batches(api):
     """Screening-stream workload shapes (drug-like mix, 2,000-atom pocket, 64 poses x 40 evaluations) as a
     stream of uneven batches with device-resident buffers and host packing overlapped:
