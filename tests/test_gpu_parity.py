@@ -381,8 +381,8 @@ def test_adjoint_check_full_size_score_sampled(api):
 
 def test_blind_docking_three_cavities_sampled(api):
     """Blind-docking workload shapes: 6,000-atom region around three cavities, one docking box per
-    cavity (pose p in box p mod 3), 512 poses; 48 ligands x 100 evaluations, 96 traced
-    poses checked per evaluation against the oracle."""
+    cavity (pose p in box p mod 3), 512 poses; 48 ligands x 100 evaluations, 256 seeded
+    traced poses checked per evaluation against the oracle."""
     w = synth.workload("blind_docking", n_lig=48)
     sp = score_params(0)
     pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, cell=1.0)
@@ -390,7 +390,7 @@ def test_blind_docking_three_cavities_sampled(api):
     b = api.Batch.from_ligands(pk, w.ligands)
     P, S, seed = w.poses, w.steps, 5005
     rng = np.random.default_rng(5)
-    poses_g = np.sort(rng.choice(b.n_lig * P, 96, replace=False))
+    poses_g = np.sort(rng.choice(b.n_lig * P, 256, replace=False))
     out = api.sample(pk, b, P, S, mc_loops=w.mc_loops, seed=seed, trace_poses=poses_g.tolist())
     assert api.sync(b, P, out["state"], timeout_ms=120000) == 0
     lo = (w.box_centers - w.box_sizes / 2).astype(np.float32).astype(np.float64)
