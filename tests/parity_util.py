@@ -71,6 +71,7 @@ class Stats:
     straddles: int = 0
     near_ties: int = 0
     fails: list = dataclasses.field(default_factory=list)
+    g_worst: str = ""
     e_abs_all: list = dataclasses.field(default_factory=list)
     g_rel_all: list = dataclasses.field(default_factory=list)
     s_err_all: list = dataclasses.field(default_factory=list)
@@ -84,7 +85,9 @@ class Stats:
         self.e_rel = max(self.e_rel, d / max(abs(ref), 1e-30))
         self.e_abs_all.append(d)
 
-    def grad(self, r):
+    def grad(self, r, what=""):
+        if r > self.g_rel:
+            self.g_worst = what
         self.g_rel = max(self.g_rel, r)
         self.g_rel_all.append(r)
 
@@ -100,7 +103,7 @@ class Stats:
         return (f"[{what}] n={self.n} |dE| max {self.e_abs:.3e} p99 {self._p99(self.e_abs_all):.3e}, "
                 f"rel dE max {self.e_rel:.3e}; grad rel max {self.g_rel:.3e} p99 {self._p99(self.g_rel_all):.3e}; "
                 f"state err max {self.s_err:.3e} p99 {self._p99(self.s_err_all):.3e}; straddles={self.straddles} "
-                f"near ties={self.near_ties}")
+                f"near ties={self.near_ties}" + (f"; worst gradient block: {self.g_worst}" if self.g_worst else ""))
 
 
 def report(st: Stats, what):
@@ -125,7 +128,7 @@ def block_ok(g_gpu, g_ref, slack, st: Stats, what=""):
         return
     num = np.linalg.norm(g_gpu - g_ref)
     den = max(np.linalg.norm(g_ref), G_FLOOR)
-    st.grad(num / den)
+    st.grad(num / den, f"{what}: |dg| {num:.2e}, |g| {np.linalg.norm(g_ref):.2e}, allowed {G_REL * den + slack:.2e}")
     if not (num <= G_REL * den + slack):
         st.fail(f"{what}: |dg| {num:.3e} |g| {np.linalg.norm(g_ref):.3e} slack {slack:.2e}")
 
