@@ -136,6 +136,12 @@ def block_ok(g_gpu, g_ref, slack, st: Stats, what=""):
 EPS32 = 2.0 ** -24
 
 
+def t_slack(ev):
+    # dE/dt is the sum of the ligand atoms' forces: a jump J of one pair's dE/dr moves it by
+    # at most J (an intra pair's jumps cancel in the sum), with no lever arm
+    return ev.g_slack
+
+
 def grad_slack(ev):
     # a force jump J on one atom moves a rotation or torsion gradient by at most J times
     # the lever arm (< 40 A inside a pocket)
@@ -205,7 +211,7 @@ def check_trace(trace, poses_g, P, ligs_or, pxyz, ptype, op, cfg_or, S, Lmc, see
             st.n += 1
             energy_ok(E, ev, st, f"pose {g} step {s}")
             sl = grad_slack(ev)
-            block_ok(gt, ev.g_dof[:3], sl + round_slack(ev, 0, 3), st, f"pose {g} step {s} dE/dt")
+            block_ok(gt, ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"pose {g} step {s} dE/dt")
             block_ok(tau, ev.tau[:], sl + round_slack(ev, 3, 7), st, f"pose {g} step {s} torque")
             block_ok(gth, ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"pose {g} step {s} dE/dtheta")
             loop, j, n = sched[s]

@@ -6,7 +6,7 @@ import pytest
 import oracle
 from paper_2510_24186_b300 import synth
 
-from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, oracle_ligands, oracle_params,
+from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, t_slack, oracle_ligands, oracle_params,
                          pocket_arrays, round_slack, score_params)
 
 pytestmark = pytest.mark.gpu
@@ -56,7 +56,7 @@ def test_map_score_parity(api, term_set):
         st.n += 1
         energy_ok(out["energy"][0, p], ev, st, f"pose {p}")
         sl = grad_slack(ev)
-        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], sl + round_slack(ev, 0, 3), st, f"pose {p} t")
+        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"pose {p} t")
         block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"pose {p} q")
         block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"pose {p} th")
     assert 0 < mapped < P * lg.n_atoms      # both forms occur
@@ -149,7 +149,7 @@ def test_maps_with_residue_terms(api):
         st.n += 1
         energy_ok(out["energy"][0, p], ev, st, f"pose {p}")
         sl = grad_slack(ev)
-        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], sl + round_slack(ev, 0, 3), st, f"pose {p} t")
+        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"pose {p} t")
         block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"pose {p} q")
         block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"pose {p} th")
     assert mapped > 0 and res_pairs > 0

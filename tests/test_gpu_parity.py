@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_2510_24186_b300 import synth
 
-from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, oracle_ligands, oracle_params,
+from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, t_slack, oracle_ligands, oracle_params,
                          pocket_arrays, round_slack, score_params, state_err)
 
 pytestmark = pytest.mark.gpu
@@ -78,7 +78,7 @@ def test_score_grad_parity_single_ligand(api, term_set):
         energy_ok(out["energy"][0, p], ev, st, f"pose {p}")
         sl = grad_slack(ev)
         assert abs(out["e_inter"][0, p] - ev.e_inter) <= max(1e-3, 1e-5 * abs(ev.e_inter)) + ev.e_slack
-        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], sl + round_slack(ev, 0, 3), st, f"pose {p} t")
+        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"pose {p} t")
         block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"pose {p} q")
         block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"pose {p} theta")
         assert np.all(out["g_dof"][0, p, 7 + T:] == 0)
@@ -106,7 +106,7 @@ def test_score_grad_parity_batch_ragged(api, term_set):
             st.n += 1
             energy_ok(out["energy"][l, p], ev, st, f"lig {l} pose {p}")
             sl = grad_slack(ev)
-            block_ok(out["g_dof"][l, p, :3], ev.g_dof[:3], sl + round_slack(ev, 0, 3), st, f"lig {l} pose {p} t")
+            block_ok(out["g_dof"][l, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"lig {l} pose {p} t")
             block_ok(out["g_dof"][l, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"lig {l} pose {p} q")
             block_ok(out["g_dof"][l, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st,
                      f"lig {l} pose {p} theta")
@@ -362,7 +362,7 @@ def test_adjoint_check_full_size_score_sampled(api):
         st.n += 1
         energy_ok(Eh[l, p], ev, st, f"lig {l} pose {p}")
         sl = grad_slack(ev)
-        block_ok(gd[l, p, :3], ev.g_dof[:3], sl + round_slack(ev, 0, 3), st, f"lig {l} pose {p} t")
+        block_ok(gd[l, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"lig {l} pose {p} t")
         block_ok(gd[l, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"lig {l} pose {p} q")
         block_ok(gd[l, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"lig {l} pose {p} theta")
     # parameter gradients over every pose: oracle sums over all 16,384 poses
