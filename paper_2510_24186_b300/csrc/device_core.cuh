@@ -449,8 +449,8 @@ __device__ __forceinline__ void trids_x2(uint32_t wd, const float4* __restrict__
     // E_MDN over atom pairs (term set 1, ligand-pocket): -sum_k pi_k exp(-(r - mu_k)^2 / (2 sigma_k^2))
     if (gmm) {
         const float2 m5 = make_float2(r.x < 5.f ? 1.f : 0.f, r.y < 5.f ? 1.f : 0.f);
-        const float4* __restrict__ ga = gmm + ptype[ja] * kK;
-        const float4* __restrict__ gc = gmm + ptype[jb] * kK;
+        const float4* __restrict__ ga = gmm + ptype[ja] * kKP;
+        const float4* __restrict__ gc = gmm + ptype[jb] * kKP;
         float2 e0 = make_float2(0.f, 0.f), d0 = make_float2(0.f, 0.f);
         for (int k = 0; k < K; ++k) {
             const float4 u = ga[k], v = gc[k];

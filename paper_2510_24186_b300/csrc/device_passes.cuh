@@ -340,7 +340,7 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
             const float in = r2 < nc2 ? 1.f : 0.f;
             const float rinv = rsqrtf(fmaxf(r2, 1e-12f));
             const float r = r2 * rinv;
-            const float4* gk = g + S.ptype[j] * kK;
+            const float4* gk = g + S.ptype[j] * kKP;
             float e0 = 0.f, d0 = 0.f;
             for (int k = 0; k < K; ++k) {
                 const float4 u = gk[k];                          // (pi, mu, -log2(e)/(2 sigma^2), 1/sigma^2)

@@ -22,6 +22,12 @@ constexpr int kTmax = TRIDS_MAX_TOR;
 constexpr int kNT = TRIDS_MAX_TYPES;
 constexpr float kLog2e = 1.4426950408889634f;   // log2(e): exp(x) = 2^(x log2 e)
 constexpr int kK = TRIDS_MAX_GMM;
+// Row stride of the staged GMM table (float4 per (ligand type, pocket type) row) and the row
+// count per ligand type, both padded by one: the 16-byte shared-memory bank group of kernel k
+// of row (a, b) is then (5 (a + b) + k) mod 8 instead of (4 b + k) mod 8, so lanes reading
+// rows of different types rarely collide in a bank group.
+constexpr int kKP = kK + 1;
+constexpr int kNTP = kNT + 1;
 constexpr int kMaxBoxes = TRIDS_MAX_BOXES;
 static_assert(kTmax <= 32, "per-atom torsion masks are 32-bit");
 
@@ -100,8 +106,8 @@ struct alignas(16) DevParams {
     float radius[kNT];
     uint32_t tflags[kNT];          // per type: bit0 hydrophobic, bit1 donor, bit2 acceptor
     float2 pairtab[kNT][kNT];      // (R_a + R_b, pair flags as int bits: 1 hydrophobic, 2 donor-acceptor)
-    float4 gmm[kNT][kNT][kK];      // (pi, mu, -log2(e)/(2 sigma^2), 1/sigma^2): exp(-z^2/(2 sigma^2))
-                                   // = ex2(z^2 * .z)
+    float4 gmm[kNT][kNTP][kKP];    // (pi, mu, -log2(e)/(2 sigma^2), 1/sigma^2): exp(-z^2/(2 sigma^2))
+                                   // = ex2(z^2 * .z); [a][b][k] for b < kNT, k < kK (the rest is padding)
 };
 
 struct DevPocket {
