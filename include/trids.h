@@ -196,6 +196,8 @@ int trids_set_params(trids_pocket* pk, const trids_params* prm, void* stream);
  */
 int trids_set_boxes(trids_pocket* pk, int32_t n_boxes, const float* centers, const float* sizes);
 
+/* Free a pocket and its device arrays (maps, residue lists included).  NULL is a no-op;
+ * the caller must not free a pocket while work that uses it is in flight. */
 int trids_free_pocket(trids_pocket* pk);
 
 /*
@@ -255,6 +257,8 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
                        const float* xyz, const int32_t* type, const int32_t* n_bonds,
                        const int32_t* bonds, const uint8_t* rotatable, trids_batch** out);
 
+/* Free a batch, its device arrays, work lists and cached CUDA graph.  NULL is a no-op;
+ * the caller must not free a batch while work that uses it is in flight. */
 int trids_free_batch(trids_batch* b);
 
 /*
@@ -270,6 +274,8 @@ int trids_free_batch(trids_batch* b);
  */
 int trids_set_mdn(trids_batch* b, int32_t n_res, int32_t K, const float* mdn, void* stream);
 
+/* Sizes of a packed batch (trids_batch_dims above), written to the host struct `dims`.
+ * TRIDS_EINVAL for NULL arguments. */
 int trids_batch_info(const trids_batch* b, trids_batch_dims* dims);
 
 /*
