@@ -176,32 +176,29 @@ def check_trace(trace, poses_g, P, ligs_or, pxyz, ptype, op, cfg_or, S, Lmc, see
 
     trace [S, n_trace, rec] (GPU float32), poses_g = global pose ids (l * P + p) of the slots.
     For every traced pose and evaluation: the oracle re-scores the GPU's state in FP64 and
-    compares energy and gradient; it then applies the method's next action (Adam update,
-    or Metropolis decision + perturbation at a loop boundary) in FP64 to the GPU's state
-    and gradient and compares with the GPU's next state; finally the returned state and
-    energy are checked.  mds: per-ligand residue-level E_MDN inputs (term set 2); mp: the
-    grid-map domain when the GPU scored with maps.
+    compares energy and gradient; the Monte-Carlo helper ``McPose`` (the statement of the
+    loop that the oracle's own sampler is pinned to) then applies the method's next action
+    (update, or Metropolis decision + perturbation at a loop boundary) in FP64 to the GPU's
+    state, energy and gradient, and the result is compared with the GPU's next state;
+    finally the returned state and energy are checked.  A Metropolis decision that the
+    oracle marks as a near tie may go either way: the other branch is followed when the
+    GPU's next state matches it.  mds: per-ligand residue-level E_MDN inputs (term set 2);
+    mp: the grid-map domain when the GPU scored with maps.
     """
+    from mc_replay import McPose
     st = st or Stats()
     trace = np.asarray(trace, dtype=np.float64)
     D = (trace.shape[2] - 14) // 2 + 7
-    sched = []
-    for l in range(Lmc):
-        for j in range(oracle.loop_steps(S, Lmc, l)):
-            sched.append((l, j, oracle.loop_steps(S, Lmc, l)))
     for slot, g in enumerate(poses_g):
         l, p = divmod(int(g), P)
         lg = ligs_or[l]
         T = lg.n_tor
-        lig_id = lig_base + l
-        init = oracle.init_pose(cfg_or, T, lig_id, p)
+        mc = McPose(cfg_or, T, lig_base + l, p, S, Lmc, seed)
+        init = mc.start()
         e0 = state_err(trace[0, slot, :7 + T], init, T)
         st.state(e0)
         if e0 > S_TOL:
             st.fail(f"pose {g}: initial state differs by {e0:.2e}")
-        m = v = None
-        e_cur = e_saved = None
-        saved = None
         for s in range(S):
             rec = trace[s, slot]
             dof = rec[:7 + T]
@@ -214,50 +211,22 @@ def check_trace(trace, poses_g, P, ligs_or, pxyz, ptype, op, cfg_or, S, Lmc, see
             block_ok(gt, ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"pose {g} step {s} dE/dt")
             block_ok(tau, ev.tau[:], sl + round_slack(ev, 3, 7), st, f"pose {g} step {s} torque")
             block_ok(gth, ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"pose {g} step {s} dE/dtheta")
-            loop, j, n = sched[s]
-            if j == 0:
-                m, v = np.zeros(6 + T), np.zeros(6 + T)
-            grad = np.concatenate([gt, tau, gth]).astype(np.float64)
-            if j < n - 1:
-                nxt = dof.copy()
-                oracle.adam_step(cfg_or, T, j + 1, grad, m, v, nxt, pose=p)
-            else:
-                e_new = float(E)
-                if loop == 0:
-                    base, e_cur = dof.copy(), e_new
-                else:
-                    u = oracle.metropolis_u(seed, lig_id, p, loop)
-                    acc = oracle.metropolis_accept(e_new, e_saved, cfg_or.beta, u)
-                    thr = math.exp(min(50.0, -cfg_or.beta * (e_new - e_saved)))
-                    near = abs(u - thr) < 1e-5
-                    alt_base = saved.copy() if acc else dof.copy()
-                    base = dof.copy() if acc else saved.copy()
-                    e_cur = e_new if acc else e_saved
-                    alt_e = e_saved if acc else e_new
-                nxt = None
-                if s + 1 < S:
-                    l2 = sched[s + 1][0]
-                    saved, e_saved = base.copy(), e_cur
-                    _, nxt = oracle.perturb(cfg_or, T, lig_id, p, l2, base)
-                    if loop > 0 and near:
-                        _, alt = oracle.perturb(cfg_or, T, lig_id, p, l2, alt_base)
-                        if state_err(trace[s + 1, slot, :7 + T], alt, T) <= S_TOL:
-                            st.near_ties += 1
-                            nxt, saved, e_saved, e_cur = alt, alt_base.copy(), alt_e, alt_e
-                else:
-                    fin = base
-                    if loop > 0 and near and state_err(dof_final[l, p, :7 + T], alt_base, T) <= S_TOL:
-                        st.near_ties += 1
-                        fin, e_cur = alt_base, alt_e
-                    ef = state_err(dof_final[l, p, :7 + T], fin, T)
-                    st.state(ef)
-                    if ef > S_TOL:
-                        st.fail(f"pose {g}: final state differs by {ef:.2e}")
-                    if float(e_final[l, p]) != float(np.float32(e_cur)):
-                        st.fail(f"pose {g}: final energy {float(e_final[l, p])} vs {e_cur}")
-            if nxt is not None and s + 1 < S:
+            nxt = mc.step(dof, E, np.concatenate([gt, tau, gth]))
+            if mc.near:
+                got = trace[s + 1, slot, :7 + T] if nxt is not None else dof_final[l, p, :7 + T]
+                if state_err(got, mc.alternative(), T) <= S_TOL:
+                    st.near_ties += 1
+                    nxt = mc.alternative()
+                    mc.take_alternative()
+            if nxt is not None:
                 es = state_err(trace[s + 1, slot, :7 + T], nxt, T)
                 st.state(es)
                 if es > S_TOL:
                     st.fail(f"pose {g} step {s}->{s + 1}: state differs by {es:.2e}")
+        ef = state_err(dof_final[l, p, :7 + T], mc.final, T)
+        st.state(ef)
+        if ef > S_TOL:
+            st.fail(f"pose {g}: final state differs by {ef:.2e}")
+        if float(e_final[l, p]) != float(np.float32(mc.e_cur)):
+            st.fail(f"pose {g}: final energy {float(e_final[l, p])} vs {mc.e_cur}")
     return st
