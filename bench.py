@@ -133,14 +133,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(mhz)}
 
 
-def gemm_load_mhz():
-    """Median SM clock a seconds-long dense bf16 GEMM settled at on this pool (measured peaks)."""
-    try:
-        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["clocks_under_load"]["sm_mhz_median"])
-    except Exception:
-        return None
-
-
 def cpu_threads():
     try:
         return len(os.sched_getaffinity(0))
@@ -328,14 +320,19 @@ def main():
 
     # in-cutoff pair counts of the same trajectories (untimed counting variant; the
     # energies must come out bit-identical to the timed runs)
+    # and the SM cycles the warps spent in each phase of an evaluation (the same counting
+    # variant times its phases; their shares apportion the timed kernel's duration)
     pairs = []
+    cycles = np.zeros(len(api.PHASES))
     identical = True
     with torch.cuda.stream(stream):
         for k in range(args.steps):
             o = one_step(seeds[k], count_pairs=True)
             stream.synchronize()
             pairs.append(int(o["pair_count"].item()))
+            cycles += o["phase_cycles"].cpu().numpy().astype(np.float64)
             identical &= bool(torch.equal(energy, energies[k]))
+    phase_share = {n: float(c / cycles.sum()) for n, c in zip(api.PHASES, cycles)}
 
     # plain per-ligand form, same device code
     pl_ms = None
@@ -392,6 +389,8 @@ def main():
     f_pair = F_PAIR_VINA if sp.term_set == 0 else F_PAIR_TRIDS
     flops = [p * f_pair for p in pairs]
     achieved = sum(flops) / (sum(t_sample) / 1000.0) / 1e12
+    pair_ms = statistics.mean(t_sample) * phase_share["pairs"]
+    achieved_pair = sum(flops) / len(flops) / (pair_ms / 1000.0) / 1e12
     clocks = clk.summary()
     traffic = None
     prof = os.path.join(ROOT, "profiles", "sample_persistent_vina5_batched_screening.json")
@@ -419,7 +418,11 @@ def main():
                                 "not counted (a lower bound)")
                              + ("" if maps is None else "; with maps only the atoms outside the map grid sum "
                                 "pairs, so this counts the direct pairs alone")},
-        "kernel": {"sample_ms": statistics.mean(t_sample), "topk_ms": statistics.mean(
+        "kernel": {"sample_ms": statistics.mean(t_sample), "phase_share": phase_share,
+            "phase_share_note": "share of the warps' SM clock cycles per phase, from the counting variant of the "
+                                "sampler (same trajectories); pairs = per-atom candidate set-up, pair sums and "
+                                "lane-order combine",
+            "topk_ms": statistics.mean(
             [t_step[k] - t_sample[k] for k in range(args.steps)]), "pairs_per_step": statistics.mean(pairs),
             "pairs_per_pose_step": statistics.mean(pairs) / units, "count_run_bit_identical": identical,
             "status": rc},
@@ -437,13 +440,12 @@ def main():
                                      "CUDA graph), less the L2-flush buffer"},
         "clocks": clocks,
     }
+    # the pair phase alone: its FLOPs over its share of the timed kernel's duration
+    line["roofline"]["achieved_pair"] = achieved_pair
+    line["roofline"]["frac_pair"] = achieved_pair / peak
+    line["roofline"]["pair_ms"] = pair_ms
     if clocks["sm_mhz"]:
         line["roofline"]["frac_at_load_clock"] = achieved / (peak * clocks["sm_mhz"] / mhz)
-    gemm_mhz = gemm_load_mhz()
-    if gemm_mhz:
-        # the same fraction against the clock a power-capped dense GEMM settles at on this part
-        line["roofline"]["frac_at_gemm_load_clock"] = achieved / (peak * gemm_mhz / mhz)
-        line["roofline"]["gemm_load_mhz"] = gemm_mhz
     if not args.no_cpu and world == 1:
         r, cores, n, dt = oracle_sample_rate(w, budget_s=12.0, terms=args.terms)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",

@@ -72,6 +72,15 @@ extern "C" {
 #define TRIDS_OPT_ADAGRAD 3
 #define TRIDS_OPT_SGD 4
 
+/* Phases of one evaluation timed by trids_sample_cfg.phase_cycles (counting runs only). */
+#define TRIDS_PHASE_FK 0        /* forward kinematics */
+#define TRIDS_PHASE_PAIRS 1     /* pair loop: per-atom candidate set-up, pair sums, lane-order combine */
+#define TRIDS_PHASE_PASSES 2    /* grid-map, atom-pair E_MDN and residue E_MDN passes */
+#define TRIDS_PHASE_ADJOINT 3   /* forces -> dE/dt, torque, dE/dtheta */
+#define TRIDS_PHASE_UPDATE 4    /* update rule, Monte-Carlo save/perturb/accept, trace records */
+#define TRIDS_PHASE_OTHER 5     /* taking a pose, initial or resumed state, storing it */
+#define TRIDS_PHASES 6
+
 #define TRIDS_MODE_PERSISTENT 0 /* one persistent fused launch (optionally a CUDA graph) */
 #define TRIDS_MODE_PER_LIGAND 1 /* plain form: one launch per (ligand, step) */
 
@@ -159,6 +168,11 @@ typedef struct trids_sample_cfg {
     float weight_decay;      /* AdamW decay (torch default 0.01), >= 0 */
     float momentum;          /* SGD momentum in [0, 1) (torch default 0) */
     float alpha;             /* RMSprop smoothing in [0, 1) (torch default 0.99) */
+    unsigned long long* phase_cycles; /* nullable device [TRIDS_PHASES]: adds the SM clock cycles each
+                                       * warp spent in each phase (TRIDS_PHASE_*).  Like pair_count it
+                                       * selects the counting form of the sampler, which follows the
+                                       * same trajectories; the sums give each phase's share of the
+                                       * warps' time */
 } trids_sample_cfg;
 
 /* Message of the calling thread's last failure ("" if none). */

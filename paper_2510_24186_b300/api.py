@@ -240,6 +240,9 @@ def score_grad(pocket: Pocket, batch: Batch, dof: torch.Tensor, grad: bool = Tru
     return out
 
 
+PHASES = _lib.PHASES
+
+
 def sample(pocket: Pocket, batch: Batch, poses: int, steps: int, mc_loops: int = 8, lr: float = 0.1,
            beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, beta: float = 0.069, seed: int = 0,
            lig_base: int = 0, mode: int = _lib.MODE_PERSISTENT, warps_per_block: int = 0, use_graph: bool = True,
@@ -250,7 +253,9 @@ def sample(pocket: Pocket, batch: Batch, poses: int, steps: int, mc_loops: int =
            alpha: float = 0.99) -> dict:
     """Monte-Carlo + gradient sampling of every ligand's poses (trids_sample).  optimizer:
     adam (the paper's), adamw, rmsprop, adagrad or sgd; eps is passed as given (torch's
-    defaults are 1e-8, except Adagrad's 1e-10)."""
+    defaults are 1e-8, except Adagrad's 1e-10).  count_pairs runs the counting form of the
+    sampler (same trajectories): out["pair_count"] gets the in-cutoff pairs evaluated and
+    out["phase_cycles"] the warps' SM clock cycles per phase (names in PHASES)."""
     _require_cuda()
     dev = torch.device("cuda", torch.cuda.current_device())
     n_lig, D = batch.n_lig, batch.dof_stride
@@ -284,6 +289,9 @@ def sample(pocket: Pocket, batch: Batch, poses: int, steps: int, mc_loops: int =
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
         cfg.pair_count = cnt.data_ptr()
         out["pair_count"] = cnt
+        cyc = torch.zeros(len(_lib.PHASES), dtype=torch.int64, device=dev)
+        cfg.phase_cycles = cyc.data_ptr()
+        out["phase_cycles"] = cyc
     check(_lib.lib().trids_sample(pocket.handle, batch.handle, C.byref(cfg), _ptr(dof), _ptr(state),
                                   _ptr(energy), _stream(stream)))
     return out

@@ -128,11 +128,15 @@ __host__ __device__ inline size_t pose_warp_core_bytes(int Lm, int Tm) {
 
 constexpr size_t kRigidStateBytes = 128;   // sizeof(RigidState), checked below
 constexpr size_t kTorStateBytes = 16;      // sizeof(TorState)
-// per-warp region: [core][rigid pose state][torsion state, 32 lanes][per-lane dE/dR
-// (parameter-gradient kernels)]
+constexpr size_t kClockBytes = 8 * (TRIDS_PHASES + 1);   // phase clock of the counting sampler
+// per-warp region: [core][rigid pose state][torsion state, 32 lanes][phase clock][per-lane
+// dE/dR (parameter-gradient kernels)]
 __host__ __device__ inline size_t pose_state_off(int Lm, int Tm) { return align_up(pose_warp_core_bytes(Lm, Tm), 16); }
-__host__ __device__ inline size_t pose_grs_off(int Lm, int Tm) {
+__host__ __device__ inline size_t pose_clk_off(int Lm, int Tm) {
     return align_up(pose_state_off(Lm, Tm) + kRigidStateBytes + 32 * kTorStateBytes, 16);
+}
+__host__ __device__ inline size_t pose_grs_off(int Lm, int Tm) {
+    return align_up(pose_clk_off(Lm, Tm) + kClockBytes, 16);
 }
 __host__ __device__ inline size_t pose_warp_bytes(int Lm, int Tm, bool params) {
     size_t b = pose_grs_off(Lm, Tm);
@@ -219,6 +223,7 @@ __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t par
 //   tor TorState[32]    lane k's torsion angle, moments and saved angle
 //                       (kept in shared memory, the state holds no registers across the pair
 //                       loop: the sampler fits 96 registers per thread, 20 warps per SM)
+//   clk u64[7]          per-phase cycle sums and the last lap's time (counting sampler)
 //   grs float[kNT][32]  per-lane dE/dR_a (parameter-gradient kernels only)
 struct RigidState;
 struct TorState;
@@ -235,6 +240,7 @@ struct PW {
     int* ip;        // per atom: first intra-partner block
     int* pre;
     float* grs;
+    unsigned long long* clk;   // phase clock (counting sampler)
     int lane;
 };
 
@@ -252,6 +258,7 @@ __device__ __forceinline__ PW make_pw(unsigned char* smem, size_t warp_off, size
     W.rig = reinterpret_cast<RigidState*>(base + pose_state_off(Lm, Tm));
     W.tor = reinterpret_cast<TorState*>(base + pose_state_off(Lm, Tm) + kRigidStateBytes);
     W.grs = reinterpret_cast<float*>(base + pose_grs_off(Lm, Tm));
+    W.clk = reinterpret_cast<unsigned long long*>(base + pose_clk_off(Lm, Tm));
     W.lane = threadIdx.x & 31;
     return W;
 }
@@ -311,6 +318,37 @@ struct VinaX2 {
     float w3, w4;
 };
 
+// The ligand atom's flag-dependent piece of the Vina-form pair.  A type that is
+// hydrophobic but neither donor nor acceptor meets only the hydrophobic term
+// w3 sat(1.5 - d) (with hydrophobic candidates); a donor and/or acceptor type that is not
+// hydrophobic meets only the H-bond term w4 sat(-d / 0.7) (with candidates of the
+// complementary flag).  Either is one masked term w sat(a - b d) with per-atom (a, b, w)
+// and candidate-flag mask m, evaluated once instead of twice; a type with no flags gets
+// m = 0.  The full two-term evaluation serves parameter sets with a type that is both.
+struct FlagTerm {
+    uint32_t m;     // candidate flag bits (low entry; shifted by 16 for the high entry)
+    float nb, a;    // -b, a
+    float w;        // weight
+    float b;        // b
+    uint32_t mh, mb;   // two-term form: hydrophobic / donor-acceptor candidate bits
+};
+
+// fi = the ligand atom's type flags (bit0 hydrophobic, bit1 donor, bit2 acceptor); w3, w4
+// the hydrophobic and H-bond weights.
+__device__ __forceinline__ FlagTerm make_flag_term(uint32_t fi, float w3, float w4) {
+    FlagTerm F;
+    F.mh = (fi & 1u) << 13;
+    F.mb = (((fi & 2u) << 1) | ((fi & 4u) >> 1)) << 13;   // donor_i -> acceptor_j, acceptor_i -> donor_j
+    const bool hyd = (fi & 1u) != 0u;
+    F.m = hyd ? F.mh : F.mb;
+    const float nb = hyd ? -1.f : -1.f / 0.7f, a = hyd ? 1.5f : 0.f, b = hyd ? 1.f : 1.f / 0.7f;
+    F.nb = nb;
+    F.a = a;
+    F.b = b;
+    F.w = hyd ? w3 : w4;
+    return F;
+}
+
 __device__ __forceinline__ VinaX2 make_vina_x2(const float w[5]) {
     VinaX2 K;
     K.w0 = make_float2(w[0], w[0]);
@@ -336,13 +374,15 @@ __device__ __forceinline__ VinaX2 make_vina_x2(const float w[5]) {
 // candidate-list word, on the packed FP32 pipe (f32x2).  The gradient's sign is folded
 // into the constants so that no operand needs negating: with p = x_j - x_i and
 // ng = -dE/dd, the force on atom i gains ng / r * p.  nxy = -(x_i, y_i) and
-// nzr = -(z_i, R_i); mh / mb select the candidate's hydrophobic / donor-acceptor flag
-// bits (low entry; shifted by 16 for the high entry).  in-cutoff pairs are masked by
-// multiplying with 0/1, which is exact for the finite values every candidate (the far
-// sentinel included) produces.
-template <bool COUNT>
+// nzr = -(z_i, R_i); F holds the ligand atom's flag-term operands (ONE: the single masked
+// term of FlagTerm; else both terms with F.mh / F.mb selecting the candidate's
+// hydrophobic / donor-acceptor bits).  in-cutoff pairs are masked by multiplying with
+// 0/1, which is exact for the finite values every candidate (the far sentinel included)
+// produces.  Both forms give the same bits: the term the single form leaves out is
+// exactly zero for such a type.
+template <bool COUNT, bool ONE>
 __device__ __forceinline__ void vina_x2(uint32_t wd, const float4* __restrict__ src, float2 nxy, float2 nzr,
-                                        float cut2, const VinaX2& K, uint32_t mh, uint32_t mb, float2& eb,
+                                        float cut2, const VinaX2& K, const FlagTerm& F, float2& eb,
                                         float& ax, float& ay, float& az, uint32_t& cnt, uint32_t cw) {
     const float4 a = src[wd & 0x1fffu], c = src[(wd >> 16) & 0x1fffu];
     const float2 pm = make_float2(1.f, -1.f);
@@ -362,24 +402,33 @@ __device__ __forceinline__ void vina_x2(uint32_t wd, const float4* __restrict__ 
     const float2 q2 = __fmul2_rn(__fmul2_rn(b, b), K.c2);
     const float2 g2 = make_float2(ex2_approx(q2.x), ex2_approx(q2.y));
     const float2 dn = make_float2(fminf(d.x, 0.f), fminf(d.y, 0.f));
-    const float2 hr = __ffma2_rn(d, K.m1, K.p15);                      // 1.5 - d
-    const float2 hy = make_float2(__saturatef(hr.x), __saturatef(hr.y));
-    const float2 ih = make_float2(hy.x == hr.x ? 1.f : 0.f, hy.y == hr.y ? 1.f : 0.f);
-    const float2 br = __fmul2_rn(d, K.m07);                            // -d / 0.7
-    const float2 hb = make_float2(__saturatef(br.x), __saturatef(br.y));
-    const float2 ib = make_float2(hb.x == br.x ? 1.f : 0.f, hb.y == br.y ? 1.f : 0.f);
-    const float2 w3h = make_float2((wd & mh) ? K.w3 : 0.f, (wd & (mh << 16)) ? K.w3 : 0.f);
-    const float2 w4h = make_float2((wd & mb) ? K.w4 : 0.f, (wd & (mb << 16)) ? K.w4 : 0.f);
     float2 e = __fmul2_rn(K.w0, g1);
     e = __ffma2_rn(K.w1, g2, e);
     e = __ffma2_rn(K.w2, __fmul2_rn(dn, dn), e);
-    e = __ffma2_rn(w3h, hy, e);
-    e = __ffma2_rn(w4h, hb, e);
     float2 ng = __fmul2_rn(__fmul2_rn(d, K.n0), g1);                    // 8 w0 d g1
     ng = __ffma2_rn(__fmul2_rn(b, K.w1), g2, ng);                       // + w1 b g2
     ng = __ffma2_rn(K.n2, dn, ng);                                      // - 2 w2 dn
-    ng = __ffma2_rn(ih, w3h, ng);
-    ng = __ffma2_rn(ib, __fmul2_rn(w4h, K.k07), ng);
+    if constexpr (ONE) {
+        const float2 hr = make_float2(fmaf(d.x, F.nb, F.a), fmaf(d.y, F.nb, F.a));   // a - b d
+        const float2 hy = make_float2(__saturatef(hr.x), __saturatef(hr.y));
+        const float2 ih = make_float2(hy.x == hr.x ? 1.f : 0.f, hy.y == hr.y ? 1.f : 0.f);
+        const float2 wf = make_float2((wd & F.m) ? F.w : 0.f, (wd & (F.m << 16)) ? F.w : 0.f);
+        e = __ffma2_rn(wf, hy, e);
+        ng = __ffma2_rn(ih, make_float2(wf.x * F.b, wf.y * F.b), ng);  // + w b inside the ramp
+    } else {
+        const float2 hr = __ffma2_rn(d, K.m1, K.p15);                  // 1.5 - d
+        const float2 hy = make_float2(__saturatef(hr.x), __saturatef(hr.y));
+        const float2 ih = make_float2(hy.x == hr.x ? 1.f : 0.f, hy.y == hr.y ? 1.f : 0.f);
+        const float2 br = __fmul2_rn(d, K.m07);                        // -d / 0.7
+        const float2 hb = make_float2(__saturatef(br.x), __saturatef(br.y));
+        const float2 ib = make_float2(hb.x == br.x ? 1.f : 0.f, hb.y == br.y ? 1.f : 0.f);
+        const float2 w3h = make_float2((wd & F.mh) ? K.w3 : 0.f, (wd & (F.mh << 16)) ? K.w3 : 0.f);
+        const float2 w4h = make_float2((wd & F.mb) ? K.w4 : 0.f, (wd & (F.mb << 16)) ? K.w4 : 0.f);
+        e = __ffma2_rn(w3h, hy, e);
+        e = __ffma2_rn(w4h, hb, e);
+        ng = __ffma2_rn(ih, w3h, ng);
+        ng = __ffma2_rn(ib, __fmul2_rn(w4h, K.k07), ng);
+    }
     eb = __ffma2_rn(e, in, eb);
     const float2 f = __fmul2_rn(__fmul2_rn(ng, in), ri);
     float2 axy = make_float2(ax, ay);

@@ -54,6 +54,7 @@ struct SampleArgs {
     const int* trace_slot;
     int n_trace;
     unsigned long long* pair_count;
+    unsigned long long* phase_cycles;
     const int* lig_order;      // ligands by decreasing cost; item it = (lig_order[it / P], it % P)
     int n_items;
     unsigned int* counter;
@@ -200,7 +201,7 @@ __device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float p
 // warp except the per-torsion lanes.
 template <int TS, bool COUNT, bool GEN>
 __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h, const PW& W, int l, int p, int s,
-                            const Sched& sc, PoseState& st, uint32_t& npairs) {
+                            const Sched& sc, PoseState& st, uint32_t& npairs, PhaseClock& pc) {
     __syncwarp();               // the rigid state is one shared copy written by every lane
     if (st.status & 1) return;  // frozen after a non-finite energy
     const int T = h.n_tor, lane = W.lane;
@@ -235,12 +236,15 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
         st.mth = st.vth = 0.f;
     }
     // evaluate
+    if (COUNT) pc.lap(TRIDS_PHASE_UPDATE);
     fk_warp(A.B, h, W, st.t, st.q, st.th, S.P->radius);
+    if (COUNT) pc.lap(TRIDS_PHASE_FK);
     ParamAcc acc;
     float e_inter;
-    const float E = score_warp<TS, false, COUNT, GEN>(A.B, A.pk, S, h, W, 1.f, acc, &e_inter, npairs);
+    const float E = score_warp<TS, false, COUNT, GEN>(A.B, A.pk, S, h, W, 1.f, acc, &e_inter, npairs, &pc);
     float gt[3], tau[3];
     const float gth = adjoint_warp(A.B, h, W, st.t, gt, tau);
+    if (COUNT) pc.lap(TRIDS_PHASE_ADJOINT);
     if (A.trace) {
         const int slot = A.trace_slot[(size_t)l * A.P + p];
         if (slot >= 0) {
@@ -304,7 +308,7 @@ __device__ __forceinline__ void flush_count(unsigned long long* cnt, uint32_t n)
     unsigned long long v = n;
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if ((threadIdx.x & 31) == 0 && v) atomicAdd(cnt, v >> 1);
+    if ((threadIdx.x & 31) == 0 && v && cnt) atomicAdd(cnt, v >> 1);
 }
 
 // Persistent fused sampler: each warp pops poses from a global counter (ligands in
@@ -317,6 +321,8 @@ __global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
            reinterpret_cast<const uint8_t*>(smem + A.ptype_off)};
     const PW W = make_pw(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor);
     uint32_t npairs = 0;
+    PhaseClock pc(W);
+    if (COUNT) pc.start();
     for (;;) {
         int it = 0;
         if (W.lane == 0) it = (int)atomicAdd(A.counter, 1u);
@@ -329,9 +335,11 @@ __global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
         if (A.step_begin == 0) init_pose(A, h, W.lane, l, p, st);
         else load_pose(A, h, W.lane, l, p, st);
         __syncwarp();
+        if (COUNT) pc.lap(TRIDS_PHASE_OTHER);
         Sched sc = schedule(A.S, A.Lmc, A.step_begin);
         for (int s = A.step_begin; s < A.step_end; ++s) {
-            sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, sc, st, npairs);
+            sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, sc, st, npairs, pc);
+            if (COUNT) pc.lap(TRIDS_PHASE_UPDATE);
             if (++sc.j == sc.n) {   // next Monte-Carlo loop: the schedule of evaluation s + 1
                 ++sc.loop;
                 sc.j = 0;
@@ -341,8 +349,12 @@ __global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
         __syncwarp();
         store_pose(A, h, W.lane, l, p, st);
         __syncwarp();
+        if (COUNT) pc.lap(TRIDS_PHASE_OTHER);
     }
-    if (COUNT) flush_count(A.pair_count, npairs);
+    if (COUNT) {
+        flush_count(A.pair_count, npairs);
+        pc.flush(A.phase_cycles);
+    }
 }
 
 // Plain form: one launch per (ligand, evaluation), one warp per pose, the state in
@@ -358,14 +370,22 @@ __global__ void __launch_bounds__(640, 1) k_sample_step(SampleArgs A, int l, int
     if (p >= A.P) return;
     const LigHdr h = A.B.lig[l];
     uint32_t npairs = 0;
+    PhaseClock pc(W);
+    if (COUNT) pc.start();
     PoseState st(*W.rig, W.tor[W.lane]);
     if (s == 0) init_pose(A, h, W.lane, l, p, st);
     else load_pose(A, h, W.lane, l, p, st);
     __syncwarp();
-    sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, schedule(A.S, A.Lmc, s), st, npairs);
+    if (COUNT) pc.lap(TRIDS_PHASE_OTHER);
+    sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, schedule(A.S, A.Lmc, s), st, npairs, pc);
+    if (COUNT) pc.lap(TRIDS_PHASE_UPDATE);
     __syncwarp();
     store_pose(A, h, W.lane, l, p, st);
-    if (COUNT) flush_count(A.pair_count, npairs);
+    if (COUNT) {
+        pc.lap(TRIDS_PHASE_OTHER);
+        flush_count(A.pair_count, npairs);
+        pc.flush(A.phase_cycles);
+    }
 }
 
 // ------------------------------------------------------------------ score + gradient

@@ -127,7 +127,7 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
         float ri = xa.w;
         // per-atom operands of the packed evaluation, set when the lane changes atom
         float2 nxy = make_float2(-xa.x, -xa.y), nzr = make_float2(-xa.z, -ri);
-        uint32_t mh = (fi & 1u) << 13, mb = (((fi & 2u) << 1) | ((fi & 4u) >> 1)) << 13;
+        FlagTerm F = make_flag_term(fi, P.w[3], P.w[4]);
         float ax = 0.f, ay = 0.f, az = 0.f;
         auto block_ptr = [&](int blk) -> const uint4* {
             const int loc = blk - first;
@@ -152,8 +152,7 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                 ri = xa.w;
                 nxy = make_float2(-xa.x, -xa.y);
                 nzr = make_float2(-xa.z, -ri);
-                mh = (fi & 1u) << 13;
-                mb = (((fi & 2u) << 1) | ((fi & 4u) >> 1)) << 13;
+                F = make_flag_term(fi, P.w[3], P.w[4]);
                 v = __ldg(block_ptr(blk));
             }
             const uint4 vc = v;
@@ -176,13 +175,13 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                 if constexpr (TS == TRIDS_TERMS_VINA5 && !PARAMS) {
 #pragma unroll
                     for (int u = 0; u < 2; ++u)
-                        vina_x2<COUNT>(wv[u], src, nxy, nzr, cut2, K, mh, mb, eb2, ax, ay, az, npairs,
-                                       intra ? 1u : 2u);   // doubled: intra pairs come twice
+                        vina_x2<COUNT, !MAPS>(wv[u], src, nxy, nzr, cut2, K, F, eb2, ax, ay, az, npairs,
+                                              intra ? 1u : 2u);   // doubled: intra pairs come twice
                 } else if constexpr (!PARAMS) {
                     const float4* gm = nullptr;   // term set 1: the atom-pair E_MDN runs in gmm_warp
 #pragma unroll
                     for (int u = 0; u < 2; ++u)
-                        trids_x2<COUNT>(wv[u], src, nxy, nzr, cut2, w, mb, gm, S.ptype, P.gmm_k, eb2, ax, ay, az,
+                        trids_x2<COUNT>(wv[u], src, nxy, nzr, cut2, w, F.mb, gm, S.ptype, P.gmm_k, eb2, ax, ay, az,
                                         npairs, intra ? 1u : 2u);
                 } else {
 #pragma unroll
@@ -462,18 +461,49 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
     return e;
 }
 
-// E_total of the warp's pose (same value on every lane); forces in W.gs.
+// Per-phase SM clock cycles of a warp (the counting form of the sampler only), kept in
+// the warp's shared-memory clock slots so that the timed code keeps its registers: lap(k)
+// charges the cycles since the previous lap to phase k (TRIDS_PHASE_*); lane 0 keeps the
+// books.
+struct PhaseClock {
+    unsigned long long* c;   // W.clk: [TRIDS_PHASES] sums, then the time of the last lap
+    __device__ __forceinline__ explicit PhaseClock(const PW& W) : c(W.clk) {}
+    __device__ __forceinline__ void start() {
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int k = 0; k < TRIDS_PHASES; ++k) c[k] = 0ull;
+            c[TRIDS_PHASES] = (unsigned long long)clock64();
+        }
+    }
+    __device__ __forceinline__ void lap(int k) {
+        if ((threadIdx.x & 31) == 0) {
+            const unsigned long long n = (unsigned long long)clock64();
+            c[k] += n - c[TRIDS_PHASES];
+            c[TRIDS_PHASES] = n;
+        }
+    }
+    __device__ __forceinline__ void flush(unsigned long long* out) const {
+        if (out && (threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int k = 0; k < TRIDS_PHASES; ++k) atomicAdd(out + k, c[k]);
+    }
+};
+
+// E_total of the warp's pose (same value on every lane); forces in W.gs.  COUNT kernels
+// time the pair loop and the other passes on pc.
 template <int TS, bool PARAMS, bool COUNT, bool MAPS>
 __device__ float score_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
-                            float ebar, ParamAcc& acc, float* e_inter, uint32_t& npairs) {
+                            float ebar, ParamAcc& acc, float* e_inter, uint32_t& npairs, PhaseClock* pc = nullptr) {
     float w[5];
 #pragma unroll
     for (int t = 0; t < 5; ++t) w[t] = S.P->w[t];
     float ein2;
     float el = pairs_warp<TS, PARAMS, COUNT, MAPS>(B, pk, S, h, W, w, ebar, acc, npairs, &ein2);
+    if (COUNT && pc) pc->lap(TRIDS_PHASE_PAIRS);
     if (MAPS && pk.use_maps) el += map_warp(B, pk, h, W);
     if constexpr (TS == TRIDS_TERMS_TRIDS && !PARAMS) el += gmm_warp<MAPS>(B, pk, S, h, W, w[0]);
     if constexpr (TS == TRIDS_TERMS_TRIDS_RES) el += residue_warp<PARAMS>(B, pk, S, h, W, w[0], ebar, acc);
+    if (COUNT && pc) pc->lap(TRIDS_PHASE_PASSES);
     const float e_lp = warp_sum(el);
     *e_inter = e_lp;
     return e_lp + 0.5f * warp_sum(ein2);

@@ -693,7 +693,8 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     if ((rc = check_device_ptr(dof, "dof", false)) || (rc = check_device_ptr(state, "state", false)) ||
         (rc = check_device_ptr(energy, "energy", false)) || (rc = check_device_ptr(c.trace, "trace", true)) ||
         (rc = check_device_ptr(c.trace_slot, "trace_slot", true)) ||
-        (rc = check_device_ptr(c.pair_count, "pair_count", true)) || (rc = check_terms(pk, b)))
+        (rc = check_device_ptr(c.pair_count, "pair_count", true)) ||
+        (rc = check_device_ptr(c.phase_cycles, "phase_cycles", true)) || (rc = check_terms(pk, b)))
         return rc;
     if ((rc = ensure_items(b, c.poses))) return rc;
     Layout L;
@@ -706,16 +707,21 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     A.beta = c.beta; A.opt = c.optimizer; A.wd = c.weight_decay; A.momentum = c.momentum; A.alpha = c.alpha;
     A.seed = c.seed; A.lig_base = c.lig_base; A.dof = dof; A.state = state; A.energy = energy;
     A.trace = c.trace; A.trace_slot = c.trace_slot; A.n_trace = c.n_trace; A.pair_count = c.pair_count;
+    A.phase_cycles = c.phase_cycles;
     A.lig_order = b->d_lig_order; A.n_items = b->dims.n_lig * c.poses; A.counter = b->d_counter; A.err = b->d_err;
     A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.ptype_off = L.ptype_off;
     A.mbar_off = L.mbar_off;
     A.warp_off = L.warp_off; A.warp_bytes = L.warp_bytes;
     cudaStream_t st = (cudaStream_t)stream;
     const int ts = pk->prm.term_set;
-    const bool cnt = c.pair_count != nullptr;
-    // the general kernels carry the other update rules and the grid maps; the plain ones
-    // (Adam, direct pair sums: the paper's configuration) leave that code out
-    const bool gen = c.optimizer != TRIDS_OPT_ADAM || pk->d_maps != nullptr;
+    const bool cnt = c.pair_count != nullptr || c.phase_cycles != nullptr;
+    // the general kernels carry the other update rules, the grid maps and the two-term
+    // flag evaluation; the plain ones (Adam, direct pair sums, no type both hydrophobic and
+    // donor/acceptor: the paper's configuration) leave that code out
+    bool dual = false;
+    for (int t = 0; t < pk->prm.n_types; ++t)
+        dual |= (pk->prm.flags[t] & 1) && (pk->prm.flags[t] & 6);
+    const bool gen = c.optimizer != TRIDS_OPT_ADAM || pk->d_maps != nullptr || dual;
     if (c.mode == TRIDS_MODE_PER_LIGAND) {
         const StepKernel kern = step_kernel(ts, cnt, gen);
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
