@@ -9,9 +9,12 @@ on a bounded sample, and an end-to-end pass that packs host ligand arrays, sampl
 ranks and copies the results back.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {trids,reference}]
-Multi-GPU (torchrun): every rank samples its own 1,024-ligand batch (weak scaling);
-no collective touches the data path; the timed region is bracketed by barriers and
-the slowest rank's time is used.
+Multi-GPU (torchrun): the one ligand set is split over the ranks by
+longest-processing-time on each ligand's cost (strong scaling: the total work is fixed);
+every rank samples its shard with the ligands' global indices as random-stream ids, so
+the results do not depend on the split.  No collective touches the data path; the timed
+region is bracketed by barriers, the slowest rank's time is used, and the shards' top-k
+are gathered on rank 0 on the host after it.
 """
 from __future__ import annotations
 
@@ -189,7 +192,7 @@ def run_reference(args, rank):
     value = statistics.mean(rates)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w.poses * w.steps / value,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "n_lig": len(w.ligands), "poses": w.poses, "steps": w.steps,
                        "pocket_atoms": len(w.pocket.type)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -239,17 +242,26 @@ def main():
     if w.cell and not args.cell:
         args.cell = w.cell
     if args.per_ligand_steps is None:
-        args.per_ligand_steps = 1 if args.workload == "batched_screening" else 0
+        args.per_ligand_steps = 1 if args.workload == "batched_screening" and world == 1 else 0
     sp, res = score_setup(args.terms, w)
-    arrays = synth.concat_ligands(w.ligands)
+    all_arrays = synth.concat_ligands(w.ligands)
+    # this rank's shard of the ligand set (all of it on one GPU)
+    mine = parallel.shard_lpt(parallel.ligand_cost([len(l.type) for l in w.ligands],
+                                                   [l.n_tor for l in w.ligands]), world)[rank]
+    arrays = synth.concat_ligands([w.ligands[i] for i in mine]) if world > 1 else all_arrays
     tuned = None
     if sp.term_set != 0:
         args.cell, args.warps = args.cell or 0.5, args.warps or 20
     if not args.cell and not args.warps:
-        from paper_2510_24186_b300 import autotune
-        tuned = autotune.autotune(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, arrays, w.poses,
-                                  steps=w.steps, mc_loops=w.mc_loops)
-        args.cell, args.warps = tuned.cell, tuned.warps_per_block
+        shape = [None]
+        if rank == 0:
+            from paper_2510_24186_b300 import autotune
+            tuned = autotune.autotune(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp, all_arrays,
+                                      w.poses, steps=w.steps, mc_loops=w.mc_loops)
+            shape = [(tuned.cell, tuned.warps_per_block)]
+        if dist:
+            dist.broadcast_object_list(shape, src=0)   # every rank runs rank 0's tuned shape
+        args.cell, args.warps = shape[0]
     torch.cuda.synchronize()
     torch.cuda.empty_cache()               # so the job's tensors are not served from the tuner's cached blocks
     free0 = torch.cuda.mem_get_info()[0]   # device memory of the job: pocket, batch, state, work lists, graph
@@ -268,14 +280,19 @@ def main():
     mdn = None
     if res is not None:
         pk.set_residues(res)
-        mdn = torch.from_numpy(mdn_kernels(w, int(arrays[0].sum()), res)).cuda()
+        rows = mdn_kernels(w, int(all_arrays[0].sum()), res)
+        offs = np.concatenate([[0], np.cumsum(all_arrays[0])])
+        rows = np.concatenate([rows[offs[i]:offs[i + 1]] for i in mine]) if world > 1 else rows
+        mdn = torch.from_numpy(rows).cuda()
     b = api.Batch(pk, *arrays)
+    b.set_stream_ids(mine)          # global ligand ids: the samples do not depend on the split
     if mdn is not None:
         b.set_mdn(mdn)
     P, S, Lm = w.poses, w.steps, w.mc_loops
     n_lig = b.n_lig
-    units = n_lig * P * S
-    lig_base = rank * n_lig
+    units = n_lig * P * S                   # this rank's pose-evaluations per step
+    units_all = len(w.ligands) * P * S      # the whole job's
+    lig_base = 0
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 126 MB L2
     dof = torch.zeros(n_lig, P, b.dof_stride, device="cuda")
@@ -300,6 +317,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    g0 = pk.graph_stats()
     with ClockSampler(local) as clk:
         with torch.cuda.stream(stream):
             for k in range(args.steps):
@@ -313,10 +331,14 @@ def main():
         stream.synchronize()
     if dist:
         dist.barrier()
+    g1 = pk.graph_stats()
+    graph_timed = {k: g1[k] - g0[k] for k in g1}
     t_sample = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
     t_step = [ev[k][0].elapsed_time(ev[k][2]) for k in range(args.steps)]
     total_ms = parallel.max_over_ranks(sum(t_step), device="cuda")
     rc = api.sync(b, P, state, timeout_ms=60000)
+    # the last step's top-k of every shard, gathered on rank 0 in global ligand order (host)
+    gathered = parallel.gather_topk(mine, idx.cpu().numpy(), etop.cpu().numpy())
 
     # in-cutoff pair counts of the same trajectories (untimed counting variant; the
     # energies must come out bit-identical to the timed runs)
@@ -362,9 +384,11 @@ def main():
         cuts = [0]
         while cuts[-1] < len(w.ligands):
             cuts.append(min(len(w.ligands), cuts[-1] + int(rng4.integers(500, 5001))))
-        batches = [synth.concat_ligands(w.ligands[a:b]) for a, b in zip(cuts[:-1], cuts[1:])]
-        e2e_units = sum(b - a for a, b in zip(cuts[1:-1], cuts[2:])) * P * S
-        e2e_note = f"one pass over {len(w.ligands)} ligands in {len(batches)} uneven batches (500-5,000), first untimed"
+        spans = list(zip(cuts[:-1], cuts[1:]))[rank::world]      # every world-th batch on this rank
+        batches = [synth.concat_ligands(w.ligands[a:b]) for a, b in spans]
+        e2e_units = sum(b - a for a, b in spans[1:]) * P * S
+        e2e_note = (f"one pass over {len(w.ligands)} ligands in {len(cuts) - 1} uneven batches (500-5,000), "
+                    f"every {world}th on each rank, each rank's first untimed")
     else:
         batches = [arrays] * (args.warmup + args.steps)
         e2e_units = units * args.steps
@@ -375,14 +399,21 @@ def main():
     n_untimed = 1 if len(batches) != args.warmup + args.steps else args.warmup
     e2e_s = marks[-1] - marks[n_untimed - 1]
     e2e_ms = 1000 * e2e_s / (len(marks) - n_untimed)
-    e2e_value = e2e_units / e2e_s
+    # the whole job: every rank's pose-evaluations over the slowest rank's time
+    e2e_s_max = parallel.max_over_ranks(e2e_s, device="cuda")
+    e2e_units_all = e2e_units
+    if dist:
+        t = torch.tensor([float(e2e_units)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t)
+        e2e_units_all = float(t.item())
+    e2e_value = e2e_units_all / e2e_s_max
     h2d, d2h = stats["h2d_bytes"], stats["d2h_bytes"]
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    value = world * units / (total_ms / 1000.0 / args.steps)
+    value = units_all / (total_ms / 1000.0 / args.steps)
     mhz, mhz_src = sm_max_mhz()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     peak = n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
@@ -401,15 +432,20 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "n_lig": n_lig, "poses": P, "steps": S, "mc_loops": Lm,
                    "pocket_atoms": len(w.pocket.type), "top_k": w.topk, "term_set": args.terms,
                    "optimizer": args.optimizer, "maps": maps,
-                   "graph": True, "l2": "flushed between steps (256 MB write)", "cell": args.cell or 0.5,
+                   "graph": {"timed_region": graph_timed, "total": g1,
+                             "note": "one CUDA graph per launch shape, built in the warm-up; each timed step "
+                                     "replays it after updating its nodes with that step's seed"},
+                   "l2": "flushed between steps (256 MB write)", "cell": args.cell or 0.5,
                    "warps_per_block": args.warps or 20,
                    "autotuned": None if tuned is None else {"table_ms": tuned.table, "probe": f"first 128 ligands x "
                                                             f"{P} poses x {S} evaluations per shape"},
-                   "parallelism": f"ligand shards x{world}"},
+                   "parallelism": f"ligand shards x{world}",
+                   "shards": {"split": "longest-processing-time on ligand cost, global ligand ids as stream ids",
+                              "rank0_ligands": len(mine), "topk_gathered_ligands": len(gathered[0])}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "note": f"in-cutoff atom pairs x {f_pair} FP32 FLOP / persistent-sampler time; peak = "

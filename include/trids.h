@@ -159,7 +159,9 @@ typedef struct trids_sample_cfg {
     int32_t lig_base;        /* random-stream id of ligand 0 of this batch */
     int32_t mode;            /* TRIDS_MODE_* */
     int32_t warps_per_block; /* poses (warps) per block, 1..20; 0 = 20, or fewer if the pocket needs the shared memory */
-    int32_t use_graph;       /* persistent mode: capture the launch in a CUDA graph and replay it */
+    int32_t use_graph;       /* persistent mode: launch through the pocket's CUDA graph (counter reset +
+                              * persistent kernel), built once per launch shape and replayed; other
+                              * arguments update its nodes (see trids_graph_stats) */
     float* trace;            /* nullable device buffer, see trids_sample */
     const int32_t* trace_slot; /* device [n_lig*poses]: trace slot of each pose or -1 */
     int32_t n_trace;         /* number of trace slots */
@@ -210,7 +212,8 @@ int trids_set_params(trids_pocket* pk, const trids_params* prm, void* stream);
  */
 int trids_set_boxes(trids_pocket* pk, int32_t n_boxes, const float* centers, const float* sizes);
 
-/* Free a pocket and its device arrays (maps, residue lists included).  NULL is a no-op;
+/* Free a pocket, its device arrays (maps, residue lists included) and its sampler CUDA
+ * graph.  NULL is a no-op;
  * the caller must not free a pocket while work that uses it is in flight. */
 int trids_free_pocket(trids_pocket* pk);
 
@@ -271,8 +274,8 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
                        const float* xyz, const int32_t* type, const int32_t* n_bonds,
                        const int32_t* bonds, const uint8_t* rotatable, trids_batch** out);
 
-/* Free a batch, its device arrays, work lists and cached CUDA graph.  NULL is a no-op;
- * the caller must not free a batch while work that uses it is in flight. */
+/* Free a batch, its device arrays and work lists.  NULL is a no-op; the caller must not
+ * free a batch while work that uses it is in flight. */
 int trids_free_batch(trids_batch* b);
 
 /*
@@ -287,6 +290,17 @@ int trids_free_batch(trids_batch* b);
  * TRIDS_ECUDA.
  */
 int trids_set_mdn(trids_batch* b, int32_t n_res, int32_t K, const float* mdn, void* stream);
+
+/*
+ * Random-stream ids of the batch's ligands (host int32 [n_lig], each >= 0): ligand l then
+ * draws its random numbers as ligand lig_base + ids[l] (trids_sample), instead of
+ * lig_base + l.  A ligand's samples depend only on its stream id, the seed and the
+ * pocket, not on which batch holds it, so a ligand set split into shards (one per GPU,
+ * say) and sampled with each ligand's global index as its id gives the same results as
+ * the whole set in one batch.  Synchronous.  Errors: TRIDS_EINVAL (NULL, negative id),
+ * TRIDS_ECUDA.
+ */
+int trids_set_stream_ids(trids_batch* b, const int32_t* ids);
 
 /* Sizes of a packed batch (trids_batch_dims above), written to the host struct `dims`.
  * TRIDS_EINVAL for NULL arguments. */
@@ -382,7 +396,8 @@ int64_t trids_state_floats(const trids_batch* b, int32_t poses);
  *   u < exp(-beta (E_new - E_old)), else the state from before its perturbation is
  *   restored.  Random numbers: Philox4x32-10, key = seed, counter = (pose, lig_base +
  *   ligand, loop<<16 | purpose<<8 | block, 0), purpose 0 init, 1 perturbation,
- *   2 acceptance; uniform = (word >> 8) * 2^-24.
+ *   2 acceptance; uniform = (word >> 8) * 2^-24.  (lig_base + ligand is lig_base + the
+ *   ligand's stream id when trids_set_stream_ids set one.)
  *   dof     device [n_lig][poses][dof_stride], out (in as well when step_begin > 0).
  *   state   device [trids_state_floats] scratch: Adam moments, saved state, loop
  *           energies, per-pose status.  Keep it between calls to resume.
@@ -396,6 +411,16 @@ int64_t trids_state_floats(const trids_batch* b, int32_t poses);
  */
 int trids_sample(const trids_pocket* pk, const trids_batch* b, const trids_sample_cfg* cfg,
                  float* dof, float* state, float* energy, void* stream);
+
+/*
+ * Counters of the pocket's CUDA graph of the persistent sampler (Sec. 4 item 2: the
+ * repeated operators are compiled once as a graph and kept on the GPU): how many times
+ * it was built (once per launch shape: kernel, grid, block, shared memory), how many
+ * calls updated its nodes in place (a new seed, ligand ids, step range, buffers or a
+ * batch of the same shape), and how many times it was launched.  Host pointers,
+ * nullable.  TRIDS_EINVAL for a NULL pocket.
+ */
+int trids_graph_stats(const trids_pocket* pk, int64_t* instantiations, int64_t* updates, int64_t* launches);
 
 /*
  * trids_topk -- rank and cluster (Sec. 2, end of "Conformation sampling"): per ligand,

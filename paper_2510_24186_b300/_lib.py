@@ -17,7 +17,7 @@ EXPORTS = ("trids_last_error", "trids_version", "trids_make_pocket", "trids_set_
            "trids_free_pocket", "trids_set_residues", "trids_build_maps", "trids_maps_info",
            "trids_pack_ligands", "trids_free_batch", "trids_set_mdn", "trids_batch_info", "trids_batch_query",
            "trids_pack_topology", "trids_score_grad", "trids_score_grad_noalloc", "trids_state_floats",
-           "trids_sample", "trids_topk", "trids_screen_energy", "trids_sync")
+           "trids_sample", "trids_topk", "trids_screen_energy", "trids_sync", "trids_graph_stats", "trids_set_stream_ids")
 
 
 class Params(C.Structure):
@@ -90,6 +90,8 @@ def lib(build_if_missing: bool = True):
     L.trids_topk.argtypes = [vp, i32, vp, vp, i32, fp, vp, vp, vp]
     L.trids_screen_energy.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
     L.trids_sync.argtypes = [vp, i32, vp, vp, C.c_double]
+    L.trids_graph_stats.argtypes = [vp, P(i64), P(i64), P(i64)]
+    L.trids_set_stream_ids.argtypes = [vp, vp]
     for name in EXPORTS:
         if name not in ("trids_last_error", "trids_version", "trids_state_floats"):
             getattr(L, name).restype = C.c_int

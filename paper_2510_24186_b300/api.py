@@ -115,6 +115,13 @@ class Pocket:
         check(_lib.lib().trids_maps_info(self.handle, C.byref(lo), C.byref(h), C.byref(n)))
         return np.array(lo[:], dtype=np.float32), float(h.value), tuple(n[:])
 
+    def graph_stats(self) -> dict:
+        """Counters of the pocket's sampler CUDA graph (trids_graph_stats): instantiations,
+        in-place node updates and launches."""
+        v = [C.c_int64(0) for _ in range(3)]
+        check(_lib.lib().trids_graph_stats(self.handle, *[C.byref(x) for x in v]))
+        return {"instantiations": v[0].value, "updates": v[1].value, "launches": v[2].value}
+
     def close(self):
         if getattr(self, "handle", None):
             _lib.lib().trids_free_pocket(self.handle)
@@ -165,6 +172,14 @@ class Batch:
         check(_lib.lib().trids_batch_query(self.handle, None, None, lig, out.ctypes.data, cap))
         L, T, P = out[0], out[1], out[2]
         return out[:3 + 2 * L + 5 * T + 2 * P].copy()
+
+    def set_stream_ids(self, ids):
+        """Random-stream ids of the ligands (trids_set_stream_ids): ligand l samples as ligand
+        lig_base + ids[l], e.g. its index in a larger set this batch is a shard of."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        if ids.shape != (self.n_lig,):
+            raise ValueError(f"need {self.n_lig} stream ids, got shape {ids.shape}")
+        check(_lib.lib().trids_set_stream_ids(self.handle, ids.ctypes.data))
 
     def state_floats(self, poses: int) -> int:
         return int(_lib.lib().trids_state_floats(self.handle, poses))
@@ -385,3 +400,37 @@ def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd:
             yield base, idx_h.numpy().copy(), e_h.numpy().copy()
             base += b.n_lig
             b.close()
+
+
+def screen_sharded(pocket: Pocket, ligands, poses: int, steps: int, k: int, rmsd: float = 1.0, seed: int = 0,
+                   mc_loops: int = 8, rank: Optional[int] = None, world: Optional[int] = None, gather: bool = True,
+                   stream=None, **sample_kw):
+    """Screen a ligand set split over GPUs, one process per GPU (torch.distributed supplies
+    rank and world size unless given).  The set is split by longest-processing-time on each
+    ligand's cost; this rank packs its shard, gives every ligand its global index as its
+    random-stream id (so the results do not depend on the split), samples, ranks, and copies
+    the top-k back; rank 0 then gathers every shard's top-k on the host in global ligand order
+    (ids [n], pose indices [n, k], energies [n, k]; other ranks get None).  gather=False
+    returns each rank's own shard instead.  ligands: objects with xyz, type, bonds, rotatable
+    (as synth.Ligand)."""
+    from . import parallel
+    from .synth import concat_ligands
+    _require_cuda()
+    n_atoms = [len(l.type) for l in ligands]
+    n_tor = [int(np.asarray(l.rotatable).sum()) for l in ligands]
+    st = stream or torch.cuda.current_stream()
+
+    def run_shard(ids):
+        b = Batch(pocket, *concat_ligands([ligands[i] for i in ids]))
+        try:
+            b.set_stream_ids(ids)
+            with torch.cuda.stream(st):
+                out = sample(pocket, b, poses, steps, mc_loops=mc_loops, seed=seed, lig_base=0, stream=st,
+                             **sample_kw)
+                idx, e = topk(b, out["energy"], out["dof"], k, rmsd, stream=st)
+            st.synchronize()
+            return idx.cpu().numpy(), e.cpu().numpy()
+        finally:
+            b.close()
+
+    return parallel.screen_shards(n_atoms, n_tor, run_shard, rank, world, gather)

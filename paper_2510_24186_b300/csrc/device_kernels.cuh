@@ -84,7 +84,7 @@ __device__ __forceinline__ float* fld(const SampleArgs& A, int l, int f, int p) 
 }
 
 __device__ void init_pose(const SampleArgs& A, const LigHdr& h, int lane, int l, int p, PoseState& st) {
-    const uint32_t lig = (uint32_t)(A.lig_base + l);
+    const uint32_t lig = (uint32_t)(A.lig_base + h.sid);
     const uint4 r0 = rand_block(A.seed, lig, (uint32_t)p, 0u, 0u, 0u);
     const uint4 r1 = rand_block(A.seed, lig, (uint32_t)p, 0u, 0u, 1u);
     const float u[6] = {u01(r0.x), u01(r0.y), u01(r0.z), u01(r0.w), u01(r1.x), u01(r1.y)};
@@ -207,7 +207,7 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
     const int T = h.n_tor, lane = W.lane;
     const int bx = A.pk.n_boxes > 1 ? p % A.pk.n_boxes : 0;   // the pose's docking box
     const bool own = lane < T;
-    const uint32_t lig = (uint32_t)(A.lig_base + l);
+    const uint32_t lig = (uint32_t)(A.lig_base + h.sid);
     if (sc.j == 0) {
         if (sc.loop > 0) {
             // save the state, then resample one of the 6+T variables in its range

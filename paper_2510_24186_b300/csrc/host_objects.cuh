@@ -10,6 +10,34 @@ constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // =============================================================== host objects
+// CUDA graph of the persistent sampler (Sec. 4 item 2: the repeated operators are kept
+// on the GPU as a graph): a counter-reset node and one persistent-kernel node, built once
+// per launch shape (kernel, grid, block, shared memory) and replayed.  A call with other
+// arguments (seed, ligand ids, step range, buffers, another batch of the same shape)
+// updates the two nodes of the executable graph in place instead of building a new one.
+struct GraphCache {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t reset = nullptr, launch = nullptr;
+    const void* func = nullptr;
+    int grid = 0, block = 0;
+    size_t smem = 0;
+    std::vector<unsigned char> args;   // kernel arguments of the last launch
+    const void* counter = nullptr;     // the reset node's target
+    int64_t instantiations = 0, updates = 0, launches = 0;
+    std::mutex mu;
+    void clear() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        reset = launch = nullptr;
+        func = nullptr;
+        args.clear();
+        counter = nullptr;
+    }
+};
+
 struct trids_pocket {
     int device = 0;
     int M = 0;
@@ -42,6 +70,7 @@ struct trids_pocket {
     uint32_t* d_rcell = nullptr;
     uint32_t* d_rlist = nullptr;
     uint16_t* d_rlevels = nullptr;
+    GraphCache graph;                    // the persistent sampler's CUDA graph
     DevPocket view() const {
         DevPocket v;
         v.atoms = d_atoms; v.ptype = d_ptype; v.cell_start = d_cell; v.cand = d_cand; v.params = d_params; v.M = M;
@@ -65,11 +94,6 @@ struct trids_pocket {
             for (int d = 0; d < 3; ++d) { v.box_lo[b][d] = box_lo[b][d]; v.box_hi[b][d] = box_hi[b][d]; }
         return v;
     }
-};
-
-struct GraphCache {
-    cudaGraphExec_t exec = nullptr;
-    std::vector<unsigned char> key;
 };
 
 struct trids_batch {
@@ -102,7 +126,6 @@ struct trids_batch {
     size_t partials_cap = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
-    GraphCache graph;
     float4* d_mdn = nullptr;        // residue-level E_MDN kernels, packed rows
     int mdn_res = 0, mdn_k = 0;
     DevBatch view() const {

@@ -161,6 +161,7 @@ int trids_set_boxes(trids_pocket* pk, int32_t n_boxes, const float* centers, con
 int trids_free_pocket(trids_pocket* pk) {
     if (!pk) return TRIDS_OK;
     for (trids_batch* b : pk->batches) b->owner = nullptr;
+    pk->graph.clear();
     cudaFree(pk->d_atoms);
     cudaFree(pk->d_ptype);
     cudaFree(pk->d_cell);
@@ -423,6 +424,7 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
         h.ipre_off = (int)poff[l];
         h.ient_off = (int)eoff[l];
         h.n_pairs = (int)lg.pairs.size();
+        h.sid = l;
         b->hdr[l] = h;
         const float* X = xyz + 3 * aoff[l];
         const int32_t* Ty = type + aoff[l];
@@ -522,7 +524,6 @@ int trids_free_batch(trids_batch* b) {
         auto& v = b->owner->batches;
         v.erase(std::remove(v.begin(), v.end(), b), v.end());
     }
-    if (b->graph.exec) cudaGraphExecDestroy(b->graph.exec);
     if (b->side) cudaStreamDestroy(b->side);
     if (b->ev_a) cudaEventDestroy(b->ev_a);
     if (b->ev_b) cudaEventDestroy(b->ev_b);
@@ -576,6 +577,20 @@ int trids_set_mdn(trids_batch* b, int32_t n_res, int32_t K, const float* mdn, vo
     b->d_mdn = d_out;
     b->mdn_res = n_res;
     b->mdn_k = K;
+    return TRIDS_OK;
+}
+
+int trids_set_stream_ids(trids_batch* b, const int32_t* ids) {
+    g_err.clear();
+    if (!b || !ids) return fail(TRIDS_EINVAL, "NULL argument");
+    for (int l = 0; l < b->dims.n_lig; ++l)
+        if (ids[l] < 0) return fail(TRIDS_EINVAL, "stream id of ligand %d is negative", l);
+    int rc = device_guard(b->device);
+    if (rc) return rc;
+    std::vector<LigHdr> hdr = b->hdr;
+    for (int l = 0; l < b->dims.n_lig; ++l) hdr[l].sid = ids[l];
+    CK(cudaMemcpy(b->d_lig, hdr.data(), hdr.size() * sizeof(LigHdr), cudaMemcpyHostToDevice));
+    b->hdr = hdr;
     return TRIDS_OK;
 }
 
@@ -701,7 +716,7 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     const int warps = pick_warps(c.warps_per_block > 0 ? c.warps_per_block : 20, pk, b, false, &L);
     if (!warps) return fail(TRIDS_EINVAL, "pocket of %d atoms does not fit in shared memory", pk->M);
     SampleArgs A;
-    std::memset(&A, 0, sizeof A);  // the bytes form the graph-cache key
+    std::memset(&A, 0, sizeof A);  // padding too: the bytes are compared with the graph's last arguments
     A.pk = pk->view(); A.B = b->view(); A.P = c.poses; A.S = c.steps; A.step_begin = c.step_begin;
     A.step_end = c.step_end; A.Lmc = c.mc_loops; A.lr = c.lr; A.b1 = c.beta1; A.b2 = c.beta2; A.eps = c.eps;
     A.beta = c.beta; A.opt = c.optimizer; A.wd = c.weight_decay; A.momentum = c.momentum; A.alpha = c.alpha;
@@ -742,14 +757,10 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         CK(cudaGetLastError());
         return TRIDS_OK;
     }
-    // CUDA graph (Sec. 4 item 2): counter reset + persistent launch, captured once per
-    // argument set and replayed on the caller's stream.  The legacy default stream
-    // cannot be captured; for it capture and replay run on a side stream ordered
-    // against the caller's by events.
-    std::vector<unsigned char> key(sizeof(SampleArgs) + 4 * sizeof(int));
-    std::memcpy(key.data(), &A, sizeof(SampleArgs));
-    const int extra[4] = {grid, warps, ts, (cnt ? 1 : 0) | (gen ? 2 : 0)};
-    std::memcpy(key.data() + sizeof(SampleArgs), extra, sizeof extra);
+    // CUDA graph (Sec. 4 item 2), kept on the pocket: built once per launch shape and
+    // replayed; other arguments update its nodes.  The legacy default stream cannot carry
+    // graph work ordered like a capture-free launch, so for it the graph runs on a side
+    // stream ordered against the caller's by events.
     const bool legacy = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
     if (legacy && !b->side) {
         CK(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
@@ -757,31 +768,70 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         CK(cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming));
     }
     cudaStream_t run = legacy ? b->side : st;
-    if (!b->graph.exec || b->graph.key != key) {
-        if (b->graph.exec) { cudaGraphExecDestroy(b->graph.exec); b->graph.exec = nullptr; }
-        if (!b->side) CK(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
-        cudaStream_t cs = b->side;
-        cudaGraph_t g;
-        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        cudaMemsetAsync(A.counter, 0, sizeof(unsigned int), cs);
-        kern<<<grid, 32 * warps, L.total, cs>>>(A);
-        cudaError_t le = cudaGetLastError();
-        CK(cudaStreamEndCapture(cs, &g));
-        if (le != cudaSuccess) { cudaGraphDestroy(g); return fail(TRIDS_ECUDA, "launch during capture: %s", cudaGetErrorString(le)); }
-        cudaError_t ie = cudaGraphInstantiate(&b->graph.exec, g, 0);
-        cudaGraphDestroy(g);
-        if (ie != cudaSuccess) return fail(TRIDS_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
-        b->graph.key = key;
+    GraphCache& G = const_cast<trids_pocket*>(pk)->graph;
+    std::lock_guard<std::mutex> lock(G.mu);
+    void* kargs[] = {&A};
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.func = reinterpret_cast<void*>(kern);
+    kp.gridDim = dim3((unsigned)grid);
+    kp.blockDim = dim3(32u * (unsigned)warps);
+    kp.sharedMemBytes = (unsigned)L.total;
+    kp.kernelParams = kargs;
+    cudaMemsetParams mp;
+    std::memset(&mp, 0, sizeof mp);
+    mp.dst = A.counter;
+    mp.value = 0;
+    mp.elementSize = sizeof(unsigned int);
+    mp.width = 1;
+    mp.height = 1;
+    const unsigned char* ab = reinterpret_cast<const unsigned char*>(&A);
+    const bool same_shape = G.exec && G.func == kp.func && G.grid == grid && G.block == 32 * warps &&
+                            G.smem == L.total;
+    if (!same_shape) {
+        G.clear();
+        CK(cudaGraphCreate(&G.graph, 0));
+        CK(cudaGraphAddMemsetNode(&G.reset, G.graph, nullptr, 0, &mp));
+        CK(cudaGraphAddKernelNode(&G.launch, G.graph, &G.reset, 1, &kp));
+        cudaError_t ie = cudaGraphInstantiate(&G.exec, G.graph, 0);
+        if (ie != cudaSuccess) {
+            G.clear();
+            return fail(TRIDS_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+        }
+        G.func = kp.func; G.grid = grid; G.block = 32 * warps; G.smem = L.total;
+        G.counter = A.counter;
+        G.args.assign(ab, ab + sizeof(SampleArgs));
+        ++G.instantiations;
+    } else if (G.counter != A.counter || G.args.size() != sizeof(SampleArgs) ||
+               std::memcmp(G.args.data(), ab, sizeof(SampleArgs)) != 0) {
+        if (G.counter != A.counter) CK(cudaGraphExecMemsetNodeSetParams(G.exec, G.reset, &mp));
+        CK(cudaGraphExecKernelNodeSetParams(G.exec, G.launch, &kp));
+        G.counter = A.counter;
+        G.args.assign(ab, ab + sizeof(SampleArgs));
+        ++G.updates;
     }
     if (!legacy) {
-        CK(cudaGraphLaunch(b->graph.exec, run));
+        CK(cudaGraphLaunch(G.exec, run));
+        ++G.launches;
         return TRIDS_OK;
     }
     CK(cudaEventRecord(b->ev_a, st));
     CK(cudaStreamWaitEvent(run, b->ev_a, 0));
-    CK(cudaGraphLaunch(b->graph.exec, run));
+    CK(cudaGraphLaunch(G.exec, run));
+    ++G.launches;
     CK(cudaEventRecord(b->ev_b, run));
     CK(cudaStreamWaitEvent(st, b->ev_b, 0));
+    return TRIDS_OK;
+}
+
+int trids_graph_stats(const trids_pocket* pk, int64_t* instantiations, int64_t* updates, int64_t* launches) {
+    g_err.clear();
+    if (!pk) return fail(TRIDS_EINVAL, "pocket is NULL");
+    GraphCache& G = const_cast<trids_pocket*>(pk)->graph;
+    std::lock_guard<std::mutex> lock(G.mu);
+    if (instantiations) *instantiations = G.instantiations;
+    if (updates) *updates = G.updates;
+    if (launches) *launches = G.launches;
     return TRIDS_OK;
 }
 

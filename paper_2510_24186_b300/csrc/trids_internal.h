@@ -143,8 +143,10 @@ struct DevPocket {
 
 struct LigHdr {
     int n_atoms, n_tor, atom_off, tor_off;
-    int ipre_off, ient_off, n_pairs, pad0;   // intra partner lists: per-atom block prefix at ipre_off
-                                             // (L + 1 ints), entries at ient_off (8 per block)
+    int ipre_off, ient_off, n_pairs;   // intra partner lists: per-atom block prefix at ipre_off
+                                       // (L + 1 ints), entries at ient_off (8 per block)
+    int sid;                           // random-stream id of the ligand (before lig_base is added):
+                                       // its batch index unless trids_set_stream_ids gave another
 };
 
 struct DevBatch {

@@ -34,9 +34,13 @@ def shard_lpt(costs, world: int) -> list:
     return [np.array(sorted(o), dtype=np.int64) for o in out]
 
 
-def ligand_cost(n_atoms, n_tor, n_pairs) -> np.ndarray:
-    """Relative sampling cost of ligands (atoms dominate through the pocket pairs)."""
-    return 60.0 * np.asarray(n_atoms) + 2.0 * np.asarray(n_pairs) + 20.0 * np.asarray(n_tor) + 10.0
+def ligand_cost(n_atoms, n_tor, n_pairs=None) -> np.ndarray:
+    """Relative sampling cost of ligands (atoms dominate through the pocket pairs).  Without
+    intra-pair counts, L (L - 1) / 2 stands in for them."""
+    n_atoms = np.asarray(n_atoms, dtype=np.float64)
+    if n_pairs is None:
+        n_pairs = n_atoms * (n_atoms - 1) / 2
+    return 60.0 * n_atoms + 2.0 * np.asarray(n_pairs) + 20.0 * np.asarray(n_tor) + 10.0
 
 
 def max_over_ranks(value: float, device=None) -> float:
@@ -48,6 +52,15 @@ def max_over_ranks(value: float, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def merge_topk(parts):
+    """Per-shard (global ligand ids, top-k pose indices, energies) -> one set in global ligand
+    order."""
+    ids = np.concatenate([np.asarray(p[0]) for p in parts])
+    order = np.argsort(ids, kind="stable")
+    return (ids[order], np.concatenate([np.asarray(p[1]) for p in parts])[order],
+            np.concatenate([np.asarray(p[2]) for p in parts])[order])
 
 
 def gather_topk(global_ids, idx, energies):
@@ -62,6 +75,28 @@ def gather_topk(global_ids, idx, energies):
         dist.all_gather_object(parts, item)
         if dist.get_rank() != 0:
             return None
-    ids = np.concatenate([p[0] for p in parts])
-    order = np.argsort(ids, kind="stable")
-    return ids[order], np.concatenate([p[1] for p in parts])[order], np.concatenate([p[2] for p in parts])[order]
+    return merge_topk(parts)
+
+
+def rank_world(rank=None, world=None):
+    """(rank, world size): the given values, else the process group's, else (0, 1)."""
+    if rank is not None and world is not None:
+        return int(rank), int(world)
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        return dist.get_rank(), dist.get_world_size()
+    return 0, 1
+
+
+def screen_shards(n_atoms, n_tor, run_shard, rank=None, world=None, gather=True):
+    """Screening of one ligand set split over ranks (one process per GPU): the ligands are
+    split by shard_lpt on ligand_cost; this rank runs run_shard(ids) on its own global ligand
+    ids (sorted) and gets (top-k pose indices [n, k], energies [n, k]) back; with gather, rank
+    0 receives every shard's results in global ligand order (other ranks get None), else each
+    rank returns its own (ids, idx, energies).  No collective touches the sampling itself."""
+    rank, world = rank_world(rank, world)
+    mine = shard_lpt(ligand_cost(n_atoms, n_tor), world)[rank]
+    idx, e = run_shard(mine)
+    if not gather:
+        return mine, np.asarray(idx), np.asarray(e)
+    return gather_topk(mine, idx, e)

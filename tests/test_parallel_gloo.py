@@ -34,20 +34,33 @@ def _run_shard(lig_ids, ligs, pk, seed, P, S):
     return np.array(tops), np.array(es)
 
 
+def _ligands():
+    rng = np.random.default_rng(3)
+    return [synth.gen_ligand(rng, int(rng.integers(6, 14)), int(rng.integers(0, 3))) for _ in range(7)]
+
+
 def _worker(rank, world, port, out_path):
+    """One rank of the sharded screening host logic (parallel.screen_shards, the logic
+    api.screen_sharded runs around its GPU calls), with the oracle standing in for the
+    rank's GPU sampling of its shard."""
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     w = synth.workload("single_ligand")
-    rng = np.random.default_rng(3)
-    ligs = [synth.gen_ligand(rng, int(rng.integers(6, 14)), int(rng.integers(0, 3))) for _ in range(7)]
-    costs = parallel.ligand_cost([len(l.type) for l in ligs], [l.n_tor for l in ligs], [0] * len(ligs))
-    mine = parallel.shard_lpt(costs, world)[rank]
-    tops, es = _run_shard(mine, ligs, w.pocket, 11, 6, 4)
+    ligs = _ligands()
+    seen = []
+
+    def run_shard(ids):
+        seen.append(np.asarray(ids))
+        return _run_shard(ids, ligs, w.pocket, 11, 6, 4)
+
+    got = parallel.screen_shards([len(l.type) for l in ligs], [l.n_tor for l in ligs], run_shard)
     t = parallel.max_over_ranks(float(rank + 1))
-    got = parallel.gather_topk(mine, tops, es)
+    mine = parallel.gather_topk(seen[0], np.zeros((len(seen[0]), 1)), np.zeros((len(seen[0]), 1)))
     if rank == 0:
-        np.savez(out_path, ids=got[0], idx=got[1], e=got[2], tmax=t)
+        np.savez(out_path, ids=got[0], idx=got[1], e=got[2], tmax=t, shard_ids=mine[0])
+    else:
+        assert got is None and mine is None
     dist.barrier()
     dist.destroy_process_group()
 
@@ -69,9 +82,9 @@ def test_two_rank_gloo_matches_single_process(tmp_path):
     mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
     r = np.load(out)
     assert r["tmax"] == 2.0
+    np.testing.assert_array_equal(r["shard_ids"], np.arange(7))   # every ligand on exactly one rank
     w = synth.workload("single_ligand")
-    rng = np.random.default_rng(3)
-    ligs = [synth.gen_ligand(rng, int(rng.integers(6, 14)), int(rng.integers(0, 3))) for _ in range(7)]
+    ligs = _ligands()
     tops, es = _run_shard(np.arange(7), ligs, w.pocket, 11, 6, 4)
     np.testing.assert_array_equal(r["ids"], np.arange(7))
     np.testing.assert_array_equal(r["idx"], tops)
