@@ -140,9 +140,55 @@ def _bond_direction(rng, nbr_dirs):
     return _unit(_rotate(d, _perp(d, rng), math.radians(rng.uniform(-5.0, 5.0))))
 
 
+def _units(v):
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def _rand_units(rng, n):
+    v = rng.normal(size=(n, 3))
+    nrm = np.linalg.norm(v, axis=1, keepdims=True)
+    return v / np.where(nrm > 1e-6, nrm, 1.0)
+
+
+def _perps(u, rng, n):
+    """n random unit vectors perpendicular to the unit vector(s) u ([3] or [n, 3])."""
+    w = _rand_units(rng, n)
+    return _units(w - u * np.sum(u * w, axis=-1, keepdims=True))
+
+
+def _bond_directions(rng, nbr_dirs, n):
+    """n candidate directions for a new bond, each drawn as _bond_direction draws one."""
+    k = len(nbr_dirs)
+    if k == 0:
+        return _rand_units(rng, n)
+    if k == 1:
+        u = np.asarray(nbr_dirs[0])
+        ang = TETRA + np.radians(rng.uniform(-5.0, 5.0, n))[:, None]
+        return _units(u * np.cos(ang) + _perps(u, rng, n) * np.sin(ang))
+    if k == 2:
+        u1, u2 = np.asarray(nbr_dirs[0]), np.asarray(nbr_dirs[1])
+        bis = _units(-u1 - u2)
+        nc = np.cross(u1, u2)
+        nn = np.linalg.norm(nc)
+        nv = _perps(bis, rng, n) if nn < 1e-6 else np.broadcast_to(nc / nn, (n, 3))
+        sgn = np.where(rng.random(n) < 0.5, 1.0, -1.0)[:, None]
+        half = 0.5 * TETRA
+        d = _units(bis * math.cos(half) + nv * sgn * math.sin(half))
+    else:
+        d = np.broadcast_to(_units(-(np.asarray(nbr_dirs[0]) + nbr_dirs[1] + nbr_dirs[2])), (n, 3))
+    # scatter by up to 5 degrees about a random perpendicular axis (Rodrigues)
+    ax = _perps(d, rng, n)
+    ang = np.radians(rng.uniform(-5.0, 5.0, n))[:, None]
+    c, s_ = np.cos(ang), np.sin(ang)
+    return _units(d * c + np.cross(ax, d) * s_ + ax * np.sum(ax * d, axis=1, keepdims=True) * (1.0 - c))
+
+
 def gen_ligand(rng: np.random.Generator, n_atoms: int, n_tor: int,
-               type_probs=UNIFORM_MIX, center=(0.0, 0.0, 0.0)) -> Ligand:
-    """Random bonded tree ligand (see module docstring for the recipe)."""
+               type_probs=UNIFORM_MIX, center=(0.0, 0.0, 0.0), vector_tries: bool = False) -> Ligand:
+    """Random bonded tree ligand (see module docstring for the recipe).  vector_tries draws
+    a parent's 100 candidate placements at once and keeps the first that clears the 2 A
+    test: the same distribution as trying them one by one, with the random stream
+    consumed in another order (several times faster; used for the 100,000-ligand set)."""
     assert n_atoms >= 1
     xyz = np.zeros((n_atoms, 3))
     pos_l = [(0.0, 0.0, 0.0)]
@@ -155,6 +201,15 @@ def gen_ligand(rng: np.random.Generator, n_atoms: int, n_tor: int,
             par = cand[rng.integers(len(cand))]
             pp = pos_l[par]
             dirs = [_unit(_lin(pos_l[n], 1.0, pp, -1.0)) for n in nbrs[par]]
+            if vector_tries:
+                pts = np.asarray(pp) + BOND * _bond_directions(rng, dirs, 100)
+                d2 = np.sum((pts[:, None, :] - xyz[None, :a, :]) ** 2, axis=2)
+                d2[:, par] = 1e9
+                ok = np.nonzero(d2.min(axis=1) >= 4.0)[0]
+                if len(ok):
+                    pos = tuple(pts[ok[0]].tolist())
+                    placed = True
+                continue
             for _ in range(100):
                 pos = _lin(pp, 1.0, _bond_direction(rng, dirs), BOND)
                 d2 = np.sum((xyz[:a] - np.asarray(pos)) ** 2, axis=1)
@@ -316,6 +371,36 @@ def _ligand_set(rng, n_lig, l_range, t_range, mix, center):
     return out
 
 
+def _indexed_chunk(args):
+    seed, lo, hi, l_range, t_range, mix, center = args
+    out = []
+    for i in range(lo, hi):
+        rng = np.random.default_rng([seed, i])
+        L = int(rng.integers(l_range[0], l_range[1] + 1))
+        T = int(rng.integers(t_range[0], t_range[1] + 1))
+        out.append(gen_ligand(rng, L, T, mix, center, vector_tries=True))
+    return out
+
+
+def _ligand_set_indexed(seed, n_lig, l_range, t_range, mix, center, workers=None, min_parallel=2000):
+    """Ligand i drawn from its own generator, seeded (seed, i): the set does not depend on
+    how it is split, so large sets are generated on worker processes (spawned, so that a
+    process that already uses CUDA is never forked)."""
+    import os
+    workers = workers or len(os.sched_getaffinity(0))
+    if n_lig < min_parallel or workers <= 1:
+        return _indexed_chunk((seed, 0, n_lig, l_range, t_range, mix, center))
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    step = -(-n_lig // (4 * workers))
+    jobs = [(seed, lo, min(n_lig, lo + step), l_range, t_range, mix, center) for lo in range(0, n_lig, step)]
+    out = []
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        for part in ex.map(_indexed_chunk, jobs):
+            out.extend(part)
+    return out
+
+
 # Named seeded workloads and their seeds.
 WORKLOAD_SEEDS = {
     "single_ligand": 1001,
@@ -332,7 +417,8 @@ def workload(name: str, n_lig: int | None = None) -> Workload:
     single_ligand:     1 ligand, L=24, T=4, M=300, P=64, S=30.
     batched_screening: 1,024 ligands, L~U{10..60}, T~U{0..15}, M=1,500, P=128, S=50, top-9.
     adjoint_check:     256 ligands, L~U{10..40}, T~U{0..10}, M=1,500, P=64 random poses.
-    screening_stream:  100,000 ligands, L~U{10..70}, T~U{0..20}, drug-like mix, M=2,000, P=64, S=40.
+    screening_stream:  100,000 ligands, L~U{10..70}, T~U{0..20}, drug-like mix, M=2,000, P=64, S=40;
+                       ligand i from its own generator seeded (1004, i), built on worker processes.
     blind_docking:     6,000 atoms around 3 cavities, 4,096 ligands, L~U{20..60}, T<=15, P=512, S=100.
     """
     if name not in WORKLOAD_SEEDS:
@@ -358,7 +444,7 @@ def workload(name: str, n_lig: int | None = None) -> Workload:
                         pk, ligs, c0, box, 64, 0, 8, 8.0, 9, seed)
     if name == "screening_stream":
         pk = gen_pocket(rng, 2000, c0, type_probs=DRUGLIKE_MIX)
-        ligs = _ligand_set(rng, n_lig or 100000, (10, 70), (0, 20), DRUGLIKE_MIX, c0)
+        ligs = _ligand_set_indexed(seed, n_lig or 100000, (10, 70), (0, 20), DRUGLIKE_MIX, c0)
         return Workload("screening stream: 100,000 ligands (L 10-70, T 0-20) x 64 poses x 40 steps, "
                         "2,000-atom pocket", pk, ligs, c0, box, 64, 40, 8, 8.0, 9, seed)
     if name == "blind_docking":
