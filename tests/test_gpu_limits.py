@@ -56,10 +56,10 @@ def test_max_pocket_score_parity(api, big):
             st.n += 1
             energy_ok(out["energy"][l, p], ev, st, f"lig {l} pose {p}")
             sl = grad_slack(ev)
-            block_ok(out["g_dof"][l, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"lig {l} pose {p} t")
-            block_ok(out["g_dof"][l, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"lig {l} pose {p} q")
-            block_ok(out["g_dof"][l, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st,
-                     f"lig {l} pose {p} theta")
+            block_ok(out["g_dof"][l, p, :3], ev.g_dof[:3], t_slack(ev), st, f"lig {l} pose {p} t", rnd=round_slack(ev, 0, 3))
+            block_ok(out["g_dof"][l, p, 3:7], ev.g_dof[3:7], sl, st, f"lig {l} pose {p} q", rnd=round_slack(ev, 3, 7))
+            block_ok(out["g_dof"][l, p, 7:7 + T], ev.g_dof[7:7 + T], sl, st, f"lig {l} pose {p} theta",
+                     rnd=round_slack(ev, 7, 7 + T))
     report(st, "max pocket score")
 
 

@@ -56,9 +56,9 @@ def test_map_score_parity(api, term_set):
         st.n += 1
         energy_ok(out["energy"][0, p], ev, st, f"pose {p}")
         sl = grad_slack(ev)
-        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"pose {p} t")
-        block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"pose {p} q")
-        block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"pose {p} th")
+        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], t_slack(ev), st, f"pose {p} t", rnd=round_slack(ev, 0, 3))
+        block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl, st, f"pose {p} q", rnd=round_slack(ev, 3, 7))
+        block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl, st, f"pose {p} th", rnd=round_slack(ev, 7, 7 + T))
     assert 0 < mapped < P * lg.n_atoms      # both forms occur
     report(st, f"map score term_set={term_set}")
 
@@ -149,8 +149,8 @@ def test_maps_with_residue_terms(api):
         st.n += 1
         energy_ok(out["energy"][0, p], ev, st, f"pose {p}")
         sl = grad_slack(ev)
-        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"pose {p} t")
-        block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"pose {p} q")
-        block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"pose {p} th")
+        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], t_slack(ev), st, f"pose {p} t", rnd=round_slack(ev, 0, 3))
+        block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl, st, f"pose {p} q", rnd=round_slack(ev, 3, 7))
+        block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl, st, f"pose {p} th", rnd=round_slack(ev, 7, 7 + T))
     assert mapped > 0 and res_pairs > 0
     report(st, "maps + residue E_MDN")

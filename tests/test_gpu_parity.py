@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_2510_24186_b300 import synth
 
-from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, t_slack, oracle_ligands, oracle_params,
+from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, t_slack, xyz_slack, oracle_ligands, oracle_params,
                          pocket_arrays, round_slack, score_params, state_err)
 
 pytestmark = pytest.mark.gpu
@@ -78,13 +78,13 @@ def test_score_grad_parity_single_ligand(api, term_set):
         energy_ok(out["energy"][0, p], ev, st, f"pose {p}")
         sl = grad_slack(ev)
         assert abs(out["e_inter"][0, p] - ev.e_inter) <= max(1e-3, 1e-5 * abs(ev.e_inter)) + ev.e_slack
-        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"pose {p} t")
-        block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"pose {p} q")
-        block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"pose {p} theta")
+        block_ok(out["g_dof"][0, p, :3], ev.g_dof[:3], t_slack(ev), st, f"pose {p} t", rnd=round_slack(ev, 0, 3))
+        block_ok(out["g_dof"][0, p, 3:7], ev.g_dof[3:7], sl, st, f"pose {p} q", rnd=round_slack(ev, 3, 7))
+        block_ok(out["g_dof"][0, p, 7:7 + T], ev.g_dof[7:7 + T], sl, st, f"pose {p} theta", rnd=round_slack(ev, 7, 7 + T))
         assert np.all(out["g_dof"][0, p, 7 + T:] == 0)
         gx = np.zeros((b.max_atoms, 3))
         gx[perm] = np.array(ev.g_x)[:lg.n_atoms]
-        block_ok(out["g_xyz"][0, p].ravel(), gx.ravel(), 40 * sl, st, f"pose {p} xyz")
+        block_ok(out["g_xyz"][0, p].ravel(), gx.ravel(), xyz_slack(ev), st, f"pose {p} xyz")
     report(st, f"score term_set={term_set}")
 
 
@@ -106,10 +106,10 @@ def test_score_grad_parity_batch_ragged(api, term_set):
             st.n += 1
             energy_ok(out["energy"][l, p], ev, st, f"lig {l} pose {p}")
             sl = grad_slack(ev)
-            block_ok(out["g_dof"][l, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"lig {l} pose {p} t")
-            block_ok(out["g_dof"][l, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"lig {l} pose {p} q")
-            block_ok(out["g_dof"][l, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st,
-                     f"lig {l} pose {p} theta")
+            block_ok(out["g_dof"][l, p, :3], ev.g_dof[:3], t_slack(ev), st, f"lig {l} pose {p} t", rnd=round_slack(ev, 0, 3))
+            block_ok(out["g_dof"][l, p, 3:7], ev.g_dof[3:7], sl, st, f"lig {l} pose {p} q", rnd=round_slack(ev, 3, 7))
+            block_ok(out["g_dof"][l, p, 7:7 + T], ev.g_dof[7:7 + T], sl, st, f"lig {l} pose {p} theta",
+                     rnd=round_slack(ev, 7, 7 + T))
     report(st, f"score batch term_set={term_set}")
 
 
@@ -143,8 +143,8 @@ def test_parameter_gradients_and_autograd(api, term_set):
             stt, ev = oracle.score(op, pxyz, ptype, ligs[l], dof[l, p, :7 + T])
             gw += eb[l, p] * np.array(ev.g_w)
             gr += eb[l, p] * np.array(ev.g_R)
-            sl = abs(eb[l, p]) * (grad_slack(ev) + round_slack(ev, 0, 7 + T))
-            block_ok(gd[l, p, :7 + T], eb[l, p] * np.array(ev.g_dof[:7 + T]), sl, st, f"lig {l} pose {p}")
+            block_ok(gd[l, p, :7 + T], eb[l, p] * np.array(ev.g_dof[:7 + T]), abs(eb[l, p]) * grad_slack(ev), st,
+                     f"lig {l} pose {p}", rnd=abs(eb[l, p]) * round_slack(ev, 0, 7 + T))
     block_ok(W.grad.numpy(), gw, 0.0, st, "dE/dw")
     block_ok(R.grad.numpy(), gr[:8], 0.0, st, "dE/dR")
     report(st, f"param grads term_set={term_set}")
@@ -362,9 +362,9 @@ def test_adjoint_check_full_size_score_sampled(api):
         st.n += 1
         energy_ok(Eh[l, p], ev, st, f"lig {l} pose {p}")
         sl = grad_slack(ev)
-        block_ok(gd[l, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"lig {l} pose {p} t")
-        block_ok(gd[l, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"lig {l} pose {p} q")
-        block_ok(gd[l, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"lig {l} pose {p} theta")
+        block_ok(gd[l, p, :3], ev.g_dof[:3], t_slack(ev), st, f"lig {l} pose {p} t", rnd=round_slack(ev, 0, 3))
+        block_ok(gd[l, p, 3:7], ev.g_dof[3:7], sl, st, f"lig {l} pose {p} q", rnd=round_slack(ev, 3, 7))
+        block_ok(gd[l, p, 7:7 + T], ev.g_dof[7:7 + T], sl, st, f"lig {l} pose {p} theta", rnd=round_slack(ev, 7, 7 + T))
     # parameter gradients over every pose: oracle sums over all 16,384 poses
     gw = np.zeros(5)
     gr = np.zeros(16)

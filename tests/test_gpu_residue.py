@@ -5,7 +5,7 @@ import pytest
 import oracle
 from paper_2510_24186_b300 import synth
 
-from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, t_slack, oracle_ligands, oracle_params,
+from parity_util import (report, Stats, block_ok, check_trace, energy_ok, grad_slack, t_slack, xyz_slack, oracle_ligands, oracle_params,
                          pocket_arrays, round_slack)
 
 pytestmark = pytest.mark.gpu
@@ -40,9 +40,9 @@ def res_setup(api, w, ligs, K=4, seed=21, cell=0.0):
 def _check_pose(st, out, l, p, ev, T, what):
     energy_ok(out["energy"][l, p], ev, st, what)
     sl = grad_slack(ev)
-    block_ok(out["g_dof"][l, p, :3], ev.g_dof[:3], t_slack(ev) + round_slack(ev, 0, 3), st, f"{what} t")
-    block_ok(out["g_dof"][l, p, 3:7], ev.g_dof[3:7], sl + round_slack(ev, 3, 7), st, f"{what} q")
-    block_ok(out["g_dof"][l, p, 7:7 + T], ev.g_dof[7:7 + T], sl + round_slack(ev, 7, 7 + T), st, f"{what} theta")
+    block_ok(out["g_dof"][l, p, :3], ev.g_dof[:3], t_slack(ev), st, f"{what} t", rnd=round_slack(ev, 0, 3))
+    block_ok(out["g_dof"][l, p, 3:7], ev.g_dof[3:7], sl, st, f"{what} q", rnd=round_slack(ev, 3, 7))
+    block_ok(out["g_dof"][l, p, 7:7 + T], ev.g_dof[7:7 + T], sl, st, f"{what} theta", rnd=round_slack(ev, 7, 7 + T))
 
 
 def test_residue_score_parity_single_ligand(api):
@@ -69,7 +69,7 @@ def test_residue_score_parity_single_ligand(api):
         _check_pose(st, out, 0, p, ev, lg.n_tor, f"pose {p}")
         gx = np.zeros((b.max_atoms, 3))
         gx[perm] = np.array(ev.g_x)[:lg.n_atoms]
-        block_ok(out["g_xyz"][0, p].ravel(), gx.ravel(), 40 * grad_slack(ev), st, f"pose {p} xyz")
+        block_ok(out["g_xyz"][0, p].ravel(), gx.ravel(), xyz_slack(ev), st, f"pose {p} xyz")
     assert n_res_pairs > 100 * P
     report(st, "residue score single ligand")
 
