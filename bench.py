@@ -37,10 +37,30 @@ from paper_2510_24186_b300 import synth  # noqa: E402
 
 METRIC = "poses×steps/sec (score + DOF gradient) at 1 B300 vs plain per-ligand launch"
 UNIT = "pose-steps/s"
-F_PAIR_VINA = 53            # FP32 FLOPs per in-cutoff pair of the Vina-form terms (FMA = 2)
-MUFU_PAIR_VINA = 3          # rsqrt + 2 exp per in-cutoff pair
-F_PAIR_TRIDS = 36           # FP32 FLOPs per in-cutoff atom pair of the TRIDS terms at the E_long cost
+# Algorithmic FP32 FLOPs (FMA = 2; rsqrt, exp and log counted apart as transcendentals),
+# counted from the evaluations' expressions, per unit of work the counting run reports:
+F_PAIR_VINA = 53            # an in-cutoff pair of the Vina-form terms (5 terms, + 3 transcendentals)
+F_PAIR_TRIDS = 27           # an in-cutoff pair of the TRIDS atom-pair terms: distance, E_long, force
+F_CLASH = 5                 # + a pair inside the E_clash range
+F_HBOND = 8                 # + a donor-acceptor pair inside the E_Hbond range
+F_MDN_PAIR = 19             # an atom-pair E_MDN pair inside 5 A (term set 1): distance, force ...
+F_MDN_KERNEL = 8            # ... + per Gaussian kernel
+F_RES_SCAN = 8              # a residue atom scanned for the residue minimum (term set 2)
+F_RES_PAIR = 13             # a (ligand atom, residue) pair inside 5 A: distance, force, + 8 per kernel
 FP32_LANES_PER_SM = 128
+
+
+def pair_flops(term_set, pairs, work, K):
+    """Algorithmic FLOPs of the pairwise-energy phase of one sampling pass from its counts
+    (work: the counting run's TRIDS_WORK_* counts)."""
+    if term_set == 0:
+        return pairs * F_PAIR_VINA
+    f = pairs * F_PAIR_TRIDS + work["clash"] * F_CLASH + work["hbond"] * F_HBOND
+    if term_set == 1:
+        f += work["mdn_pairs"] * (F_MDN_PAIR + F_MDN_KERNEL * K)
+    else:
+        f += work["res_scan"] * F_RES_SCAN + work["res_pairs"] * (F_RES_PAIR + F_MDN_KERNEL * K)
+    return f
 TERMS = {"vina5": 0, "trids": 1, "trids_res": 2}
 GMM_K = 4                   # Gaussian kernels per type pair (term set 1) / per atom-residue pair (2)
 
@@ -344,7 +364,7 @@ def main():
     # energies must come out bit-identical to the timed runs)
     # and the SM cycles the warps spent in each phase of an evaluation (the same counting
     # variant times its phases; their shares apportion the timed kernel's duration)
-    pairs = []
+    pairs, works = [], []
     cycles = np.zeros(len(api.PHASES))
     identical = True
     with torch.cuda.stream(stream):
@@ -352,6 +372,7 @@ def main():
             o = one_step(seeds[k], count_pairs=True)
             stream.synchronize()
             pairs.append(int(o["pair_count"].item()))
+            works.append(dict(zip(api.WORK, o["work_count"].cpu().numpy().tolist())))
             cycles += o["phase_cycles"].cpu().numpy().astype(np.float64)
             identical &= bool(torch.equal(energy, energies[k]))
     phase_share = {n: float(c / cycles.sum()) for n, c in zip(api.PHASES, cycles)}
@@ -417,10 +438,10 @@ def main():
     mhz, mhz_src = sm_max_mhz()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     peak = n_sm * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-    f_pair = F_PAIR_VINA if sp.term_set == 0 else F_PAIR_TRIDS
-    flops = [p * f_pair for p in pairs]
+    flops = [pair_flops(sp.term_set, p, wk, GMM_K) for p, wk in zip(pairs, works)]
     achieved = sum(flops) / (sum(t_sample) / 1000.0) / 1e12
-    pair_ms = statistics.mean(t_sample) * phase_share["pairs"]
+    # the pairwise-energy phase: the pair loop plus, for the TRIDS terms, the E_MDN passes
+    pair_ms = statistics.mean(t_sample) * (phase_share["pairs"] + phase_share["passes"])
     achieved_pair = sum(flops) / len(flops) / (pair_ms / 1000.0) / 1e12
     clocks = clk.summary()
     traffic = None
@@ -448,10 +469,14 @@ def main():
                               "rank0_ligands": len(mine), "topk_gathered_ligands": len(gathered[0])}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "note": f"in-cutoff atom pairs x {f_pair} FP32 FLOP / persistent-sampler time; peak = "
-                             f"{n_sm} SM x 128 lanes x 2 x {mhz:.0f} MHz ({mhz_src})"
-                             + ("" if sp.term_set == 0 else "; extra Gaussian kernels and the residue phase are "
-                                "not counted (a lower bound)")
+                     "note": ("in-cutoff atom pairs x 53 FP32 FLOP" if sp.term_set == 0 else
+                              f"counted work x FLOPs per unit: pairs x {F_PAIR_TRIDS} + E_clash pairs x {F_CLASH} + "
+                              f"E_Hbond pairs x {F_HBOND} + "
+                              + (f"E_MDN pairs x ({F_MDN_PAIR} + {F_MDN_KERNEL} K)" if sp.term_set == 1 else
+                                 f"residue atoms scanned x {F_RES_SCAN} + residue pairs x ({F_RES_PAIR} + "
+                                 f"{F_MDN_KERNEL} K)") + f", K = {GMM_K}")
+                             + f" / persistent-sampler time; peak = {n_sm} SM x 128 lanes x 2 x {mhz:.0f} MHz "
+                               f"({mhz_src})"
                              + ("" if maps is None else "; with maps only the atoms outside the map grid sum "
                                 "pairs, so this counts the direct pairs alone")},
         "kernel": {"sample_ms": statistics.mean(t_sample), "phase_share": phase_share,
@@ -461,6 +486,8 @@ def main():
             "topk_ms": statistics.mean(
             [t_step[k] - t_sample[k] for k in range(args.steps)]), "pairs_per_step": statistics.mean(pairs),
             "pairs_per_pose_step": statistics.mean(pairs) / units, "count_run_bit_identical": identical,
+            "work_per_pose_step": {k: statistics.mean(wk[k] for wk in works) / units for k in api.WORK},
+            "flops_per_pose_step": statistics.mean(flops) / units,
             "status": rc},
         "per_ligand": None if pl_ms is None else {
             "value": units / (pl_ms / 1000.0), "ms_per_step": pl_ms, "launches_per_step": n_lig * S,

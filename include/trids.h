@@ -81,6 +81,15 @@ extern "C" {
 #define TRIDS_PHASE_OTHER 5     /* taking a pose, initial or resumed state, storing it */
 #define TRIDS_PHASES 6
 
+/* Work counted by trids_sample_cfg.work_count (counting runs only), beyond the in-cutoff
+ * pairs of pair_count; the algorithmic FLOPs of an evaluation follow from them. */
+#define TRIDS_WORK_CLASH 0      /* in-cutoff pairs inside the E_clash range (TRIDS terms) */
+#define TRIDS_WORK_HBOND 1      /* donor-acceptor pairs inside the E_Hbond range (TRIDS terms) */
+#define TRIDS_WORK_MDN_PAIRS 2  /* atom-pair E_MDN pairs inside 5 A (term set 1) */
+#define TRIDS_WORK_RES_SCAN 3   /* residue atoms scanned for the residue minima (term set 2) */
+#define TRIDS_WORK_RES_PAIRS 4  /* (ligand atom, residue) pairs inside 5 A (term set 2) */
+#define TRIDS_WORK_COUNTS 5
+
 #define TRIDS_MODE_PERSISTENT 0 /* one persistent fused launch (optionally a CUDA graph) */
 #define TRIDS_MODE_PER_LIGAND 1 /* plain form: one launch per (ligand, step) */
 
@@ -175,6 +184,8 @@ typedef struct trids_sample_cfg {
                                        * selects the counting form of the sampler, which follows the
                                        * same trajectories; the sums give each phase's share of the
                                        * warps' time */
+    unsigned long long* work_count;   /* nullable device [TRIDS_WORK_COUNTS]: adds the work counts
+                                       * TRIDS_WORK_* (selects the counting form, like pair_count) */
 } trids_sample_cfg;
 
 /* Message of the calling thread's last failure ("" if none). */
@@ -367,8 +378,8 @@ int trids_score_grad(const trids_pocket* pk, const trids_batch* b, int32_t poses
  *   bytes per item.  Larger requests fail with TRIDS_EINVAL and a message giving the
  *   bytes needed; split the batch or use trids_score_grad.
  *   The first call on a device looks up the array's device address (set-up done once per
- *   device, with that device current); make that first call before any stream capture
- *   begins.  Every call reuses the same
+ *   device, with that device current, and again after the device's context has been
+ *   reset); make that first call before any stream capture begins.  Every call reuses the same
  *   array (it keeps the previous call's contents; each call resets what must start at
  *   zero), so calls that can overlap on the GPU -- on two streams, or from two host
  *   threads -- race with each other and must be serialised by the caller.

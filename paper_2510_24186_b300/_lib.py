@@ -12,6 +12,7 @@ TERMS_VINA5, TERMS_TRIDS, TERMS_TRIDS_RES = 0, 1, 2
 MAX_MDN_K, MAX_RESIDUES = 16, 8191
 MODE_PERSISTENT, MODE_PER_LIGAND = 0, 1
 PHASES = ("fk", "pairs", "passes", "adjoint", "update", "other")
+WORK = ("clash", "hbond", "mdn_pairs", "res_scan", "res_pairs")
 
 EXPORTS = ("trids_last_error", "trids_version", "trids_make_pocket", "trids_set_params", "trids_set_boxes",
            "trids_free_pocket", "trids_set_residues", "trids_build_maps", "trids_maps_info",
@@ -40,7 +41,8 @@ class SampleCfg(C.Structure):
                 ("mode", C.c_int32), ("warps_per_block", C.c_int32), ("use_graph", C.c_int32),
                 ("trace", C.c_void_p), ("trace_slot", C.c_void_p), ("n_trace", C.c_int32),
                 ("pair_count", C.c_void_p), ("optimizer", C.c_int32), ("weight_decay", C.c_float),
-                ("momentum", C.c_float), ("alpha", C.c_float), ("phase_cycles", C.c_void_p)]
+                ("momentum", C.c_float), ("alpha", C.c_float), ("phase_cycles", C.c_void_p),
+                ("work_count", C.c_void_p)]
 
 
 OPTIMIZERS = {"adam": 0, "adamw": 1, "rmsprop": 2, "adagrad": 3, "sgd": 4}

@@ -256,6 +256,7 @@ def score_grad(pocket: Pocket, batch: Batch, dof: torch.Tensor, grad: bool = Tru
 
 
 PHASES = _lib.PHASES
+WORK = _lib.WORK
 
 
 def sample(pocket: Pocket, batch: Batch, poses: int, steps: int, mc_loops: int = 8, lr: float = 0.1,
@@ -269,8 +270,9 @@ def sample(pocket: Pocket, batch: Batch, poses: int, steps: int, mc_loops: int =
     """Monte-Carlo + gradient sampling of every ligand's poses (trids_sample).  optimizer:
     adam (the paper's), adamw, rmsprop, adagrad or sgd; eps is passed as given (torch's
     defaults are 1e-8, except Adagrad's 1e-10).  count_pairs runs the counting form of the
-    sampler (same trajectories): out["pair_count"] gets the in-cutoff pairs evaluated and
-    out["phase_cycles"] the warps' SM clock cycles per phase (names in PHASES)."""
+    sampler (same trajectories): out["pair_count"] gets the in-cutoff pairs evaluated,
+    out["phase_cycles"] the warps' SM clock cycles per phase (names in PHASES) and
+    out["work_count"] the other work counts (names in WORK)."""
     _require_cuda()
     dev = torch.device("cuda", torch.cuda.current_device())
     n_lig, D = batch.n_lig, batch.dof_stride
@@ -307,6 +309,9 @@ def sample(pocket: Pocket, batch: Batch, poses: int, steps: int, mc_loops: int =
         cyc = torch.zeros(len(_lib.PHASES), dtype=torch.int64, device=dev)
         cfg.phase_cycles = cyc.data_ptr()
         out["phase_cycles"] = cyc
+        wk = torch.zeros(len(_lib.WORK), dtype=torch.int64, device=dev)
+        cfg.work_count = wk.data_ptr()
+        out["work_count"] = wk
     check(_lib.lib().trids_sample(pocket.handle, batch.handle, C.byref(cfg), _ptr(dof), _ptr(state),
                                   _ptr(energy), _stream(stream)))
     return out

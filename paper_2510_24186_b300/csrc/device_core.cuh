@@ -132,9 +132,10 @@ constexpr size_t kClockBytes = 8 * (TRIDS_PHASES + 1);   // phase clock of the c
 // per-warp region: [core][rigid pose state][torsion state, 32 lanes][phase clock][per-lane
 // dE/dR (parameter-gradient kernels)]
 __host__ __device__ inline size_t pose_state_off(int Lm, int Tm) { return align_up(pose_warp_core_bytes(Lm, Tm), 16); }
-__host__ __device__ inline size_t pose_clk_off(int Lm, int Tm) {
+__host__ __device__ inline size_t pose_hdr_off(int Lm, int Tm) {
     return align_up(pose_state_off(Lm, Tm) + kRigidStateBytes + 32 * kTorStateBytes, 16);
 }
+__host__ __device__ inline size_t pose_clk_off(int Lm, int Tm) { return pose_hdr_off(Lm, Tm) + sizeof(LigHdr); }
 __host__ __device__ inline size_t pose_grs_off(int Lm, int Tm) {
     return align_up(pose_clk_off(Lm, Tm) + kClockBytes, 16);
 }
@@ -223,6 +224,7 @@ __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t par
 //   tor TorState[32]    lane k's torsion angle, moments and saved angle
 //                       (kept in shared memory, the state holds no registers across the pair
 //                       loop: the sampler fits 96 registers per thread, 20 warps per SM)
+//   hdr LigHdr          the pose's ligand header (sampler kernels)
 //   clk u64[7]          per-phase cycle sums and the last lap's time (counting sampler)
 //   grs float[kNT][32]  per-lane dE/dR_a (parameter-gradient kernels only)
 struct RigidState;
@@ -241,6 +243,7 @@ struct PW {
     int* pre;
     float* grs;
     unsigned long long* clk;   // phase clock (counting sampler)
+    LigHdr* hdr;               // the pose's ligand header (sampler kernels)
     int lane;
 };
 
@@ -259,6 +262,7 @@ __device__ __forceinline__ PW make_pw(unsigned char* smem, size_t warp_off, size
     W.tor = reinterpret_cast<TorState*>(base + pose_state_off(Lm, Tm) + kRigidStateBytes);
     W.grs = reinterpret_cast<float*>(base + pose_grs_off(Lm, Tm));
     W.clk = reinterpret_cast<unsigned long long*>(base + pose_clk_off(Lm, Tm));
+    W.hdr = reinterpret_cast<LigHdr*>(base + pose_hdr_off(Lm, Tm));
     W.lane = threadIdx.x & 31;
     return W;
 }
@@ -316,6 +320,14 @@ __device__ __forceinline__ float vina_eval(float r2, float rsum, float hyd, floa
 struct VinaX2 {
     float2 w0, w1, w2, n0, n2, c1, c2, half, m15, m1, p15, m07, k07, tiny;
     float w3, w4;
+};
+
+// Work counts of the counting sampler, per lane: in-cutoff pairs and, for the TRIDS terms,
+// the pairs inside the E_clash and E_Hbond ranges (all three doubled: an intra pair is seen
+// from both of its atoms), atom-pair E_MDN pairs inside 5 A, residue atoms scanned for the
+// residue minima and (atom, residue) pairs inside 5 A.
+struct WorkCount {
+    uint32_t pairs = 0, clash = 0, hb = 0, mdn = 0, scan = 0, res = 0;
 };
 
 // The ligand atom's flag-dependent piece of the Vina-form pair.  A type that is
@@ -456,7 +468,7 @@ template <bool COUNT>
 __device__ __forceinline__ void trids_x2(uint32_t wd, const float4* __restrict__ src, float2 nxy, float2 nzr,
                                          float cut2, const float w[5], uint32_t mb, const float4* __restrict__ gmm,
                                          const uint8_t* __restrict__ ptype, int K, float2& eb, float& ax, float& ay,
-                                         float& az, uint32_t& cnt, uint32_t cw) {
+                                         float& az, WorkCount& wc, uint32_t cw) {
     constexpr float kL2e = 1.4426950408889634f, kLn2 = 0.6931471805599453f;
     const uint32_t ja = wd & 0x1fffu, jb = (wd >> 16) & 0x1fffu;
     const float4 a = src[ja], c = src[jb];
@@ -519,7 +531,12 @@ __device__ __forceinline__ void trids_x2(uint32_t wd, const float4* __restrict__
     axy = __ffma2_rn(make_float2(f.x, f.x), pa, axy); az = fmaf(f.x, qa.x, az);
     axy = __ffma2_rn(make_float2(f.y, f.y), pc, axy); az = fmaf(f.y, qc.x, az);
     ax = axy.x; ay = axy.y;
-    if (COUNT) cnt += ((r2.x < cut2) + (r2.y < cut2)) * cw;
+    if (COUNT) {
+        const bool ia = r2.x < cut2, ic = r2.y < cut2;
+        wc.pairs += (ia + ic) * cw;
+        wc.clash += ((ia && mcl.x != 0.f) + (ic && mcl.y != 0.f)) * cw;
+        wc.hb += ((ia && mh.x != 0.f) + (ic && mh.y != 0.f)) * cw;
+    }
 }
 
 // Candidate-grid cell range (entries [beg, end) of pk.cand) of a point; empty outside

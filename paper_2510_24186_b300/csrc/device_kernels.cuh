@@ -12,7 +12,8 @@ struct RigidState {
     float t[3], q[4], m[6], v[6], st[3], sq[4];
     float ecur, esaved;
     int status;
-    float pad[3];
+    int sid;          // the ligand's random-stream id (lig_base + stream id)
+    float pad[2];
 };
 struct TorState {
     float th, mth, vth, sth;
@@ -29,12 +30,13 @@ struct PoseState {
     float& ecur;
     float& esaved;
     int& status;
+    int& sid;
     float& th;
     float& mth;
     float& vth;
     float& sth;
     __device__ PoseState(RigidState& r, TorState& k)
-        : t(r.t), q(r.q), m(r.m), v(r.v), st(r.st), sq(r.sq), ecur(r.ecur), esaved(r.esaved), status(r.status),
+        : t(r.t), q(r.q), m(r.m), v(r.v), st(r.st), sq(r.sq), ecur(r.ecur), esaved(r.esaved), status(r.status), sid(r.sid),
           th(k.th), mth(k.mth), vth(k.vth), sth(k.sth) {}
 };
 
@@ -55,6 +57,7 @@ struct SampleArgs {
     int n_trace;
     unsigned long long* pair_count;
     unsigned long long* phase_cycles;
+    unsigned long long* work_count;
     const int* lig_order;      // ligands by decreasing cost; item it = (lig_order[it / P], it % P)
     int n_items;
     unsigned int* counter;
@@ -85,6 +88,7 @@ __device__ __forceinline__ float* fld(const SampleArgs& A, int l, int f, int p) 
 
 __device__ void init_pose(const SampleArgs& A, const LigHdr& h, int lane, int l, int p, PoseState& st) {
     const uint32_t lig = (uint32_t)(A.lig_base + h.sid);
+    st.sid = (int)lig;
     const uint4 r0 = rand_block(A.seed, lig, (uint32_t)p, 0u, 0u, 0u);
     const uint4 r1 = rand_block(A.seed, lig, (uint32_t)p, 0u, 0u, 1u);
     const float u[6] = {u01(r0.x), u01(r0.y), u01(r0.z), u01(r0.w), u01(r1.x), u01(r1.y)};
@@ -119,6 +123,7 @@ __device__ void load_pose(const SampleArgs& A, const LigHdr& h, int lane, int l,
     for (int d = 0; d < 6; ++d) { st.m[d] = *fld(A, l, kFieldM + d, p); st.v[d] = *fld(A, l, kFieldV + d, p); }
     for (int d = 0; d < 3; ++d) st.st[d] = *fld(A, l, kFieldSaved + d, p);
     for (int d = 0; d < 4; ++d) st.sq[d] = *fld(A, l, kFieldSaved + 3 + d, p);
+    st.sid = A.lig_base + h.sid;
     st.ecur = *fld(A, l, kFieldEcur, p);
     st.esaved = *fld(A, l, kFieldEsaved, p);
     st.status = __float_as_int(*fld(A, l, kFieldStatus, p));
@@ -201,13 +206,13 @@ __device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float p
 // warp except the per-torsion lanes.
 template <int TS, bool COUNT, bool GEN>
 __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h, const PW& W, int l, int p, int s,
-                            const Sched& sc, PoseState& st, uint32_t& npairs, PhaseClock& pc) {
+                            const Sched& sc, PoseState& st, WorkCount& wc, PhaseClock& pc) {
     __syncwarp();               // the rigid state is one shared copy written by every lane
     if (st.status & 1) return;  // frozen after a non-finite energy
     const int T = h.n_tor, lane = W.lane;
     const int bx = A.pk.n_boxes > 1 ? p % A.pk.n_boxes : 0;   // the pose's docking box
     const bool own = lane < T;
-    const uint32_t lig = (uint32_t)(A.lig_base + h.sid);
+    const uint32_t lig = (uint32_t)st.sid;
     if (sc.j == 0) {
         if (sc.loop > 0) {
             // save the state, then resample one of the 6+T variables in its range
@@ -241,7 +246,7 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
     if (COUNT) pc.lap(TRIDS_PHASE_FK);
     ParamAcc acc;
     float e_inter;
-    const float E = score_warp<TS, false, COUNT, GEN>(A.B, A.pk, S, h, W, 1.f, acc, &e_inter, npairs, &pc);
+    const float E = score_warp<TS, false, COUNT, GEN>(A.B, A.pk, S, h, W, 1.f, acc, &e_inter, wc, &pc);
     float gt[3], tau[3];
     const float gth = adjoint_warp(A.B, h, W, st.t, gt, tau);
     if (COUNT) pc.lap(TRIDS_PHASE_ADJOINT);
@@ -302,13 +307,24 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
     }
 }
 
-// Pair counts are kept doubled per lane (an intra pair is seen from both of its atoms,
-// possibly by different lanes); the warp total is halved here.
-__device__ __forceinline__ void flush_count(unsigned long long* cnt, uint32_t n) {
+// Warp totals of the lanes' work counts.  Pair counts are kept doubled per lane (an intra
+// pair is seen from both of its atoms, possibly by different lanes) and halved here.
+__device__ __forceinline__ unsigned long long warp_total(uint32_t n) {
     unsigned long long v = n;
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if ((threadIdx.x & 31) == 0 && v && cnt) atomicAdd(cnt, v >> 1);
+    return v;
+}
+
+__device__ __forceinline__ void flush_count(unsigned long long* cnt, unsigned long long* work, const WorkCount& wc) {
+    const unsigned long long v[TRIDS_WORK_COUNTS + 1] = {warp_total(wc.pairs) >> 1, warp_total(wc.clash) >> 1,
+                                                        warp_total(wc.hb) >> 1, warp_total(wc.mdn),
+                                                        warp_total(wc.scan), warp_total(wc.res)};
+    if ((threadIdx.x & 31) != 0) return;
+    if (cnt && v[0]) atomicAdd(cnt, v[0]);
+    if (work)
+        for (int k = 0; k < TRIDS_WORK_COUNTS; ++k)
+            if (v[k + 1]) atomicAdd(work + k, v[k + 1]);
 }
 
 // Persistent fused sampler: each warp pops poses from a global counter (ligands in
@@ -320,7 +336,7 @@ __global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
     Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
            reinterpret_cast<const uint8_t*>(smem + A.ptype_off)};
     const PW W = make_pw(smem, A.warp_off, A.warp_bytes, A.B.max_atoms, A.B.max_tor);
-    uint32_t npairs = 0;
+    WorkCount wc;
     PhaseClock pc(W);
     if (COUNT) pc.start();
     for (;;) {
@@ -330,7 +346,9 @@ __global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
         if (it >= A.n_items) break;
         const int l = A.lig_order[it / A.P];
         const int p = it % A.P;
-        const LigHdr h = A.B.lig[l];
+        if (W.lane == 0) *W.hdr = A.B.lig[l];
+        __syncwarp();
+        const LigHdr& h = *W.hdr;              // in shared memory, like the pose state
         PoseState st(*W.rig, W.tor[W.lane]);   // in shared memory: no registers across the pair loop
         if (A.step_begin == 0) init_pose(A, h, W.lane, l, p, st);
         else load_pose(A, h, W.lane, l, p, st);
@@ -338,7 +356,7 @@ __global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
         if (COUNT) pc.lap(TRIDS_PHASE_OTHER);
         Sched sc = schedule(A.S, A.Lmc, A.step_begin);
         for (int s = A.step_begin; s < A.step_end; ++s) {
-            sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, sc, st, npairs, pc);
+            sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, sc, st, wc, pc);
             if (COUNT) pc.lap(TRIDS_PHASE_UPDATE);
             if (++sc.j == sc.n) {   // next Monte-Carlo loop: the schedule of evaluation s + 1
                 ++sc.loop;
@@ -352,7 +370,7 @@ __global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
         if (COUNT) pc.lap(TRIDS_PHASE_OTHER);
     }
     if (COUNT) {
-        flush_count(A.pair_count, npairs);
+        flush_count(A.pair_count, A.work_count, wc);
         pc.flush(A.phase_cycles);
     }
 }
@@ -369,7 +387,7 @@ __global__ void __launch_bounds__(640, 1) k_sample_step(SampleArgs A, int l, int
     const int p = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     if (p >= A.P) return;
     const LigHdr h = A.B.lig[l];
-    uint32_t npairs = 0;
+    WorkCount wc;
     PhaseClock pc(W);
     if (COUNT) pc.start();
     PoseState st(*W.rig, W.tor[W.lane]);
@@ -377,13 +395,13 @@ __global__ void __launch_bounds__(640, 1) k_sample_step(SampleArgs A, int l, int
     else load_pose(A, h, W.lane, l, p, st);
     __syncwarp();
     if (COUNT) pc.lap(TRIDS_PHASE_OTHER);
-    sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, schedule(A.S, A.Lmc, s), st, npairs, pc);
+    sample_step<TS, COUNT, GEN>(A, S, h, W, l, p, s, schedule(A.S, A.Lmc, s), st, wc, pc);
     if (COUNT) pc.lap(TRIDS_PHASE_UPDATE);
     __syncwarp();
     store_pose(A, h, W.lane, l, p, st);
     if (COUNT) {
         pc.lap(TRIDS_PHASE_OTHER);
-        flush_count(A.pair_count, npairs);
+        flush_count(A.pair_count, A.work_count, wc);
         pc.flush(A.phase_cycles);
     }
 }
@@ -439,8 +457,8 @@ __global__ void __launch_bounds__(512, 1) k_score(ScoreArgs A) {
             const float ebar = A.e_bar ? A.e_bar[gp] : 1.f;
             fk_warp(A.B, h, W, t, q, th, S.P->radius);
             float e_inter;
-            uint32_t np = 0;
-            const float E = score_warp<TS, PARAMS, false, !PARAMS>(A.B, A.pk, S, h, W, ebar, acc, &e_inter, np);
+            WorkCount wc;
+            const float E = score_warp<TS, PARAMS, false, !PARAMS>(A.B, A.pk, S, h, W, ebar, acc, &e_inter, wc);
             if (lane == 0) {
                 A.energy[gp] = E;
                 if (A.e_inter) A.e_inter[gp] = e_inter;

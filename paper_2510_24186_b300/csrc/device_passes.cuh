@@ -87,7 +87,7 @@ __device__ __forceinline__ void seg_combine(const PW& W, int L, int N) {
 // returns the lane's ligand-pocket energy and, in *e_in2, twice its intra energy.
 template <int TS, bool PARAMS, bool COUNT, bool MAPS>
 __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
-                           const float w[5], float ebar, ParamAcc& acc, uint32_t& npairs, float* e_in2) {
+                           const float w[5], float ebar, ParamAcc& acc, WorkCount& wc, float* e_in2) {
     const DevParams& P = *S.P;
     const float cut2 = P.cut2;
     const VinaX2 K = make_vina_x2(w);
@@ -134,7 +134,10 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             return loc < cbk ? reinterpret_cast<const uint4*>(cand + csb + 8u * (uint32_t)loc)
                              : reinterpret_cast<const uint4*>(ient + 8 * (ipb + loc - cbk));
         };
-        uint4 v = __ldg(block_ptr(lo));
+        const uint4* pb = block_ptr(lo);          // address of the block held in v
+        uint4 v = __ldg(pb);
+        int icut = first + cbk;                   // the atom's first intra block
+        const uint4* ib = reinterpret_cast<const uint4*>(ient + 8 * ipb);
         for (int blk = lo; blk < hi; ++blk) {
             if (blk == nxt) {                      // move to the atom owning block blk
                 W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
@@ -153,11 +156,17 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                 nxy = make_float2(-xa.x, -xa.y);
                 nzr = make_float2(-xa.z, -ri);
                 F = make_flag_term(fi, P.w[3], P.w[4]);
-                v = __ldg(block_ptr(blk));
+                icut = first + cbk;
+                ib = reinterpret_cast<const uint4*>(ient + 8 * ipb);
+                pb = block_ptr(blk);
+                v = __ldg(pb);
             }
             const uint4 vc = v;
-            const bool intra = blk - first >= cbk;
-            if (blk + 1 < hi && blk + 1 < nxt) v = __ldg(block_ptr(blk + 1));
+            const bool intra = blk >= icut;
+            if (blk + 1 < hi && blk + 1 < nxt) {   // the atom's lists are contiguous blocks
+                pb = blk + 1 == icut ? ib : pb + 1;
+                v = __ldg(pb);
+            }
             const float4* __restrict__ src = intra ? W.xs : S.pocket;
             // pair-flag selectors: hydrophobic needs both bit0; donor-acceptor needs
             // (donor_i & acceptor_j) | (acceptor_i & donor_j)
@@ -175,14 +184,14 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                 if constexpr (TS == TRIDS_TERMS_VINA5 && !PARAMS) {
 #pragma unroll
                     for (int u = 0; u < 2; ++u)
-                        vina_x2<COUNT, !MAPS>(wv[u], src, nxy, nzr, cut2, K, F, eb2, ax, ay, az, npairs,
+                        vina_x2<COUNT, !MAPS>(wv[u], src, nxy, nzr, cut2, K, F, eb2, ax, ay, az, wc.pairs,
                                               intra ? 1u : 2u);   // doubled: intra pairs come twice
                 } else if constexpr (!PARAMS) {
                     const float4* gm = nullptr;   // term set 1: the atom-pair E_MDN runs in gmm_warp
 #pragma unroll
                     for (int u = 0; u < 2; ++u)
                         trids_x2<COUNT>(wv[u], src, nxy, nzr, cut2, w, F.mb, gm, S.ptype, P.gmm_k, eb2, ax, ay, az,
-                                        npairs, intra ? 1u : 2u);
+                                        wc, intra ? 1u : 2u);
                 } else {
 #pragma unroll
                     for (int s = 0; s < 4; ++s) {
@@ -225,7 +234,7 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                                 if (!intra) W.grs[tj * 32 + lane] += ebar * dRs;
                             }
                         }
-                        if (COUNT) npairs += in ? (intra ? 1u : 2u) : 0u;   // doubled: intra pairs come twice
+                        if (COUNT) wc.pairs += in ? (intra ? 1u : 2u) : 0u;   // doubled: intra pairs come twice
                     }
                 }
             }
@@ -287,9 +296,9 @@ __device__ __noinline__ float map_warp(const DevBatch& B, const DevPocket& pk, c
 // split into 32 equal contiguous lane segments; per-atom partials go to slot (atom + lane)
 // of W.rec and are added to W.gs in lane order.  Atoms that the grid maps cover are
 // skipped (their maps hold this term).  Returns the lane's energy.
-template <bool MAPS>
+template <bool MAPS, bool COUNT>
 __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
-                          float w0) {
+                          float w0, WorkCount& wc) {
     const DevParams& P = *S.P;
     const int K = P.gmm_k, L = h.n_atoms, lane = W.lane;
     const float nc2 = pk.near_cut2;
@@ -349,6 +358,7 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
                 d0 = fmaf(ex * z, u.w, d0);
             }
             ei = fmaf(-in, e0, ei);
+            if (COUNT) wc.mdn += r2 < nc2;
             const float f = in * w0 * d0 * rinv;                 // (dE/dr) / r
             gx = fmaf(f, dx, gx); gy = fmaf(f, dy, gy); gz = fmaf(f, dz, gz);
         }
@@ -367,9 +377,9 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
 // The (atom, residue) items are numbered atom by atom and split into 32 equal contiguous
 // segments, one per lane, as in the pair loop; per-atom partial forces go to slot
 // (atom + lane) of W.rec and are added to W.gs in lane order.  Returns the lane's energy.
-template <bool PARAMS>
+template <bool PARAMS, bool COUNT>
 __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
-                              float w0, float ebar, ParamAcc& acc) {
+                              float w0, float ebar, ParamAcc& acc, WorkCount& wc) {
     constexpr float kCut2 = kMdnCut * kMdnCut;
     const int K = B.mdn_k, R = B.mdn_res, L = h.n_atoms, lane = W.lane;
     int carry = 0;
@@ -433,11 +443,13 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
                 const float rp = fmaf(pz, pz, fmaf(py, py, px * px));
                 if (rp < b0) { b0 = rp; i0 = a; }
             }
+            if (COUNT) wc.scan += (uint32_t)(a1 - a0);
             const bool take1 = b1 < b0 || (b1 == b0 && i1 < i0);
             const float best = take1 ? b1 : b0;
             const float4 pb = S.pocket[take1 ? i1 : i0];
             const float bx = x.x - pb.x, by = x.y - pb.y, bz = x.z - pb.z;
             if (best < kCut2) {
+                if (COUNT) ++wc.res;
                 const float rinv = rsqrtf(fmaxf(best, 1e-12f));
                 const float d = best * rinv;
                 float P = 0.f, dP = 0.f;
@@ -493,16 +505,16 @@ struct PhaseClock {
 // time the pair loop and the other passes on pc.
 template <int TS, bool PARAMS, bool COUNT, bool MAPS>
 __device__ float score_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
-                            float ebar, ParamAcc& acc, float* e_inter, uint32_t& npairs, PhaseClock* pc = nullptr) {
+                            float ebar, ParamAcc& acc, float* e_inter, WorkCount& wc, PhaseClock* pc = nullptr) {
     float w[5];
 #pragma unroll
     for (int t = 0; t < 5; ++t) w[t] = S.P->w[t];
     float ein2;
-    float el = pairs_warp<TS, PARAMS, COUNT, MAPS>(B, pk, S, h, W, w, ebar, acc, npairs, &ein2);
+    float el = pairs_warp<TS, PARAMS, COUNT, MAPS>(B, pk, S, h, W, w, ebar, acc, wc, &ein2);
     if (COUNT && pc) pc->lap(TRIDS_PHASE_PAIRS);
     if (MAPS && pk.use_maps) el += map_warp(B, pk, h, W);
-    if constexpr (TS == TRIDS_TERMS_TRIDS && !PARAMS) el += gmm_warp<MAPS>(B, pk, S, h, W, w[0]);
-    if constexpr (TS == TRIDS_TERMS_TRIDS_RES) el += residue_warp<PARAMS>(B, pk, S, h, W, w[0], ebar, acc);
+    if constexpr (TS == TRIDS_TERMS_TRIDS && !PARAMS) el += gmm_warp<MAPS, COUNT>(B, pk, S, h, W, w[0], wc);
+    if constexpr (TS == TRIDS_TERMS_TRIDS_RES) el += residue_warp<PARAMS, COUNT>(B, pk, S, h, W, w[0], ebar, acc, wc);
     if (COUNT && pc) pc->lap(TRIDS_PHASE_PASSES);
     const float e_lp = warp_sum(el);
     *e_inter = e_lp;

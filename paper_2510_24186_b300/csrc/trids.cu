@@ -14,6 +14,7 @@
 // The device code is split over device_core.cuh, device_passes.cuh and device_kernels.cuh,
 // the host objects over host_objects.cuh; this file holds the C-ABI and includes them all,
 // so the whole library is one translation unit.
+#include <cuda.h>   // driver types (CUcontext); the entry points are fetched at run time
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -709,7 +710,8 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         (rc = check_device_ptr(energy, "energy", false)) || (rc = check_device_ptr(c.trace, "trace", true)) ||
         (rc = check_device_ptr(c.trace_slot, "trace_slot", true)) ||
         (rc = check_device_ptr(c.pair_count, "pair_count", true)) ||
-        (rc = check_device_ptr(c.phase_cycles, "phase_cycles", true)) || (rc = check_terms(pk, b)))
+        (rc = check_device_ptr(c.phase_cycles, "phase_cycles", true)) ||
+        (rc = check_device_ptr(c.work_count, "work_count", true)) || (rc = check_terms(pk, b)))
         return rc;
     if ((rc = ensure_items(b, c.poses))) return rc;
     Layout L;
@@ -723,13 +725,14 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     A.seed = c.seed; A.lig_base = c.lig_base; A.dof = dof; A.state = state; A.energy = energy;
     A.trace = c.trace; A.trace_slot = c.trace_slot; A.n_trace = c.n_trace; A.pair_count = c.pair_count;
     A.phase_cycles = c.phase_cycles;
+    A.work_count = c.work_count;
     A.lig_order = b->d_lig_order; A.n_items = b->dims.n_lig * c.poses; A.counter = b->d_counter; A.err = b->d_err;
     A.params_bytes = L.params_bytes; A.pocket_off = L.pocket_off; A.ptype_off = L.ptype_off;
     A.mbar_off = L.mbar_off;
     A.warp_off = L.warp_off; A.warp_bytes = L.warp_bytes;
     cudaStream_t st = (cudaStream_t)stream;
     const int ts = pk->prm.term_set;
-    const bool cnt = c.pair_count != nullptr || c.phase_cycles != nullptr;
+    const bool cnt = c.pair_count != nullptr || c.phase_cycles != nullptr || c.work_count != nullptr;
     // the general kernels carry the other update rules, the grid maps and the two-term
     // flag evaluation; the plain ones (Adam, direct pair sums, no type both hydrophobic and
     // donor/acceptor: the paper's configuration) leave that code out
@@ -902,19 +905,53 @@ int trids_sync(const trids_batch* b, int32_t poses, const float* state, void* st
     return TRIDS_OK;
 }
 
-// Device address of g_noalloc_scratch for `dev`, looked up once per device with that
-// device current (host code cannot use the symbol itself as a device address).
+// Id of the calling thread's current CUDA context (the device's primary context after
+// device_guard), through driver entry points fetched at run time; 0 when they are not
+// available.  A context gets a new id when it is created again (after cudaDeviceReset, say).
+static unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
+
+// Device address of g_noalloc_scratch for `dev` (current): looked up once per device and
+// context with that device current (host code cannot use the symbol itself as a device
+// address), and looked up again when the device's context has changed since, as after a
+// cudaDeviceReset, when the old address would be stale.  Where the driver gives no
+// context id, every call looks it up.
 static int noalloc_scratch(int dev, unsigned char** out) {
     static std::mutex mu;
     static void* addr[256] = {};
+    static unsigned long long ctx_of[256] = {};
     if (dev < 0 || dev >= 256) return fail(TRIDS_EINVAL, "device %d out of range", dev);
+    const unsigned long long ctx = current_context_id();
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (!addr[dev] || ctx_of[dev] != ctx || ctx == 0) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return fail(TRIDS_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
         addr[dev] = p;
+        ctx_of[dev] = ctx;
     }
     *out = static_cast<unsigned char*>(addr[dev]);
     return TRIDS_OK;

