@@ -271,7 +271,7 @@ def main():
     arrays = synth.concat_ligands([w.ligands[i] for i in mine]) if world > 1 else all_arrays
     tuned = None
     if sp.term_set != 0:
-        args.cell, args.warps = args.cell or 0.5, args.warps or 20
+        args.cell, args.warps = args.cell or 0.5, args.warps or 24
     if not args.cell and not args.warps:
         shape = [None]
         if rank == 0:
@@ -461,7 +461,7 @@ def main():
                              "note": "one CUDA graph per launch shape, built in the warm-up; each timed step "
                                      "replays it after updating its nodes with that step's seed"},
                    "l2": "flushed between steps (256 MB write)", "cell": args.cell or 0.5,
-                   "warps_per_block": args.warps or 20,
+                   "warps_per_block": args.warps,
                    "autotuned": None if tuned is None else {"table_ms": tuned.table, "probe": f"first 128 ligands x "
                                                             f"{P} poses x {S} evaluations per shape"},
                    "parallelism": f"ligand shards x{world}",

@@ -167,7 +167,9 @@ typedef struct trids_sample_cfg {
     uint64_t seed;           /* Philox4x32-10 key */
     int32_t lig_base;        /* random-stream id of ligand 0 of this batch */
     int32_t mode;            /* TRIDS_MODE_* */
-    int32_t warps_per_block; /* poses (warps) per block, 1..20; 0 = 20, or fewer if the pocket needs the shared memory */
+    int32_t warps_per_block; /* poses (warps) per block: 1..28 for the plain Vina-form sampler (Adam,
+                              * direct pair sums), 1..24 otherwise (larger values are capped); 0 = the
+                              * maximum; fewer if the pocket needs the shared memory */
     int32_t use_graph;       /* persistent mode: launch through the pocket's CUDA graph (counter reset +
                               * persistent kernel), built once per launch shape and replayed; other
                               * arguments update its nodes (see trids_graph_stats) */

@@ -345,6 +345,18 @@ struct FlagTerm {
     uint32_t mh, mb;   // two-term form: hydrophobic / donor-acceptor candidate bits
 };
 
+// The single flag term of a ligand type from its table row (DevParams::ftab).
+__device__ __forceinline__ FlagTerm flag_term_of(float4 t) {
+    FlagTerm F;
+    F.m = __float_as_uint(t.x);
+    F.nb = t.y;
+    F.a = t.z;
+    F.w = t.w;
+    F.b = -t.y;
+    F.mh = F.mb = 0u;
+    return F;
+}
+
 // fi = the ligand atom's type flags (bit0 hydrophobic, bit1 donor, bit2 acceptor); w3, w4
 // the hydrophobic and H-bond weights.
 __device__ __forceinline__ FlagTerm make_flag_term(uint32_t fi, float w3, float w4) {

@@ -327,10 +327,17 @@ __device__ __forceinline__ void flush_count(unsigned long long* cnt, unsigned lo
             if (v[k + 1]) atomicAdd(work + k, v[k + 1]);
 }
 
+// Warps per block the sampler kernels are compiled for (their register budget): 28 for the
+// plain Vina-form kernels (72 registers per thread), 24 for the others (80), the counts that
+// ran fastest on a B300; fewer warps per block are allowed.
+__host__ __device__ constexpr int sample_warps_max(int ts, bool gen) {
+    return ts == TRIDS_TERMS_VINA5 && !gen ? 28 : 24;
+}
+
 // Persistent fused sampler: each warp pops poses from a global counter (ligands in
 // decreasing-cost order) and runs every evaluation of the pose with its state on chip.
 template <int TS, bool COUNT, bool GEN>
-__global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
+__global__ void __launch_bounds__(32 * sample_warps_max(TS, GEN), 1) k_sample_persistent(SampleArgs A) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
     Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),
@@ -378,7 +385,7 @@ __global__ void __launch_bounds__(640, 1) k_sample_persistent(SampleArgs A) {
 // Plain form: one launch per (ligand, evaluation), one warp per pose, the state in
 // global memory between launches; the same device code as the persistent sampler.
 template <int TS, bool COUNT, bool GEN>
-__global__ void __launch_bounds__(640, 1) k_sample_step(SampleArgs A, int l, int s) {
+__global__ void __launch_bounds__(32 * sample_warps_max(TS, GEN), 1) k_sample_step(SampleArgs A, int l, int s) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (!stage_block(smem, A.pk, A.params_bytes, A.pocket_off, A.ptype_off, A.mbar_off, A.err)) return;
     Smem S{reinterpret_cast<const DevParams*>(smem), reinterpret_cast<const float4*>(smem + A.pocket_off),

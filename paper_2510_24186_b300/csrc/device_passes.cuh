@@ -127,7 +127,9 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
         float ri = xa.w;
         // per-atom operands of the packed evaluation, set when the lane changes atom
         float2 nxy = make_float2(-xa.x, -xa.y), nzr = make_float2(-xa.z, -ri);
-        FlagTerm F = make_flag_term(fi, P.w[3], P.w[4]);
+        // the plain Vina-form kernels take the single flag term from the type table; the two-term
+        // form and the TRIDS terms (donor-acceptor bits) build the operands from the flags
+        FlagTerm F = (MAPS || TS != TRIDS_TERMS_VINA5) ? make_flag_term(fi, P.w[3], P.w[4]) : flag_term_of(P.ftab[ti]);
         float ax = 0.f, ay = 0.f, az = 0.f;
         auto block_ptr = [&](int blk) -> const uint4* {
             const int loc = blk - first;
@@ -143,7 +145,7 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                 W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
                 ax = ay = az = 0.f;
                 do { ++i; } while (W.pre[i + 1] == blk);
-                first = W.pre[i];
+                first = blk;                       // a lane enters an atom at its first block
                 nxt = W.pre[i + 1];
                 cbw = W.cb[i];
                 cbk = cbw & 0xffffff;
@@ -155,10 +157,10 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                 ri = xa.w;
                 nxy = make_float2(-xa.x, -xa.y);
                 nzr = make_float2(-xa.z, -ri);
-                F = make_flag_term(fi, P.w[3], P.w[4]);
+                F = (MAPS || TS != TRIDS_TERMS_VINA5) ? make_flag_term(fi, P.w[3], P.w[4]) : flag_term_of(P.ftab[ti]);
                 icut = first + cbk;
                 ib = reinterpret_cast<const uint4*>(ient + 8 * ipb);
-                pb = block_ptr(blk);
+                pb = cbk ? reinterpret_cast<const uint4*>(cand + csb) : ib;
                 v = __ldg(pb);
             }
             const uint4 vc = v;

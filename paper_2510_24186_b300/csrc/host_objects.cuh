@@ -194,6 +194,16 @@ void fill_dev_params(const trids_params* p, DevParams* d) {
     d->w_tor = p->w_tor;
     for (int a = 0; a < kNT; ++a) d->radius[a] = a < p->n_types ? p->radius[a] : 0.f;
     for (int a = 0; a < kNT; ++a) d->tflags[a] = a < p->n_types ? (uint32_t)(p->flags[a] & 7) : 0u;
+    for (int a = 0; a < kNT; ++a) {
+        // a hydrophobic type meets w3 sat(1.5 - d) with hydrophobic candidates; a donor and/or
+        // acceptor type w4 sat(-d / 0.7) with candidates of the complementary flag
+        const uint32_t f = d->tflags[a];
+        const bool hyd = (f & 1u) != 0u;
+        const uint32_t m = hyd ? (1u << 13) : ((((f & 2u) << 1) | ((f & 4u) >> 1)) << 13);
+        float mb;
+        std::memcpy(&mb, &m, 4);
+        d->ftab[a] = make_float4(mb, hyd ? -1.f : -1.f / 0.7f, hyd ? 1.5f : 0.f, hyd ? p->w[3] : p->w[4]);
+    }
     for (int a = 0; a < kNT; ++a)
         for (int b = 0; b < kNT; ++b) {
             const bool in = a < p->n_types && b < p->n_types;
@@ -339,10 +349,12 @@ size_t max_smem(int dev) {
     return (size_t)v;
 }
 
-// Pick warps per block: the requested count, capped so the block fits in shared memory.
-int pick_warps(int requested, const trids_pocket* pk, const trids_batch* b, bool params, Layout* L) {
+// Pick warps per block: the requested count (at most max_warps), capped so the block fits
+// in shared memory.
+int pick_warps(int requested, const trids_pocket* pk, const trids_batch* b, bool params, Layout* L,
+               int max_warps = 20) {
     const size_t cap = max_smem(pk->device);
-    int w = requested > 0 ? std::min(requested, 20) : 8;
+    int w = requested > 0 ? std::min(requested, max_warps) : 8;
     for (; w >= 1; --w) {
         *L = make_layout(pk->prm.term_set, pk->M, b->dims.max_atoms, b->dims.max_tor, w, params);
         if (L->total <= cap) return w;

@@ -715,7 +715,17 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         return rc;
     if ((rc = ensure_items(b, c.poses))) return rc;
     Layout L;
-    const int warps = pick_warps(c.warps_per_block > 0 ? c.warps_per_block : 20, pk, b, false, &L);
+    const int ts = pk->prm.term_set;
+    const bool cnt = c.pair_count != nullptr || c.phase_cycles != nullptr || c.work_count != nullptr;
+    // the general kernels carry the other update rules, the grid maps and the two-term
+    // flag evaluation; the plain ones (Adam, direct pair sums, no type both hydrophobic and
+    // donor/acceptor: the paper's configuration) leave that code out
+    bool dual = false;
+    for (int t = 0; t < pk->prm.n_types; ++t)
+        dual |= (pk->prm.flags[t] & 1) && (pk->prm.flags[t] & 6);
+    const bool gen = c.optimizer != TRIDS_OPT_ADAM || pk->d_maps != nullptr || dual;
+    const int wmax = sample_warps_max(ts, gen);
+    const int warps = pick_warps(c.warps_per_block > 0 ? c.warps_per_block : wmax, pk, b, false, &L, wmax);
     if (!warps) return fail(TRIDS_EINVAL, "pocket of %d atoms does not fit in shared memory", pk->M);
     SampleArgs A;
     std::memset(&A, 0, sizeof A);  // padding too: the bytes are compared with the graph's last arguments
@@ -731,15 +741,6 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
     A.mbar_off = L.mbar_off;
     A.warp_off = L.warp_off; A.warp_bytes = L.warp_bytes;
     cudaStream_t st = (cudaStream_t)stream;
-    const int ts = pk->prm.term_set;
-    const bool cnt = c.pair_count != nullptr || c.phase_cycles != nullptr || c.work_count != nullptr;
-    // the general kernels carry the other update rules, the grid maps and the two-term
-    // flag evaluation; the plain ones (Adam, direct pair sums, no type both hydrophobic and
-    // donor/acceptor: the paper's configuration) leave that code out
-    bool dual = false;
-    for (int t = 0; t < pk->prm.n_types; ++t)
-        dual |= (pk->prm.flags[t] & 1) && (pk->prm.flags[t] & 6);
-    const bool gen = c.optimizer != TRIDS_OPT_ADAM || pk->d_maps != nullptr || dual;
     if (c.mode == TRIDS_MODE_PER_LIGAND) {
         const StepKernel kern = step_kernel(ts, cnt, gen);
         CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));

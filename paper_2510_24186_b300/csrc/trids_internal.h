@@ -106,6 +106,8 @@ struct alignas(16) DevParams {
     float radius[kNT];
     uint32_t tflags[kNT];          // per type: bit0 hydrophobic, bit1 donor, bit2 acceptor
     float2 pairtab[kNT][kNT];      // (R_a + R_b, pair flags as int bits: 1 hydrophobic, 2 donor-acceptor)
+    float4 ftab[kNT];              // per ligand type, its Vina-form flag term w sat(a - b d) against
+                                   // candidates with mask bits m: (m as bits << 13, -b, a, w)
     float4 gmm[kNT][kNTP][kKP];    // (pi, mu, -log2(e)/(2 sigma^2), 1/sigma^2): exp(-z^2/(2 sigma^2))
                                    // = ex2(z^2 * .z); [a][b][k] for b < kNT, k < kK (the rest is padding)
 };
