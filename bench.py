@@ -43,7 +43,7 @@ F_PAIR_VINA = 53            # an in-cutoff pair of the Vina-form terms (5 terms,
 F_PAIR_TRIDS = 27           # an in-cutoff pair of the TRIDS atom-pair terms: distance, E_long, force
 F_CLASH = 5                 # + a pair inside the E_clash range
 F_HBOND = 8                 # + a donor-acceptor pair inside the E_Hbond range
-F_MDN_PAIR = 19             # an atom-pair E_MDN pair inside 5 A (term set 1): distance, force ...
+F_MDN_PAIR = 20             # an atom-pair E_MDN pair inside 5 A (term set 1): distance, mask, force ...
 F_MDN_KERNEL = 8            # ... + per Gaussian kernel
 F_RES_SCAN = 8              # a residue atom scanned for the residue minimum (term set 2)
 F_RES_PAIR = 13             # a (ligand atom, residue) pair inside 5 A: distance, force, + 8 per kernel
@@ -163,7 +163,7 @@ def cpu_threads():
         return os.cpu_count() or 1
 
 
-def oracle_sample_rate(w, budget_s=12.0, max_ligs=64, n_threads=None, first=0, terms="vina5"):
+def oracle_sample_rate(w, budget_s=12.0, max_ligs=64, n_threads=None, first=0, terms="vina5", optimizer="adam"):
     """FP64 oracle sampler on whole ligands of the workload until ~budget_s of wall time."""
     import oracle
     n_threads = n_threads or cpu_threads()
@@ -182,7 +182,7 @@ def oracle_sample_rate(w, budget_s=12.0, max_ligs=64, n_threads=None, first=0, t
     else:
         lo = w.box_center - w.box_size / 2
         hi = w.box_center + w.box_size / 2
-    cfg = oracle.sample_cfg(steps=w.steps, mc_loops=w.mc_loops, seed=7, box_lo=lo, box_hi=hi)
+    cfg = oracle.sample_cfg(steps=w.steps, mc_loops=w.mc_loops, seed=7, box_lo=lo, box_hi=hi, optimizer=optimizer)
     pxyz = w.pocket.xyz.astype(np.float32).astype(np.float64)
     ptype = w.pocket.type.astype(np.int32)
     t0 = time.perf_counter()
@@ -200,21 +200,29 @@ def oracle_sample_rate(w, budget_s=12.0, max_ligs=64, n_threads=None, first=0, t
     return units / dt, n_threads, n, dt
 
 
+def workload_config(w, args, world):
+    """The workload a bench line measures (the same dict for both arms of the comparison)."""
+    return {"workload": w.name, "n_lig": len(w.ligands), "poses": w.poses, "steps": w.steps,
+            "mc_loops": w.mc_loops, "pocket_atoms": len(w.pocket.type), "top_k": w.topk, "term_set": args.terms,
+            "optimizer": args.optimizer, "maps_spacing": args.maps or None,
+            "l2": "flushed between steps (256 MB write)", "parallelism": f"ligand shards x{world}"}
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
-    w = synth.workload("batched_screening")
+    w = synth.workload(args.workload, n_lig=args.n_lig or None)
     rates = []
     for k in range(args.warmup + args.steps):
-        r, cores, n, dt = oracle_sample_rate(w, budget_s=0.0, max_ligs=1, first=k % len(w.ligands))
+        r, cores, n, dt = oracle_sample_rate(w, budget_s=0.0, max_ligs=1, first=k % len(w.ligands), terms=args.terms,
+                                             optimizer=args.optimizer)
         if k >= args.warmup:
             rates.append(r)
     value = statistics.mean(rates)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w.poses * w.steps / value,
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "n_lig": len(w.ligands), "poses": w.poses, "steps": w.steps,
-                       "pocket_atoms": len(w.pocket.type)},
+            "config": workload_config(w, args, int(os.environ.get("WORLD_SIZE", "1"))),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"one ligand x {w.poses} poses x {w.steps} evaluations per step, FP64 "
                                        "all-pairs oracle on all host threads"},
@@ -454,17 +462,13 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "n_lig": n_lig, "poses": P, "steps": S, "mc_loops": Lm,
-                   "pocket_atoms": len(w.pocket.type), "top_k": w.topk, "term_set": args.terms,
-                   "optimizer": args.optimizer, "maps": maps,
-                   "graph": {"timed_region": graph_timed, "total": g1,
+        "config": workload_config(w, args, world),
+        "launch": {"graph": {"timed_region": graph_timed, "total": g1,
                              "note": "one CUDA graph per launch shape, built in the warm-up; each timed step "
                                      "replays it after updating its nodes with that step's seed"},
-                   "l2": "flushed between steps (256 MB write)", "cell": args.cell or 0.5,
-                   "warps_per_block": args.warps,
+                   "cell": args.cell or 0.5, "warps_per_block": args.warps, "maps": maps,
                    "autotuned": None if tuned is None else {"table_ms": tuned.table, "probe": f"first 128 ligands x "
                                                             f"{P} poses x {S} evaluations per shape"},
-                   "parallelism": f"ligand shards x{world}",
                    "shards": {"split": "longest-processing-time on ligand cost, global ligand ids as stream ids",
                               "rank0_ligands": len(mine), "topk_gathered_ligands": len(gathered[0])}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
