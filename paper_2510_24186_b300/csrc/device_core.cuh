@@ -123,7 +123,7 @@ struct Layout {
 
 __host__ __device__ inline size_t pose_warp_core_bytes(int Lm, int Tm) {
     return 16 * (size_t)(Lm + 1) + 16 * (size_t)Lm + 48 * (size_t)(Tm > 0 ? Tm : 1) + 16 * (size_t)(Lm + 32) +
-           12 * (size_t)Lm + 4 * (size_t)(Lm + 1);
+           16 * (size_t)(Lm + 1);
 }
 
 constexpr size_t kRigidStateBytes = 128;   // sizeof(RigidState), checked below
@@ -216,8 +216,9 @@ __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t par
 //   rk  float4[3 Tm]    rows of each torsion's rotation matrix; .w of the three rows holds
 //                       the torsion's pivot (parent axis atom, local coordinates)
 //   rec float4[Lm + 32] partial ligand-pocket forces, slot (atom + lane)
-//   cs  uint32[Lm]      candidate-list offset of each atom's cell
-//   pre int[Lm + 1]     exclusive prefix of each atom's candidate blocks
+//   meta int4[Lm + 1]   per atom, one 16-byte record: candidate-list offset of its cell,
+//                       candidate blocks | flags | type, first intra block, and the exclusive
+//                       prefix of the atoms' work items (.w, Lm + 1 entries)
 //   rig RigidState      the pose's rigid sampler state (t, q, Adam moments, saved state,
 //                       loop energies, status), one copy per warp: every lane computes the
 //                       same values
@@ -236,11 +237,10 @@ struct PW {
     float4* gs;
     float4* rk;
     float4* rec;
-    uint32_t* cs;   // per atom: candidate-list offset of its cell
-    int* cb;        // per atom: candidate blocks of its cell | type flags << 24 | type << 27
-                    // (the pair loop); the atom type (the atom-pair E_MDN pass)
-    int* ip;        // per atom: first intra-partner block
-    int* pre;
+    int4* meta;     // per atom: (.x candidate-list offset of its cell; .y candidate blocks of its
+                    // cell | type flags << 24 | type << 27 in the pair loop, the atom type in the
+                    // atom-pair E_MDN pass; .z first intra-partner block; .w exclusive prefix of
+                    // the atom's work items, [Lm + 1])
     float* grs;
     unsigned long long* clk;   // phase clock (counting sampler)
     LigHdr* hdr;               // the pose's ligand header (sampler kernels)
@@ -254,10 +254,7 @@ __device__ __forceinline__ PW make_pw(unsigned char* smem, size_t warp_off, size
     W.gs = W.xs + Lm + 1;
     W.rk = W.gs + Lm;
     W.rec = W.rk + 3 * (Tm > 0 ? Tm : 1);
-    W.cs = reinterpret_cast<uint32_t*>(W.rec + Lm + 32);
-    W.cb = reinterpret_cast<int*>(W.cs + Lm);
-    W.ip = W.cb + Lm;
-    W.pre = W.ip + Lm;
+    W.meta = reinterpret_cast<int4*>(W.rec + Lm + 32);
     W.rig = reinterpret_cast<RigidState*>(base + pose_state_off(Lm, Tm));
     W.tor = reinterpret_cast<TorState*>(base + pose_state_off(Lm, Tm) + kRigidStateBytes);
     W.grs = reinterpret_cast<float*>(base + pose_grs_off(Lm, Tm));

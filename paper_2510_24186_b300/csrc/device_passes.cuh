@@ -12,9 +12,9 @@ namespace {
 // because atoms never decrease along the lanes.  The partials of an atom are then added in
 // lane order, so the result does not depend on timing.
 
-// Per-atom item counts -> exclusive prefix W.pre[0..L], 32 atoms per call: atom i =
+// Per-atom item counts -> exclusive prefix W.meta[0..L].w, 32 atoms per call: atom i =
 // base + lane has n items (0 for i >= L); carry runs over the calls.  seg_finish then sets
-// W.pre[0], clears W.rec and returns the total.
+// W.meta[0].w, clears W.rec and returns the total.
 __device__ __forceinline__ void seg_scan(const PW& W, int L, int i, int n, int& carry) {
     const int lane = W.lane;
     int v = n;
@@ -23,12 +23,12 @@ __device__ __forceinline__ void seg_scan(const PW& W, int L, int i, int n, int& 
         const int t = __shfl_up_sync(kFull, v, o);
         if (lane >= o) v += t;
     }
-    if (i < L) W.pre[i + 1] = carry + v;
+    if (i < L) W.meta[i + 1].w = carry + v;
     carry += __shfl_sync(kFull, v, 31);
 }
 
 __device__ __forceinline__ int seg_finish(const PW& W, int L, int carry) {
-    if (W.lane == 0) W.pre[0] = 0;
+    if (W.lane == 0) W.meta[0].w = 0;
     for (int r = W.lane; r < L + 32; r += 32) W.rec[r] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncwarp();
     return carry;
@@ -41,7 +41,7 @@ __device__ __forceinline__ int seg_range(const PW& W, int L, int N, int& lo, int
     int a = 0, b = L - 1;
     while (a < b) {
         const int m = (a + b + 1) >> 1;
-        if (W.pre[m] <= lo) a = m; else b = m - 1;
+        if (W.meta[m].w <= lo) a = m; else b = m - 1;
     }
     return a;
 }
@@ -52,7 +52,7 @@ __device__ __forceinline__ void seg_combine(const PW& W, int L, int N) {
     __syncwarp();
     for (int i = W.lane; i < L; i += 32) {
         float gx = 0.f, gy = 0.f, gz = 0.f;
-        const int b0 = W.pre[i], b1 = W.pre[i + 1];
+        const int b0 = W.meta[i].w, b1 = W.meta[i + 1].w;
         if (b0 < b1) {
             const int l0 = min(31, (32 * (b0 + 1) - 1) / N), l1 = min(31, (32 * b1 - 1) / N);
             for (int l = l0; l <= l1; ++l) {
@@ -78,7 +78,7 @@ __device__ __forceinline__ void seg_combine(const PW& W, int L, int N) {
 // both in blocks of 8 uint16 entries (target index, 13 bits | target's flags << 13;
 // padding points at a far sentinel).  Pocket targets are read from the block's staged
 // pocket, ligand targets from the pose's own coordinates (W.xs); both float4 carry
-// (x, y, z, radius).  The pose's blocks are numbered atom by atom (prefix in W.pre) and
+// (x, y, z, radius).  The pose's blocks are numbered atom by atom (prefix in W.meta[].w) and
 // split into 32 equal contiguous segments, one per lane, so the lanes stay balanced
 // whatever the atoms' list lengths.  A lane accumulates the force on its current atom
 // in registers and leaves a partial in slot (atom + lane) of W.rec; the partials of an
@@ -107,9 +107,9 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             const int i0 = __ldg(&B.ipre[h.ipre_off + i]), i1 = __ldg(&B.ipre[h.ipre_off + i + 1]);
             const int cbk = (MAPS && map_cell(pk, x.x, x.y, x.z, nullptr)) ? 0 : nb;
             const int ty = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);
-            W.cs[i] = beg;
-            W.cb[i] = cbk | (int)((P.tflags[ty] & 7u) << 24) | (ty << 27);   // blocks | flags | type
-            W.ip[i] = i0;
+            W.meta[i].x = beg;
+            W.meta[i].y = cbk | (int)((P.tflags[ty] & 7u) << 24) | (ty << 27);   // blocks | flags | type
+            W.meta[i].z = i0;
             nblk = cbk + (i1 - i0);
         }
         seg_scan(W, L, i, nblk, carry);
@@ -119,10 +119,10 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
     int i = seg_range(W, L, N, lo, hi);
     float e_lp = 0.f, e_in = 0.f;
     if (lo < hi) {
-        int first = W.pre[i], nxt = W.pre[i + 1], cbw = W.cb[i], ipb = W.ip[i];
+        int first = W.meta[i].w, nxt = W.meta[i + 1].w, cbw = W.meta[i].y, ipb = W.meta[i].z;
         int cbk = cbw & 0xffffff, ti = cbw >> 27;
         uint32_t fi = (uint32_t)(cbw >> 24) & 7u;
-        uint32_t csb = W.cs[i];
+        uint32_t csb = W.meta[i].x;
         float4 xa = W.xs[i];
         float ri = xa.w;
         // per-atom operands of the packed evaluation, set when the lane changes atom
@@ -144,15 +144,16 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             if (blk == nxt) {                      // move to the atom owning block blk
                 W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
                 ax = ay = az = 0.f;
-                do { ++i; } while (W.pre[i + 1] == blk);
+                do { ++i; } while (W.meta[i + 1].w == blk);
                 first = blk;                       // a lane enters an atom at its first block
-                nxt = W.pre[i + 1];
-                cbw = W.cb[i];
+                nxt = W.meta[i + 1].w;
+                const int4 mt = W.meta[i];             // (cell list, blocks | flags | type, intra list, prefix)
+                cbw = mt.y;
                 cbk = cbw & 0xffffff;
                 ti = cbw >> 27;
                 fi = (uint32_t)(cbw >> 24) & 7u;
-                ipb = W.ip[i];
-                csb = W.cs[i];
+                ipb = mt.z;
+                csb = (uint32_t)mt.x;
                 xa = W.xs[i];
                 ri = xa.w;
                 nxy = make_float2(-xa.x, -xa.y);
@@ -313,8 +314,8 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
             uint32_t beg = 0;
             if (!(MAPS && map_cell(pk, x.x, x.y, x.z, nullptr)))
                 cell_levels(pk, pk.ncell_start, pk.nlevels, x.x, x.y, x.z, beg, n);
-            W.cs[i] = beg;
-            W.cb[i] = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);   // the atom's type
+            W.meta[i].x = beg;
+            W.meta[i].y = __float_as_int(__ldg(&B.atom_y[h.atom_off + i]).w);   // the atom's type
         }
         seg_scan(W, L, i, n, carry);
     }
@@ -323,10 +324,10 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
     int i = seg_range(W, L, N, lo, hi);
     float e = 0.f;
     if (lo < hi) {
-        int first = W.pre[i], nxt = W.pre[i + 1];
-        uint32_t cs = W.cs[i];
+        int first = W.meta[i].w, nxt = W.meta[i + 1].w;
+        uint32_t cs = W.meta[i].x;
         float4 x = W.xs[i];
-        const float4* g = &P.gmm[W.cb[i]][0][0];
+        const float4* g = &P.gmm[W.meta[i].y][0][0];
         float gx = 0.f, gy = 0.f, gz = 0.f, ei = 0.f;
         int jn = __ldg(&pk.nlist[cs + (uint32_t)(lo - first)]);
         for (int it = lo; it < hi; ++it) {
@@ -334,12 +335,12 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
                 W.rec[i + lane] = make_float4(gx, gy, gz, 0.f);
                 e = fmaf(w0, ei, e);
                 gx = gy = gz = ei = 0.f;
-                do { ++i; } while (W.pre[i + 1] == it);
-                first = W.pre[i];
-                nxt = W.pre[i + 1];
-                cs = W.cs[i];
+                do { ++i; } while (W.meta[i + 1].w == it);
+                first = W.meta[i].w;
+                nxt = W.meta[i + 1].w;
+                cs = W.meta[i].x;
                 x = W.xs[i];
-                g = &P.gmm[W.cb[i]][0][0];
+                g = &P.gmm[W.meta[i].y][0][0];
                 jn = __ldg(&pk.nlist[cs + (uint32_t)(it - first)]);
             }
             const int j = jn;
@@ -392,7 +393,7 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
             const float4 x = W.xs[i];
             uint32_t beg;
             cell_levels(pk, pk.rcell_start, pk.rlevels, x.x, x.y, x.z, beg, n);
-            W.cs[i] = beg;
+            W.meta[i].x = beg;
         }
         seg_scan(W, L, i, n, carry);
     }
@@ -401,8 +402,8 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
     int i = seg_range(W, L, N, lo, hi);
     float e = 0.f;
     if (lo < hi) {
-        int first = W.pre[i], nxt = W.pre[i + 1];
-        uint32_t cs = W.cs[i];
+        int first = W.meta[i].w, nxt = W.meta[i + 1].w;
+        uint32_t cs = W.meta[i].x;
         float4 x = W.xs[i];
         const float4* __restrict__ kern = B.mdn + (size_t)(h.atom_off + i) * R * K;
         float gx = 0.f, gy = 0.f, gz = 0.f, ei = 0.f;
@@ -413,10 +414,10 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
                 e = fmaf(w0, ei, e);
                 if (PARAMS) acc.gw[0] = fmaf(ebar, ei, acc.gw[0]);
                 gx = gy = gz = ei = 0.f;
-                do { ++i; } while (W.pre[i + 1] == it);
-                first = W.pre[i];
-                nxt = W.pre[i + 1];
-                cs = W.cs[i];
+                do { ++i; } while (W.meta[i + 1].w == it);
+                first = W.meta[i].w;
+                nxt = W.meta[i + 1].w;
+                cs = W.meta[i].x;
                 x = W.xs[i];
                 kern = B.mdn + (size_t)(h.atom_off + i) * R * K;
                 ent = __ldg(&pk.rlist[cs + (uint32_t)(it - first)]);
@@ -534,7 +535,7 @@ __device__ float adjoint_warp(const DevBatch& B, const LigHdr& h, const PW& W, c
                               float tau[3]) {
     const int L = h.n_atoms, T = h.n_tor, lane = W.lane;
     float4* __restrict__ pu = W.rec;                                  // U prefix, [L]
-    float4* __restrict__ pg = reinterpret_cast<float4*>(W.cs);       // G prefix, [L]
+    float4* __restrict__ pg = reinterpret_cast<float4*>(W.meta);       // G prefix, [L]
     float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};                      // totals of the rounds so far
     for (int base = 0; base < L; base += 32) {
         const int i = base + lane;
