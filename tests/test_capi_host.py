@@ -83,6 +83,34 @@ def test_new_entry_points_reject_null_handles_without_a_gpu():
     assert L.trids_set_boxes(None, 1, None, None) == _lib.EINVAL
     assert L.trids_screen_energy(None, None, 1, 1, None, None, None, None) == _lib.EINVAL
     assert b"NULL" in L.trids_last_error()
+    v = C.c_int64(-1)
+    assert L.trids_graph_stats(None, C.byref(v), None, None) == _lib.EINVAL and v.value == -1
+    assert L.trids_set_stream_ids(None, None) == _lib.EINVAL
+
+
+def test_sharded_screening_host_logic_on_one_process():
+    """parallel.screen_shards without a process group: world 1 runs the whole set as one
+    shard; an explicit rank/world runs that rank's longest-processing-time shard, and the
+    shards of all ranks cover the set once."""
+    import numpy as np
+    from paper_2510_24186_b300 import parallel
+    n_atoms = [12, 40, 25, 33, 18, 60, 27]
+    n_tor = [1, 9, 3, 4, 2, 15, 5]
+    seen = []
+
+    def run(ids):
+        seen.append(list(ids))
+        return np.array([[i, -1] for i in ids]), np.array([[-float(i), np.nan] for i in ids])
+
+    ids, idx, e = parallel.screen_shards(n_atoms, n_tor, run)
+    assert list(ids) == list(range(7)) and seen[-1] == list(range(7))
+    assert idx[:, 0].tolist() == list(range(7))
+    parts = [parallel.screen_shards(n_atoms, n_tor, run, rank=r, world=3, gather=False) for r in range(3)]
+    assert sorted(sum((list(p[0]) for p in parts), [])) == list(range(7))
+    merged = parallel.merge_topk(parts)
+    assert merged[0].tolist() == list(range(7)) and merged[1][:, 0].tolist() == list(range(7))
+    loads = [parallel.ligand_cost(np.array(n_atoms)[p[0]], np.array(n_tor)[p[0]]).sum() for p in parts]
+    assert max(loads) - min(loads) <= parallel.ligand_cost(n_atoms, n_tor).max()
 
 
 def test_python_api_fails_loudly_without_cuda():
