@@ -62,6 +62,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// 1/sqrt(x) for normal x > 0 (every caller guards x >= 1e-12): the hardware approximation
+// without the subnormal-input handling of rsqrtf, the same value for such x.
+__device__ __forceinline__ float rsqrt_normal(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ------------------------------------------------------------------ pair terms
 // TRIDS E_dock terms on r (see trids.h).
 template <bool TERMS>
@@ -411,11 +419,11 @@ __device__ __forceinline__ void vina_x2(uint32_t wd, const float4* __restrict__ 
     const float2 qa = __ffma2_rn(make_float2(a.z, a.w), pm, nzr);     // (z_j - z_i, -(R_i + R_j))
     const float2 pc = __fadd2_rn(make_float2(c.x, c.y), nxy);
     const float2 qc = __ffma2_rn(make_float2(c.z, c.w), pm, nzr);
-    const float2 sa = __fmul2_rn(pa, pa), sc = __fmul2_rn(pc, pc);
-    const float2 r2 = make_float2(fmaf(qa.x, qa.x, sa.x) + sa.y, fmaf(qc.x, qc.x, sc.x) + sc.y);
-    const float2 in = make_float2(r2.x < cut2 ? 1.f : 0.f, r2.y < cut2 ? 1.f : 0.f);
-    const float2 rr = __fadd2_rn(r2, K.tiny);
-    const float2 ri = make_float2(rsqrtf(rr.x), rsqrtf(rr.y));
+    // r^2 + 2e-12 (1e-12 added to each of two squares): keeps 1/r finite at r = 0
+    const float2 sa = __ffma2_rn(pa, pa, K.tiny), sc = __ffma2_rn(pc, pc, K.tiny);
+    const float2 rr = make_float2(fmaf(qa.x, qa.x, sa.x) + sa.y, fmaf(qc.x, qc.x, sc.x) + sc.y);
+    const float2 in = make_float2(rr.x < cut2 ? 1.f : 0.f, rr.y < cut2 ? 1.f : 0.f);
+    const float2 ri = make_float2(rsqrt_normal(rr.x), rsqrt_normal(rr.y));
     const float2 d = make_float2(fmaf(rr.x, ri.x, qa.y), fmaf(rr.y, ri.y, qc.y));
     const float2 q1 = __fmul2_rn(__fmul2_rn(d, d), K.c1);
     const float2 g1 = make_float2(ex2_approx(q1.x), ex2_approx(q1.y));
@@ -456,7 +464,7 @@ __device__ __forceinline__ void vina_x2(uint32_t wd, const float4* __restrict__ 
     axy = __ffma2_rn(make_float2(f.x, f.x), pa, axy); az = fmaf(f.x, qa.x, az);
     axy = __ffma2_rn(make_float2(f.y, f.y), pc, axy); az = fmaf(f.y, qc.x, az);
     ax = axy.x; ay = axy.y;
-    if (COUNT) cnt += ((r2.x < cut2) + (r2.y < cut2)) * cw;
+    if (COUNT) cnt += ((rr.x < cut2) + (rr.y < cut2)) * cw;
 }
 
 __device__ __forceinline__ float lg2_approx(float x) {
@@ -490,7 +498,7 @@ __device__ __forceinline__ void trids_x2(uint32_t wd, const float4* __restrict__
     const float2 r2 = make_float2(fmaf(qa.x, qa.x, sa.x) + sa.y, fmaf(qc.x, qc.x, sc.x) + sc.y);
     const float2 in = make_float2(r2.x < cut2 ? 1.f : 0.f, r2.y < cut2 ? 1.f : 0.f);
     const float2 rr = __fadd2_rn(r2, make_float2(1e-12f, 1e-12f));
-    const float2 ri = make_float2(rsqrtf(rr.x), rsqrtf(rr.y));
+    const float2 ri = make_float2(rsqrt_normal(rr.x), rsqrt_normal(rr.y));
     const float2 r = __fmul2_rn(rr, ri);
     const float2 rs = make_float2(-qa.y, -qc.y);                            // R_i + R_j
     const float2 hb = make_float2((wd & mb) ? 1.f : 0.f, (wd & (mb << 16)) ? 1.f : 0.f);

@@ -349,7 +349,7 @@ __device__ float gmm_warp(const DevBatch& B, const DevPocket& pk, const Smem& S,
             const float dx = x.x - p.x, dy = x.y - p.y, dz = x.z - p.z;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             const float in = r2 < nc2 ? 1.f : 0.f;
-            const float rinv = rsqrtf(fmaxf(r2, 1e-12f));
+            const float rinv = rsqrt_normal(fmaxf(r2, 1e-12f));
             const float r = r2 * rinv;
             const float4* gk = g + S.ptype[j] * kKP;
             float e0 = 0.f, d0 = 0.f;
@@ -453,7 +453,7 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
             const float bx = x.x - pb.x, by = x.y - pb.y, bz = x.z - pb.z;
             if (best < kCut2) {
                 if (COUNT) ++wc.res;
-                const float rinv = rsqrtf(fmaxf(best, 1e-12f));
+                const float rinv = rsqrt_normal(fmaxf(best, 1e-12f));
                 const float d = best * rinv;
                 float P = 0.f, dP = 0.f;
                 for (int k = 0; k < K; ++k) {
