@@ -35,9 +35,33 @@ __device__ __forceinline__ uint32_t pick(uint4 v, int i) {
     return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 1/sqrt(x) for normal x > 0 (the callers' arguments: squared distances guarded to
+// >= 1e-12, quaternion norms near 1, Adam's bias correction 1 - b2^k): the hardware
+// approximation without the subnormal-input handling of rsqrtf, the same value for such x.
+__device__ __forceinline__ float rsqrt_normal(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// sqrt(x), x >= 0, by the hardware approximation (relative error about 2^-22; subnormal x
+// gives 0).  Used by the pose update only (Adam's sqrt(v), the rotation-step length), where
+// that error is far below the update's own rounding budget.
+__device__ __forceinline__ float sqrt_fast(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // quaternion (w,x,y,z) -> rotation matrix of q/|q|
 __device__ __forceinline__ void quat_to_mat(const float q[4], float R[9]) {
-    float n = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    float n = rsqrt_normal(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
     float w = q[0] * n, x = q[1] * n, y = q[2] * n, z = q[3] * n;
     R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
     R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
@@ -50,25 +74,11 @@ __device__ __forceinline__ void quat_premul(const float r[4], float q[4]) {
     float o1 = r[0] * q[1] + q[0] * r[1] + r[2] * q[3] - r[3] * q[2];
     float o2 = r[0] * q[2] + q[0] * r[2] + r[3] * q[1] - r[1] * q[3];
     float o3 = r[0] * q[3] + q[0] * r[3] + r[1] * q[2] - r[2] * q[1];
-    float n = rsqrtf(o0 * o0 + o1 * o1 + o2 * o2 + o3 * o3);
+    float n = rsqrt_normal(o0 * o0 + o1 * o1 + o2 * o2 + o3 * o3);
     q[0] = o0 * n; q[1] = o1 * n; q[2] = o2 * n; q[3] = o3 * n;
 }
 
 __device__ __forceinline__ float wrap_pi(float a) { return a - kTwoPi * floorf((a + kPi) * (1.0f / kTwoPi)); }
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// 1/sqrt(x) for normal x > 0 (every caller guards x >= 1e-12): the hardware approximation
-// without the subnormal-input handling of rsqrtf, the same value for such x.
-__device__ __forceinline__ float rsqrt_normal(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 // ------------------------------------------------------------------ pair terms
 // TRIDS E_dock terms on r (see trids.h).
@@ -76,7 +86,7 @@ template <bool TERMS>
 __device__ __forceinline__ float pair_trids(float r2, float rsum, int pf, const float4* __restrict__ gmm,
                                             int K, bool inter, const float* __restrict__ w, float& fr,
                                             float* et, float& dRs) {
-    const float rinv = rsqrtf(r2);
+    const float rinv = rsqrt_normal(r2);
     const float r = r2 * rinv;
     float e0 = 0.f, d0 = 0.f, e1 = 0.f, d1 = 0.f, e2 = 0.f, d2 = 0.f, r2d = 0.f, e3 = 0.f, d3 = 0.f;
     if (inter && r < 5.f) {
@@ -293,7 +303,7 @@ __device__ __forceinline__ float vina_eval(float r2, float rsum, float hyd, floa
     constexpr float kC1 = -5.770780163555854f;   // -4 log2(e): exp(-(d/0.5)^2) = 2^(kC1 d^2)
     constexpr float kC2 = -1.4426950408889634f;  // -log2(e)
     const float rr = fmaxf(r2, 1e-12f);
-    rinv = rsqrtf(rr);
+    rinv = rsqrt_normal(rr);
     const float d = rr * rinv - rsum;
     const float g1 = ex2_approx(d * d * kC1);
     const float b = fmaf(0.5f, d, -1.5f);

@@ -183,10 +183,10 @@ __device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float p
         switch (A.opt) {
         case TRIDS_OPT_RMSPROP:
             v = fmaf(A.alpha, v, (1.f - A.alpha) * g * g);
-            return -A.lr * g / (sqrtf(v) + A.eps);
+            return -A.lr * g / (sqrt_fast(v) + A.eps);
         case TRIDS_OPT_ADAGRAD:
             v = fmaf(g, g, v);
-            return -A.lr * g / (sqrtf(v) + A.eps);
+            return -A.lr * g / (sqrt_fast(v) + A.eps);
         case TRIDS_OPT_SGD:
             m = fmaf(A.momentum, m, g);
             return -A.lr * m;
@@ -196,7 +196,7 @@ __device__ __forceinline__ float opt_delta(const SampleArgs& A, float g, float p
     }
     m = fmaf(A.b1, m, (1.f - A.b1) * g);
     v = fmaf(A.b2, v, (1.f - A.b2) * g * g);
-    const float denom = fmaf(sqrtf(v), rsbc2, A.eps);
+    const float denom = fmaf(sqrt_fast(v), rsbc2, A.eps);
     const float d = -lr_bc1 * __fdividef(m, denom);
     return GEN && A.opt == TRIDS_OPT_ADAMW ? fmaf(-A.lr * A.wd, pv, d) : d;
 }
@@ -230,7 +230,7 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
             } else if (c < 6) {
                 const float ang = fmaf(u1, kTwoPi, -kPi);
                 float sh, ch;
-                sincosf(0.5f * ang, &sh, &ch);
+                __sincosf(0.5f * ang, &sh, &ch);   // half angles in [-pi/2, pi/2]: hardware sin/cos
                 const float rq[4] = {ch, c == 3 ? sh : 0.f, c == 4 ? sh : 0.f, c == 5 ? sh : 0.f};
                 quat_premul(rq, st.q);
             } else if (lane == c - 6) {
@@ -275,7 +275,7 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
     if (sc.j < sc.n - 1) {
         const int ta = sc.j + 1;
         const float lr_bc1 = __fdividef(A.lr, 1.f - ipowf(A.b1, ta));
-        const float rsbc2 = rsqrtf(1.f - ipowf(A.b2, ta));
+        const float rsbc2 = rsqrt_normal(1.f - ipowf(A.b2, ta));
         if (own) st.th = wrap_pi(st.th + opt_delta<GEN>(A, gth, st.th, st.mth, st.vth, lr_bc1, rsbc2));
         for (int d = 0; d < 3; ++d) {
             const float lo = A.pk.box_lo[bx][d], hi = A.pk.box_hi[bx][d];
@@ -284,11 +284,11 @@ __device__ void sample_step(const SampleArgs& A, const Smem& S, const LigHdr& h,
         }
         float dw[3];
         for (int d = 0; d < 3; ++d) dw[d] = opt_delta<GEN>(A, tau[d], 0.f, st.m[3 + d], st.v[3 + d], lr_bc1, rsbc2);
-        const float phi = sqrtf(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
+        const float phi = sqrt_fast(dw[0] * dw[0] + dw[1] * dw[1] + dw[2] * dw[2]);
         if (phi > 0.f) {
             float sh, ch;
-            sincosf(0.5f * phi, &sh, &ch);
-            const float sc2 = sh / phi;
+            __sincosf(0.5f * phi, &sh, &ch);   // absolute error about 4e-7, far below a step's own size
+            const float sc2 = __fdividef(sh, phi);
             const float rq[4] = {ch, sc2 * dw[0], sc2 * dw[1], sc2 * dw[2]};
             quat_premul(rq, st.q);
         }
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(512, 1) k_score(ScoreArgs A) {
                 if (lane == 0) {
                     for (int d = 0; d < 3; ++d) o[d] = sc * gt[d];
                     // dE/dq of E(q/|q|) = 4 M(qhat) tau / |q|, M(q) = 1/2 [-v^T ; w I - [v]x]
-                    const float n = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+                    const float n = rsqrt_normal(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
                     const float w = q[0] * n, vx = q[1] * n, vy = q[2] * n, vz = q[3] * n;
                     const float c0 = vy * tau[2] - vz * tau[1], c1 = vz * tau[0] - vx * tau[2],
                                 c2 = vx * tau[1] - vy * tau[0];

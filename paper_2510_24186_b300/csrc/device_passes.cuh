@@ -83,8 +83,10 @@ __device__ __forceinline__ void seg_combine(const PW& W, int L, int N) {
 // whatever the atoms' list lengths.  A lane accumulates the force on its current atom
 // in registers and leaves a partial in slot (atom + lane) of W.rec; the partials of an
 // atom are added in lane order (bit-reproducible).  The Vina-form block is branch-free:
-// all candidates are evaluated and masked by r^2 < cutoff^2.  Writes the forces to W.gs;
-// returns the lane's ligand-pocket energy and, in *e_in2, twice its intra energy.
+// all candidates are evaluated and masked by r^2 < cutoff^2.  While the loop runs, W.gs
+// holds each atom's negated (x, y, z, R), the packed evaluation's atom operands, so that a
+// lane changing atom loads them ready-made.  Writes the forces to W.gs; returns the lane's
+// ligand-pocket energy and, in *e_in2, twice its intra energy.
 template <int TS, bool PARAMS, bool COUNT, bool MAPS>
 __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& S, const LigHdr& h, const PW& W,
                            const float w[5], float ebar, ParamAcc& acc, WorkCount& wc, float* e_in2) {
@@ -101,6 +103,7 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
         int nblk = 0;
         if (i < L) {
             const float4 x = W.xs[i];
+            W.gs[i] = make_float4(-x.x, -x.y, -x.z, -x.w);   // the packed pair's atom operands
             uint32_t beg;
             int nb;
             cell_levels(pk, pk.cell_start, pk.cell_levels, x.x, x.y, x.z, beg, nb);
@@ -154,10 +157,15 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
                 fi = (uint32_t)(cbw >> 24) & 7u;
                 ipb = mt.z;
                 csb = (uint32_t)mt.x;
-                xa = W.xs[i];
-                ri = xa.w;
-                nxy = make_float2(-xa.x, -xa.y);
-                nzr = make_float2(-xa.z, -ri);
+                if constexpr (PARAMS) {
+                    xa = W.xs[i];
+                    ri = xa.w;
+                }
+                {
+                    const float4 ng = W.gs[i];
+                    nxy = make_float2(ng.x, ng.y);
+                    nzr = make_float2(ng.z, ng.w);
+                }
                 F = (MAPS || TS != TRIDS_TERMS_VINA5) ? make_flag_term(fi, P.w[3], P.w[4]) : flag_term_of(P.ftab[ti]);
                 icut = first + cbk;
                 ib = reinterpret_cast<const uint4*>(ient + 8 * ipb);
@@ -582,7 +590,7 @@ __device__ float adjoint_warp(const DevBatch& B, const LigHdr& h, const PW& W, c
         const float sy = (uw.y - uz.y) - (pz * dgx - px * dgz);
         const float sz = (uw.z - uz.z) - (px * dgy - py * dgx);
         const float ax = cc.x - p.x, ay = cc.y - p.y, az = cc.z - p.z;
-        const float n = rsqrtf(ax * ax + ay * ay + az * az);
+        const float n = rsqrt_normal(ax * ax + ay * ay + az * az);
         mine = (ax * sx + ay * sy + az * sz) * n;
     }
     return mine;
