@@ -203,7 +203,8 @@ int trids_version(void);
  *   xyz   host [n_atoms][3] float32 coordinates (A), type host [n_atoms] int32 in
  *         [0, prm->n_types); n_atoms in [1, 8191].
  *   cell  edge (A) of the candidate grid used to cull ligand-pocket pairs; 0 selects
- *         0.5 A.  The grid changes no result, only which pairs are tested.
+ *         0.5 A.  The grid changes which pairs outside the cutoff are tested (they add
+ *         exact zeros) and the order of the pair sums, so only the last bits of a result.
  *   prm   scoring parameters, copied.
  * The pocket's device arrays live on the current CUDA device.  Errors: TRIDS_EINVAL
  * (bad sizes, non-finite values, types out of range), TRIDS_ENOMEM, TRIDS_ECUDA.
