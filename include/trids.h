@@ -289,7 +289,11 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
                        const int32_t* bonds, const uint8_t* rotatable, trids_batch** out);
 
 /* Free a batch, its device arrays and work lists.  NULL is a no-op; the caller must not
- * free a batch while work that uses it is in flight. */
+ * free a batch while work that uses it is in flight.  The call waits for the work of the
+ * last library call that used the batch (on that call's stream) and keeps the batch's main
+ * device block for the next trids_pack_ligands on that device (at most two blocks per
+ * device stay pooled, until the process exits), so a stream of batches allocates its device
+ * memory once instead of once per batch. */
 int trids_free_batch(trids_batch* b);
 
 /*

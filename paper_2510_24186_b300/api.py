@@ -357,7 +357,8 @@ def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd:
     pocket.  The next batch is packed on a host thread while the current one samples; the
     DOF, state and energy buffers stay on the device and are reused.  Yields
     (first ligand id, top-k indices [n, k], top-k energies [n, k]) per batch as numpy arrays.
-    Ligand ids (the random-stream ids) run on across batches.  stats (optional dict) receives
+    Ligand ids (the random-stream ids) run on across batches; each batch is freed on the packing
+    thread once its results are back (its device block then serves a later batch).  stats (optional dict) receives
     the host-to-device and device-to-host bytes of the last batch; prepare(batch), if given,
     runs on each packed batch before it samples (e.g. Batch.set_mdn); sample_kw go to sample()."""
     stats = {} if stats is None else stats
@@ -404,7 +405,7 @@ def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd:
             stats["d2h_bytes"] = idx_h.numel() * idx_h.element_size() + e_h.numel() * e_h.element_size()
             yield base, idx_h.numpy().copy(), e_h.numpy().copy()
             base += b.n_lig
-            b.close()
+            ex.submit(b.close)   # on the packing thread, after the next batch's packing
 
 
 def screen_sharded(pocket: Pocket, ligands, poses: int, steps: int, k: int, rmsd: float = 1.0, seed: int = 0,

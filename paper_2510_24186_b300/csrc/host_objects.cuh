@@ -103,6 +103,8 @@ struct trids_batch {
     std::vector<PackedLigand> ligs;
     std::vector<LigHdr> hdr;
     unsigned char* d_block = nullptr;   // one allocation holding the arrays below up to d_err
+    size_t block_bytes = 0;             // its capacity (a reused block may be larger than needed)
+    std::vector<int> lig_order_h;       // ligands by decreasing cost (host copy of d_lig_order)
     LigHdr* d_lig = nullptr;
     float4* d_atom_y = nullptr;
     int* d_atom_orig = nullptr;
@@ -119,13 +121,14 @@ struct trids_batch {
     int items_P = -1;
     int2* d_items = nullptr;        // (ligand, first pose of a 32-pose tile), by decreasing cost
     int n_items = 0;
-    int* d_lig_order = nullptr;     // ligands by decreasing cost
+    int* d_lig_order = nullptr;     // ligands by decreasing cost (a section of d_block)
     unsigned int* d_counter = nullptr;   // [4]
     int* d_err = nullptr;                // [2]: staging timeout, status OR
     float* d_partials = nullptr;
     size_t partials_cap = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+    cudaEvent_t ev_use = nullptr;   // recorded after each call's work on the batch (UseMark)
     float4* d_mdn = nullptr;        // residue-level E_MDN kernels, packed rows
     int mdn_res = 0, mdn_k = 0;
     DevBatch view() const {
@@ -307,34 +310,104 @@ int device_guard(int dev) {
     return TRIDS_OK;
 }
 
-int ensure_items(trids_batch* b, int P) {
-    if (b->items_P == P) return TRIDS_OK;
-    const int tiles = (P + 31) / 32;
-    std::vector<std::pair<double, int>> lc(b->dims.n_lig);
-    for (int l = 0; l < b->dims.n_lig; ++l) {
-        const LigHdr& h = b->hdr[l];
-        lc[l] = {60.0 * h.n_atoms + 2.0 * h.n_pairs + 20.0 * h.n_tor + 10.0, l};
+// Ligands by decreasing estimated cost (atoms, intra pairs, torsions; ties by index): the
+// order in which the persistent sampler pops them and the scorer's items run.
+std::vector<int> lig_cost_order(const std::vector<LigHdr>& hdr) {
+    std::vector<std::pair<double, int>> lc(hdr.size());
+    for (size_t l = 0; l < hdr.size(); ++l) {
+        const LigHdr& h = hdr[l];
+        lc[l] = {60.0 * h.n_atoms + 2.0 * h.n_pairs + 20.0 * h.n_tor + 10.0, (int)l};
     }
     std::stable_sort(lc.begin(), lc.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& c) {
         return a.first > c.first;
     });
     std::vector<int> order(lc.size());
+    for (size_t i = 0; i < lc.size(); ++i) order[i] = lc[i].second;
+    return order;
+}
+
+// The scorer's (ligand, 32-pose tile) items for P poses, ligands by decreasing cost.
+int ensure_items(trids_batch* b, int P) {
+    if (b->items_P == P) return TRIDS_OK;
+    const int tiles = (P + 31) / 32;
     std::vector<int2> items;
     items.reserve((size_t)b->dims.n_lig * tiles);
-    for (size_t i = 0; i < lc.size(); ++i) {
-        order[i] = lc[i].second;
-        for (int t = 0; t < tiles; ++t) items.push_back(make_int2(lc[i].second, t * 32));
-    }
+    for (int l : b->lig_order_h)
+        for (int t = 0; t < tiles; ++t) items.push_back(make_int2(l, t * 32));
     cudaFree(b->d_items);
-    cudaFree(b->d_lig_order);
     b->d_items = nullptr;
-    b->d_lig_order = nullptr;
     int rc = upload(&b->d_items, items);
     if (rc) return rc;
-    if ((rc = upload(&b->d_lig_order, order))) return rc;
     b->n_items = (int)items.size();
     b->items_P = P;
     return TRIDS_OK;
+}
+
+// Records the batch's use event on the call's stream when the entry point returns (whatever
+// it launched), so that trids_free_batch waits for the batch's last work before it pools the
+// batch's memory.
+struct UseMark {
+    const trids_batch* b;
+    cudaStream_t st;
+    UseMark(const trids_batch* b_, void* stream) : b(b_), st((cudaStream_t)stream) {}
+    ~UseMark() {
+        if (b && b->ev_use) cudaEventRecord(b->ev_use, st);
+    }
+};
+
+// Device blocks of freed batches, kept for the next batches of the same device: a stream of
+// batches then allocates and frees its device memory once instead of once per batch.
+// trids_free_batch waits for the batch's last recorded work before it pools a block, so no
+// launch still reads a block that a new batch takes.  At most kPoolBlocks blocks stay
+// pooled (the smallest goes first); they are released when the process exits.
+constexpr size_t kPoolBlocks = 2;
+struct BlockPool {
+    struct Entry {
+        int device;
+        unsigned char* p;
+        size_t bytes;
+    };
+    std::mutex mu;
+    std::vector<Entry> free;
+};
+inline BlockPool& block_pool() {
+    static BlockPool pool;
+    return pool;
+}
+
+// A pooled block of the device with at least `bytes` (and at most 4 x bytes + 1 MiB, so a
+// small batch does not pin a large block), or nullptr; *cap gets its size.
+unsigned char* pool_take(int device, size_t bytes, size_t* cap) {
+    BlockPool& P = block_pool();
+    std::lock_guard<std::mutex> lock(P.mu);
+    int at = -1;
+    for (size_t k = 0; k < P.free.size(); ++k) {
+        const BlockPool::Entry& e = P.free[k];
+        if (e.device == device && e.bytes >= bytes && e.bytes <= 4 * bytes + (1u << 20) &&
+            (at < 0 || e.bytes < P.free[at].bytes))
+            at = (int)k;
+    }
+    if (at < 0) return nullptr;
+    unsigned char* p = P.free[at].p;
+    *cap = P.free[at].bytes;
+    P.free.erase(P.free.begin() + at);
+    return p;
+}
+
+// Pool a block of the current device (the caller has synchronized it).
+void pool_give(int device, unsigned char* p, size_t bytes) {
+    BlockPool& P = block_pool();
+    std::lock_guard<std::mutex> lock(P.mu);
+    P.free.push_back({device, p, bytes});
+    size_t n_dev = 0;
+    for (const BlockPool::Entry& e : P.free) n_dev += e.device == device;
+    if (n_dev > kPoolBlocks) {   // drop this device's smallest block
+        int at = -1;
+        for (size_t k = 0; k < P.free.size(); ++k)
+            if (P.free[k].device == device && (at < 0 || P.free[k].bytes < P.free[at].bytes)) at = (int)k;
+        cudaFree(P.free[at].p);
+        P.free.erase(P.free.begin() + at);
+    }
 }
 
 int n_sms(int dev) {

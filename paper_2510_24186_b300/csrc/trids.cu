@@ -408,7 +408,8 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
                  o_orig = section(sizeof(int) * A), o_tidx = section(sizeof(int4) * T),
                  o_tu = section(sizeof(float4) * T), o_tp = section(sizeof(float4) * T), o_ipre = section(sizeof(int) * P),
                  o_ient = section(sizeof(uint16_t) * E), o_mask = section(sizeof(uint32_t) * A),
-                 o_cnt = section(4 * sizeof(unsigned int)), o_err = section(2 * sizeof(int));
+                 o_order = section(sizeof(int) * n_lig), o_cnt = section(4 * sizeof(unsigned int)),
+                 o_err = section(2 * sizeof(int));
     std::vector<unsigned char> stage(total, 0);
     unsigned char* hs = stage.data();
     b->hdr.resize(n_lig);
@@ -480,11 +481,18 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
     for (int l = 0; l < n_lig; ++l)
         if (!msg[l].empty()) return fail(TRIDS_EINVAL, "ligand %d: %s", l, msg[l].c_str());
     std::memcpy(hs + o_hdr, b->hdr.data(), sizeof(LigHdr) * n_lig);
-    // 4. one allocation, one copy (a private non-blocking stream: the copy neither waits
-    // for nor stalls kernels on other streams)
-    if (cudaMalloc(&b->d_block, total) != cudaSuccess) {
-        trids_free_batch(b.release());
-        return fail(TRIDS_ENOMEM, "cudaMalloc of %zu bytes failed", total);
+    b->lig_order_h = lig_cost_order(b->hdr);
+    std::memcpy(hs + o_order, b->lig_order_h.data(), sizeof(int) * n_lig);
+    // 4. one allocation (a pooled block of a freed batch if one fits), one copy (a private
+    // non-blocking stream: the copy neither waits for nor stalls kernels on other streams)
+    b->d_block = pool_take(pk->device, total, &b->block_bytes);
+    if (!b->d_block) {
+        if (cudaMalloc(&b->d_block, total) != cudaSuccess) {
+            b->d_block = nullptr;
+            trids_free_batch(b.release());
+            return fail(TRIDS_ENOMEM, "cudaMalloc of %zu bytes failed", total);
+        }
+        b->block_bytes = total;
     }
     {
         cudaStream_t s;
@@ -510,6 +518,12 @@ int trids_pack_ligands(const trids_pocket* pk, int32_t n_lig, const int32_t* n_a
     b->d_ipre = reinterpret_cast<int*>(d + o_ipre);
     b->d_ient = reinterpret_cast<uint16_t*>(d + o_ient);
     b->d_atom_mask = reinterpret_cast<uint32_t*>(d + o_mask);
+    b->d_lig_order = reinterpret_cast<int*>(d + o_order);
+    if (cudaEventCreateWithFlags(&b->ev_use, cudaEventDisableTiming) != cudaSuccess) {
+        b->ev_use = nullptr;
+        trids_free_batch(b.release());
+        return fail(TRIDS_ECUDA, "cudaEventCreateWithFlags failed");
+    }
     b->d_counter = reinterpret_cast<unsigned int*>(d + o_cnt);
     b->d_err = reinterpret_cast<int*>(d + o_err);
     b->dims.upload_bytes = (int64_t)total;
@@ -528,14 +542,25 @@ int trids_free_batch(trids_batch* b) {
     if (b->side) cudaStreamDestroy(b->side);
     if (b->ev_a) cudaEventDestroy(b->ev_a);
     if (b->ev_b) cudaEventDestroy(b->ev_b);
-    cudaFree(b->d_block);   // every packed array, the pop counter and the error words
-    cudaFree(b->d_items); cudaFree(b->d_lig_order); cudaFree(b->d_partials); cudaFree(b->d_mdn);
+    if (b->d_block) {   // every packed array, the ligand order, the pop counter and the error words
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && cur != b->device) cudaSetDevice(b->device);
+        // the batch's last recorded work must be done before a new batch may take its block
+        const cudaError_t e = b->ev_use ? cudaEventSynchronize(b->ev_use) : cudaSuccess;
+        if (e == cudaSuccess) pool_give(b->device, b->d_block, b->block_bytes);
+        else cudaFree(b->d_block);
+    }
+    if (b->ev_use) cudaEventDestroy(b->ev_use);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_partials) cudaFree(b->d_partials);
+    if (b->d_mdn) cudaFree(b->d_mdn);
     delete b;
     return TRIDS_OK;
 }
 
 int trids_set_mdn(trids_batch* b, int32_t n_res, int32_t K, const float* mdn, void* stream) {
     g_err.clear();
+    UseMark use_mark(b, stream);   // the batch's last work, for trids_free_batch
     if (!b) return fail(TRIDS_EINVAL, "batch is NULL");
     if (n_res < 1 || n_res > TRIDS_MAX_RESIDUES) return fail(TRIDS_EINVAL, "n_res %d outside 1..%d", n_res, TRIDS_MAX_RESIDUES);
     if (K < 1 || K > TRIDS_MAX_MDN_K) return fail(TRIDS_EINVAL, "K %d outside 1..%d", K, TRIDS_MAX_MDN_K);
@@ -628,6 +653,7 @@ int trids_score_grad(const trids_pocket* pk, const trids_batch* bc, int32_t pose
                      float* e_inter, float* g_dof, float* g_xyz, const float* e_bar, float* g_w, float* g_radius,
                      void* stream) {
     g_err.clear();
+    UseMark use_mark(bc, stream);   // the batch's last work, for trids_free_batch
     trids_batch* b = const_cast<trids_batch*>(bc);
     if (!pk || !b) return fail(TRIDS_EINVAL, "pocket or batch is NULL");
     if (pk->device != b->device) return fail(TRIDS_EINVAL, "pocket and batch live on different devices");
@@ -684,6 +710,7 @@ int trids_score_grad(const trids_pocket* pk, const trids_batch* bc, int32_t pose
 int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_sample_cfg* cfg, float* dof, float* state,
                  float* energy, void* stream) {
     g_err.clear();
+    UseMark use_mark(bc, stream);   // the batch's last work, for trids_free_batch
     trids_batch* b = const_cast<trids_batch*>(bc);
     if (!pk || !b || !cfg) return fail(TRIDS_EINVAL, "pocket, batch or cfg is NULL");
     if (pk->device != b->device) return fail(TRIDS_EINVAL, "pocket and batch live on different devices");
@@ -713,7 +740,6 @@ int trids_sample(const trids_pocket* pk, const trids_batch* bc, const trids_samp
         (rc = check_device_ptr(c.phase_cycles, "phase_cycles", true)) ||
         (rc = check_device_ptr(c.work_count, "work_count", true)) || (rc = check_terms(pk, b)))
         return rc;
-    if ((rc = ensure_items(b, c.poses))) return rc;
     Layout L;
     const int ts = pk->prm.term_set;
     const bool cnt = c.pair_count != nullptr || c.phase_cycles != nullptr || c.work_count != nullptr;
@@ -842,6 +868,7 @@ int trids_graph_stats(const trids_pocket* pk, int64_t* instantiations, int64_t* 
 int trids_topk(const trids_batch* b, int32_t poses, const float* energy, const float* dof, int32_t k, float rmsd,
                int32_t* idx, float* e_out, void* stream) {
     g_err.clear();
+    UseMark use_mark(b, stream);   // the batch's last work, for trids_free_batch
     if (!b) return fail(TRIDS_EINVAL, "batch is NULL");
     if (poses < 1 || k < 1 || k > 64) return fail(TRIDS_EINVAL, "need poses >= 1 and 1 <= k <= 64");
     if (!(rmsd >= 0.f) || !std::isfinite(rmsd)) return fail(TRIDS_EINVAL, "rmsd must be finite and >= 0");
@@ -862,6 +889,7 @@ int trids_topk(const trids_batch* b, int32_t poses, const float* energy, const f
 int trids_screen_energy(const trids_pocket* pk, const trids_batch* b, int32_t poses, int32_t k,
                         const int32_t* idx, const float* e_inter, float* e_screen, void* stream) {
     g_err.clear();
+    UseMark use_mark(b, stream);   // the batch's last work, for trids_free_batch
     if (!pk || !b) return fail(TRIDS_EINVAL, "pocket or batch is NULL");
     if (pk->device != b->device) return fail(TRIDS_EINVAL, "pocket and batch live on different devices");
     if (poses < 1 || k < 1) return fail(TRIDS_EINVAL, "need poses >= 1 and k >= 1");
@@ -881,6 +909,7 @@ int trids_screen_energy(const trids_pocket* pk, const trids_batch* b, int32_t po
 
 int trids_sync(const trids_batch* b, int32_t poses, const float* state, void* stream, double timeout_ms) {
     g_err.clear();
+    UseMark use_mark(b, stream);   // the batch's last work, for trids_free_batch
     if (!b) return fail(TRIDS_EINVAL, "batch is NULL");
     int rc = device_guard(b->device);
     if (rc) return rc;
@@ -962,6 +991,7 @@ int trids_score_grad_noalloc(const trids_pocket* pk, const trids_batch* b, int32
                              float* energy, float* e_inter, float* g_dof, float* g_xyz, const float* e_bar,
                              float* g_w, float* g_radius, void* stream) {
     g_err.clear();
+    UseMark use_mark(b, stream);   // the batch's last work, for trids_free_batch
     if (!pk || !b) return fail(TRIDS_EINVAL, "pocket or batch is NULL");
     if (pk->device != b->device) return fail(TRIDS_EINVAL, "pocket and batch live on different devices");
     if (poses < 1) return fail(TRIDS_EINVAL, "poses must be >= 1");
