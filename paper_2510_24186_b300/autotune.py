@@ -30,7 +30,7 @@ import torch
 
 from . import api
 
-CELLS = (0.4, 0.5, 0.75, 1.0)
+CELLS = (0.5, 0.75, 1.0)
 WARPS = (20, 24, 28)   # the library caps each at the kernel's compiled maximum
 
 
