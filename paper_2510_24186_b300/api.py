@@ -352,18 +352,23 @@ def sync(batch: Batch, poses: int, state: Optional[torch.Tensor] = None, timeout
 
 def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd: float = 1.0, seed: int = 0,
                   mc_loops: int = 8, warps_per_block: int = 0, stream=None, stats: Optional[dict] = None,
-                  prepare=None, **sample_kw):
+                  prepare=None, lookahead: int = 2, **sample_kw):
     """Screen an iterable of ligand batches (each a tuple of arrays as for Batch) through one
-    pocket.  The next batch is packed on a host thread while the current one samples; the
+    pocket.  A host thread packs the next `lookahead` batches while the current one samples (so
+    a small batch's short pass does not leave the GPU waiting for a large batch's packing); the
     DOF, state and energy buffers stay on the device and are reused.  Yields
     (first ligand id, top-k indices [n, k], top-k energies [n, k]) per batch as numpy arrays.
     Ligand ids (the random-stream ids) run on across batches; each batch is freed on the packing
-    thread once its results are back (its device block then serves a later batch).  stats (optional dict) receives
-    the host-to-device and device-to-host bytes of the last batch; prepare(batch), if given,
-    runs on each packed batch before it samples (e.g. Batch.set_mdn); sample_kw go to sample()."""
+    thread once its results are back (its device block then serves a later batch).  stats
+    (optional dict) receives the host-to-device and device-to-host bytes of the last batch;
+    prepare(batch), if given, runs on each packed batch before it samples (e.g. Batch.set_mdn);
+    sample_kw go to sample()."""
     stats = {} if stats is None else stats
+    import collections
     import concurrent.futures as cf
     _require_cuda()
+    if lookahead < 1:
+        raise ValueError("lookahead must be >= 1")
     st = stream or torch.cuda.current_stream()
     dev = torch.device("cuda", torch.cuda.current_device())
     bufs = {"dof": torch.empty(0, device=dev), "state": torch.empty(0, device=dev),
@@ -377,15 +382,23 @@ def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd:
     it = iter(batches)
     base = 0
     pinned = None
+    # one packing thread: packs (and frees) run in submission order, so only this thread
+    # touches the pocket's list of batches
     with cf.ThreadPoolExecutor(max_workers=1) as ex:
-        nxt = next(it, None)
-        fut = ex.submit(Batch, pocket, *nxt) if nxt is not None else None
-        while fut is not None:
-            b = fut.result()
+        pending = collections.deque()
+
+        def submit_next():
+            nxt = next(it, None)
+            if nxt is not None:
+                pending.append(ex.submit(Batch, pocket, *nxt))
+
+        for _ in range(lookahead):
+            submit_next()
+        while pending:
+            b = pending.popleft().result()
             if prepare is not None:
                 prepare(b)
-            nxt = next(it, None)
-            fut = ex.submit(Batch, pocket, *nxt) if nxt is not None else None
+            submit_next()
             D = b.dof_stride
             dof = view("dof", b.n_lig * poses * D).view(b.n_lig, poses, D)
             state = view("state", b.state_floats(poses))
@@ -405,7 +418,7 @@ def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd:
             stats["d2h_bytes"] = idx_h.numel() * idx_h.element_size() + e_h.numel() * e_h.element_size()
             yield base, idx_h.numpy().copy(), e_h.numpy().copy()
             base += b.n_lig
-            ex.submit(b.close)   # on the packing thread, after the next batch's packing
+            ex.submit(b.close)   # on the packing thread, after the packing already queued
 
 
 def screen_sharded(pocket: Pocket, ligands, poses: int, steps: int, k: int, rmsd: float = 1.0, seed: int = 0,

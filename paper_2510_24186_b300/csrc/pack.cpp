@@ -13,9 +13,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
-#include <functional>
-#include <numeric>
-#include <queue>
+#include <cstring>
 
 #include "trids_internal.h"
 
@@ -23,20 +21,61 @@ namespace trids {
 
 namespace {
 
-struct DisjointSets {
-    std::vector<int> up;
-    explicit DisjointSets(int n) : up(n) { std::iota(up.begin(), up.end(), 0); }
-    int find(int a) {
-        while (up[a] != a) a = up[a] = up[up[a]];
-        return a;
-    }
-    void join(int a, int b) { up[find(a)] = find(b); }
-};
-
 std::string fmt(const char* f, int a, int b = 0) {
     char buf[160];
     std::snprintf(buf, sizeof buf, f, a, b);
     return buf;
+}
+
+}  // namespace
+
+namespace {
+
+constexpr int kFmax = kTmax + 1;   // a connected ligand with <= kTmax rotatable bonds has <= kTmax + 1 fragments
+
+// The fragment tree's working arrays (fixed size: no heap traffic per ligand, so that many
+// ligands pack in parallel without contending for the allocator).
+struct FragTree {
+    int nf = 0;
+    int n_nbr[kFmax];
+    int nbr_f[kFmax][kFmax];   // neighbour fragments, ascending
+    int nbr_a[kFmax][kFmax];   // ... and this fragment's atom of the joining bond
+    int other_atom[kFmax][kFmax];
+    int parent[kFmax], tor_of[kFmax], first[kFmax], sub[kFmax], count[kFmax];
+};
+
+// Eccentricity of fragment s in the fragment tree.
+int frag_height(const FragTree& F, int s) {
+    int d[kFmax], q[kFmax];
+    for (int f = 0; f < F.nf; ++f) d[f] = -1;
+    int head = 0, tail = 0, h = 0;
+    d[s] = 0;
+    q[tail++] = s;
+    while (head < tail) {
+        const int u = q[head++];
+        h = std::max(h, d[u]);
+        for (int k = 0; k < F.n_nbr[u]; ++k) {
+            const int v = F.nbr_f[u][k];
+            if (d[v] < 0) { d[v] = d[u] + 1; q[tail++] = v; }
+        }
+    }
+    return h;
+}
+
+// DFS pre-order layout from fragment u: its atoms (ascending input index), then its
+// children in ascending fragment number.
+void frag_dfs(FragTree& F, int u, int n, const int* fragof, std::vector<int>* perm) {
+    F.first[u] = (int)perm->size();
+    for (int i = 0; i < n; ++i)
+        if (fragof[i] == u) perm->push_back(i);
+    F.sub[u] = F.count[u];
+    for (int k = 0; k < F.n_nbr[u]; ++k) {
+        const int v = F.nbr_f[u][k];
+        if (F.parent[v] == u) {
+            frag_dfs(F, v, n, fragof, perm);
+            F.sub[u] += F.sub[v];
+        }
+    }
 }
 
 }  // namespace
@@ -51,7 +90,8 @@ std::string pack_ligand(int n, const float* xyz, const int32_t* type, int n_type
             return fmt("atom %d has a non-finite coordinate", i);
     }
     // bond matrix: 0 none, 1 rigid, 2 rotatable
-    std::vector<uint8_t> bm(n * n, 0);
+    uint8_t bm[kLmax * kLmax];
+    std::memset(bm, 0, (size_t)n * n);
     int n_rot = 0;
     for (int b = 0; b < nb; ++b) {
         int a0 = bonds[2 * b], a1 = bonds[2 * b + 1];
@@ -64,107 +104,124 @@ std::string pack_ligand(int n, const float* xyz, const int32_t* type, int n_type
     }
     if (n_rot > kTmax) return fmt("%d rotatable bonds (at most %d)", n_rot, kTmax);
 
-    // bond distances: breadth-first search from every atom over adjacency lists
-    const int INF = 1 << 20;
-    std::vector<std::vector<int>> adj(n);
+    // adjacency as bit sets; atoms within three bonds of each other (walks of up to three
+    // bonds reach exactly the atoms at bond distance <= 3)
+    constexpr int kW = (kLmax + 63) / 64;
+    uint64_t adj[kLmax][kW], near2[kLmax][kW], near3[kLmax][kW];
+    std::memset(adj, 0, sizeof adj);
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j)
-            if (bm[i * n + j]) adj[i].push_back(j);
-    std::vector<int> D(n * n, INF);
-    std::vector<int> frontier;
-    frontier.reserve(n);
-    for (int s = 0; s < n; ++s) {
-        int* row = &D[s * n];
-        row[s] = 0;
-        frontier.assign(1, s);
-        for (size_t h = 0; h < frontier.size(); ++h) {
-            const int u = frontier[h];
-            for (int v : adj[u])
-                if (row[v] == INF) { row[v] = row[u] + 1; frontier.push_back(v); }
+            if (bm[i * n + j]) adj[i][j >> 6] |= 1ull << (j & 63);
+    auto spread = [&](const uint64_t (*from)[kW], uint64_t (*to)[kW]) {
+        for (int i = 0; i < n; ++i) {
+            for (int w = 0; w < kW; ++w) to[i][w] = from[i][w];
+            for (int w = 0; w < kW; ++w)
+                for (uint64_t m = adj[i][w]; m; m &= m - 1) {
+                    const int j = 64 * w + __builtin_ctzll(m);
+                    for (int x = 0; x < kW; ++x) to[i][x] |= from[j][x];
+                }
         }
+    };
+    spread(adj, near2);     // within two bonds (and the atom itself through its neighbours)
+    spread(near2, near3);   // within three bonds
+    // connectivity: the atoms reachable from atom 0
+    {
+        uint64_t seen[kW] = {0}, front[kW] = {0};
+        seen[0] = front[0] = 1ull;
+        for (bool grew = true; grew;) {
+            uint64_t next[kW] = {0};
+            for (int w = 0; w < kW; ++w)
+                for (uint64_t m = front[w]; m; m &= m - 1) {
+                    const int j = 64 * w + __builtin_ctzll(m);
+                    for (int x = 0; x < kW; ++x) next[x] |= adj[j][x];
+                }
+            grew = false;
+            for (int w = 0; w < kW; ++w) {
+                front[w] = next[w] & ~seen[w];
+                seen[w] |= front[w];
+                grew |= front[w] != 0;
+            }
+        }
+        for (int i = 1; i < n; ++i)
+            if (!((seen[i >> 6] >> (i & 63)) & 1ull)) return fmt("atom %d is not connected to atom 0", i);
     }
-    for (int i = 1; i < n; ++i)
-        if (D[i] >= INF) return fmt("atom %d is not connected to atom 0", i);
 
     // fragments: union over rigid bonds, numbered by their smallest atom index
-    DisjointSets ds(n);
+    int up[kLmax];
+    for (int i = 0; i < n; ++i) up[i] = i;
+    auto find = [&](int a) {
+        while (up[a] != a) a = up[a] = up[up[a]];
+        return a;
+    };
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j)
-            if (bm[i * n + j] == 1) ds.join(i, j);
-    std::vector<int> rep_to_frag(n, -1), fragof(n);
+            if (bm[i * n + j] == 1) up[find(i)] = find(j);
+    int rep_to_frag[kLmax], fragof[kLmax];
+    for (int i = 0; i < n; ++i) rep_to_frag[i] = -1;
     int nf = 0;
     for (int i = 0; i < n; ++i) {   // ascending i: first atom seen is the fragment minimum
-        int r = ds.find(i);
+        int r = find(i);
         if (rep_to_frag[r] < 0) rep_to_frag[r] = nf++;
         fragof[i] = rep_to_frag[r];
     }
     if (n_rot != nf - 1) return "a rotatable bond lies in a ring (the fragments do not form a tree)";
     // fragment tree edges with the bond atoms on each side
-    std::vector<std::vector<std::pair<int, int>>> nbr(nf);  // (other fragment, my atom)
-    std::vector<std::vector<int>> other_atom(nf, std::vector<int>(nf, -1));
+    FragTree F;
+    F.nf = nf;
+    for (int f = 0; f < nf; ++f) {
+        F.n_nbr[f] = 0;
+        F.count[f] = 0;
+        for (int g = 0; g < nf; ++g) F.other_atom[f][g] = -1;
+    }
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j)
             if (bm[i * n + j] == 2) {
                 int fi = fragof[i], fj = fragof[j];
                 if (fi == fj) return "a rotatable bond lies inside a rigid fragment (ring)";
-                if (other_atom[fi][fj] >= 0 && other_atom[fi][fj] != i)
+                if (F.other_atom[fi][fj] >= 0 && F.other_atom[fi][fj] != i)
                     return "two rotatable bonds join the same pair of fragments (ring)";
-                if (other_atom[fi][fj] < 0) nbr[fi].push_back({fj, i});
-                other_atom[fi][fj] = i;
+                if (F.other_atom[fi][fj] < 0) {
+                    F.nbr_f[fi][F.n_nbr[fi]] = fj;
+                    F.nbr_a[fi][F.n_nbr[fi]++] = i;
+                }
+                F.other_atom[fi][fj] = i;
             }
-    for (auto& v : nbr) std::sort(v.begin(), v.end());
+    for (int f = 0; f < nf; ++f) {   // neighbours by ascending fragment (each appears once)
+        for (int x = 1; x < F.n_nbr[f]; ++x)
+            for (int y = x; y > 0 && F.nbr_f[f][y - 1] > F.nbr_f[f][y]; --y) {
+                std::swap(F.nbr_f[f][y - 1], F.nbr_f[f][y]);
+                std::swap(F.nbr_a[f][y - 1], F.nbr_a[f][y]);
+            }
+    }
 
     // root: smallest height (eccentricity in the fragment tree), ties by fragment number
-    auto height = [&](int s) {
-        std::vector<int> d(nf, -1);
-        std::queue<int> q;
-        d[s] = 0;
-        q.push(s);
-        int h = 0;
-        while (!q.empty()) {
-            int u = q.front();
-            q.pop();
-            h = std::max(h, d[u]);
-            for (auto& e : nbr[u])
-                if (d[e.first] < 0) { d[e.first] = d[u] + 1; q.push(e.first); }
-        }
-        return h;
-    };
-    int root = 0, best = INF;
+    int root = 0, best = 1 << 20;
     for (int f = 0; f < nf; ++f) {
-        int h = height(f);
+        int h = frag_height(F, f);
         if (h < best) { best = h; root = f; }
     }
     // BFS: torsion numbers and parents
-    std::vector<int> parent(nf, -2), tor_of(nf, -1), bfs;
-    parent[root] = -1;
-    bfs.push_back(root);
-    for (size_t h = 0; h < bfs.size(); ++h) {
+    int bfs[kFmax], nbfs = 0;
+    for (int f = 0; f < nf; ++f) { F.parent[f] = -2; F.tor_of[f] = -1; }
+    F.parent[root] = -1;
+    bfs[nbfs++] = root;
+    for (int h = 0; h < nbfs; ++h) {
         int u = bfs[h];
-        for (auto& e : nbr[u])
-            if (parent[e.first] == -2) {
-                parent[e.first] = u;
-                tor_of[e.first] = (int)bfs.size() - 1;
-                bfs.push_back(e.first);
+        for (int k = 0; k < F.n_nbr[u]; ++k) {
+            const int v = F.nbr_f[u][k];
+            if (F.parent[v] == -2) {
+                F.parent[v] = u;
+                F.tor_of[v] = nbfs - 1;
+                bfs[nbfs++] = v;
             }
+        }
     }
     // DFS pre-order layout and subtree atom counts
-    std::vector<int> first(nf), count(nf, 0), sub(nf, 0);
-    for (int i = 0; i < n; ++i) count[fragof[i]]++;
+    for (int i = 0; i < n; ++i) F.count[fragof[i]]++;
     out->perm.clear();
-    std::function<void(int)> dfs = [&](int u) {
-        first[u] = (int)out->perm.size();
-        for (int i = 0; i < n; ++i)
-            if (fragof[i] == u) out->perm.push_back(i);
-        sub[u] = count[u];
-        for (auto& e : nbr[u])
-            if (parent[e.first] == u) {
-                dfs(e.first);
-                sub[u] += sub[e.first];
-            }
-    };
-    dfs(root);
-    std::vector<int> packed_of(n);
+    out->perm.reserve(n);
+    frag_dfs(F, root, n, fragof, &out->perm);
+    int packed_of[kLmax];
     for (int k = 0; k < n; ++k) packed_of[out->perm[k]] = k;
 
     int T = nf - 1;
@@ -173,18 +230,18 @@ std::string pack_ligand(int n, const float* xyz, const int32_t* type, int n_type
     out->frag.assign(n, 0);
     for (int k = 0; k < n; ++k) {
         int f = fragof[out->perm[k]];
-        out->frag[k] = (f == root) ? 0 : tor_of[f] + 1;
+        out->frag[k] = (f == root) ? 0 : F.tor_of[f] + 1;
     }
     out->tp.assign(T, 0); out->th.assign(T, 0); out->tpar.assign(T, -1);
     out->sb.assign(T, 0); out->se.assign(T, 0);
     for (int f = 0; f < nf; ++f) {
         if (f == root) continue;
-        int k = tor_of[f], p = parent[f];
-        out->tp[k] = packed_of[other_atom[p][f]];
-        out->th[k] = packed_of[other_atom[f][p]];
-        out->tpar[k] = (p == root) ? -1 : tor_of[p];
-        out->sb[k] = first[f];
-        out->se[k] = first[f] + sub[f];
+        int k = F.tor_of[f], p = F.parent[f];
+        out->tp[k] = packed_of[F.other_atom[p][f]];
+        out->th[k] = packed_of[F.other_atom[f][p]];
+        out->tpar[k] = (p == root) ? -1 : F.tor_of[p];
+        out->sb[k] = F.first[f];
+        out->se[k] = F.first[f] + F.sub[f];
     }
     double s[3] = {0, 0, 0};
     int cnt = 0;
@@ -194,11 +251,16 @@ std::string pack_ligand(int n, const float* xyz, const int32_t* type, int n_type
             ++cnt;
         }
     for (int d = 0; d < 3; ++d) out->c[d] = s[d] / cnt;
+    // intra pairs: different fragments, at least four bonds apart
     out->pairs.clear();
-    for (int a = 0; a < n; ++a)
-        for (int b = a + 1; b < n; ++b)
-            if (out->frag[a] != out->frag[b] && D[out->perm[a] * n + out->perm[b]] >= 4)
+    for (int a = 0; a < n; ++a) {
+        const int ia = out->perm[a];
+        for (int b = a + 1; b < n; ++b) {
+            const int ib = out->perm[b];
+            if (out->frag[a] != out->frag[b] && !((near3[ia][ib >> 6] >> (ib & 63)) & 1ull))
                 out->pairs.push_back({a, b});
+        }
+    }
     return "";
 }
 
