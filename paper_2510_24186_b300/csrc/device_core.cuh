@@ -484,10 +484,11 @@ __device__ __forceinline__ float lg2_approx(float x) {
 }
 
 // The TRIDS atom-pair terms (pair_trids) for the two candidates of one candidate-list
-// word, branch-free on the packed FP32 pipe: every term is evaluated and masked (cutoff,
-// r < 10 for E_long, r < d_clash, donor-acceptor pair with r < 3.4, r < 5 for the
-// atom-pair E_MDN) by
-// multiplying with 0/1, exact for the finite values every candidate gives.  exp and log
+// word, branch-free on the packed FP32 pipe: every term is evaluated and masked (r^2 <
+// min(cutoff^2, 100), which also ends E_long at 10 A; r < d_clash; donor-acceptor pair with
+// r < 3.4; r < 5 for the atom-pair E_MDN) by multiplying with 0/1, exact for the finite
+// values every candidate gives.  r^2 carries 1e-12 per square term (keeps 1/r finite at r =
+// 0).  exp and log
 // go through ex2 / lg2.  mb selects the candidate's donor/acceptor flag bits (low entry;
 // shifted by 16 for the high entry).  gmm (term set 1, ligand-pocket pairs only; else
 // null): the ligand atom type's row of (pi, mu, -1/(2 sigma^2), 1/sigma^2) by pocket type.
@@ -504,10 +505,12 @@ __device__ __forceinline__ void trids_x2(uint32_t wd, const float4* __restrict__
     const float2 qa = __ffma2_rn(make_float2(a.z, a.w), pm, nzr);      // (z_j - z_i, -(R_i + R_j))
     const float2 pc = __fadd2_rn(make_float2(c.x, c.y), nxy);
     const float2 qc = __ffma2_rn(make_float2(c.z, c.w), pm, nzr);
-    const float2 sa = __fmul2_rn(pa, pa), sc = __fmul2_rn(pc, pc);
-    const float2 r2 = make_float2(fmaf(qa.x, qa.x, sa.x) + sa.y, fmaf(qc.x, qc.x, sc.x) + sc.y);
-    const float2 in = make_float2(r2.x < cut2 ? 1.f : 0.f, r2.y < cut2 ? 1.f : 0.f);
-    const float2 rr = __fadd2_rn(r2, make_float2(1e-12f, 1e-12f));
+    const float2 tiny = make_float2(1e-12f, 1e-12f);
+    const float2 sa = __ffma2_rn(pa, pa, tiny), sc = __ffma2_rn(pc, pc, tiny);
+    const float2 rr = make_float2(fmaf(qa.x, qa.x, sa.x) + sa.y, fmaf(qc.x, qc.x, sc.x) + sc.y);
+    // one mask for every term: E_long ends at 10 A, E_clash and E_Hbond far inside it
+    const float c2 = fminf(cut2, 100.f);
+    const float2 in = make_float2(rr.x < c2 ? 1.f : 0.f, rr.y < c2 ? 1.f : 0.f);
     const float2 ri = make_float2(rsqrt_normal(rr.x), rsqrt_normal(rr.y));
     const float2 r = __fmul2_rn(rr, ri);
     const float2 rs = make_float2(-qa.y, -qc.y);                            // R_i + R_j
@@ -515,7 +518,7 @@ __device__ __forceinline__ void trids_x2(uint32_t wd, const float4* __restrict__
     // E_long: -exp(-(r - R_i - R_j - 3)^2 / 4); dE/dr = 0.5 gl z
     const float2 z = __fadd2_rn(r, make_float2(qa.y - 3.f, qc.y - 3.f));
     const float2 al = __fmul2_rn(__fmul2_rn(z, z), make_float2(-0.25f * kL2e, -0.25f * kL2e));
-    const float2 gl = make_float2(r.x < 10.f ? ex2_approx(al.x) : 0.f, r.y < 10.f ? ex2_approx(al.y) : 0.f);
+    const float2 gl = make_float2(ex2_approx(al.x), ex2_approx(al.y));
     float2 e = __fmul2_rn(make_float2(-w[1], -w[1]), gl);
     float2 d = __fmul2_rn(__fmul2_rn(make_float2(0.5f * w[1], 0.5f * w[1]), gl), z);
     // E_clash: -ln(max(r, 0.5) / d_clash) for r < d_clash (2.6 for a donor-acceptor pair,
@@ -559,7 +562,7 @@ __device__ __forceinline__ void trids_x2(uint32_t wd, const float4* __restrict__
     axy = __ffma2_rn(make_float2(f.y, f.y), pc, axy); az = fmaf(f.y, qc.x, az);
     ax = axy.x; ay = axy.y;
     if (COUNT) {
-        const bool ia = r2.x < cut2, ic = r2.y < cut2;
+        const bool ia = rr.x < cut2, ic = rr.y < cut2;
         wc.pairs += (ia + ic) * cw;
         wc.clash += ((ia && mcl.x != 0.f) + (ic && mcl.y != 0.f)) * cw;
         wc.hb += ((ia && mh.x != 0.f) + (ic && mh.y != 0.f)) * cw;

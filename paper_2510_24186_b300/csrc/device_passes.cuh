@@ -185,10 +185,10 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
             const uint32_t f_hb = ((fi & 2u) << 1) | ((fi & 4u) >> 1);
             float eb = 0.f;
             float2 eb2 = make_float2(0.f, 0.f);
-            // two halves of four candidates: unrolled in the plain Vina-form kernels; the
-            // TRIDS evaluation and the general kernels (other update rules, grid maps) keep
-            // one half per iteration (unrolled they spill and run slower)
-            constexpr int kHalves = (TS == TRIDS_TERMS_VINA5 && !PARAMS && !MAPS) ? 2 : 1;
+            // two halves of four candidates: unrolled in the plain Vina-form and atom-pair TRIDS
+            // kernels; the residue-level TRIDS kernel and the general kernels (other update
+            // rules, grid maps) keep one half per iteration (unrolled they run slower)
+            constexpr int kHalves = (TS != TRIDS_TERMS_TRIDS_RES && !PARAMS && !MAPS) ? 2 : 1;
 #pragma unroll kHalves
             for (int hv = 0; hv < 2; ++hv) {
                 const uint32_t wv[2] = {hv ? vc.z : vc.x, hv ? vc.w : vc.y};
