@@ -448,12 +448,12 @@ __device__ __forceinline__ void vina_x2(uint32_t wd, const float4* __restrict__ 
     ng = __ffma2_rn(__fmul2_rn(b, K.w1), g2, ng);                       // + w1 b g2
     ng = __ffma2_rn(K.n2, dn, ng);                                      // - 2 w2 dn
     if constexpr (ONE) {
-        const float2 hr = make_float2(fmaf(d.x, F.nb, F.a), fmaf(d.y, F.nb, F.a));   // a - b d
+        const float2 hr = __ffma2_rn(d, make_float2(F.nb, F.nb), make_float2(F.a, F.a));   // a - b d
         const float2 hy = make_float2(__saturatef(hr.x), __saturatef(hr.y));
         const float2 ih = make_float2(hy.x == hr.x ? 1.f : 0.f, hy.y == hr.y ? 1.f : 0.f);
         const float2 wf = make_float2((wd & F.m) ? F.w : 0.f, (wd & (F.m << 16)) ? F.w : 0.f);
         e = __ffma2_rn(wf, hy, e);
-        ng = __ffma2_rn(ih, make_float2(wf.x * F.b, wf.y * F.b), ng);  // + w b inside the ramp
+        ng = __ffma2_rn(ih, __fmul2_rn(wf, make_float2(F.b, F.b)), ng);  // + w b inside the ramp
     } else {
         const float2 hr = __ffma2_rn(d, K.m1, K.p15);                  // 1.5 - d
         const float2 hy = make_float2(__saturatef(hr.x), __saturatef(hr.y));

@@ -145,12 +145,16 @@ __device__ float pairs_warp(const DevBatch& B, const DevPocket& pk, const Smem& 
         const uint4* ib = reinterpret_cast<const uint4*>(ient + 8 * ipb);
         for (int blk = lo; blk < hi; ++blk) {
             if (blk == nxt) {                      // move to the atom owning block blk
-                W.rec[i + lane] = make_float4(ax, ay, az, 0.f);
-                ax = ay = az = 0.f;
-                do { ++i; } while (W.meta[i + 1].w == blk);
+                // the new atom's records are read before the old atom's partial is stored, so
+                // that the search's last prefix read is the new nxt (no reload after the store)
+                const int io = i;
+                int nx;
+                do { ++i; nx = W.meta[i + 1].w; } while (nx == blk);
                 first = blk;                       // a lane enters an atom at its first block
-                nxt = W.meta[i + 1].w;
+                nxt = nx;
                 const int4 mt = W.meta[i];             // (cell list, blocks | flags | type, intra list, prefix)
+                W.rec[io + lane] = make_float4(ax, ay, az, 0.f);
+                ax = ay = az = 0.f;
                 cbw = mt.y;
                 cbk = cbw & 0xffffff;
                 ti = cbw >> 27;
@@ -464,6 +468,7 @@ __device__ float residue_warp(const DevBatch& B, const DevPocket& pk, const Smem
                 const float rinv = rsqrt_normal(fmaxf(best, 1e-12f));
                 const float d = best * rinv;
                 float P = 0.f, dP = 0.f;
+#pragma unroll 4   // the kernel-row loads of four kernels in flight together
                 for (int k = 0; k < K; ++k) {
                     const float4 g = __ldg(&kern[r * K + k]);   // (pi, mu, -log2(e)/(2 sigma^2), 1/sigma^2)
                     const float z = d - g.y;
