@@ -23,6 +23,7 @@ import hashlib
 import json
 import math
 import os
+import select
 import statistics
 import subprocess
 import sys
@@ -122,8 +123,12 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                       "-lms", "50", "-i", str(self.index)], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
+            # wait for the first sample (taken before the timed region; dropped), so that the
+            # sampler is running when the region starts
+            if select.select([self.p.stdout], [], [], 10.0)[0]:
+                self.p.stdout.readline()
         except Exception:
             self.p = None
         return self
