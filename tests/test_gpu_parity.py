@@ -333,6 +333,23 @@ def test_batched_screening_full_size_sampled(api):
             np.testing.assert_array_equal(idx[l], ref)
 
 
+def test_trids_atom_pair_terms_full_size_sampled(api):
+    """The benchmark's workload with the TRIDS terms and the atom-pair E_MDN (term set 1,
+    10 A cutoff, K = 4; 1,024 ligands x 128 poses x 50 evaluations, persistent launch in a
+    CUDA graph): 96 seeded poses traced and checked per evaluation against the oracle."""
+    w = synth.workload("batched_screening")
+    sp, pk, b = make(api, w, term_set=1)
+    P, S, seed = w.poses, w.steps, 2102
+    rng = np.random.default_rng(21)
+    poses_g = np.sort(rng.choice(b.n_lig * P, 96, replace=False))
+    out = api.sample(pk, b, P, S, mc_loops=w.mc_loops, seed=seed, trace_poses=poses_g.tolist())
+    assert api.sync(b, P, out["state"], timeout_ms=120000) == 0
+    st = check_trace(out["trace"].cpu().numpy(), poses_g, P, oracle_ligands(w.ligands), *pocket_arrays(w.pocket),
+                     oracle_params(sp), cfg_for(w, seed), S, w.mc_loops, seed, out["dof"].cpu().numpy(),
+                     out["energy"].cpu().numpy())
+    report(st, "TRIDS atom-pair terms, batched screening, sampled")
+
+
 def test_adjoint_check_full_size_score_sampled(api):
     """Adjoint-check workload at full size (256 ligands x 64 random poses) through the autograd Function:
     energies, DOF gradients (t, q, theta) and parameter gradients against the oracle on a
