@@ -22,12 +22,16 @@
  *   grid maps              pinned: trilinear reproduces linear fields exactly, grid-point values
  *                          equal the direct one-atom energy, FD of the interpolated energy,
  *                          convergence to the direct sum as the spacing shrinks
- *   residue E_MDN          pinned: closed forms (tests/golden/terms.txt), a numpy brute force of
+ *   residue E_MDN          pinned: closed forms (tests/golden/residue_mdn.txt), a numpy brute force of
  *                          the residue minimum, FD, rigid-motion invariance, argmin tie rule
  *   or_opt_step            pinned: torch.optim.Adam / AdamW / RMSprop / Adagrad / SGD
  *   or_init/perturb/metro  pinned: Philox pin + Shoemake uniformity + beta property
- *   or_sample              pinned through its parts; end-to-end trajectories are chaotic,
- *                          so the whole trajectory is "parity unpinned" beyond per-step checks
+ *   or_sample              pinned: the Monte-Carlo loop (save, perturb, moment reset, accept
+ *                          or restore) by a two-loop one-atom trajectory worked without the
+ *                          oracle (numpy terms, torch.optim.Adam, raw Philox words) and by a
+ *                          replay from the pinned parts, bit for bit, on 1-atom and T = 3-5
+ *                          ligands; end-to-end trajectories are chaotic, so a whole sampled
+ *                          trajectory is "parity unpinned" beyond the per-step checks
  *   or_topk                pinned: brute-force enumeration on tiny inputs
  *   or_screen_energy       pinned: hand-computed values (w_tor = 0.01), the w_tor = 0 and
  *                          N_tor = 0 identities, the sign of the torsion penalty
