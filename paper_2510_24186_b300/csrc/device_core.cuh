@@ -242,7 +242,8 @@ __device__ bool stage_block(unsigned char* smem, const DevPocket& pk, size_t par
 //                       same values
 //   tor TorState[32]    lane k's torsion angle, moments and saved angle
 //                       (kept in shared memory, the state holds no registers across the pair
-//                       loop: the sampler fits 96 registers per thread, 20 warps per SM)
+//                       loop, so the plain Vina-form sampler runs 28 warps per SM at 72
+//                       registers per thread)
 //   hdr LigHdr          the pose's ligand header (sampler kernels)
 //   clk u64[7]          per-phase cycle sums and the last lap's time (counting sampler)
 //   grs float[kNT][32]  per-lane dE/dR_a (parameter-gradient kernels only)
