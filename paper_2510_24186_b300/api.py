@@ -355,12 +355,14 @@ def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd:
                   prepare=None, lookahead: int = 2, **sample_kw):
     """Screen an iterable of ligand batches (each a tuple of arrays as for Batch) through one
     pocket.  A host thread packs the next `lookahead` batches while the current one samples (so
-    a small batch's short pass does not leave the GPU waiting for a large batch's packing); the
-    DOF, state and energy buffers stay on the device and are reused.  Yields
-    (first ligand id, top-k indices [n, k], top-k energies [n, k]) per batch as numpy arrays.
-    Ligand ids (the random-stream ids) run on across batches; each batch is freed on the packing
-    thread once its results are back (its device block then serves a later batch).  stats
-    (optional dict) receives the host-to-device and device-to-host bytes of the last batch;
+    a small batch's short pass does not leave the GPU waiting for a large batch's packing), and
+    each batch's sampling is queued on the stream before the previous batch's results are
+    waited for (so the GPU does not idle while the host takes them); the DOF, state and energy
+    buffers stay on the device and are reused in stream order.  Yields (first ligand id, top-k
+    indices [n, k], top-k energies [n, k]) per batch, in order, as numpy arrays.  Ligand ids
+    (the random-stream ids) run on across batches; each batch is freed on the packing thread
+    once its results are back (its device block then serves a later batch).  stats (optional
+    dict) receives the host-to-device and device-to-host bytes of the last batch;
     prepare(batch), if given, runs on each packed batch before it samples (e.g. Batch.set_mdn);
     sample_kw go to sample()."""
     stats = {} if stats is None else stats
@@ -381,7 +383,9 @@ def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd:
 
     it = iter(batches)
     base = 0
-    pinned = None
+    # pinned result buffers, one pair per batch in flight: batch n's copies land in slot n % 2,
+    # which batch n + 2 reuses only after batch n's results have been taken
+    slots = [None, None]
     # one packing thread: packs (and frees) run in submission order, so only this thread
     # touches the pocket's list of batches
     with cf.ThreadPoolExecutor(max_workers=1) as ex:
@@ -392,33 +396,51 @@ def screen_stream(pocket: Pocket, batches, poses: int, steps: int, k: int, rmsd:
             if nxt is not None:
                 pending.append(ex.submit(Batch, pocket, *nxt))
 
+        def finish(q):
+            q_base, q_batch, idx_h, e_h, done = q
+            done.synchronize()
+            stats["h2d_bytes"] = q_batch.upload_bytes
+            stats["d2h_bytes"] = idx_h.numel() * idx_h.element_size() + e_h.numel() * e_h.element_size()
+            out = (q_base, idx_h.numpy().copy(), e_h.numpy().copy())
+            ex.submit(q_batch.close)   # on the packing thread, after the packing already queued
+            return out
+
         for _ in range(lookahead):
             submit_next()
+        prev = None
+        n = 0
         while pending:
             b = pending.popleft().result()
             if prepare is not None:
                 prepare(b)
             submit_next()
             D = b.dof_stride
-            dof = view("dof", b.n_lig * poses * D).view(b.n_lig, poses, D)
-            state = view("state", b.state_floats(poses))
-            energy = view("energy", b.n_lig * poses).view(b.n_lig, poses)
             with torch.cuda.stream(st):
+                # allocated on the sampling stream: a buffer replaced here while the previous
+                # batch still uses it goes back to the allocator in that stream's order
+                dof = view("dof", b.n_lig * poses * D).view(b.n_lig, poses, D)
+                state = view("state", b.state_floats(poses))
+                energy = view("energy", b.n_lig * poses).view(b.n_lig, poses)
                 sample(pocket, b, poses, steps, mc_loops=mc_loops, seed=seed, lig_base=base, dof=dof, state=state,
                        energy=energy, warps_per_block=warps_per_block, stream=st, **sample_kw)
                 idx, e = topk(b, energy, dof, k, rmsd, stream=st)
-                if pinned is None or pinned[0].shape != idx.shape:
-                    pinned = (torch.empty(idx.shape, dtype=idx.dtype, pin_memory=True),
-                              torch.empty(e.shape, dtype=e.dtype, pin_memory=True))
-                idx_h, e_h = pinned
+                s = n & 1
+                if slots[s] is None or slots[s][0].shape != idx.shape:
+                    slots[s] = (torch.empty(idx.shape, dtype=idx.dtype, pin_memory=True),
+                                torch.empty(e.shape, dtype=e.dtype, pin_memory=True))
+                idx_h, e_h = slots[s]
                 idx_h.copy_(idx, non_blocking=True)
                 e_h.copy_(e, non_blocking=True)
-            st.synchronize()
-            stats["h2d_bytes"] = b.upload_bytes
-            stats["d2h_bytes"] = idx_h.numel() * idx_h.element_size() + e_h.numel() * e_h.element_size()
-            yield base, idx_h.numpy().copy(), e_h.numpy().copy()
+                done = torch.cuda.Event()
+                done.record(st)
+            cur = (base, b, idx_h, e_h, done)
             base += b.n_lig
-            ex.submit(b.close)   # on the packing thread, after the packing already queued
+            n += 1
+            if prev is not None:
+                yield finish(prev)       # the previous batch, while this one samples
+            prev = cur
+        if prev is not None:
+            yield finish(prev)
 
 
 def screen_sharded(pocket: Pocket, ligands, poses: int, steps: int, k: int, rmsd: float = 1.0, seed: int = 0,
