@@ -33,7 +33,7 @@ def test_host_pack_matches_oracle_bit_exact(orc):
         np.testing.assert_array_equal(a, orc.topology(ol))
 
 
-@pytest.mark.parametrize("case", ["ring_rot", "disconnected", "dup", "type", "nan", "big", "self"])
+@pytest.mark.parametrize("case", ["ring_rot", "disconnected", "dup", "type", "nan", "big", "self", "empty"])
 def test_host_pack_rejects_bad_ligands(case):
     lg = synth.workload("single_ligand").ligands[0]
     xyz, t, b, r = lg.xyz.copy(), lg.type.copy(), lg.bonds.copy(), lg.rotatable.copy()
@@ -54,6 +54,9 @@ def test_host_pack_rejects_bad_ligands(case):
     elif case == "self":
         b = np.vstack([b, [[3, 3]]])
         r = np.concatenate([r, [0]])
+    elif case == "empty":                       # a ligand without atoms
+        xyz, t = np.zeros((0, 3), np.float32), np.zeros(0, np.int32)
+        b, r = np.zeros((0, 2), np.int32), np.zeros(0, np.uint8)
     with pytest.raises(_lib.TridsError) as e:
         api.pack_topology(xyz, t, b, r)
     assert e.value.code == _lib.EINVAL
@@ -123,3 +126,22 @@ def test_python_api_fails_loudly_without_cuda():
     sp = api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, 8.0)
     with pytest.raises(RuntimeError, match="CUDA"):
         api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
+
+
+@pytest.mark.parametrize("n_atoms", [0, -1, 8192])
+def test_pocket_size_outside_the_limits_is_rejected_without_a_gpu(n_atoms):
+    """An empty pocket and one beyond the 13-bit candidate index fail on the host, before
+    any device work."""
+    from paper_2510_24186_b300 import api
+    L = _lib.lib()
+    sp = api.ScoreParams(0, synth.TYPE_RADIUS, synth.TYPE_FLAGS, synth.VINA_WEIGHTS, 8.0)
+    n = max(n_atoms, 1)
+    xyz = np.zeros((n, 3), np.float32)
+    ty = np.zeros(n, np.int32)
+    c, size = (C.c_float * 3)(0, 0, 0), (C.c_float * 3)(22.5, 22.5, 22.5)
+    cp = sp.to_c()
+    out = C.c_void_p()
+    rc = L.trids_make_pocket(xyz.ctypes.data, ty.ctypes.data, n_atoms, C.byref(c), C.byref(size), 0.0,
+                             C.byref(cp), C.byref(out))
+    assert rc == _lib.EINVAL and out.value is None
+    assert b"atoms" in L.trids_last_error()

@@ -85,3 +85,43 @@ def test_pocket_size_limit_is_enforced(api):
     xyz = rng.uniform(-60, 60, (8192, 3))
     with pytest.raises(TridsError, match="8191"):
         api.Pocket(xyz, np.zeros(8192, np.int32), np.zeros(3), np.full(3, 10.0), score_params(0))
+
+
+def test_empty_and_degenerate_sizes_are_rejected(api):
+    """Empty inputs and sizes outside the documented ranges fail with TRIDS_EINVAL on the
+    host, before any launch, and leave the pocket and the batch usable: a batch without
+    ligands, a ligand without atoms, zero poses, zero evaluations or loops, an empty step
+    range, k outside 1..64; a stream without batches yields nothing."""
+    from paper_2510_24186_b300 import _lib
+    w = synth.workload("single_ligand")
+    sp = score_params(0, cutoff=8.0)
+    pk = api.Pocket(w.pocket.xyz, w.pocket.type, w.box_center, w.box_size, sp)
+    lig = w.ligands[0]
+
+    def einval(fn, *a, **kw):
+        with pytest.raises(_lib.TridsError) as e:
+            fn(*a, **kw)
+        assert e.value.code == _lib.EINVAL, e.value
+        return str(e.value)
+
+    einval(api.Batch, pk, np.zeros(0), np.zeros((0, 3)), np.zeros(0), np.zeros(0), np.zeros((0, 2)), np.zeros(0))
+    msg = einval(api.Batch, pk, [len(lig.type), 0], lig.xyz, lig.type, [len(lig.bonds), 0], lig.bonds,
+                 lig.rotatable)
+    assert "ligand 1" in msg
+    b = api.Batch.from_ligands(pk, w.ligands)
+    P, S = 8, 4
+    bufs = {"dof": torch.zeros(b.n_lig, P, b.dof_stride, device="cuda"),
+            "state": torch.zeros(b.state_floats(P), device="cuda"),
+            "energy": torch.empty(b.n_lig, P, device="cuda")}
+    for kw in ({"poses": 0, "steps": S}, {"poses": P, "steps": 0}, {"poses": P, "steps": S, "mc_loops": 0},
+               {"poses": P, "steps": S, "step_begin": 2, "step_end": 2}):
+        einval(api.sample, pk, b, seed=3, **kw, **bufs)
+    einval(api.score_grad, pk, b, torch.zeros(b.n_lig, 0, b.dof_stride, device="cuda"))
+    out = api.sample(pk, b, P, S, mc_loops=2, seed=3, **bufs)
+    for k in (0, 65):
+        einval(api.topk, b, out["energy"], out["dof"], k)
+    idx, e = api.topk(b, out["energy"], out["dof"], 3)
+    torch.cuda.synchronize()
+    assert idx.shape == (b.n_lig, 3) and bool(torch.isfinite(e[:, 0]).all())
+    assert (idx[:, 0] >= 0).all() and (idx < P).all()
+    assert list(api.screen_stream(pk, [], P, S, 3)) == []
