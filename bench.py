@@ -9,10 +9,12 @@ on a bounded sample, and an end-to-end pass that packs host ligand arrays, sampl
 ranks and copies the results back.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {trids,reference}]
-Multi-GPU (torchrun): the one ligand set is split over the ranks by
-longest-processing-time on each ligand's cost (strong scaling: the total work is fixed);
-every rank samples its shard with the ligands' global indices as random-stream ids, so
-the results do not depend on the split.  No collective touches the data path; the timed
+Multi-GPU (torchrun): the ligand set is split over the ranks by longest-processing-time
+on each ligand's cost.  For the batched-screening workload the job on N GPUs is N times the
+one-GPU set (its first 1,024 ligands are that set, the rest drawn from the same seeded
+generator), so every GPU gets about 1,024 ligands (weak scaling); the larger workloads
+split their one fixed set (strong scaling).  Every rank samples its shard with the
+ligands' global indices as random-stream ids, so the results do not depend on the split.  No collective touches the data path; the timed
 region is bracketed by barriers, the slowest rank's time is used, and the shards' top-k
 are gathered on rank 0 on the host after it.
 """
@@ -205,9 +207,31 @@ def oracle_sample_rate(w, budget_s=12.0, max_ligs=64, n_threads=None, first=0, t
     return units / dt, n_threads, n, dt
 
 
+# Workloads whose job grows with the GPU count (weak scaling), with their one-GPU ligand
+# count; the others split one fixed ligand set over the GPUs (strong scaling).
+WEAK_LIGANDS = {"batched_screening": 1024}
+
+
+def job_ligands(args, world):
+    """Ligands of the whole job (None: the workload's own set): N times the one-GPU set for a
+    weakly scaled workload on N GPUs."""
+    if args.workload in WEAK_LIGANDS and world > 1:
+        return world * (args.n_lig or WEAK_LIGANDS[args.workload])
+    return args.n_lig or None
+
+
+def scaling_of(args):
+    return "weak" if args.workload in WEAK_LIGANDS else "strong"
+
+
 def workload_config(w, args, world):
     """The workload a bench line measures (the same dict for both arms of the comparison)."""
-    return {"workload": w.name, "n_lig": len(w.ligands), "poses": w.poses, "steps": w.steps,
+    name = w.name
+    if world > 1:
+        name += (f"; on {world} GPUs {len(w.ligands)} ligands ({world} x the one-GPU set) in {world} "
+                 "longest-processing-time shards" if scaling_of(args) == "weak" else
+                 f"; split over {world} GPUs in longest-processing-time shards")
+    return {"workload": name, "n_lig": len(w.ligands), "poses": w.poses, "steps": w.steps,
             "mc_loops": w.mc_loops, "pocket_atoms": len(w.pocket.type), "top_k": w.topk, "term_set": args.terms,
             "optimizer": args.optimizer, "maps_spacing": args.maps or None,
             "l2": "flushed between steps (256 MB write)", "parallelism": f"ligand shards x{world}"}
@@ -216,7 +240,8 @@ def workload_config(w, args, world):
 def run_reference(args, rank):
     if rank != 0:
         return
-    w = synth.workload(args.workload, n_lig=args.n_lig or None)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    w = synth.workload(args.workload, n_lig=job_ligands(args, world))
     rates = []
     for k in range(args.warmup + args.steps):
         r, cores, n, dt = oracle_sample_rate(w, budget_s=0.0, max_ligs=1, first=k % len(w.ligands), terms=args.terms,
@@ -226,8 +251,8 @@ def run_reference(args, rank):
     value = statistics.mean(rates)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * w.poses * w.steps / value,
-            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(w, args, int(os.environ.get("WORLD_SIZE", "1"))),
+            "higher_is_better": True, "scaling": scaling_of(args), "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, args, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"one ligand x {w.poses} poses x {w.steps} evaluations per step, FP64 "
                                        "all-pairs oracle on all host threads"},
@@ -271,7 +296,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    w = synth.workload(args.workload, n_lig=args.n_lig or None)
+    w = synth.workload(args.workload, n_lig=job_ligands(args, world))
     if w.cell and not args.cell:
         args.cell = w.cell
     if args.per_ligand_steps is None:
@@ -466,7 +491,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": scaling_of(args), "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(w, args, world),
         "launch": {"graph": {"timed_region": graph_timed, "total": g1,
                              "note": "one CUDA graph per launch shape, built in the warm-up; each timed step "
